@@ -1,0 +1,218 @@
+"""Pins of the oracle's SmoothMin (Eq. 4), loss (Eq. 3), straight-through
+gradient, Eq. 5 chain rule, AdamW and the learning-rate schedule (Sec. IV-A).
+
+Independent references: scipy's logistic function for a two-valued column,
+the tau -> infinity limit stated after Eq. 4, central finite differences
+(of the smooth surrogate for the STE layer, directly for the relaxed layer),
+numpy means for Eq. 5, and torch.optim.AdamW + LambdaLR in FP64."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.special import expit
+
+import oracle
+from paper_2511_07737_b300 import cnfgen
+from tests.conftest import rel_err
+
+
+def test_smoothmin_two_values_is_logistic():
+    for tau in (0.3, 1.0, 2.5):
+        R = np.array([[0.0], [1.0]])
+        S = oracle.smoothmin(R, tau)
+        assert abs(S[0] - expit(-tau)) < 1e-15
+
+
+def test_smoothmin_constant_column_and_shift():
+    R = np.full((7, 3), 2.0)
+    S, d = oracle.smoothmin(R, 1.7, grad=True)
+    np.testing.assert_allclose(S, 2.0, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(d.sum(axis=0), 1.0, atol=1e-14)
+    rng = np.random.default_rng(0)
+    R = rng.integers(0, 4, size=(9, 5)).astype(float)
+    S0, d0 = oracle.smoothmin(R, 1.3, grad=True)
+    S1 = oracle.smoothmin(R + 0.75, 1.3)
+    np.testing.assert_allclose(S1 - S0, 0.75, atol=1e-13)
+    np.testing.assert_allclose(d0.sum(axis=0), 1.0, atol=1e-13)
+
+
+def test_smoothmin_tends_to_min():
+    rng = np.random.default_rng(1)
+    R = rng.integers(0, 5, size=(40, 16)).astype(float)
+    S = oracle.smoothmin(R, 50.0)
+    np.testing.assert_allclose(S, R.min(axis=0), atol=40 * 4 * np.exp(-50.0) * 5)
+
+
+def test_smoothmin_finite_difference():
+    rng = np.random.default_rng(2)
+    R = rng.normal(size=(11, 4)) + 1.0
+    tau = 1.4
+    S, d = oracle.smoothmin(R, tau, grad=True)
+    h = 1e-6
+    for c in range(11):
+        Rp, Rm = R.copy(), R.copy()
+        Rp[c] += h
+        Rm[c] -= h
+        fd = (oracle.smoothmin(Rp, tau) - oracle.smoothmin(Rm, tau)) / (2 * h)
+        assert rel_err(d[c], fd) < 1e-8
+
+
+def _PD(cnf):
+    """Sparse C x V matrix P D: +1 for x_v in clause c, -1 for x_v'."""
+    rows = np.repeat(np.arange(cnf.C), np.diff(cnf.cptr))
+    vals = np.where(cnf.neg.astype(bool), -1.0, 1.0)
+    return sp.csr_matrix((vals, (rows, cnf.var)), shape=(cnf.C, cnf.V))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_ste_gradient_surrogate_fd(mode):
+    """F(z) = -sum_i SmoothMin(R0 + P D (zt(z) - zt(z0))) has gradient equal
+    to the STE gradient at z0 (Sec. III-B, Fig. 3), chained through Eq. 5."""
+    inst = cnfgen.planted_ksat(30, 120, 3, 5)
+    cnf = oracle.CNF(30, inst.clause_ptr, inst.lits)
+    N, tau = 6, 1.2
+    rng = np.random.default_rng(3)
+    z0 = rng.normal(size=(30, N)) + 0.3
+    nu0, zt0 = oracle.normalize(z0, mode)
+    X = (zt0 > 0).astype(np.uint8)
+    R0 = oracle.result_matrix(cnf, X).astype(float)
+    S, L, G, _ = oracle.objective(cnf, X=X, tau=tau)
+    g = oracle.normalize_backward(z0, nu0, G, mode)
+    PD = _PD(cnf)
+
+    def F(z):
+        _, zt = oracle.normalize(z, mode)
+        return -oracle.smoothmin(R0 + PD @ (zt - zt0), tau).sum()
+
+    assert abs(F(z0) - L) < 1e-12
+    fd = np.zeros_like(z0)
+    for v in range(30):
+        for i in range(N):
+            h = 1e-6 * max(1.0, abs(z0[v, i]))
+            zp, zm = z0.copy(), z0.copy()
+            zp[v, i] += h
+            zm[v, i] -= h
+            fd[v, i] = (F(zp) - F(zm)) / (2 * h)
+    assert rel_err(g, fd) < 1e-6
+    # at mode 2 the chain rule is the identity, so G itself is pinned
+    if mode == 2:
+        assert rel_err(G, fd) < 1e-6
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_relaxed_gradient_fd(mode):
+    inst = cnfgen.structured_mixed(64, 200, 4, communities=4)
+    cnf = oracle.CNF(64, inst.clause_ptr, inst.lits)
+    N, tau = 4, 0.9
+    rng = np.random.default_rng(4)
+    z0 = rng.normal(size=(64, N)) + 0.2
+
+    def Lz(z):
+        _, zt = oracle.normalize(z, mode)
+        return oracle.objective(cnf, zt=zt, tau=tau, grad=False)[1]
+
+    nu, zt = oracle.normalize(z0, mode)
+    _, L, G, _ = oracle.objective(cnf, zt=zt, tau=tau)
+    g = oracle.normalize_backward(z0, nu, G, mode)
+    fd = np.zeros_like(z0)
+    for v in range(64):
+        for i in range(N):
+            h = 1e-6 * max(1.0, abs(z0[v, i]))
+            zp, zm = z0.copy(), z0.copy()
+            zp[v, i] += h
+            zm[v, i] -= h
+            fd[v, i] = (Lz(zp) - Lz(zm)) / (2 * h)
+    assert rel_err(g, fd) < 1e-6
+
+
+def test_normalize_matches_numpy_means():
+    rng = np.random.default_rng(5)
+    z = rng.normal(size=(8, 32))
+    nu, zt = oracle.normalize(z, 0)
+    np.testing.assert_allclose(nu, z.mean(axis=1), rtol=1e-14)
+    np.testing.assert_allclose(zt, z / z.mean(axis=1, keepdims=True), rtol=1e-14)
+    nu1, _ = oracle.normalize(z, 1)
+    np.testing.assert_allclose(nu1, np.abs(z).mean(axis=1), rtol=1e-14)
+    nu2, zt2 = oracle.normalize(z, 2)
+    np.testing.assert_array_equal(nu2, 1.0)
+    np.testing.assert_array_equal(zt2, z)
+    # guard: a row with zero mean is divided by +1e-12
+    zz = np.array([[1.0, -1.0, 2.0, -2.0]])
+    nug, _ = oracle.normalize(zz, 0)
+    assert nug[0] == 1e-12
+
+
+def test_lr_schedule_values_of_sec_iv_a():
+    assert oracle.lr_at(0) == pytest.approx(1e-1, rel=1e-15)
+    assert oracle.lr_at(29) == pytest.approx(1e-1, rel=1e-15)
+    assert oracle.lr_at(30) == pytest.approx(1e-2, rel=1e-15)
+    assert oracle.lr_at(359) == pytest.approx(1e-12, rel=1e-12)
+    assert oracle.lr_at(360) == pytest.approx(1e-1, rel=1e-15)          # restart
+    assert oracle.lr_at(390) == pytest.approx(1e-2, rel=1e-15)
+    assert oracle.lr_at(20, restart=10_000, period=1) == pytest.approx(1e-15)   # floor
+
+
+def test_adamw_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(6)
+    V, N = 5, 7
+    z = rng.normal(size=(V, N))
+    m = np.zeros_like(z)
+    v = np.zeros_like(z)
+    p = torch.nn.Parameter(torch.tensor(z.copy(), dtype=torch.float64))
+    opt = torch.optim.AdamW([p], lr=0.1, betas=(0.9, 0.999), eps=1e-8, weight_decay=0.01)
+    sched = torch.optim.lr_scheduler.LambdaLR(opt, lambda t: 0.1 ** ((t % 360) // 30))
+    for t in range(75):
+        g = rng.normal(size=(V, N)) * (0.1 + t % 3)
+        p.grad = torch.tensor(g)
+        opt.step()
+        sched.step()
+        oracle.adamw(z, m, v, g, t + 1, oracle.lr_at(t))
+        assert rel_err(z, p.detach().numpy()) < 1e-12, t
+
+
+def test_step_composes_the_pinned_pieces():
+    inst = cnfgen.planted_ksat(40, 170, 3, 9)
+    cnf = oracle.CNF(40, inst.clause_ptr, inst.lits)
+    rng = np.random.default_rng(7)
+    N = 8
+    z = rng.normal(size=(40, N)) + 0.1
+    m = rng.normal(size=(40, N)) * 0.01
+    v = np.abs(rng.normal(size=(40, N))) * 0.01
+    hp = oracle.hparams(tau=1.5, norm=0)
+    nu, zt = oracle.normalize(z, 0)
+    X = (zt > 0).astype(np.uint8)
+    S, L, G, unsat = oracle.objective(cnf, X=X, tau=1.5)
+    g = oracle.normalize_backward(z, nu, G, 0)
+    z2, m2, v2 = z.copy(), m.copy(), v.copy()
+    oracle.adamw(z2, m2, v2, g, 13, oracle.lr_at(12))
+    out = oracle.step(cnf, hp, 12, z, m, v, X=X)
+    assert rel_err(out["G"], G) == 0.0 and rel_err(out["g"], g) == 0.0
+    assert rel_err(z, z2) == 0.0 and rel_err(m, m2) == 0.0 and rel_err(v, v2) == 0.0
+    np.testing.assert_array_equal(out["unsat"], unsat)
+    np.testing.assert_allclose(out["nu_next"], z.mean(axis=1), rtol=1e-14)
+
+
+def test_oracle_solves_small_planted():
+    """End to end: the method finds a model of a small planted formula under
+    the sign-keeping normaliser (mean |z|); the exact check confirms it.
+    (Eq. 5 read as the signed mean drives rows to one sign, after which every
+    sample sets the variable True; that reading stalls on this instance.)"""
+    inst = cnfgen.planted_ksat(30, 120, 3, 11)
+    cnf = oracle.CNF(30, inst.clause_ptr, inst.lits)
+    N = 32
+    hp = oracle.hparams(tau=1.0, norm=1)
+    z = oracle.init_normal(30, N, 5).astype(np.float64)
+    m = np.zeros_like(z)
+    v = np.zeros_like(z)
+    found = False
+    for t in range(300):
+        nu = oracle.nu_f32(z.astype(np.float32), 1)
+        X = oracle.binarize_f32(z.astype(np.float32), nu.astype(np.float32), 0)
+        out = oracle.step(cnf, hp, t, z, m, v, X=X)
+        if (out["unsat"] == 0).any():
+            i = int(np.argmax(out["unsat"] == 0))
+            u, _ = oracle.check(cnf, X[:, i:i + 1])
+            assert u[0] == 0
+            found = True
+            break
+    assert found
