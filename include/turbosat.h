@@ -1,0 +1,241 @@
+/*
+ * turbosat.h -- C ABI of the B300 (sm_103a) gradient-guided SAT hot path.
+ *
+ * Method: TurboSAT, arXiv 2511.07737.  A CNF with V variables and C clauses
+ * becomes the binarised product R = P A (Sec. III-A, Eq. 1) of the 0/1
+ * clause-literal matrix P (C x 2V) and N candidate assignments A (2V x N).
+ * Each step evaluates SmoothMin over every column of R (Eq. 4), the loss
+ * L = -sum_i S_i (Eq. 3), back-propagates through the straight-through
+ * estimator (Sec. III-B, Fig. 3) and the per-variable normalisation (Eq. 5),
+ * applies AdamW with the step-decay / restart schedule (Sec. IV-A) and
+ * re-binarises (Eq. 2, optionally Philox-sampled).  Exact satisfaction is
+ * decided with bit-packed clause checks (Sec. III-A, Satisfiability Matrix);
+ * the hand-off to CDCL takes the best sample and the k most confident
+ * variables, ranked by the smallest |gradient| (Sec. IV-B).
+ *
+ * Conventions for every call:
+ *   - Return value: TSAT_OK (0) or a negative TSAT_E* status; no call aborts.
+ *     tsat_strerror() names a status, tsat_last_error() gives the detail of
+ *     the most recent failure in this thread.
+ *   - Pointers named h_* are host memory, d_* are device memory on the
+ *     current device.  All device memory is owned by the caller (typically a
+ *     torch tensor); the library never frees it and keeps the pointer for the
+ *     life of the handle that was built on it.
+ *   - Calls that take a cudaStream_t are asynchronous on that stream unless
+ *     stated otherwise.  The state keeps an internal stream; calls order
+ *     themselves after the work already queued on the caller's stream and
+ *     make the caller's stream wait for their own work.
+ *   - Sample count N is a power of two in [32, 1024].  Clause length after
+ *     de-duplication is at most TSAT_MAX_CLAUSE_LEN.  The total number of
+ *     literal occurrences of a problem is below 2^31.
+ */
+#ifndef TURBOSAT_H
+#define TURBOSAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSAT_OK 0
+#define TSAT_EINVAL -1    /* bad argument (NULL, size out of range, N not a power of two) */
+#define TSAT_EVAR -2      /* a literal is 0 or names a variable outside 1..n_vars */
+#define TSAT_EEMPTY -3    /* an empty clause: the formula is unsatisfiable by definition */
+#define TSAT_EWS -4       /* workspace / state buffer smaller than the queried size */
+#define TSAT_ECUDA -5     /* a CUDA runtime call failed; see tsat_last_error() */
+#define TSAT_ETIMEOUT -6  /* a device-side wait gave up (reserved; no kernel waits today) */
+#define TSAT_ENOMEM -7    /* host allocation failed */
+#define TSAT_ELEN -8      /* a clause is longer than TSAT_MAX_CLAUSE_LEN after de-duplication */
+#define TSAT_ESTATE -9    /* handle used with a state it was not built for, or not initialised */
+#define TSAT_ERANGE -10   /* instance index, k or another count outside its range */
+
+#define TSAT_MAX_CLAUSE_LEN 31
+#define TSAT_MIN_SAMPLES 32
+#define TSAT_MAX_SAMPLES 1024
+#define TSAT_MAX_PARTIAL_K 16384
+
+/* Normalisation before binarisation (Eq. 5 and the readings of it). */
+#define TSAT_NORM_SIGNED_MEAN 0 /* Eq. 5 as printed: z / mean_i z            */
+#define TSAT_NORM_ABSMEAN 1     /* sign-keeping: z / mean_i |z|              */
+#define TSAT_NORM_NONE 2        /* z itself                                  */
+
+/* Binarisation (Eq. 2 and the stochastic exploration of the abstract). */
+#define TSAT_BIN_DET 0    /* x = [zt > 0]                                       */
+#define TSAT_BIN_PHILOX 1 /* x = [u < clamp(1/2 + c zt, 0, 1)], u from Philox4x32-10 */
+
+/* Literal values in the forward pass. */
+#define TSAT_LAYER_STE 0     /* binary literals, straight-through gradient (Fig. 3) */
+#define TSAT_LAYER_RELAXED 1 /* sigmoid(zt) literals, exact gradient              */
+
+/* Storage type of the relaxed literal values. */
+#define TSAT_DTYPE_F32 0
+#define TSAT_DTYPE_BF16 1
+
+/* Hyper-parameters (Sec. IV-A where stated; readings where the paper is silent). */
+typedef struct tsat_hparams {
+  float tau;              /* SmoothMin temperature of Eq. 4 (not given in the paper; default 1) */
+  float lr0;              /* initial learning rate, 1e-1 (Sec. IV-A) */
+  float lr_factor;        /* multiplier per decay period, 0.1 (Sec. IV-A) */
+  float lr_floor;         /* lower bound, 1e-15 (Sec. IV-A "final learning rate") */
+  int32_t decay_period;   /* iterations per decay, 30 (Sec. IV-A) */
+  int32_t restart_period; /* iterations per restart, 360 (Sec. IV-A) */
+  float beta1, beta2, eps, weight_decay; /* AdamW; PyTorch defaults 0.9, 0.999, 1e-8, 0.01 */
+  int32_t norm;           /* TSAT_NORM_* (default TSAT_NORM_SIGNED_MEAN) */
+  int32_t binarize;       /* TSAT_BIN_* (default TSAT_BIN_DET) */
+  float bin_temp;         /* T of the Philox rule, c = 0.25 / T (default 1) */
+  int32_t layer;          /* TSAT_LAYER_* (default TSAT_LAYER_STE) */
+  uint64_t seed;          /* Philox key (init and sampled binarisation) */
+} tsat_hparams;
+
+/* One CNF in DIMACS form: clause c holds h_lits[h_clause_ptr[c] .. h_clause_ptr[c+1]),
+ * literals are +-(1..n_vars), no zeros.  Host memory, read during the call only. */
+typedef struct tsat_cnf_desc {
+  int32_t n_vars;
+  int32_t n_clauses;
+  const int64_t *h_clause_ptr; /* n_clauses + 1 entries, non-decreasing, [0] = 0 */
+  const int32_t *h_lits;
+} tsat_cnf_desc;
+
+typedef struct tsat_problem tsat_problem; /* host handle; device arrays live in the caller's workspace */
+typedef struct tsat_state tsat_state;     /* host handle over a caller-owned device state buffer */
+
+/* Per-instance progress (host copy). */
+typedef struct tsat_inst_status {
+  int32_t found;        /* 1 once a sample satisfied every clause (max S > 0, Sec. III-A) */
+  int32_t found_sample; /* that sample, else -1 */
+  int64_t found_step;   /* step at which it was found, else -1 */
+  int32_t min_unsat;    /* fewest unsatisfied clauses over the samples at the last step */
+  int32_t best_sample;  /* sample with min_unsat (lowest index on ties) */
+  float loss;           /* L = -sum_i S_i of the last step (Eq. 3) */
+  float pad;
+} tsat_inst_status;
+
+const char *tsat_strerror(int status);
+const char *tsat_last_error(void);
+void tsat_hparams_default(tsat_hparams *hp);
+
+/* ---- problem (Sec. III-A "Problem Matrix", Sec. IV-A compressed sparse P) ----
+ * tsat_problem_bytes: pure host computation of the device workspace size for a
+ * batch of n_inst CNFs (a single CNF is a batch of one).
+ * tsat_load_batch: copies the CNFs to the device and builds, on the device,
+ *   - the clause-major CSR of P (duplicate literals removed, Sec. III-A: P is 0/1),
+ *   - the variable-major occurrence records used by the backward pass (P^T),
+ *   - the forward work list of (instance, clause range) items.
+ * Errors: TSAT_EINVAL, TSAT_EVAR, TSAT_EEMPTY, TSAT_ELEN, TSAT_EWS, TSAT_ECUDA,
+ * TSAT_ENOMEM.  Synchronous (waits for the build to finish, to report input
+ * errors).  d_ws must stay allocated until tsat_problem_free. */
+int tsat_problem_bytes(int32_t n_inst, const tsat_cnf_desc *descs, size_t *ws_bytes);
+int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size_t ws_bytes,
+                    cudaStream_t stream, tsat_problem **out);
+int tsat_load(int32_t n_vars, int32_t n_clauses, const int64_t *h_clause_ptr,
+              const int32_t *h_lits, void *d_ws, size_t ws_bytes, cudaStream_t stream,
+              tsat_problem **out);
+void tsat_problem_free(tsat_problem *p);
+/* Sizes after de-duplication: h_info = {n_inst, n_vars, n_clauses, nnz, lmax, n_items,
+ * occurrence-record words, workspace bytes in use}. */
+int tsat_problem_info(const tsat_problem *p, int64_t h_info[8]);
+/* Device CSR views for inspection (clause-major, lit = (global var << 1) | negated):
+ * copies cptr (n_clauses+1 int32) and clit (nnz int32) to host buffers. */
+int tsat_problem_csr(const tsat_problem *p, int32_t *h_cptr, int32_t *h_clit);
+
+/* ---- state: N assignment samples per instance (Sec. III-A "Assignment Matrix") ----
+ * Layout inside d_state (all row-major, row = global variable):
+ *   z, m, v   float [V][N]     trainable A_real (one row per variable) and AdamW moments
+ *   bits      uint32 [2][V][N/32]  binarised A, bit (i mod 32) of word i/32 = x_vi
+ *   nu        float [V]        normaliser of the current z (Eq. 5)
+ * plus per-instance histograms, gamma tables, S and status records. */
+int tsat_state_bytes(const tsat_problem *p, int32_t n_samples, int32_t layer,
+                     int32_t relaxed_dtype, size_t *state_bytes);
+int tsat_state_create(tsat_problem *p, void *d_state, size_t state_bytes, int32_t n_samples,
+                      int32_t layer, int32_t relaxed_dtype, tsat_state **out);
+void tsat_state_free(tsat_state *s);
+
+/* Random init of A_real (Sec. IV-A: standard normal, balanced 0/1 after B).
+ * d_logits (nullable, float [V]) shifts row v by d_logits[v] * logit_scale (a
+ * learned proposal); the random part stays as the fallback.  Sets step t = 0
+ * and binarises with hp->norm / hp->binarize.  Async. */
+int tsat_init(tsat_state *s, const tsat_hparams *hp, const float *d_logits, float logit_scale,
+              cudaStream_t stream);
+
+/* n_steps optimisation steps (Sec. III-B and IV-A), replayed from a cached
+ * CUDA graph.  An instance whose sample satisfies every clause is frozen at
+ * that step (its bits keep the model).  With stop_on_sat, the remaining steps
+ * become no-ops once every instance is frozen.  Async; hp is copied. */
+int tsat_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
+              cudaStream_t stream);
+
+/* Capture and instantiate the graph tsat_step(hp, n_steps, stop_on_sat) would
+ * replay, without running it (keeps graph building out of timed regions). */
+int tsat_step_prepare(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat);
+
+/* Runs n_steps steps as individual launches on the state's stream with CUDA
+ * events around each kernel and returns the average device time per launch
+ * in milliseconds: h_ms[0] forward, h_ms[1] gamma, h_ms[2] update (relaxed
+ * layer: h_ms[3] exact check).  Synchronous.  The steps are real steps (the
+ * state advances). */
+int tsat_profile_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, float h_ms[4]);
+
+/* Exact check of the current bits (Sec. III-A): d_unsat int32 [n_inst][N]
+ * unsatisfied-clause counts, d_satmask uint32 [n_inst][N/32] bit set = sample
+ * satisfies every clause.  d_loss (nullable, float [n_inst]) receives
+ * L = -sum_i S_i (Eq. 3, Eq. 4 with hp->tau) of the current bits.  Async. */
+int tsat_evaluate(tsat_state *s, const tsat_hparams *hp, int32_t *d_unsat, uint32_t *d_satmask,
+                  float *d_loss, cudaStream_t stream);
+
+/* Hand-off of instance `inst` (Sec. IV-B).  Chooses the sample with unsat = 0
+ * (lowest index) or else the fewest unsatisfied clauses (lowest index on
+ * ties), computes the STE gradient of its current bits, and returns the k
+ * variables with the smallest |gradient| (ties to the lower index), k in
+ * [1, min(TSAT_MAX_PARTIAL_K, n_vars)], in increasing |gradient| order.
+ * Host outputs: h_bits uint32 [ceil(n_vars/32)] the chosen sample's full
+ * assignment (bit v%32 of word v/32, instance-local variable numbering),
+ * h_unsat, h_sample, h_part_var int32 [k] (1-based DIMACS variables),
+ * h_part_val uint8 [k], h_ready (nullable) = 1 when more than 99 % of clauses
+ * are satisfied (Sec. IV-B hand-off trigger).  Synchronous.  Returns 1 if the
+ * chosen sample satisfies every clause, 0 if not, < 0 on error. */
+int tsat_best(tsat_state *s, const tsat_hparams *hp, int32_t inst, int32_t k, uint32_t *h_bits,
+              int32_t *h_unsat, int32_t *h_sample, int32_t *h_part_var, uint8_t *h_part_val,
+              int32_t *h_ready, cudaStream_t stream);
+/* k = max(20, ceil(1e-4 * n_vars)) capped at n_vars (Sec. IV-B: 0.01 %, at least 20). */
+int32_t tsat_partial_k(int32_t n_vars);
+
+/* Step counter and per-instance progress; synchronous copy to the host. */
+int tsat_status(tsat_state *s, int64_t *h_step, int32_t *h_all_done,
+                tsat_inst_status *h_inst /* n_inst entries, nullable */, cudaStream_t stream);
+
+/* Raw views of the state for tests and checkpoints (device pointers into d_state). */
+int tsat_state_views(tsat_state *s, float **z, float **m, float **v, uint32_t **bits_cur,
+                     float **nu, float **gamma, int32_t **hist);
+
+/* ---- differentiation (Fig. 3 as a layer; torch.autograd.Function hooks) ----
+ * tsat_forward: from d_z (float [V][N], caller-owned, not the state's z)
+ * computes the normaliser, binarises (hp->norm, hp->binarize at step t_bin),
+ * evaluates R and SmoothMin, and writes d_S float [n_inst][N] and d_loss
+ * float [n_inst].  Keeps bits / gamma in the state for tsat_backward.
+ * tsat_backward: gradient of sum_inst dL * L_inst with respect to d_z
+ * (straight-through or relaxed chain rule, then Eq. 5), written to d_grad
+ * float [V][N].  Must follow tsat_forward on the same d_z.  Async. */
+int tsat_forward(tsat_state *s, const tsat_hparams *hp, const float *d_z, int64_t t_bin,
+                 float *d_S, float *d_loss, cudaStream_t stream);
+int tsat_backward(tsat_state *s, const tsat_hparams *hp, const float *d_z, float dL,
+                  float *d_grad, cudaStream_t stream);
+
+/* ---- schedules ----
+ * Launch shapes of the forward and update kernels.  tsat_autotune times the
+ * candidate shapes on this state with hp (state contents are restored) and
+ * keeps the fastest; tsat_get_tuning / tsat_set_tuning read or force them.
+ * h_tuning = {fwd_chunk_clauses, fwd_block_threads, upd_blocks_per_sm, upd_rows_per_item}. */
+int tsat_autotune(tsat_state *s, const tsat_hparams *hp, cudaStream_t stream, int32_t h_tuning[4]);
+int tsat_get_tuning(const tsat_state *s, int32_t h_tuning[4]);
+int tsat_set_tuning(tsat_state *s, const int32_t h_tuning[4]);
+
+/* Number of kernel launches one step issues (for launch accounting). */
+int32_t tsat_launches_per_step(const tsat_state *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TURBOSAT_H */

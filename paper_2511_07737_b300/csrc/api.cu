@@ -1,0 +1,658 @@
+// api.cu -- C ABI: state buffers, init, graph-replayed steps, exact
+// evaluation, hand-off selection, autograd hooks and launch-shape tuning.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace tsat {
+
+struct StatePlan {
+  size_t hdr, inst, sp, z, m, v, bits, nu, hist, gamma, S, unsat;
+  size_t ehist, eunsat, gcol, sel, digits, selstate, outbits, small, part_var, part_val, fwdS, hist1;
+  size_t lit, rbuf, zy, zs;
+  size_t total;
+};
+
+static StatePlan plan_state(const tsat_problem *p, int32_t N, int32_t layer, int32_t dt) {
+  StatePlan S{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+  const size_t V = (size_t)p->V, W = (size_t)N / 32, I = (size_t)p->n_inst, lm1 = (size_t)p->lmax + 1;
+  int32_t maxv = 0;
+  for (auto &x : p->inst) maxv = std::max(maxv, x.n_vars);
+  S.hdr = take(sizeof(StateHdr));
+  S.inst = take(sizeof(InstState) * I);
+  S.sp = take(sizeof(StepParams));
+  S.z = take(sizeof(float) * V * N);
+  S.m = take(sizeof(float) * V * N);
+  S.v = take(sizeof(float) * V * N);
+  S.bits = take(sizeof(uint32_t) * 2 * V * W);
+  S.nu = take(sizeof(float) * V);
+  S.hist = take(sizeof(int32_t) * I * lm1 * N);
+  S.gamma = take(sizeof(float) * I * lm1 * N);
+  S.S = take(sizeof(float) * I * N);
+  S.unsat = take(sizeof(int32_t) * I * N);
+  S.ehist = take(sizeof(int32_t) * I * lm1 * N);
+  S.eunsat = take(sizeof(int32_t) * I * N);
+  S.gcol = take(sizeof(float) * (size_t)maxv);
+  S.sel = take(sizeof(unsigned long long) * TSAT_MAX_PARTIAL_K);
+  S.digits = take(sizeof(int32_t) * 65536);
+  S.selstate = take(sizeof(int64_t) * 8);
+  S.outbits = take(sizeof(uint32_t) * ((size_t)maxv + 31) / 32);
+  S.small = take(sizeof(int32_t) * 64);
+  S.part_var = take(sizeof(int32_t) * TSAT_MAX_PARTIAL_K);
+  S.part_val = take(TSAT_MAX_PARTIAL_K);
+  S.fwdS = take(sizeof(float) * I * N);
+  S.hist1 = take(sizeof(int32_t) * 32);
+  if (layer == TSAT_LAYER_RELAXED) {
+    S.lit = take((dt == TSAT_DTYPE_BF16 ? 2 : 4) * V * N);
+    S.rbuf = take(sizeof(float) * (size_t)p->C * N);
+    S.zy = take(sizeof(float) * 2 * (size_t)p->lay.items_cap * N);
+    S.zs = take(sizeof(float) * 2 * I * N);
+  }
+  S.total = o;
+  return S;
+}
+
+static Hyper make_hyper(const tsat_hparams &hp, int stop) {
+  Hyper h{};
+  h.tau = hp.tau;
+  h.beta1 = hp.beta1;
+  h.beta2 = hp.beta2;
+  h.eps = hp.eps;
+  h.bin_c = 0.25f / hp.bin_temp;
+  h.norm = hp.norm;
+  h.binarize = hp.binarize;
+  h.key0 = (uint32_t)hp.seed;
+  h.key1 = (uint32_t)(hp.seed >> 32);
+  h.stop_on_sat = stop;
+  return h;
+}
+
+static LrSched make_sched(const tsat_hparams &hp) {
+  LrSched l{};
+  l.lr0 = hp.lr0;
+  l.factor = hp.lr_factor;
+  l.floor = hp.lr_floor;
+  l.wd = hp.weight_decay;
+  l.period = hp.decay_period;
+  l.restart = hp.restart_period;
+  l.beta1 = hp.beta1;
+  l.beta2 = hp.beta2;
+  return l;
+}
+
+static int check_hp(const tsat_hparams *hp) {
+  if (!hp) { set_error("hparams is NULL"); return TSAT_EINVAL; }
+  if (!(hp->tau > 0.f) || hp->norm < 0 || hp->norm > 2 || hp->binarize < 0 || hp->binarize > 1 ||
+      !(hp->bin_temp > 0.f) || !(hp->beta1 >= 0.f && hp->beta1 < 1.f) || !(hp->beta2 >= 0.f && hp->beta2 < 1.f)) {
+    set_error("hparams out of range");
+    return TSAT_EINVAL;
+  }
+  return TSAT_OK;
+}
+
+// caller stream -> internal stream ordering
+static int enter(tsat_state *s, cudaStream_t user) {
+  TSAT_CUDA(cudaEventRecord(s->ev_in, user));
+  TSAT_CUDA(cudaStreamWaitEvent(s->stream, s->ev_in, 0));
+  return TSAT_OK;
+}
+static int leave(tsat_state *s, cudaStream_t user) {
+  TSAT_CUDA(cudaEventRecord(s->ev_out, s->stream));
+  TSAT_CUDA(cudaStreamWaitEvent(user, s->ev_out, 0));
+  return TSAT_OK;
+}
+
+static int upd_grid(const tsat_state *s) { return std::max(1, s->sm_count * s->upd_blocks_per_sm); }
+
+// One optimisation step: forward histogram, gamma, fused update.
+static int issue_step(tsat_state *s, const Hyper &hy, const LrSched &ls, cudaStream_t st) {
+  const ProbDev &pd = s->prob->dev;
+  cudaError_t e;
+  if (s->layer == TSAT_LAYER_RELAXED) {
+    const size_t n = (size_t)pd.n_inst * s->N;
+    TSAT_CUDA(cudaMemsetAsync(s->dev.unsat, 0, sizeof(int32_t) * n, st));
+    if ((e = launch_check(pd, s->dev, s->dev.unsat, nullptr, st)) != cudaSuccess) return cuda_fail(e, "check");
+    if ((e = launch_relaxed_fwd(pd, s->dev, hy, 1, st)) != cudaSuccess) return cuda_fail(e, "relaxed forward");
+    if ((e = launch_relaxed_gamma(pd, s->dev, hy, ls, 1, nullptr, nullptr, st)) != cudaSuccess)
+      return cuda_fail(e, "relaxed gamma");
+  } else {
+    if ((e = launch_fwd_hist(pd, s->dev, s->dev.hist, 1, st)) != cudaSuccess) return cuda_fail(e, "forward");
+    if ((e = launch_gamma(pd, s->dev, hy, ls, s->dev.hist, 1, 1, nullptr, nullptr, st)) != cudaSuccess)
+      return cuda_fail(e, "gamma");
+  }
+  if ((e = launch_update(pd, s->dev, hy, 0, nullptr, nullptr, 0.f, upd_grid(s), s->upd_rows_per_item, st)) !=
+      cudaSuccess)
+    return cuda_fail(e, "update");
+  return TSAT_OK;
+}
+
+}  // namespace tsat
+
+using namespace tsat;
+
+extern "C" {
+
+void tsat_hparams_default(tsat_hparams *hp) {
+  if (!hp) return;
+  hp->tau = 1.0f;
+  hp->lr0 = 0.1f;
+  hp->lr_factor = 0.1f;
+  hp->lr_floor = 1e-15f;
+  hp->decay_period = 30;
+  hp->restart_period = 360;
+  hp->beta1 = 0.9f;
+  hp->beta2 = 0.999f;
+  hp->eps = 1e-8f;
+  hp->weight_decay = 0.01f;
+  hp->norm = TSAT_NORM_SIGNED_MEAN;
+  hp->binarize = TSAT_BIN_DET;
+  hp->bin_temp = 1.0f;
+  hp->layer = TSAT_LAYER_STE;
+  hp->seed = 0;
+}
+
+int tsat_state_bytes(const tsat_problem *p, int32_t N, int32_t layer, int32_t dt, size_t *bytes) {
+  if (!p || !bytes) { set_error("NULL argument"); return TSAT_EINVAL; }
+  if (N < TSAT_MIN_SAMPLES || N > TSAT_MAX_SAMPLES || (N & (N - 1))) {
+    set_error("n_samples must be a power of two in [32, 1024], got %d", N);
+    return TSAT_EINVAL;
+  }
+  if (layer != TSAT_LAYER_STE && layer != TSAT_LAYER_RELAXED) { set_error("bad layer"); return TSAT_EINVAL; }
+  if (dt != TSAT_DTYPE_F32 && dt != TSAT_DTYPE_BF16) { set_error("bad dtype"); return TSAT_EINVAL; }
+  *bytes = plan_state(p, N, layer, dt).total;
+  return TSAT_OK;
+}
+
+int tsat_state_create(tsat_problem *p, void *d_state, size_t state_bytes, int32_t N, int32_t layer, int32_t dt,
+                      tsat_state **out) {
+  if (!out) return TSAT_EINVAL;
+  *out = nullptr;
+  size_t need = 0;
+  int rc = tsat_state_bytes(p, N, layer, dt, &need);
+  if (rc) return rc;
+  if (!d_state) { set_error("state buffer is NULL"); return TSAT_EINVAL; }
+  if (state_bytes < need) { set_error("state buffer %zu < %zu bytes", state_bytes, need); return TSAT_EWS; }
+  if (((uintptr_t)d_state) % 256) { set_error("state buffer must be 256-byte aligned"); return TSAT_EINVAL; }
+  tsat_state *s = new (std::nothrow) tsat_state();
+  if (!s) return TSAT_ENOMEM;
+  StatePlan P = plan_state(p, N, layer, dt);
+  char *b = (char *)d_state;
+  s->prob = p;
+  s->base = d_state;
+  s->bytes = state_bytes;
+  s->N = N;
+  s->layer = layer;
+  s->lit_dtype = dt;
+  StateDev &D = s->dev;
+  D.N = N;
+  D.W = N / 32;
+  D.lm1 = p->lmax + 1;
+  D.layer = layer;
+  D.hdr = (StateHdr *)(b + P.hdr);
+  D.inst = (InstState *)(b + P.inst);
+  D.sp = (StepParams *)(b + P.sp);
+  D.z = (float *)(b + P.z);
+  D.m = (float *)(b + P.m);
+  D.v = (float *)(b + P.v);
+  D.bits = (uint32_t *)(b + P.bits);
+  D.nu = (float *)(b + P.nu);
+  D.hist = (int32_t *)(b + P.hist);
+  D.gamma = (float *)(b + P.gamma);
+  D.S = (float *)(b + P.S);
+  D.unsat = (int32_t *)(b + P.unsat);
+  D.V = p->V;
+  if (layer == TSAT_LAYER_RELAXED) {
+    D.lit = b + P.lit;
+    D.rbuf = (float *)(b + P.rbuf);
+    D.zy = (float *)(b + P.zy);
+    D.zs = (float *)(b + P.zs);
+    D.lit_bf16 = dt == TSAT_DTYPE_BF16;
+  }
+  s->eval_hist = (int32_t *)(b + P.ehist);
+  s->eval_unsat = (int32_t *)(b + P.eunsat);
+  s->gcol = (float *)(b + P.gcol);
+  s->sel = (unsigned long long *)(b + P.sel);
+  s->digits = (int32_t *)(b + P.digits);
+  s->selstate = (int64_t *)(b + P.selstate);
+  s->outbits = (uint32_t *)(b + P.outbits);
+  s->small = (int32_t *)(b + P.small);
+  s->part_var = (int32_t *)(b + P.part_var);
+  s->part_val = (uint8_t *)(b + P.part_val);
+  s->fwd_scratch = (float *)(b + P.fwdS);
+  s->hist1 = (int32_t *)(b + P.hist1);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  auto fail = [&](cudaError_t e, const char *w) { delete s; return cuda_fail(e, w); };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
+  if ((e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+  if ((e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+  if ((e = cudaMemsetAsync(b + P.digits, 0, sizeof(int32_t) * 65536, s->stream)) != cudaSuccess) return fail(e, "memset");
+  if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return fail(e, "sync");
+  prepare_update_attrs(p->lmax);
+  *out = s;
+  return TSAT_OK;
+}
+
+void tsat_state_free(tsat_state *s) {
+  if (!s) return;
+  for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  if (s->ev_in) cudaEventDestroy(s->ev_in);
+  if (s->ev_out) cudaEventDestroy(s->ev_out);
+  delete s;
+}
+
+__global__ void k_reset(StateDev sd, int n_inst) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j == 0) {
+    sd.hdr->t = 0;
+    sd.hdr->all_done = 0;
+    sd.hdr->err = 0;
+    sd.hdr->n_active = n_inst;
+  }
+  if (j < n_inst) {
+    InstState is{};
+    is.found = 0;
+    is.found_sample = -1;
+    is.found_step = -1;
+    is.min_unsat = -1;
+    is.best_sample = -1;
+    is.loss = 0.f;
+    sd.inst[j] = is;
+  }
+}
+
+int tsat_init(tsat_state *s, const tsat_hparams *hp, const float *d_logits, float scale, cudaStream_t stream) {
+  if (!s) return TSAT_EINVAL;
+  int rc = check_hp(hp);
+  if (rc) return rc;
+  if (hp->layer != s->layer) { set_error("hp->layer differs from the state's layer"); return TSAT_ESTATE; }
+  if ((rc = enter(s, stream))) return rc;
+  const Hyper hy = make_hyper(*hp, 0);
+  const ProbDev &pd = s->prob->dev;
+  const size_t histb = sizeof(int32_t) * (size_t)pd.n_inst * s->dev.lm1 * s->N;
+  TSAT_CUDA(cudaMemsetAsync(s->dev.hist, 0, histb, s->stream));
+  k_reset<<<(pd.n_inst + 255) / 256, 256, 0, s->stream>>>(s->dev, pd.n_inst);
+  TSAT_LAUNCH_CHECK("reset");
+  cudaError_t e = launch_init(pd, s->dev, hy, d_logits, scale, upd_grid(s), s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "init");
+  if (s->layer == TSAT_LAYER_RELAXED) {
+    e = launch_relaxed_lits(pd, s->dev, hy, nullptr, upd_grid(s), s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "relaxed literals");
+  }
+  s->initialised = true;
+  return leave(s, stream);
+}
+
+static int get_graph(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
+                     cudaGraphExec_t *out) {
+  GraphKey key;
+  key.n_steps = n_steps;
+  key.stop = stop_on_sat ? 1 : 0;
+  key.hp.assign((const uint8_t *)hp, (const uint8_t *)hp + sizeof(tsat_hparams));
+  key.hp.push_back((uint8_t)s->upd_blocks_per_sm);
+  key.hp.push_back((uint8_t)s->upd_rows_per_item);
+  key.hp.push_back((uint8_t)(s->prob->item_clauses / kItemMin));
+  auto it = s->graphs.find(key);
+  if (it != s->graphs.end()) {
+    *out = it->second;
+    return TSAT_OK;
+  }
+  const Hyper hy = make_hyper(*hp, key.stop);
+  const LrSched ls = make_sched(*hp);
+  cudaGraph_t graph = nullptr;
+  TSAT_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  int irc = TSAT_OK;
+  for (int32_t k = 0; k < n_steps && irc == TSAT_OK; ++k) irc = issue_step(s, hy, ls, s->stream);
+  cudaError_t ec = cudaStreamEndCapture(s->stream, &graph);
+  if (irc) {
+    if (graph) cudaGraphDestroy(graph);
+    return irc;
+  }
+  if (ec != cudaSuccess) return cuda_fail(ec, "end capture");
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return cuda_fail(ei, "graph instantiate");
+  if (s->graphs.size() >= 16) {
+    for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    s->graphs.clear();
+  }
+  s->graphs[key] = exec;
+  *out = exec;
+  return TSAT_OK;
+}
+
+static int check_step_args(tsat_state *s, const tsat_hparams *hp, int32_t n_steps) {
+  if (!s) return TSAT_EINVAL;
+  int rc = check_hp(hp);
+  if (rc) return rc;
+  if (!s->initialised) { set_error("state not initialised"); return TSAT_ESTATE; }
+  if (hp->layer != s->layer) { set_error("hp->layer differs from the state's layer"); return TSAT_ESTATE; }
+  if (n_steps <= 0) { set_error("n_steps must be positive"); return TSAT_EINVAL; }
+  return TSAT_OK;
+}
+
+int tsat_step_prepare(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat) {
+  int rc = check_step_args(s, hp, n_steps);
+  if (rc) return rc;
+  cudaGraphExec_t exec = nullptr;
+  return get_graph(s, hp, n_steps, stop_on_sat, &exec);
+}
+
+int tsat_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat, cudaStream_t stream) {
+  int rc = check_step_args(s, hp, n_steps);
+  if (rc) return rc;
+  if ((rc = enter(s, stream))) return rc;
+  cudaGraphExec_t exec = nullptr;
+  if ((rc = get_graph(s, hp, n_steps, stop_on_sat, &exec))) return rc;
+  TSAT_CUDA(cudaGraphLaunch(exec, s->stream));
+  return leave(s, stream);
+}
+
+int tsat_profile_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, float h_ms[4]) {
+  int rc = check_step_args(s, hp, n_steps);
+  if (rc) return rc;
+  if (!h_ms) return TSAT_EINVAL;
+  const ProbDev &pd = s->prob->dev;
+  const Hyper hy = make_hyper(*hp, 0);
+  const LrSched ls = make_sched(*hp);
+  cudaStream_t st = s->stream;
+  TSAT_CUDA(cudaStreamSynchronize(st));
+  cudaEvent_t ev[5];
+  for (auto &e : ev) TSAT_CUDA(cudaEventCreate(&e));
+  double acc[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaSuccess;
+  for (int32_t k = 0; k < n_steps && e == cudaSuccess; ++k) {
+    TSAT_CUDA(cudaEventRecord(ev[0], st));
+    if (s->layer == TSAT_LAYER_RELAXED) {
+      TSAT_CUDA(cudaMemsetAsync(s->dev.unsat, 0, sizeof(int32_t) * (size_t)pd.n_inst * s->N, st));
+      e = launch_check(pd, s->dev, s->dev.unsat, nullptr, st);
+      TSAT_CUDA(cudaEventRecord(ev[4], st));
+      if (e == cudaSuccess) e = launch_relaxed_fwd(pd, s->dev, hy, 1, st);
+      TSAT_CUDA(cudaEventRecord(ev[1], st));
+      if (e == cudaSuccess) e = launch_relaxed_gamma(pd, s->dev, hy, ls, 1, nullptr, nullptr, st);
+    } else {
+      e = launch_fwd_hist(pd, s->dev, s->dev.hist, 1, st);
+      TSAT_CUDA(cudaEventRecord(ev[1], st));
+      if (e == cudaSuccess) e = launch_gamma(pd, s->dev, hy, ls, s->dev.hist, 1, 1, nullptr, nullptr, st);
+    }
+    TSAT_CUDA(cudaEventRecord(ev[2], st));
+    if (e == cudaSuccess)
+      e = launch_update(pd, s->dev, hy, 0, nullptr, nullptr, 0.f, upd_grid(s), s->upd_rows_per_item, st);
+    TSAT_CUDA(cudaEventRecord(ev[3], st));
+    TSAT_CUDA(cudaEventSynchronize(ev[3]));
+    float a = 0, b = 0, c = 0, d = 0;
+    if (s->layer == TSAT_LAYER_RELAXED) {
+      TSAT_CUDA(cudaEventElapsedTime(&d, ev[0], ev[4]));
+      TSAT_CUDA(cudaEventElapsedTime(&a, ev[4], ev[1]));
+    } else {
+      TSAT_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
+    }
+    TSAT_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
+    TSAT_CUDA(cudaEventElapsedTime(&c, ev[2], ev[3]));
+    acc[0] += a; acc[1] += b; acc[2] += c; acc[3] += d;
+  }
+  for (auto &x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) return cuda_fail(e, "profile step");
+  for (int j = 0; j < 4; ++j) h_ms[j] = (float)(acc[j] / n_steps);
+  return TSAT_OK;
+}
+
+int tsat_evaluate(tsat_state *s, const tsat_hparams *hp, int32_t *d_unsat, uint32_t *d_satmask, float *d_loss,
+                  cudaStream_t stream) {
+  if (!s || !d_unsat || !d_satmask) { set_error("NULL argument"); return TSAT_EINVAL; }
+  if (!s->initialised) { set_error("state not initialised"); return TSAT_ESTATE; }
+  int rc = check_hp(hp);
+  if (rc) return rc;
+  if ((rc = enter(s, stream))) return rc;
+  const ProbDev &pd = s->prob->dev;
+  const size_t n = (size_t)pd.n_inst * s->N;
+  TSAT_CUDA(cudaMemsetAsync(d_unsat, 0, sizeof(int32_t) * n, s->stream));
+  cudaError_t e = launch_check(pd, s->dev, d_unsat, d_satmask, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "check");
+  if (d_loss) {
+    const Hyper hy = make_hyper(*hp, 0);
+    const LrSched ls = make_sched(*hp);
+    TSAT_CUDA(cudaMemsetAsync(s->eval_hist, 0, sizeof(int32_t) * n * s->dev.lm1, s->stream));
+    StateDev sd = s->dev;
+    sd.unsat = s->eval_unsat;
+    if ((e = launch_fwd_hist(pd, sd, s->eval_hist, 0, s->stream)) != cudaSuccess) return cuda_fail(e, "forward");
+    if ((e = launch_gamma(pd, sd, hy, ls, s->eval_hist, 0, 0, d_loss, s->fwd_scratch, s->stream)) != cudaSuccess)
+      return cuda_fail(e, "loss");
+  }
+  return leave(s, stream);
+}
+
+int tsat_best(tsat_state *s, const tsat_hparams *hp, int32_t inst, int32_t k, uint32_t *h_bits, int32_t *h_unsat,
+              int32_t *h_sample, int32_t *h_part_var, uint8_t *h_part_val, int32_t *h_ready, cudaStream_t stream) {
+  if (!s || !h_bits || !h_unsat || !h_sample || !h_part_var || !h_part_val) {
+    set_error("NULL argument");
+    return TSAT_EINVAL;
+  }
+  if (!s->initialised) { set_error("state not initialised"); return TSAT_ESTATE; }
+  int rc = check_hp(hp);
+  if (rc) return rc;
+  const tsat_problem *p = s->prob;
+  if (inst < 0 || inst >= p->n_inst) { set_error("instance %d out of range", inst); return TSAT_ERANGE; }
+  const InstInfo &I = p->inst[inst];
+  if (k < 1 || k > std::min<int32_t>(TSAT_MAX_PARTIAL_K, I.n_vars)) { set_error("k=%d out of range", k); return TSAT_ERANGE; }
+  if ((rc = enter(s, stream))) return rc;
+  const ProbDev &pd = p->dev;
+  const Hyper hy = make_hyper(*hp, 0);
+  const size_t n = (size_t)pd.n_inst * s->N;
+  cudaStream_t st = s->stream;
+  TSAT_CUDA(cudaMemsetAsync(s->eval_unsat, 0, sizeof(int32_t) * n, st));
+  cudaError_t e = launch_check(pd, s->dev, s->eval_unsat, nullptr, st);
+  if (e != cudaSuccess) return cuda_fail(e, "check");
+  if ((e = best_pick(s->eval_unsat + (size_t)inst * s->N, s->N, s->small, st)) != cudaSuccess) return cuda_fail(e, "pick");
+  TSAT_CUDA(cudaMemsetAsync(s->hist1, 0, sizeof(int32_t) * 32, st));
+  if ((e = best_gcol(pd, s->dev, hy, inst, I.n_vars, I.n_clauses, s->small, s->hist1, s->gcol, st)) != cudaSuccess)
+    return cuda_fail(e, "gradient column");
+  int64_t ss[2] = {0, (int64_t)k};
+  TSAT_CUDA(cudaMemcpyAsync(s->selstate, ss, sizeof(ss), cudaMemcpyHostToDevice, st));
+  if ((e = best_select(pd, s->dev, inst, I.n_vars, k, s->gcol, s->sel, s->digits, s->selstate, s->small, s->part_var,
+                       s->part_val, s->outbits, st)) != cudaSuccess)
+    return cuda_fail(e, "select");
+  int32_t small[4] = {0, 0, 0, 0};
+  TSAT_CUDA(cudaMemcpyAsync(small, s->small, sizeof(small), cudaMemcpyDeviceToHost, st));
+  TSAT_CUDA(cudaMemcpyAsync(h_bits, s->outbits, sizeof(uint32_t) * ((I.n_vars + 31) / 32), cudaMemcpyDeviceToHost, st));
+  TSAT_CUDA(cudaMemcpyAsync(h_part_var, s->part_var, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, st));
+  TSAT_CUDA(cudaMemcpyAsync(h_part_val, s->part_val, k, cudaMemcpyDeviceToHost, st));
+  TSAT_CUDA(cudaStreamSynchronize(st));
+  if ((rc = leave(s, stream))) return rc;
+  if (small[2] != k) { set_error("selection returned %d of %d keys", small[2], k); return TSAT_ECUDA; }
+  *h_sample = small[0];
+  *h_unsat = small[1];
+  if (h_ready) *h_ready = (double)(I.n_clauses - small[1]) / (double)I.n_clauses > 0.99 ? 1 : 0;
+  return small[1] == 0 ? 1 : 0;
+}
+
+int tsat_status(tsat_state *s, int64_t *h_step, int32_t *h_all_done, tsat_inst_status *h_inst, cudaStream_t stream) {
+  if (!s) return TSAT_EINVAL;
+  int rc = enter(s, stream);
+  if (rc) return rc;
+  StateHdr h{};
+  TSAT_CUDA(cudaMemcpyAsync(&h, s->dev.hdr, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+  std::vector<InstState> is((size_t)s->prob->n_inst);
+  if (h_inst)
+    TSAT_CUDA(cudaMemcpyAsync(is.data(), s->dev.inst, sizeof(InstState) * is.size(), cudaMemcpyDeviceToHost, s->stream));
+  TSAT_CUDA(cudaStreamSynchronize(s->stream));
+  if (h_step) *h_step = h.t;
+  if (h_all_done) *h_all_done = h.all_done;
+  if (h_inst)
+    for (size_t j = 0; j < is.size(); ++j) {
+      h_inst[j].found = is[j].found;
+      h_inst[j].found_sample = is[j].found_sample;
+      h_inst[j].found_step = is[j].found_step;
+      h_inst[j].min_unsat = is[j].min_unsat;
+      h_inst[j].best_sample = is[j].best_sample;
+      h_inst[j].loss = is[j].loss;
+      h_inst[j].pad = 0.f;
+    }
+  return leave(s, stream);
+}
+
+int tsat_state_views(tsat_state *s, float **z, float **m, float **v, uint32_t **bits_cur, float **nu, float **gamma,
+                     int32_t **hist) {
+  if (!s) return TSAT_EINVAL;
+  StateHdr h{};
+  TSAT_CUDA(cudaMemcpy(&h, s->dev.hdr, sizeof(h), cudaMemcpyDeviceToHost));
+  if (z) *z = s->dev.z;
+  if (m) *m = s->dev.m;
+  if (v) *v = s->dev.v;
+  if (bits_cur) *bits_cur = s->dev.bits + (size_t)(h.t & 1) * (size_t)s->prob->V * (s->N / 32);
+  if (nu) *nu = s->dev.nu;
+  if (gamma) *gamma = s->dev.gamma;
+  if (hist) *hist = s->dev.hist;
+  return TSAT_OK;
+}
+
+int tsat_forward(tsat_state *s, const tsat_hparams *hp, const float *d_z, int64_t t_bin, float *d_S, float *d_loss,
+                 cudaStream_t stream) {
+  if (!s || !d_z || !d_S || !d_loss) { set_error("NULL argument"); return TSAT_EINVAL; }
+  int rc = check_hp(hp);
+  if (rc) return rc;
+  if (hp->layer != s->layer) { set_error("hp->layer differs from the state's layer"); return TSAT_ESTATE; }
+  if ((rc = enter(s, stream))) return rc;
+  const ProbDev &pd = s->prob->dev;
+  const Hyper hy = make_hyper(*hp, 0);
+  const LrSched ls = make_sched(*hp);
+  if (!s->initialised) {
+    k_reset<<<(pd.n_inst + 255) / 256, 256, 0, s->stream>>>(s->dev, pd.n_inst);
+    TSAT_LAUNCH_CHECK("reset");
+  }
+  cudaError_t e;
+  if (s->layer == TSAT_LAYER_RELAXED) {
+    if ((e = launch_relaxed_lits(pd, s->dev, hy, d_z, upd_grid(s), s->stream)) != cudaSuccess)
+      return cuda_fail(e, "relaxed literals");
+    if ((e = launch_relaxed_fwd(pd, s->dev, hy, 0, s->stream)) != cudaSuccess) return cuda_fail(e, "relaxed forward");
+    if ((e = launch_relaxed_gamma(pd, s->dev, hy, ls, 0, d_loss, d_S, s->stream)) != cudaSuccess)
+      return cuda_fail(e, "relaxed gamma");
+  } else {
+    const size_t n = (size_t)pd.n_inst * s->N;
+    if ((e = launch_binarize(pd, s->dev, hy, d_z, t_bin, upd_grid(s), s->stream)) != cudaSuccess)
+      return cuda_fail(e, "binarize");
+    TSAT_CUDA(cudaMemsetAsync(s->eval_hist, 0, sizeof(int32_t) * n * s->dev.lm1, s->stream));
+    if ((e = launch_fwd_hist(pd, s->dev, s->eval_hist, 0, s->stream)) != cudaSuccess) return cuda_fail(e, "forward");
+    if ((e = launch_gamma(pd, s->dev, hy, ls, s->eval_hist, 0, 1, d_loss, d_S, s->stream)) != cudaSuccess)
+      return cuda_fail(e, "gamma");
+  }
+  return leave(s, stream);
+}
+
+int tsat_backward(tsat_state *s, const tsat_hparams *hp, const float *d_z, float dL, float *d_grad,
+                  cudaStream_t stream) {
+  if (!s || !d_z || !d_grad) { set_error("NULL argument"); return TSAT_EINVAL; }
+  int rc = check_hp(hp);
+  if (rc) return rc;
+  if ((rc = enter(s, stream))) return rc;
+  const Hyper hy = make_hyper(*hp, 0);
+  cudaError_t e = launch_update(s->prob->dev, s->dev, hy, 1, d_z, d_grad, dL, upd_grid(s), s->upd_rows_per_item,
+                                s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "backward");
+  return leave(s, stream);
+}
+
+int tsat_get_tuning(const tsat_state *s, int32_t h_tuning[4]) {
+  if (!s || !h_tuning) return TSAT_EINVAL;
+  h_tuning[0] = s->prob->item_clauses;
+  h_tuning[1] = kBlock;
+  h_tuning[2] = s->upd_blocks_per_sm;
+  h_tuning[3] = s->upd_rows_per_item;
+  return TSAT_OK;
+}
+
+int tsat_set_tuning(tsat_state *s, const int32_t h_tuning[4]) {
+  if (!s || !h_tuning) return TSAT_EINVAL;
+  if (h_tuning[0] < kItemMin || h_tuning[1] != kBlock || h_tuning[2] < 1 || h_tuning[2] > 32 || h_tuning[3] < 1 ||
+      h_tuning[3] > 4096) {
+    set_error("tuning values out of range");
+    return TSAT_EINVAL;
+  }
+  int rc = s->prob->set_items(h_tuning[0], s->stream);
+  if (rc) return rc;
+  s->upd_blocks_per_sm = h_tuning[2];
+  s->upd_rows_per_item = h_tuning[3];
+  return TSAT_OK;
+}
+
+int tsat_autotune(tsat_state *s, const tsat_hparams *hp, cudaStream_t stream, int32_t h_tuning[4]) {
+  if (!s || !h_tuning) return TSAT_EINVAL;
+  int rc = check_hp(hp);
+  if (rc) return rc;
+  if (!s->initialised) { set_error("state not initialised"); return TSAT_ESTATE; }
+  TSAT_CUDA(cudaStreamSynchronize(stream));
+  // Each candidate runs one step from a fresh init (the init is repeated at the
+  // end, so the state is left as tsat_init(hp) leaves it).
+  const int items[] = {1024, 2048, 4096, 8192};
+  const int bps[] = {2, 3, 4, 6, 8};
+  const int rpi[] = {1, 8, 64};
+  cudaEvent_t a, b;
+  TSAT_CUDA(cudaEventCreate(&a));
+  TSAT_CUDA(cudaEventCreate(&b));
+  const Hyper hy = make_hyper(*hp, 0);
+  const LrSched ls = make_sched(*hp);
+  auto time_fwd = [&](float *ms) -> int {
+    const ProbDev &pd = s->prob->dev;
+    cudaError_t e;
+    for (int rep = 0; rep < 2; ++rep) {
+      TSAT_CUDA(cudaMemsetAsync(s->eval_hist, 0, sizeof(int32_t) * pd.n_inst * s->dev.lm1 * s->N, s->stream));
+      TSAT_CUDA(cudaEventRecord(a, s->stream));
+      if ((e = launch_fwd_hist(pd, s->dev, s->eval_hist, 0, s->stream)) != cudaSuccess) return cuda_fail(e, "fwd");
+      TSAT_CUDA(cudaEventRecord(b, s->stream));
+    }
+    TSAT_CUDA(cudaEventSynchronize(b));
+    TSAT_CUDA(cudaEventElapsedTime(ms, a, b));
+    return TSAT_OK;
+  };
+  int best_items = s->prob->item_clauses;
+  float best = 1e30f;
+  for (int ic : items) {
+    if ((rc = s->prob->set_items(ic, s->stream))) return rc;
+    float ms = 0;
+    if ((rc = time_fwd(&ms))) return rc;
+    if (ms < best) { best = ms; best_items = ic; }
+  }
+  if ((rc = s->prob->set_items(best_items, s->stream))) return rc;
+  int best_b = s->upd_blocks_per_sm, best_r = s->upd_rows_per_item;
+  best = 1e30f;
+  for (int bb : bps)
+    for (int rr : rpi) {
+      s->upd_blocks_per_sm = bb;
+      s->upd_rows_per_item = rr;
+      float ms = 0;
+      for (int rep = 0; rep < 2; ++rep) {
+        if ((rc = tsat_init(s, hp, nullptr, 1.0f, s->stream))) return rc;
+        int r2 = issue_step(s, hy, ls, s->stream);  // warm the forward / gamma
+        if (r2) return r2;
+        TSAT_CUDA(cudaEventRecord(a, s->stream));
+        cudaError_t e = launch_update(s->prob->dev, s->dev, hy, 1, s->dev.z, s->dev.m, 1.0f, upd_grid(s),
+                                      s->upd_rows_per_item, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "update");
+        TSAT_CUDA(cudaEventRecord(b, s->stream));
+      }
+      TSAT_CUDA(cudaEventSynchronize(b));
+      TSAT_CUDA(cudaEventElapsedTime(&ms, a, b));
+      if (ms < best) { best = ms; best_b = bb; best_r = rr; }
+    }
+  s->upd_blocks_per_sm = best_b;
+  s->upd_rows_per_item = best_r;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if ((rc = tsat_init(s, hp, nullptr, 1.0f, s->stream))) return rc;
+  TSAT_CUDA(cudaStreamSynchronize(s->stream));
+  return tsat_get_tuning(s, h_tuning);
+}
+
+int32_t tsat_launches_per_step(const tsat_state *s) { return s ? s->launches_per_step : 0; }
+
+}  // extern "C"

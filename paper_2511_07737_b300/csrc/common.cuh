@@ -1,0 +1,156 @@
+// common.cuh -- device-side types and helpers of the sm_103a gradient-SAT path.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "turbosat.h"
+
+namespace tsat {
+
+constexpr int kBlock = 256;              // threads per block of the step kernels
+constexpr int kWarps = kBlock / 32;
+constexpr uint32_t kTagInit = 0x494E4954u;  // Philox counter word 3 for the init draw
+constexpr uint32_t kTagBin = 0x42494E41u;   // Philox counter word 3 for sampled binarisation
+
+struct InstInfo {
+  int32_t v_off, n_vars, c_off, n_clauses;
+  int32_t lmax, item_off, n_items, pad;
+};
+
+// Problem view passed by value to kernels.
+struct ProbDev {
+  int32_t n_inst, V, C, lmax;
+  int64_t nnz;
+  int32_t n_items, pad;
+  const int32_t *cptr;     // [C+1] clause offsets into clit
+  const int32_t *clit;     // [nnz] (global var << 1) | negated
+  const int64_t *xptr;     // [V+1] offsets (int32 words) into xrec, multiples of 4
+  const int32_t *xrec;     // variable-major occurrence records
+  const int32_t *vptr;     // [V+1] occurrence offsets (variable-major)
+  const int32_t *vocc;     // [nnz] (clause << 1) | negated, same order as the records
+  const int32_t *var_inst; // [V]
+  const int4 *items;       // [n_items] {inst, clause begin, clause end, 0}
+  const InstInfo *inst;    // [n_inst]
+};
+
+// Device header of a state buffer.
+struct StateHdr {
+  int64_t t;          // next step index
+  int32_t all_done;   // every instance frozen and stop requested
+  int32_t err;
+  int32_t n_active;   // instances still being optimised
+  int32_t pad[11];
+};
+
+struct InstState {
+  int32_t found, found_sample, min_unsat, best_sample;
+  int64_t found_step;
+  float loss, pad;
+};
+
+// Per-step scalars written by the gamma kernel for the update kernel.
+struct StepParams {
+  int64_t t;          // step being executed
+  int32_t src;        // bits buffer read this step (t & 1)
+  int32_t pad;
+  float lr, step_size, inv_sqrt_bc2, decay;
+};
+
+struct StateDev {
+  int32_t N, W, lm1, layer;    // samples, words per row, histogram width, layer
+  StateHdr *hdr;
+  InstState *inst;
+  StepParams *sp;
+  float *z, *m, *v;            // [V][N]
+  uint32_t *bits;              // [2][V][W]
+  float *nu;                   // [V]
+  int32_t *hist;               // [n_inst][lm1][N]
+  float *gamma;                // [n_inst][lm1][N]
+  float *S;                    // [n_inst][N]
+  int32_t *unsat;              // [n_inst][N]
+  float *zy;                   // relaxed: [n_items][2][N] partial (Z, Y) sums
+  float *zs;                   // relaxed: [n_inst][2][N] (Z, S)
+  float *rbuf;                 // relaxed: [C][N] clause sums R
+  void *lit;                   // relaxed: [V][N] literal values (f32 or bf16)
+  int32_t lit_bf16, pad;
+  int64_t V;
+};
+
+// Hyper-parameters in the form the kernels use.
+struct Hyper {
+  float tau, beta1, beta2, eps;
+  float bin_c;                 // 0.25 / T
+  int32_t norm, binarize;
+  uint32_t key0, key1;
+  int32_t stop_on_sat;
+};
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon et al., SC'11: ten rounds of two 32x32->64 products with a Weyl key
+// schedule; implemented here from the published description.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    uint32_t lo0 = 0xD2511F53u * c.x;
+    uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    uint32_t lo1 = 0xCD9E8D57u * c.z;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------- bit tricks
+// 32x32 bit transpose across a warp: afterwards bit l of lane j equals bit j
+// of lane l's input (recursive swap of off-diagonal blocks).
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int s = 16 >> k;
+    const uint32_t m = masks[k];
+    uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, s);
+    x = (lane & s) ? ((x & ~m) | ((y >> s) & m)) : ((x & m) | ((y << s) & ~m));
+  }
+  return x;
+}
+
+// Add a 1-bit-per-lane value into a P-plane bit-sliced counter.
+template <int P>
+__device__ __forceinline__ void bitslice_add(uint32_t (&pl)[P], uint32_t a) {
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    uint32_t t = pl[p] & a;
+    pl[p] ^= a;
+    a = t;
+  }
+}
+
+// Mask of lanes whose bit-sliced value equals r.
+template <int P>
+__device__ __forceinline__ uint32_t bitslice_eq(const uint32_t (&t)[P], int r) {
+  uint32_t m = 0xFFFFFFFFu;
+#pragma unroll
+  for (int p = 0; p < P; ++p) m &= ((r >> p) & 1) ? t[p] : ~t[p];
+  return m;
+}
+
+__device__ __forceinline__ float guard_nu(float mu) {
+  const float g = 1e-12f;
+  if (fabsf(mu) < g) return (mu < 0.0f) ? -g : g;
+  return mu;
+}
+
+// Eq. 2 / Philox rule on one value, decided in FP32 without contraction.
+__device__ __forceinline__ uint32_t binarize_one(float zt, int mode, float c, uint32_t word) {
+  if (mode == TSAT_BIN_DET) return zt > 0.0f ? 1u : 0u;
+  float u = __uint2float_rn(word >> 8) * (1.0f / 16777216.0f);
+  float p = __fadd_rn(0.5f, __fmul_rn(c, zt));
+  p = fminf(fmaxf(p, 0.0f), 1.0f);
+  return u < p ? 1u : 0u;
+}
+
+__device__ __forceinline__ int32_t load_nc(const int32_t *p) { return __ldg(p); }
+
+}  // namespace tsat

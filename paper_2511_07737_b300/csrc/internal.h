@@ -1,0 +1,96 @@
+// internal.h -- host-side structures shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "turbosat.h"
+
+namespace tsat {
+
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define TSAT_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return ::tsat::cuda_fail(e_, #call); \
+  } while (0)
+
+#define TSAT_LAUNCH_CHECK(what)                                        \
+  do {                                                                 \
+    cudaError_t e_ = cudaGetLastError();                               \
+    if (e_ != cudaSuccess) return ::tsat::cuda_fail(e_, what);         \
+  } while (0)
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Forward work items cover at most this many clauses (autotuned multiple of it).
+constexpr int kItemMin = 512;
+
+struct Layout {  // byte offsets inside the problem workspace
+  size_t cptr, clit, xptr, xrec, vptr, vocc, var_inst, items, inst, err;
+  size_t raw_cptr, raw_lits, tmp, clen, deg, recsz, fill, occ_j, occ_c, occ_s, scan_tmp;
+  size_t total;
+  int64_t xrec_cap, items_cap, scan_blocks;
+};
+
+}  // namespace tsat
+
+struct tsat_problem {
+  int32_t n_inst = 0, V = 0, C = 0, lmax = 0;
+  int64_t nnz = 0, nnz_raw = 0, xrec_words = 0;
+  int32_t device = 0;
+  int32_t item_clauses = 2048;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  tsat::Layout lay{};
+  tsat::ProbDev dev{};
+  std::vector<tsat::InstInfo> inst;  // host copy (lmax filled after the build)
+  int set_items(int32_t item_clauses, cudaStream_t stream);
+};
+
+struct GraphKey {
+  int32_t n_steps, stop;
+  std::vector<uint8_t> hp;
+  bool operator<(const GraphKey &o) const {
+    if (n_steps != o.n_steps) return n_steps < o.n_steps;
+    if (stop != o.stop) return stop < o.stop;
+    return hp < o.hp;
+  }
+};
+
+struct tsat_state {
+  tsat_problem *prob = nullptr;
+  void *base = nullptr;
+  size_t bytes = 0;
+  int32_t N = 0, layer = 0, lit_dtype = 0;
+  bool initialised = false;
+  tsat::StateDev dev{};
+  // scratch for tsat_best / tsat_evaluate (inside the state buffer)
+  int32_t *eval_hist = nullptr;     // [n_inst][lm1][N]
+  int32_t *eval_unsat = nullptr;    // [n_inst][N]
+  int32_t *part_var = nullptr;      // [TSAT_MAX_PARTIAL_K]
+  uint8_t *part_val = nullptr;      // [TSAT_MAX_PARTIAL_K]
+  int32_t *hist1 = nullptr;         // [32]
+  float *gcol = nullptr;            // [max instance V]
+  unsigned long long *sel = nullptr;  // [TSAT_MAX_PARTIAL_K] selected keys
+  int32_t *digits = nullptr;        // [65536] radix-select histogram
+  int64_t *selstate = nullptr;      // [8] radix-select bookkeeping
+  uint32_t *outbits = nullptr;      // [ceil(max V/32)]
+  int32_t *small = nullptr;         // [64] misc ints
+  float *fwd_scratch = nullptr;     // tsat_forward outputs staging
+  // schedules
+  int32_t upd_blocks_per_sm = 4;
+  int32_t upd_rows_per_item = 1;
+  int32_t sm_count = 148;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  int32_t launches_per_step = 3;
+};

@@ -1,0 +1,789 @@
+// kernels.cu -- sm_103a kernels of one optimisation step (Sec. III-B, IV-A).
+//
+// Data layout (row = global variable v, N samples, W = N/32 words):
+//   z, m, v  float [V][N]        bits  uint32 [2][V][W] (ping-pong by step parity)
+//   nu float [V]                 hist  int32 [n_inst][lm1][N]   gamma float [n_inst][lm1][N]
+//
+// k_fwd_hist   clause-major Eq. 1 + histogram of R per sample (integer exact)
+// k_gamma      Eq. 4 / Eq. 3 from the histogram, dL/dR table per (sample, r),
+//              exact SAT detection (a zero-unsat sample), lr schedule scalars
+// k_update     variable-major: STE backward (P^T) from the occurrence records,
+//              Eq. 5 chain rule, AdamW, new normaliser, Eq. 2 / Philox binarise
+// k_check      bit-packed exact satisfaction check (OR of literal words)
+#include <cuda_bf16.h>
+
+#include "kernels.cuh"
+
+namespace tsat {
+
+// ------------------------------------------------------------------ group sync / reductions
+// A "row group" is N/4 consecutive threads of a block; it owns one variable row.
+// Groups narrower than a warp share it with other groups that may take other
+// paths, so every warp-level primitive uses the group's own lane mask.
+struct Group {
+  int GT, grp, gl, lane;
+  __device__ __forceinline__ unsigned mask() const {
+    return (GT >= 32) ? 0xFFFFFFFFu : (((1u << GT) - 1u) << (lane & ~(GT - 1)));
+  }
+  __device__ __forceinline__ void sync() const {
+    if (GT <= 32) {
+      __syncwarp(mask());
+    } else if (GT == kBlock) {
+      __syncthreads();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(GT) : "memory");
+    }
+  }
+  // sum over the group, identical result in every thread (fixed order)
+  __device__ __forceinline__ float sum(float x, float *red) const {
+    const int span = GT < 32 ? GT : 32;
+    const unsigned m = mask();
+    for (int o = 1; o < span; o <<= 1) x += __shfl_xor_sync(m, x, o);
+    if (GT <= 32) return x;
+    const int nw = GT >> 5;
+    const int wg = gl >> 5;
+    sync();
+    if ((gl & 31) == 0) red[wg] = x;
+    sync();
+    float s = 0.0f;
+    for (int k = 0; k < nw; ++k) s += red[k];
+    return s;
+  }
+};
+
+__device__ __forceinline__ float4 ld_cs(const float *p) { return __ldcs(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ void st_cs(float *p, float4 v) { __stcs(reinterpret_cast<float4 *>(p), v); }
+
+__device__ __forceinline__ const uint32_t *cur_bits(const StateDev &sd, int64_t t) {
+  return sd.bits + (size_t)(t & 1) * (size_t)sd.V * sd.W;
+}
+
+// ------------------------------------------------------------------ init (Sec. IV-A)
+// z ~ Irwin-Hall(12) from Philox, m = v = 0, nu, bits at t = 0.
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+__device__ __forceinline__ void store_lits(const StateDev &sd, size_t off, const float a[4]) {
+  if (sd.lit_bf16) {
+    __nv_bfloat162 lo = __floats2bfloat162_rn(a[0], a[1]), hi = __floats2bfloat162_rn(a[2], a[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t *>(&lo);
+    u.y = *reinterpret_cast<uint32_t *>(&hi);
+    *reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(sd.lit) + off) = u;
+  } else {
+    *reinterpret_cast<float4 *>(reinterpret_cast<float *>(sd.lit) + off) = make_float4(a[0], a[1], a[2], a[3]);
+  }
+}
+
+// New normaliser (Eq. 5), Eq. 2 / Philox bits for step t, and (relaxed layer)
+// the literal values sigmoid(z / nu).
+__device__ __forceinline__ void row_binarize_store(const StateDev &sd, const Hyper &hy, const Group &g,
+                                                   float *red, int64_t v, const float zq[4], int64_t t,
+                                                   uint32_t *dst_bits, bool want_lits = false) {
+  const int N = sd.N;
+  float nu = 1.0f;
+  if (hy.norm != TSAT_NORM_NONE) {
+    float part = (hy.norm == TSAT_NORM_ABSMEAN)
+                     ? (fabsf(zq[0]) + fabsf(zq[1])) + (fabsf(zq[2]) + fabsf(zq[3]))
+                     : (zq[0] + zq[1]) + (zq[2] + zq[3]);
+    nu = guard_nu(g.sum(part, red) / (float)N);
+  }
+  const int s0 = g.gl * 4;
+  uint4 rnd = make_uint4(0, 0, 0, 0);
+  if (hy.binarize == TSAT_BIN_PHILOX)
+    rnd = philox4x32_10(make_uint4((uint32_t)g.gl, (uint32_t)v, (uint32_t)t, kTagBin), hy.key0, hy.key1);
+  const uint32_t rw[4] = {rnd.x, rnd.y, rnd.z, rnd.w};
+  uint32_t nib = 0;
+  float a[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    float zt = __fdiv_rn(zq[s], nu);
+    nib |= binarize_one(zt, hy.binarize, hy.bin_c, rw[s]) << s;
+    a[s] = sigmoidf_(zt);
+  }
+  if (want_lits) store_lits(sd, (size_t)v * N + s0, a);
+  uint32_t val = nib << (s0 & 31);
+  const unsigned gm = g.mask();
+  val |= __shfl_xor_sync(gm, val, 1);
+  val |= __shfl_xor_sync(gm, val, 2);
+  val |= __shfl_xor_sync(gm, val, 4);
+  if ((g.gl & 7) == 0) dst_bits[v * sd.W + (s0 >> 5)] = val;
+  if (g.gl == 0) sd.nu[v] = nu;
+}
+
+__global__ void __launch_bounds__(kBlock) k_init(ProbDev pd, StateDev sd, Hyper hy, const float *logits,
+                                                 float scale) {
+  __shared__ float red[64];
+  const int GT = sd.N >> 2, RPB = kBlock / GT;
+  Group g{GT, (int)threadIdx.x / GT, (int)threadIdx.x % GT, (int)(threadIdx.x & 31)};
+  const int64_t NG = (int64_t)gridDim.x * RPB;
+  const int64_t rows_round = ((int64_t)pd.V + NG - 1) / NG * NG;
+  for (int64_t v = (int64_t)blockIdx.x * RPB + g.grp; v < rows_round; v += NG) {
+    if (v >= pd.V) continue;  // whole group skips together (group-uniform v)
+    const int s0 = g.gl * 4;
+    float zq[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      int32_t acc = 0;
+      for (uint32_t j = 0; j < 3; ++j) {
+        uint4 o = philox4x32_10(make_uint4((uint32_t)(s0 + s), (uint32_t)v, j, kTagInit), hy.key0, hy.key1);
+        acc += (int32_t)(o.x >> 8) + (int32_t)(o.y >> 8) + (int32_t)(o.z >> 8) + (int32_t)(o.w >> 8);
+      }
+      float noise = __int2float_rn(acc - 6 * (1 << 24)) * (1.0f / 16777216.0f);
+      zq[s] = logits ? __fadd_rn(__fmul_rn(logits[v], scale), noise) : noise;
+    }
+    const size_t off = (size_t)v * sd.N + s0;
+    st_cs(sd.z + off, make_float4(zq[0], zq[1], zq[2], zq[3]));
+    st_cs(sd.m + off, make_float4(0.f, 0.f, 0.f, 0.f));
+    st_cs(sd.v + off, make_float4(0.f, 0.f, 0.f, 0.f));
+    row_binarize_store(sd, hy, g, red + (GT > 32 ? g.grp * 8 : 0), v, zq, 0, sd.bits);
+  }
+}
+
+// Binarise an external z (autograd forward) into the current bits buffer.
+__global__ void __launch_bounds__(kBlock) k_binarize(ProbDev pd, StateDev sd, Hyper hy, const float *zin,
+                                                     int64_t t_bin, int want_lits) {
+  __shared__ float red[64];
+  const int GT = sd.N >> 2, RPB = kBlock / GT;
+  Group g{GT, (int)threadIdx.x / GT, (int)threadIdx.x % GT, (int)(threadIdx.x & 31)};
+  const int64_t NG = (int64_t)gridDim.x * RPB;
+  const int64_t rows_round = ((int64_t)pd.V + NG - 1) / NG * NG;
+  uint32_t *dst = const_cast<uint32_t *>(cur_bits(sd, sd.hdr->t));
+  if (t_bin < 0) t_bin = sd.hdr->t;
+  for (int64_t v = (int64_t)blockIdx.x * RPB + g.grp; v < rows_round; v += NG) {
+    if (v >= pd.V) continue;
+    const int s0 = g.gl * 4;
+    const float *zsrc = zin ? zin : sd.z;
+    float4 z4 = *reinterpret_cast<const float4 *>(zsrc + (size_t)v * sd.N + s0);
+    float zq[4] = {z4.x, z4.y, z4.z, z4.w};
+    row_binarize_store(sd, hy, g, red + (GT > 32 ? g.grp * 8 : 0), v, zq, t_bin, dst, want_lits != 0);
+  }
+}
+
+// ------------------------------------------------------------------ forward histogram (Eq. 1)
+// Warp = 32 clauses x WB words.  Each lane forms the bit-sliced R of its
+// clause for 32*WB samples (P planes); a 32x32 warp transpose turns the
+// planes so that lane j holds, for sample j, one bit per clause; popcounts
+// of the plane-match masks give the histogram h[r] of that sample.
+template <int P, int WB>
+__global__ void __launch_bounds__(kBlock) k_fwd_hist(ProbDev pd, StateDev sd, int32_t *hist, int skip_frozen) {
+  const StateHdr *hdr = sd.hdr;
+  if (skip_frozen && hdr->all_done) return;
+  const int4 it = pd.items[blockIdx.x];
+  const int inst = it.x;
+  if (skip_frozen && sd.inst[inst].found) return;
+  const int W = sd.W, N = sd.N, lm1 = sd.lm1;
+  const int lmax = pd.inst[inst].lmax;
+  const uint32_t *bits = cur_bits(sd, hdr->t);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nWB = W / WB;
+  const bool many = nWB >= kWarps;
+  const int nsub = many ? 1 : kWarps / nWB;
+  const int sub = many ? 0 : warp / nWB;
+  const int wb0 = many ? warp : warp % nWB;
+  const int wbs = many ? kWarps : nWB;
+  for (int wb = wb0; wb < nWB; wb += wbs) {
+    int32_t cnt[WB][1 << P];
+#pragma unroll
+    for (int q = 0; q < WB; ++q)
+#pragma unroll
+      for (int r = 0; r < (1 << P); ++r) cnt[q][r] = 0;
+    for (int g0 = it.y + sub * 32; g0 < it.z; g0 += nsub * 32) {
+      const int c = g0 + lane;
+      const bool active = c < it.z;
+      uint32_t pl[WB][P];
+#pragma unroll
+      for (int q = 0; q < WB; ++q)
+#pragma unroll
+        for (int p = 0; p < P; ++p) pl[q][p] = 0;
+      if (active) {
+        const int32_t b = __ldg(pd.cptr + c), e = __ldg(pd.cptr + c + 1);
+        for (int32_t j = b; j < e; ++j) {
+          const int32_t lit = __ldg(pd.clit + j);
+          const uint32_t negm = 0u - (uint32_t)(lit & 1);
+          const uint32_t *row = bits + (size_t)(lit >> 1) * W + wb * WB;
+          if constexpr (WB == 4) {
+            uint4 x = __ldg(reinterpret_cast<const uint4 *>(row));
+            bitslice_add<P>(pl[0], x.x ^ negm);
+            bitslice_add<P>(pl[1], x.y ^ negm);
+            bitslice_add<P>(pl[2], x.z ^ negm);
+            bitslice_add<P>(pl[3], x.w ^ negm);
+          } else if constexpr (WB == 2) {
+            uint2 x = __ldg(reinterpret_cast<const uint2 *>(row));
+            bitslice_add<P>(pl[0], x.x ^ negm);
+            bitslice_add<P>(pl[1], x.y ^ negm);
+          } else {
+            bitslice_add<P>(pl[0], __ldg(row) ^ negm);
+          }
+        }
+      }
+      const uint32_t valid = __ballot_sync(0xFFFFFFFFu, active);
+#pragma unroll
+      for (int q = 0; q < WB; ++q) {
+        uint32_t tp[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) tp[p] = warp_transpose32(pl[q][p], lane);
+#pragma unroll
+        for (int r = 0; r < (1 << P); ++r) cnt[q][r] += __popc(valid & bitslice_eq<P>(tp, r));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < WB; ++q) {
+      const int sample = (wb * WB + q) * 32 + lane;
+#pragma unroll
+      for (int r = 0; r < (1 << P); ++r)
+        if (r <= lmax && cnt[q][r]) atomicAdd(hist + ((size_t)inst * lm1 + r) * N + sample, cnt[q][r]);
+    }
+  }
+}
+
+// Per-instance loss / best sample / exact-SAT freeze, then (step mode) the
+// step scalars: lr(t) of Sec. IV-A, AdamW bias corrections, t <- t + 1.
+__device__ void gamma_tail(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls,
+                           int step_mode, float *loss_out, const float *Sb, int64_t t) {
+  StateHdr *hdr = sd.hdr;
+  const int N = sd.N;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int inst = warp; inst < pd.n_inst; inst += nw) {
+    InstState *is = sd.inst + inst;
+    if (step_mode && is->found) continue;
+    float ls_ = 0.f;
+    int32_t mu = 0x7FFFFFFF, mi = 0;
+    for (int i = lane; i < N; i += 32) {
+      ls_ += Sb[(size_t)inst * N + i];
+      int32_t u = sd.unsat[(size_t)inst * N + i];
+      if (u < mu) { mu = u; mi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ls_ += __shfl_xor_sync(0xFFFFFFFFu, ls_, o);
+      int32_t u2 = __shfl_xor_sync(0xFFFFFFFFu, mu, o);
+      int32_t i2 = __shfl_xor_sync(0xFFFFFFFFu, mi, o);
+      if (u2 < mu || (u2 == mu && i2 < mi)) { mu = u2; mi = i2; }
+    }
+    if (lane == 0) {
+      if (loss_out) loss_out[inst] = -ls_;
+      if (step_mode) {
+        is->loss = -ls_;
+        is->min_unsat = mu;
+        is->best_sample = mi;
+        if (mu == 0) {
+          is->found = 1;
+          is->found_sample = mi;
+          is->found_step = t;
+        }
+      }
+    }
+  }
+  if (!step_mode) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int active = 0;
+    for (int j = 0; j < pd.n_inst; ++j) active += sd.inst[j].found ? 0 : 1;
+    hdr->n_active = active;
+    if (active == 0 && hy.stop_on_sat) {
+      hdr->all_done = 1;
+      return;
+    }
+    const int64_t tt = ls.restart > 0 ? t % ls.restart : t;
+    const int64_t kdec = ls.period > 0 ? tt / ls.period : 0;
+    double lr = (double)ls.lr0 * pow((double)ls.factor, (double)kdec);
+    if (lr < (double)ls.floor) lr = ls.floor;
+    const double bc1 = 1.0 - pow((double)ls.beta1, (double)(t + 1));
+    const double bc2 = 1.0 - pow((double)ls.beta2, (double)(t + 1));
+    StepParams sp;
+    sp.t = t;
+    sp.src = (int32_t)(t & 1);
+    sp.pad = 0;
+    sp.lr = (float)lr;
+    sp.step_size = (float)(lr / bc1);
+    sp.inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
+    sp.decay = (float)(1.0 - lr * (double)ls.wd);
+    *sd.sp = sp;
+    hdr->t = t + 1;
+  }
+}
+
+// ------------------------------------------------------------------ gamma (Eq. 3, Eq. 4)
+// One block.  For each (instance, sample) with histogram h[r]:
+//   Z = sum_r h_r e^{-tau r},  S = sum_r r h_r e^{-tau r} / Z,
+//   gamma[r] = dL/dR for a clause with R = r = -(e^{-tau r}/Z)(1 - tau (r - S)).
+// step_mode 1 also freezes instances that reached a zero-unsat sample, writes
+// the step scalars (lr schedule, AdamW bias corrections) and advances t.
+__global__ void __launch_bounds__(1024) k_gamma(ProbDev pd, StateDev sd, Hyper hy, LrSched ls, const int32_t *hist_in,
+                                                int step_mode, int write_gamma, float *loss_out, float *S_out) {
+  __shared__ float etab[32];
+  StateHdr *hdr = sd.hdr;
+  if (step_mode && hdr->all_done) return;
+  const int64_t t = hdr->t;
+  if (threadIdx.x < 32) etab[threadIdx.x] = expf(-hy.tau * (float)threadIdx.x);
+  __syncthreads();
+  const int N = sd.N, lm1 = sd.lm1;
+  int32_t *hist = const_cast<int32_t *>(hist_in);
+  float *Sb = S_out ? S_out : sd.S;
+  const int64_t total = (int64_t)pd.n_inst * N;
+  for (int64_t p = threadIdx.x; p < total; p += blockDim.x) {
+    const int inst = (int)(p / N), i = (int)(p - (int64_t)inst * N);
+    if (step_mode && sd.inst[inst].found) continue;
+    const int lmax = pd.inst[inst].lmax;
+    int32_t *h = hist + (size_t)inst * lm1 * N + i;
+    float Z = 0.f, Y = 0.f;
+    for (int r = 0; r <= lmax; ++r) {
+      float hv = (float)h[(size_t)r * N];
+      Z += hv * etab[r];
+      Y += (float)r * hv * etab[r];
+    }
+    const float S = Y / Z;
+    const float invZ = 1.0f / Z;
+    const int32_t h0 = h[0];
+    if (write_gamma) {
+      float *gm = sd.gamma + (size_t)inst * lm1 * N + i;
+      for (int r = 0; r <= lmax; ++r) gm[(size_t)r * N] = -(etab[r] * invZ) * (1.0f - hy.tau * ((float)r - S));
+    }
+    if (step_mode)
+      for (int r = 0; r <= lmax; ++r) h[(size_t)r * N] = 0;
+    Sb[(size_t)inst * N + i] = S;
+    sd.unsat[(size_t)inst * N + i] = h0;
+  }
+  gamma_tail(pd, sd, hy, ls, step_mode, loss_out, Sb, t);
+}
+
+// ------------------------------------------------------------------ fused update
+// Row group = N/4 threads, thread owns samples s0..s0+3 (one nibble of word w).
+// mode 0: backward (STE, P^T through the occurrence records), Eq. 5 chain
+//         rule, AdamW, new normaliser, binarise into the other bits buffer.
+// mode 1: backward + Eq. 5 chain rule only; grad = dL * g (autograd).
+constexpr int kRecInts = 2048;  // record staging per block (int32 words)
+
+__device__ __forceinline__ float sel4(int r, float g0, float g1, float g2, float g3) {
+  float a = (r & 1) ? g1 : g0;
+  float b = (r & 1) ? g3 : g2;
+  return (r & 2) ? b : a;
+}
+
+template <int P, bool GREG, bool RELAX>
+__global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, Hyper hy, int mode,
+                                                      const float *zin, float *grad, float dL,
+                                                      int rows_per_item) {
+  extern __shared__ int32_t smem[];
+  const StateHdr *hdr = sd.hdr;
+  if (mode == 0 && hdr->all_done) return;
+  const int N = sd.N, W = sd.W, lm1 = sd.lm1;
+  const int GT = N >> 2, RPB = kBlock / GT;
+  Group g{GT, (int)threadIdx.x / GT, (int)threadIdx.x % GT, (int)(threadIdx.x & 31)};
+  const int cap = kRecInts / RPB;
+  int32_t *rec = smem + g.grp * cap;
+  float *red = reinterpret_cast<float *>(smem + kRecInts) + g.grp * 8;
+  float *gtab = reinterpret_cast<float *>(smem + kRecInts + 8 * RPB) + (size_t)g.grp * lm1 * N;
+  const int s0 = g.gl * 4, w = s0 >> 5, sh = s0 & 31;
+  StepParams sp;
+  if (mode == 0) sp = *sd.sp;
+  const int64_t tcur = (mode == 0) ? sp.t : hdr->t;
+  const uint32_t *bsrc = cur_bits(sd, tcur);
+  uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
+  const float b1 = hy.beta1, b2 = hy.beta2;
+  float gam[4][4];
+  float Zr[4], Sr[4];
+  int cur_inst = -1;
+  const int64_t NG = (int64_t)gridDim.x * RPB;
+  const int64_t n_items = ((int64_t)pd.V + rows_per_item - 1) / rows_per_item;
+  for (int64_t item = (int64_t)blockIdx.x * RPB + g.grp; item < n_items; item += NG) {
+    const int64_t v_end = min((int64_t)pd.V, (item + 1) * rows_per_item);
+    for (int64_t v = item * rows_per_item; v < v_end; ++v) {
+      const int inst = __ldg(pd.var_inst + v);
+      if (mode == 0 && sd.inst[inst].found) {  // frozen instance: keep its model
+        if ((g.gl & 7) == 0) bdst[v * W + w] = bsrc[v * W + w];
+        continue;
+      }
+      if (inst != cur_inst) {
+        cur_inst = inst;
+        const float *gsrc = sd.gamma + (size_t)inst * lm1 * N;
+        if constexpr (RELAX) {
+          const float4 zz = *reinterpret_cast<const float4 *>(sd.zs + (size_t)inst * 2 * N + s0);
+          const float4 ss = *reinterpret_cast<const float4 *>(sd.zs + ((size_t)inst * 2 + 1) * N + s0);
+          Zr[0] = zz.x; Zr[1] = zz.y; Zr[2] = zz.z; Zr[3] = zz.w;
+          Sr[0] = ss.x; Sr[1] = ss.y; Sr[2] = ss.z; Sr[3] = ss.w;
+        } else if constexpr (GREG) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            float4 x = (r < lm1) ? *reinterpret_cast<const float4 *>(gsrc + (size_t)r * N + s0)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+            gam[0][r] = x.x; gam[1][r] = x.y; gam[2][r] = x.z; gam[3][r] = x.w;
+          }
+        } else {
+          g.sync();
+          for (int k = g.gl; k < lm1 * N; k += GT) gtab[k] = gsrc[k];
+          g.sync();
+        }
+      }
+      const size_t off = (size_t)v * N + s0;
+      const float4 z4 = (mode == 0) ? ld_cs(sd.z + off) : *reinterpret_cast<const float4 *>(zin + off);
+      float4 m4 = make_float4(0.f, 0.f, 0.f, 0.f), v4 = m4;
+      if (mode == 0) { m4 = ld_cs(sd.m + off); v4 = ld_cs(sd.v + off); }
+      const uint32_t ownw = __ldg(bsrc + v * W + w);
+      const float nu = sd.nu[v];
+      float G[4] = {0.f, 0.f, 0.f, 0.f};
+      if constexpr (RELAX) {
+        // ---- relaxed backward: dL/dR_ci = -(e^{-tau R}/Z_i)(1 - tau (R - S_i)) from the stored R
+        for (int32_t o = __ldg(pd.vptr + v); o < __ldg(pd.vptr + v + 1); ++o) {
+          const int32_t e = __ldg(pd.vocc + o);
+          const float4 R4 = __ldg(reinterpret_cast<const float4 *>(sd.rbuf + (size_t)(e >> 1) * N + s0));
+          const float Rq[4] = {R4.x, R4.y, R4.z, R4.w};
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const float gr = -(expf(-hy.tau * Rq[s]) / Zr[s]) * (1.0f - hy.tau * (Rq[s] - Sr[s]));
+            G[s] += (e & 1) ? -gr : gr;
+          }
+        }
+        const float zq_[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const float a = sigmoidf_(__fdiv_rn(zq_[s], nu));
+          G[s] *= a * (1.0f - a);
+        }
+      } else {
+      // ---- STE backward: G_vi = sum_{c owns x_v} gamma_i[R_ci] - sum_{c owns x_v'} gamma_i[R_ci]
+      int64_t pos0 = pd.xptr[v];
+      const int64_t pend = pd.xptr[v + 1];
+      while (pos0 < pend) {
+        const int n = (int)min((int64_t)cap, pend - pos0);
+        g.sync();
+        for (int k = g.gl; k < n; k += GT) rec[k] = __ldg(pd.xrec + pos0 + k);
+        g.sync();
+        int pos = 0;
+        bool end = false;
+        while (pos < n) {
+          const int32_t h = rec[pos];
+          if (h == 0) { end = true; break; }          // padding: end of this row
+          const int len = h >> 1;
+          if (pos + len > n) break;                    // record continues in the next chunk
+          const uint32_t ownneg = (uint32_t)(h & 1);
+          uint32_t pl[P];
+          pl[0] = ownw ^ (0u - ownneg);
+#pragma unroll
+          for (int p = 1; p < P; ++p) pl[p] = 0;
+          for (int q = 1; q < len; ++q) {
+            const int32_t lit = rec[pos + q];
+            const uint32_t x = __ldg(bsrc + (size_t)(lit >> 1) * W + w) ^ (0u - (uint32_t)(lit & 1));
+            bitslice_add<P>(pl, x);
+          }
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            int r = 0;
+#pragma unroll
+            for (int p = 0; p < P; ++p) r |= (int)((pl[p] >> (sh + s)) & 1u) << p;
+            float gv;
+            if constexpr (GREG) gv = sel4(r, gam[s][0], gam[s][1], gam[s][2], gam[s][3]);
+            else gv = gtab[r * N + s0 + s];
+            G[s] += ownneg ? -gv : gv;
+          }
+          pos += len;
+        }
+        pos0 = end ? pend : pos0 + pos;
+      }
+      }
+      // ---- chain rule through Eq. 5
+      const float zq[4] = {z4.x, z4.y, z4.z, z4.w};
+      float gq[4];
+      if (hy.norm == TSAT_NORM_NONE) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) gq[s] = G[s];
+      } else {
+        const float dot = g.sum((G[0] * zq[0] + G[1] * zq[1]) + (G[2] * zq[2] + G[3] * zq[3]), red);
+        const float c2 = dot / ((float)N * nu * nu);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const float dmu = (hy.norm == TSAT_NORM_ABSMEAN) ? (float)((zq[s] > 0.f) - (zq[s] < 0.f)) : 1.0f;
+          gq[s] = G[s] / nu - c2 * dmu;
+        }
+      }
+      if (mode == 1) {
+        *reinterpret_cast<float4 *>(grad + off) = make_float4(dL * gq[0], dL * gq[1], dL * gq[2], dL * gq[3]);
+        continue;
+      }
+      // ---- AdamW (decoupled weight decay, bias-corrected moments)
+      float mq[4] = {m4.x, m4.y, m4.z, m4.w}, vq[4] = {v4.x, v4.y, v4.z, v4.w}, zn[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const float gs = gq[s];
+        mq[s] = b1 * mq[s] + (1.0f - b1) * gs;
+        vq[s] = b2 * vq[s] + (1.0f - b2) * (gs * gs);
+        const float denom = sqrtf(vq[s]) * sp.inv_sqrt_bc2 + hy.eps;
+        zn[s] = zq[s] * sp.decay - sp.step_size * (mq[s] / denom);
+      }
+      st_cs(sd.z + off, make_float4(zn[0], zn[1], zn[2], zn[3]));
+      st_cs(sd.m + off, make_float4(mq[0], mq[1], mq[2], mq[3]));
+      st_cs(sd.v + off, make_float4(vq[0], vq[1], vq[2], vq[3]));
+      // ---- new normaliser and Eq. 2 for step t+1
+      row_binarize_store(sd, hy, g, red, v, zn, tcur + 1, bdst, RELAX);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ exact check (Sec. III-A)
+// unsat_i = #clauses whose literal words OR to 0 at bit i.  Same warp
+// transpose as the histogram, one plane (the unsatisfied mask).
+template <int WB>
+__global__ void __launch_bounds__(kBlock) k_check(ProbDev pd, StateDev sd, int32_t *unsat) {
+  const int4 it = pd.items[blockIdx.x];
+  const int inst = it.x;
+  const int W = sd.W, N = sd.N;
+  const uint32_t *bits = cur_bits(sd, sd.hdr->t);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nWB = W / WB;
+  const bool many = nWB >= kWarps;
+  const int nsub = many ? 1 : kWarps / nWB;
+  const int sub = many ? 0 : warp / nWB;
+  for (int wb = many ? warp : warp % nWB; wb < nWB; wb += many ? kWarps : nWB) {
+    int32_t cnt[WB];
+#pragma unroll
+    for (int q = 0; q < WB; ++q) cnt[q] = 0;
+    for (int g0 = it.y + sub * 32; g0 < it.z; g0 += nsub * 32) {
+      const int c = g0 + lane;
+      const bool active = c < it.z;
+      uint32_t orw[WB];
+#pragma unroll
+      for (int q = 0; q < WB; ++q) orw[q] = 0;
+      if (active) {
+        for (int32_t j = __ldg(pd.cptr + c); j < __ldg(pd.cptr + c + 1); ++j) {
+          const int32_t lit = __ldg(pd.clit + j);
+          const uint32_t negm = 0u - (uint32_t)(lit & 1);
+          const uint32_t *row = bits + (size_t)(lit >> 1) * W + wb * WB;
+#pragma unroll
+          for (int q = 0; q < WB; ++q) orw[q] |= __ldg(row + q) ^ negm;
+        }
+      }
+      const uint32_t valid = __ballot_sync(0xFFFFFFFFu, active);
+#pragma unroll
+      for (int q = 0; q < WB; ++q) cnt[q] += __popc(valid & warp_transpose32(~orw[q], lane));
+    }
+#pragma unroll
+    for (int q = 0; q < WB; ++q)
+      if (cnt[q]) atomicAdd(unsat + (size_t)inst * N + (wb * WB + q) * 32 + lane, cnt[q]);
+  }
+}
+
+__global__ void k_satmask(const int32_t *unsat, int64_t n, uint32_t *satmask) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = i < n && unsat[i] == 0;
+  const uint32_t b = __ballot_sync(0xFFFFFFFFu, ok);
+  if ((threadIdx.x & 31) == 0 && i < n) satmask[i >> 5] = b;
+}
+
+// ------------------------------------------------------------------ launchers
+int update_smem_bytes(int N, int lm1, bool greg) {
+  const int RPB = kBlock / (N >> 2);
+  return (int)(sizeof(int32_t) * (kRecInts + 8 * RPB) + (greg ? 0 : sizeof(float) * (size_t)RPB * lm1 * N));
+}
+
+static int planes_for(int lmax) {
+  int p = 1;
+  while ((1 << p) - 1 < lmax) ++p;
+  return p;
+}
+
+cudaError_t launch_init(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const float *logits, float scale,
+                        int grid, cudaStream_t st) {
+  k_init<<<grid, kBlock, 0, st>>>(pd, sd, hy, logits, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_binarize(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const float *zin, int64_t t_bin,
+                            int grid, cudaStream_t st) {
+  k_binarize<<<grid, kBlock, 0, st>>>(pd, sd, hy, zin, t_bin, 0);
+  return cudaGetLastError();
+}
+
+// Relaxed layer: bits, normaliser and literal values sigmoid(z/nu) of zin
+// (or of the state's z when zin is NULL), at the state's current step.
+cudaError_t launch_relaxed_lits(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const float *zin, int grid,
+                                cudaStream_t st) {
+  k_binarize<<<grid, kBlock, 0, st>>>(pd, sd, hy, zin, -1, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_hist(const ProbDev &pd, const StateDev &sd, int32_t *hist, int skip_frozen, cudaStream_t st) {
+  const int P = planes_for(pd.lmax);
+  const int W = sd.W;
+  const int WB = (P >= 4) ? 1 : (W >= 4 ? 4 : W);
+  dim3 grid(pd.n_items), block(kBlock);
+#define FWD(PP, WW) k_fwd_hist<PP, WW><<<grid, block, 0, st>>>(pd, sd, hist, skip_frozen)
+  switch (P * 10 + WB) {
+    case 11: FWD(1, 1); break;
+    case 12: FWD(1, 2); break;
+    case 14: FWD(1, 4); break;
+    case 21: FWD(2, 1); break;
+    case 22: FWD(2, 2); break;
+    case 24: FWD(2, 4); break;
+    case 31: FWD(3, 1); break;
+    case 32: FWD(3, 2); break;
+    case 34: FWD(3, 4); break;
+    case 41: FWD(4, 1); break;
+    case 51: FWD(5, 1); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef FWD
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gamma(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls,
+                         const int32_t *hist_in, int step_mode, int write_gamma, float *loss_out, float *S_out,
+                         cudaStream_t st) {
+  k_gamma<<<1, 1024, 0, st>>>(pd, sd, hy, ls, hist_in, step_mode, write_gamma, loss_out, S_out);
+  return cudaGetLastError();
+}
+
+template <int P, bool GREG, bool RELAX = false>
+static cudaError_t upd_launch(const ProbDev &pd, const StateDev &sd, const Hyper &hy, int mode, const float *zin,
+                              float *grad, float dL, int grid, int rpi, cudaStream_t st) {
+  const int smem = update_smem_bytes(sd.N, sd.lm1, GREG);
+  k_update<P, GREG, RELAX><<<grid, kBlock, smem, st>>>(pd, sd, hy, mode, zin, grad, dL, rpi);
+  return cudaGetLastError();
+}
+
+void prepare_update_attrs(int lmax) {
+  const int P = planes_for(lmax);
+  const int bytes = 160 * 1024;
+  cudaFuncSetAttribute(k_update<1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  switch (P) {
+    case 1: cudaFuncSetAttribute(k_update<1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); break;
+    case 2: cudaFuncSetAttribute(k_update<2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); break;
+    case 3: cudaFuncSetAttribute(k_update<3, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); break;
+    case 4: cudaFuncSetAttribute(k_update<4, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); break;
+    default: cudaFuncSetAttribute(k_update<5, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); break;
+  }
+}
+
+cudaError_t launch_update(const ProbDev &pd, const StateDev &sd, const Hyper &hy, int mode, const float *zin,
+                          float *grad, float dL, int grid, int rpi, cudaStream_t st) {
+  const int P = planes_for(pd.lmax);
+  if (sd.layer == TSAT_LAYER_RELAXED) return upd_launch<1, true, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);
+  switch (P) {
+    case 1: return upd_launch<1, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);
+    case 2: return upd_launch<2, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);
+    case 3: return upd_launch<3, false>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);
+    case 4: return upd_launch<4, false>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);
+    case 5: return upd_launch<5, false>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_check(const ProbDev &pd, const StateDev &sd, int32_t *unsat, uint32_t *satmask, cudaStream_t st) {
+  const int W = sd.W;
+  const int WB = W >= 4 ? 4 : W;
+  dim3 grid(pd.n_items), block(kBlock);
+  if (WB == 4) k_check<4><<<grid, block, 0, st>>>(pd, sd, unsat);
+  else if (WB == 2) k_check<2><<<grid, block, 0, st>>>(pd, sd, unsat);
+  else k_check<1><<<grid, block, 0, st>>>(pd, sd, unsat);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !satmask) return e;
+  const int64_t n = (int64_t)pd.n_inst * sd.N;
+  k_satmask<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(unsat, n, satmask);
+  return cudaGetLastError();
+}
+
+}  // namespace tsat
+
+namespace tsat {
+
+// ------------------------------------------------------------------ relaxed layer
+// Literal values a = sigmoid(zt), a' = 1 - a (stored FP32 or BF16, FP32 sums).
+// Forward: R_ci = sum_l a_li (Eq. 1 on real values), stored for the backward;
+// per sample partial sums Z = sum_c e^{-tau R}, Y = sum_c R e^{-tau R} per item.
+template <bool BF16>
+__global__ void __launch_bounds__(kBlock) k_relaxed_fwd(ProbDev pd, StateDev sd, Hyper hy, int skip_frozen) {
+  __shared__ float shZ[4 * kBlock], shY[4 * kBlock];
+  if (skip_frozen && sd.hdr->all_done) return;
+  const int4 it = pd.items[blockIdx.x];
+  const int inst = it.x;
+  const int N = sd.N, GT = N >> 2, CPB = kBlock / GT;
+  const int cs = threadIdx.x / GT, gl = threadIdx.x % GT, s0 = gl * 4;
+  float Zs[4] = {0.f, 0.f, 0.f, 0.f}, Ys[4] = {0.f, 0.f, 0.f, 0.f};
+  const bool frozen = skip_frozen && sd.inst[inst].found;
+  if (!frozen) {
+    for (int c = it.y + cs; c < it.z; c += CPB) {
+      float R[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int32_t j = __ldg(pd.cptr + c); j < __ldg(pd.cptr + c + 1); ++j) {
+        const int32_t lit = __ldg(pd.clit + j);
+        const size_t off = (size_t)(lit >> 1) * N + s0;
+        float a[4];
+        if constexpr (BF16) {
+          const uint2 u = __ldg(reinterpret_cast<const uint2 *>(reinterpret_cast<const __nv_bfloat16 *>(sd.lit) + off));
+          const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+          const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+          a[0] = lo.x; a[1] = lo.y; a[2] = hi.x; a[3] = hi.y;
+        } else {
+          const float4 x = __ldg(reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(sd.lit) + off));
+          a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) R[s] += (lit & 1) ? 1.0f - a[s] : a[s];
+      }
+      *reinterpret_cast<float4 *>(sd.rbuf + (size_t)c * N + s0) = make_float4(R[0], R[1], R[2], R[3]);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const float w = expf(-hy.tau * R[s]);
+        Zs[s] += w;
+        Ys[s] += R[s] * w;
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    shZ[cs * N + s0 + s] = Zs[s];
+    shY[cs * N + s0 + s] = Ys[s];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < N; k += kBlock) {
+    float z = 0.f, y = 0.f;
+    for (int q = 0; q < CPB; ++q) {
+      z += shZ[q * N + k];
+      y += shY[q * N + k];
+    }
+    sd.zy[((size_t)blockIdx.x * 2) * N + k] = z;
+    sd.zy[((size_t)blockIdx.x * 2 + 1) * N + k] = y;
+  }
+}
+
+// One block: S_i = Y_i / Z_i per (instance, sample) from the item partials in
+// a fixed order, loss (Eq. 3), and the step bookkeeping.  Found detection uses
+// the exact unsatisfied counts of the current bits (sd.unsat, filled by the
+// exact check earlier in the step).
+__global__ void __launch_bounds__(1024) k_relaxed_gamma(ProbDev pd, StateDev sd, Hyper hy, LrSched ls, int step_mode,
+                                                        float *loss_out, float *S_out) {
+  StateHdr *hdr = sd.hdr;
+  if (step_mode && hdr->all_done) return;
+  const int64_t t = hdr->t;
+  const int N = sd.N;
+  float *Sb = S_out ? S_out : sd.S;
+  const int64_t total = (int64_t)pd.n_inst * N;
+  for (int64_t p = threadIdx.x; p < total; p += blockDim.x) {
+    const int inst = (int)(p / N), i = (int)(p - (int64_t)inst * N);
+    if (step_mode && sd.inst[inst].found) continue;
+    const InstInfo I = pd.inst[inst];
+    float Z = 0.f, Y = 0.f;
+    for (int q = 0; q < I.n_items; ++q) {
+      Z += sd.zy[((size_t)(I.item_off + q) * 2) * N + i];
+      Y += sd.zy[((size_t)(I.item_off + q) * 2 + 1) * N + i];
+    }
+    const float S = Y / Z;
+    sd.zs[((size_t)inst * 2) * N + i] = Z;
+    sd.zs[((size_t)inst * 2 + 1) * N + i] = S;
+    Sb[(size_t)inst * N + i] = S;
+  }
+  gamma_tail(pd, sd, hy, ls, step_mode, loss_out, Sb, t);
+}
+
+cudaError_t launch_relaxed_fwd(const ProbDev &pd, const StateDev &sd, const Hyper &hy, int skip_frozen,
+                               cudaStream_t st) {
+  if (sd.lit_bf16) k_relaxed_fwd<true><<<pd.n_items, kBlock, 0, st>>>(pd, sd, hy, skip_frozen);
+  else k_relaxed_fwd<false><<<pd.n_items, kBlock, 0, st>>>(pd, sd, hy, skip_frozen);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_relaxed_gamma(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls,
+                                 int step_mode, float *loss_out, float *S_out, cudaStream_t st) {
+  k_relaxed_gamma<<<1, 1024, 0, st>>>(pd, sd, hy, ls, step_mode, loss_out, S_out);
+  return cudaGetLastError();
+}
+
+}  // namespace tsat

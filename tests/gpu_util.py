@@ -1,0 +1,58 @@
+"""Helpers shared by the GPU parity tests (CUDA path through the C ABI vs oracle)."""
+import numpy as np
+import torch
+
+import oracle
+from paper_2511_07737_b300 import turbosat as ts
+
+# Tolerances (max-norm relative error, see tests/conftest.rel_err):
+#   FP32 objective, gradient and state after one step: 1e-5
+#   BF16 storage of relaxed literal values (FP32 sums): 1e-2
+TOL_F32 = 1e-5
+TOL_BF16 = 1e-2
+
+
+def unpack_bits(words: np.ndarray, N: int) -> np.ndarray:
+    """[V][N/32] uint32 words -> [V][N] 0/1 (bit i%32 of word i/32 = sample i)."""
+    w = np.ascontiguousarray(words).view(np.uint32)
+    return np.unpackbits(w.view(np.uint8), axis=1, bitorder="little")[:, :N]
+
+
+def snapshot(st: ts.State) -> dict:
+    torch.cuda.synchronize()
+    out = {k: st.view(k).cpu().numpy().copy() for k in ("z", "m", "v", "nu")}
+    out["bits"] = st.view("bits").cpu().numpy().view(np.uint32).copy()
+    out["X"] = unpack_bits(out["bits"], st.N)
+    return out
+
+
+def oracle_hp(hp: ts.tsat_hparams) -> oracle.HParams:
+    return oracle.hparams(tau=hp.tau, lr0=hp.lr0, lr_factor=hp.lr_factor, lr_floor=hp.lr_floor,
+                          decay_period=hp.decay_period, restart_period=hp.restart_period, beta1=hp.beta1,
+                          beta2=hp.beta2, eps=hp.eps, weight_decay=hp.weight_decay, norm=hp.norm,
+                          relaxed=hp.layer)
+
+
+def lockstep(cnfs, offsets, hp, t, snap):
+    """One oracle step per instance from the GPU's FP32 state (as FP64), using
+    the GPU's bits and normaliser; returns concatenated z, m, v and per-instance
+    (S, L, unsat)."""
+    z = snap["z"].astype(np.float64)
+    m = snap["m"].astype(np.float64)
+    v = snap["v"].astype(np.float64)
+    ohp = oracle_hp(hp)
+    res = []
+    for j, cnf in enumerate(cnfs):
+        a, b = offsets[j], offsets[j + 1]
+        zj, mj, vj = z[a:b].copy(), m[a:b].copy(), v[a:b].copy()
+        out = oracle.step(cnf, ohp, t, zj, mj, vj, X=snap["X"][a:b], nu_in=snap["nu"][a:b].astype(np.float64))
+        z[a:b], m[a:b], v[a:b] = zj, mj, vj
+        res.append(out)
+    return z, m, v, res
+
+
+def make(instances, N, layer=ts.LAYER_STE, dtype=ts.DTYPE_F32):
+    prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in instances])
+    st = ts.State(prob, N, layer, dtype)
+    cnfs = [oracle.CNF(i.n_vars, i.clause_ptr, i.lits) for i in instances]
+    return prob, st, cnfs

@@ -1,0 +1,284 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Integers (CSR, unsatisfied counts, SAT masks, sampled bits, selected
+variables) must agree exactly; FP32 results within 1e-5 max-norm relative
+error, BF16 literal storage within 1e-2."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2511_07737_b300 import cnfgen
+from paper_2511_07737_b300 import turbosat as ts
+from tests.conftest import rel_err
+from tests.gpu_util import TOL_BF16, TOL_F32, lockstep, make, snapshot, unpack_bits
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    torch.cuda.set_device(0)
+
+
+def test_layout_matches_oracle_parse():
+    inst = cnfgen.tiny_random(40, 300, 3, kmin=1, kmax=9)     # duplicates and tautologies
+    prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
+    cptr, clit = ts.tsat_problem_csr(prob.h)
+    cnf = oracle.CNF(inst.n_vars, inst.clause_ptr, inst.lits)
+    np.testing.assert_array_equal(cptr.astype(np.int64), cnf.cptr)
+    for c in range(cnf.C):
+        gpu = sorted(clit[cptr[c]:cptr[c + 1]].tolist())
+        ref = sorted(((cnf.var[j] << 1) | cnf.neg[j]) for j in range(cnf.cptr[c], cnf.cptr[c + 1]))
+        assert gpu == ref
+    assert prob.info["lmax"] == cnf.lmax
+
+
+@pytest.mark.parametrize("bad,status", [
+    (([0, 2, 2], [1, 2]), -3),
+    (([0, 2], [1, 5]), -2),
+    (([0, 2], [1, 0]), -2),
+])
+def test_load_errors(bad, status):
+    ptr, lits = bad
+    with pytest.raises(ts.TsatError) as e:
+        ts.Problem([(3, np.array(ptr), np.array(lits))])
+    assert e.value.status == status
+
+
+@pytest.mark.parametrize("N,norm,binz", [(64, 0, 0), (32, 1, 1), (256, 2, 0), (1024, 1, 1)])
+def test_init_bits_and_check(N, norm, binz):
+    inst = cnfgen.planted_ksat(300, 1278, 3, 2)
+    prob, st, cnfs = make([inst], N)
+    hp = ts.hparams(seed=12345, norm=norm, binarize=binz, bin_temp=0.7)
+    ts.tsat_init(st.h, hp)
+    s = snapshot(st)
+    np.testing.assert_array_equal(s["z"], oracle.init_normal(inst.n_vars, N, 12345))
+    np.testing.assert_array_equal(s["m"], 0)
+    nu_ref = oracle.nu_f32(s["z"], norm)
+    bound = 1e-6 * np.abs(s["z"]).mean(axis=1) + 1e-6 * np.abs(nu_ref)
+    assert np.all(np.abs(s["nu"] - nu_ref) <= bound)
+    X = oracle.binarize_f32(s["z"], s["nu"], binz, c=0.25 / 0.7, seed=12345, t=0)
+    np.testing.assert_array_equal(s["X"], X)
+    unsat = torch.zeros(N, dtype=torch.int32, device="cuda")
+    sm = torch.zeros(N // 32, dtype=torch.int32, device="cuda")
+    ts.tsat_evaluate(st.h, hp, unsat, sm)
+    ref_u, ref_sm = oracle.check(cnfs[0], s["X"])
+    np.testing.assert_array_equal(unsat.cpu().numpy(), ref_u)
+    np.testing.assert_array_equal(sm.cpu().numpy().view(np.uint32), ref_sm)
+
+
+CASES = [
+    # (instances, N, hp kwargs, steps)
+    ("c0", lambda: [cnfgen.planted_ksat(100, 426, 3, 0)], 64, dict(norm=0, binarize=0), 6),
+    ("c0-philox", lambda: [cnfgen.planted_ksat(100, 426, 3, 0)], 64, dict(norm=1, binarize=1, bin_temp=0.5), 6),
+    ("ragged-items", lambda: [cnfgen.planted_ksat(3000, 12780, 3, 4)], 256, dict(norm=0, binarize=1), 3),
+    ("wide-N", lambda: [cnfgen.planted_ksat(1500, 6390, 3, 5)], 1024, dict(norm=1, binarize=0), 3),
+    ("N32-none", lambda: [cnfgen.planted_ksat(700, 2982, 3, 6)], 32, dict(norm=2, binarize=1), 3),
+    ("mixed-k", lambda: [cnfgen.structured_mixed(2048, 8000, 7, communities=8)], 128, dict(norm=1, binarize=1), 3),
+    ("k7", lambda: [cnfgen.planted_ksat(400, 14000, 7, 8)], 64, dict(norm=0, binarize=0), 2),
+    ("batch", lambda: cnfgen.batch_ksat(5, 9, n_lo=60, n_hi=900), 64, dict(norm=1, binarize=1), 3),
+]
+
+
+@pytest.mark.parametrize("name,gen,N,kw,steps", CASES, ids=[c[0] for c in CASES])
+def test_lockstep_ste(name, gen, N, kw, steps):
+    insts = gen()
+    prob, st, cnfs = make(insts, N)
+    hp = ts.hparams(seed=77, tau=1.3, **kw)
+    ts.tsat_init(st.h, hp)
+    offs = prob.var_offsets
+    for t in range(steps):
+        s0 = snapshot(st)
+        ts.tsat_step(st.h, hp, 1, stop_on_sat=False)
+        s1 = snapshot(st)
+        z, m, v, res = lockstep(cnfs, offs, hp, t, s0)
+        status = ts.tsat_status(st.h, len(insts))
+        for j, r in enumerate(res):
+            if status["inst"][j]["found"] and status["inst"][j]["found_step"] < t:
+                continue
+            assert status["inst"][j]["min_unsat"] == int(r["unsat"].min())
+            assert abs(status["inst"][j]["loss"] - r["L"]) <= TOL_F32 * abs(r["L"])
+        frozen = np.zeros(prob.info["n_vars"], bool)
+        for j in range(len(insts)):
+            if status["inst"][j]["found"]:
+                frozen[offs[j]:offs[j + 1]] = True
+        live = ~frozen
+        assert rel_err(s1["z"][live], z[live]) < TOL_F32, (name, t)
+        assert rel_err(s1["m"][live], m[live]) < TOL_F32, (name, t)
+        assert rel_err(s1["v"][live], v[live]) < TOL_F32, (name, t)
+        # bits of step t+1: Eq. 2 / Philox rule on the GPU's own FP32 z and nu
+        X = oracle.binarize_f32(s1["z"], s1["nu"], hp.binarize, c=0.25 / hp.bin_temp, seed=hp.seed, t=t + 1)
+        np.testing.assert_array_equal(s1["X"][live], X[live])
+        np.testing.assert_array_equal(s1["X"][frozen], s0["X"][frozen])
+        nu_ref = oracle.nu_f32(s1["z"], hp.norm)
+        bound = 2e-6 * np.abs(s1["z"]).mean(axis=1) + 2e-6 * np.abs(nu_ref)
+        assert np.all(np.abs(s1["nu"] - nu_ref) <= bound)
+    assert ts.tsat_status(st.h, len(insts))["step"] == steps
+
+
+@pytest.mark.parametrize("norm", [0, 1, 2])
+def test_autograd_hooks_match_oracle_gradient(norm):
+    inst = cnfgen.planted_ksat(500, 2130, 3, 3)
+    prob, st, cnfs = make([inst], 128)
+    hp = ts.hparams(seed=3, norm=norm, tau=0.8)
+    z = torch.randn(500, 128, device="cuda", generator=torch.Generator(device="cuda").manual_seed(4)) + 0.5
+    S = torch.zeros(128, device="cuda")
+    L = torch.zeros(1, device="cuda")
+    ts.tsat_forward(st.h, hp, z, 0, S, L)
+    grad = torch.zeros_like(z)
+    ts.tsat_backward(st.h, hp, z, 1.0, grad)
+    torch.cuda.synchronize()
+    zc = z.cpu().numpy()
+    nu_gpu = st.view("nu").cpu().numpy()
+    nu = oracle.nu_f32(zc, norm)
+    assert np.all(np.abs(nu_gpu - nu) <= 2e-6 * np.abs(zc).mean(axis=1) + 2e-6 * np.abs(nu))
+    nu = nu_gpu.astype(np.float64)      # FP32 statistic of the GPU, as in the lock-step tests
+    X = oracle.binarize_f32(zc, nu_gpu, 0)
+    S_ref, L_ref, G, _ = oracle.objective(cnfs[0], X=X, tau=0.8)
+    g = oracle.normalize_backward(zc.astype(np.float64), nu, G, norm)
+    assert rel_err(S.cpu().numpy(), S_ref) < TOL_F32
+    assert abs(L.item() - L_ref) < TOL_F32 * abs(L_ref)
+    assert rel_err(grad.cpu().numpy(), g) < TOL_F32
+
+
+@pytest.mark.parametrize("dtype,tol", [(ts.DTYPE_F32, TOL_F32), (ts.DTYPE_BF16, TOL_BF16)])
+def test_lockstep_relaxed(dtype, tol):
+    inst = cnfgen.structured_mixed(1024, 4000, 5, communities=8)
+    prob, st, cnfs = make([inst], 64, layer=ts.LAYER_RELAXED, dtype=dtype)
+    hp = ts.hparams(seed=5, norm=1, layer=ts.LAYER_RELAXED, tau=1.1)
+    ts.tsat_init(st.h, hp)
+    for t in range(3):
+        s0 = snapshot(st)
+        ts.tsat_step(st.h, hp, 1, stop_on_sat=False)
+        s1 = snapshot(st)
+        z, m, v, res = lockstep(cnfs, prob.var_offsets, hp, t, s0)
+        status = ts.tsat_status(st.h, 1)
+        assert abs(status["inst"][0]["loss"] - res[0]["L"]) <= tol * abs(res[0]["L"])
+        assert rel_err(s1["m"], m) < tol
+        assert rel_err(s1["z"], z) < tol
+
+
+def test_relaxed_autograd_fd():
+    """Directional finite differences of the GPU relaxed objective (FP32)."""
+    inst = cnfgen.structured_mixed(2048, 8000, 11, communities=8)
+    prob, st, cnfs = make([inst], 64, layer=ts.LAYER_RELAXED)
+    hp = ts.hparams(seed=2, norm=1, layer=ts.LAYER_RELAXED)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    z = torch.randn(2048, 64, device="cuda", generator=g) + 0.1
+    S = torch.zeros(64, device="cuda")
+    L = torch.zeros(1, device="cuda")
+    ts.tsat_forward(st.h, hp, z, 0, S, L)
+    grad = torch.zeros_like(z)
+    ts.tsat_backward(st.h, hp, z, 1.0, grad)
+    d = torch.zeros_like(z)
+    rows = torch.randperm(2048, generator=torch.Generator().manual_seed(1))[:500]
+    d[rows.cuda()] = torch.randn(500, 64, device="cuda", generator=g)
+    h = 1e-2
+    Lp, Lm = torch.zeros(1, device="cuda"), torch.zeros(1, device="cuda")
+    ts.tsat_forward(st.h, hp, z + h * d, 0, S, Lp)
+    ts.tsat_forward(st.h, hp, z - h * d, 0, S, Lm)
+    torch.cuda.synchronize()
+    fd = (Lp.item() - Lm.item()) / (2 * h)
+    an = float((grad * d).sum().item())
+    # FP32 objective of size ~C: rounding error of L ~ 1e-7 |L| / h dominates
+    bound = 1e-3 * abs(an) + 4 * 6e-8 * abs(L.item()) / h
+    assert abs(fd - an) <= bound, (fd, an)
+
+
+def test_stop_on_sat_freezes_model():
+    inst = cnfgen.planted_ksat(100, 380, 3, 21)
+    prob, st, cnfs = make([inst], 64)
+    hp = ts.hparams(seed=4, norm=1)
+    ts.tsat_init(st.h, hp)
+    ts.tsat_step(st.h, hp, 300, stop_on_sat=True)
+    status = ts.tsat_status(st.h, 1)
+    assert status["inst"][0]["found"] == 1
+    i = status["inst"][0]["found_sample"]
+    s = snapshot(st)
+    u, _ = oracle.check(cnfs[0], s["X"][:, i:i + 1])
+    assert u[0] == 0
+    assert status["step"] == status["inst"][0]["found_step"]
+    ts.tsat_step(st.h, hp, 5, stop_on_sat=True)
+    s2 = snapshot(st)
+    np.testing.assert_array_equal(s2["bits"], s["bits"])
+    best = ts.tsat_best(st.h, hp, 0, inst.n_vars)
+    assert best["complete"] and best["unsat"] == 0 and best["sample"] == i
+    np.testing.assert_array_equal(best["assignment"], s["X"][:, i])
+
+
+@pytest.mark.parametrize("N,k", [(64, None), (256, 37), (32, 1)])
+def test_best_partial_assignment(N, k):
+    inst = cnfgen.planted_ksat(2500, 10650, 3, 13)
+    prob, st, cnfs = make([inst], N)
+    hp = ts.hparams(seed=8, norm=1, tau=1.7)
+    ts.tsat_init(st.h, hp)
+    ts.tsat_step(st.h, hp, 7, stop_on_sat=False)
+    s = snapshot(st)
+    best = ts.tsat_best(st.h, hp, 0, inst.n_vars, k)
+    kk = best["part_var"].shape[0]
+    unsat, _ = oracle.check(cnfs[0], s["X"])
+    i = oracle.best_sample(unsat)
+    assert best["sample"] == i and best["unsat"] == unsat[i]
+    np.testing.assert_array_equal(best["assignment"], s["X"][:, i])
+    assert best["ready"] == ((cnfs[0].C - unsat[i]) / cnfs[0].C > 0.99)
+    _, _, G, _ = oracle.objective(cnfs[0], X=s["X"][:, i:i + 1], tau=1.7)
+    a = np.abs(G[:, 0])
+    ref = oracle.topk_confident(a, kk)
+    got = best["part_var"] - 1
+    # unique part: the selection equals the oracle's up to FP32 near-ties at the cut
+    kth = a[ref[-1]]
+    assert np.all(a[got] <= kth * (1 + 1e-5) + 1e-12)
+    assert len(set(got.tolist())) == kk
+    assert np.all(np.diff(a[got]) >= -1e-5 * kth - 1e-12)
+    np.testing.assert_array_equal(best["part_val"], s["X"][got, i])
+
+
+def test_checkpoint_resume_is_bit_exact():
+    inst = cnfgen.planted_ksat(800, 3400, 3, 17)
+    prob, st, _ = make([inst], 128)
+    hp = ts.hparams(seed=99, norm=1, binarize=1)
+    ts.tsat_init(st.h, hp)
+    ts.tsat_step(st.h, hp, 4, stop_on_sat=False)
+    torch.cuda.synchronize()
+    ckpt = st.buf.clone()
+    ts.tsat_step(st.h, hp, 5, stop_on_sat=False)
+    a = snapshot(st)
+    st.buf.copy_(ckpt)
+    ts.tsat_step(st.h, hp, 5, stop_on_sat=False)
+    b = snapshot(st)
+    for k in ("z", "m", "v", "nu", "bits"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_graph_replay_equals_single_steps():
+    inst = cnfgen.planted_ksat(600, 2556, 3, 23)
+    hp = ts.hparams(seed=5, norm=1, binarize=1)
+    _, st1, _ = make([inst], 64)
+    _, st2, _ = make([inst], 64)
+    ts.tsat_init(st1.h, hp)
+    ts.tsat_init(st2.h, hp)
+    ts.tsat_step(st1.h, hp, 12, stop_on_sat=False)
+    for _ in range(12):
+        ts.tsat_step(st2.h, hp, 1, stop_on_sat=False)
+    a, b = snapshot(st1), snapshot(st2)
+    for k in ("z", "m", "v", "bits"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_autotune_keeps_results():
+    inst = cnfgen.planted_ksat(5000, 21000, 3, 29)
+    hp = ts.hparams(seed=5, norm=1)
+    _, st1, _ = make([inst], 128)
+    _, st2, _ = make([inst], 128)
+    ts.tsat_init(st1.h, hp)
+    tun = ts.tsat_autotune(st1.h, hp)
+    assert tun[0] % 512 == 0 and tun[2] >= 1 and tun[3] >= 1
+    ts.tsat_init(st2.h, hp)
+    ts.tsat_step(st1.h, hp, 3, stop_on_sat=False)
+    ts.tsat_step(st2.h, hp, 3, stop_on_sat=False)
+    a, b = snapshot(st1), snapshot(st2)
+    for k in ("z", "bits"):
+        np.testing.assert_array_equal(a[k], b[k])
