@@ -41,6 +41,8 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "planted3sat_n1e6": dict(n=1_000_000, m=4_200_000, k=3, N=1024, seed=1,
                              desc="planted random 3-SAT n=1,000,000 m=4,200,000 (ratio 4.2), N=1024 samples"),
+    "planted3sat_n1e5": dict(n=100_000, m=420_000, k=3, N=1024, seed=1,
+                             desc="planted random 3-SAT n=100,000 m=420,000 (ratio 4.2), N=1024 samples (profiling size)"),
     "planted3sat_n100": dict(n=100, m=426, k=3, N=64, seed=0,
                              desc="planted random 3-SAT n=100 m=426 (ratio 4.26), N=64 samples"),
 }

@@ -56,3 +56,33 @@ def make(instances, N, layer=ts.LAYER_STE, dtype=ts.DTYPE_F32):
     st = ts.State(prob, N, layer, dtype)
     cnfs = [oracle.CNF(i.n_vars, i.clause_ptr, i.lits) for i in instances]
     return prob, st, cnfs
+
+
+def assert_adamw_z(z_gpu, z_ref, m_gpu, m_ref, v_gpu, v_ref, t, hp, tol=TOL_F32):
+    """z after AdamW, element by element, within a bound propagated from the
+    measured m / v differences (which are themselves held to `tol`).
+
+    z' = z (1 - lr wd) - lr u,  u = (m / bc1) / (sqrt(v / bc2) + eps).
+    First order: |dz'| <= lr (|du/dm| |dm| + |du/dv| |dv|) + tol max|z'|, with
+    du/dm = 1 / (bc1 (sqrt(vh) + eps)) and
+    |du/dv| = |mh| / (2 bc2 sqrt(vh) (sqrt(vh) + eps)^2), vh = v / bc2, mh = m / bc1.
+    Where |g| is comparable to eps the update is ill-conditioned and this
+    bound, not the flat tolerance, is what FP32 arithmetic can meet."""
+    from tests.conftest import rel_err
+    assert rel_err(m_gpu, m_ref) < tol
+    assert rel_err(v_gpu, v_ref) < tol
+    lr = oracle.lr_at(t, hp.lr0, hp.lr_factor, hp.decay_period, hp.restart_period, hp.lr_floor)
+    bc1 = 1.0 - float(hp.beta1) ** (t + 1)
+    bc2 = 1.0 - float(hp.beta2) ** (t + 1)
+    vh = np.maximum(v_ref / bc2, 0.0)
+    sq = np.sqrt(vh)
+    eps = float(hp.eps)
+    dm = np.abs(m_gpu.astype(np.float64) - m_ref)
+    dv = np.abs(v_gpu.astype(np.float64) - v_ref)
+    du_dm = 1.0 / (bc1 * (sq + eps))
+    du_dv = np.abs(m_ref / bc1) / (2.0 * bc2 * np.maximum(sq, 1e-30) * (sq + eps) ** 2)
+    du_dv = np.where(sq > 0, du_dv, 0.0)
+    bound = 2.0 * lr * (du_dm * dm + du_dv * dv) + tol * np.abs(z_ref).max()
+    err = np.abs(z_gpu.astype(np.float64) - z_ref)
+    bad = err > bound
+    assert not bad.any(), (int(bad.sum()), float(err[bad].max()), float(bound[bad].min()))

@@ -11,7 +11,7 @@ import oracle
 from paper_2511_07737_b300 import cnfgen
 from paper_2511_07737_b300 import turbosat as ts
 from tests.conftest import rel_err
-from tests.gpu_util import TOL_BF16, TOL_F32, lockstep, make, snapshot, unpack_bits
+from tests.gpu_util import TOL_BF16, TOL_F32, assert_adamw_z, lockstep, make, snapshot, unpack_bits
 
 pytestmark = pytest.mark.gpu
 
@@ -106,9 +106,7 @@ def test_lockstep_ste(name, gen, N, kw, steps):
             if status["inst"][j]["found"]:
                 frozen[offs[j]:offs[j + 1]] = True
         live = ~frozen
-        assert rel_err(s1["z"][live], z[live]) < TOL_F32, (name, t)
-        assert rel_err(s1["m"][live], m[live]) < TOL_F32, (name, t)
-        assert rel_err(s1["v"][live], v[live]) < TOL_F32, (name, t)
+        assert_adamw_z(s1["z"][live], z[live], s1["m"][live], m[live], s1["v"][live], v[live], t, hp)
         # bits of step t+1: Eq. 2 / Philox rule on the GPU's own FP32 z and nu
         X = oracle.binarize_f32(s1["z"], s1["nu"], hp.binarize, c=0.25 / hp.bin_temp, seed=hp.seed, t=t + 1)
         np.testing.assert_array_equal(s1["X"][live], X[live])
@@ -157,43 +155,47 @@ def test_lockstep_relaxed(dtype, tol):
         z, m, v, res = lockstep(cnfs, prob.var_offsets, hp, t, s0)
         status = ts.tsat_status(st.h, 1)
         assert abs(status["inst"][0]["loss"] - res[0]["L"]) <= tol * abs(res[0]["L"])
-        assert rel_err(s1["m"], m) < tol
-        assert rel_err(s1["z"], z) < tol
+        assert_adamw_z(s1["z"], z, s1["m"], m, s1["v"], v, t, hp, tol=tol)
 
 
 def test_relaxed_autograd_fd():
-    """Directional finite differences of the GPU relaxed objective (FP32)."""
-    inst = cnfgen.structured_mixed(2048, 8000, 11, communities=8)
+    """Directional central difference of the GPU relaxed objective (FP32) on a
+    5,000-variable slice, along sign(gradient) so that the signal dominates the
+    FP32 evaluation noise of L."""
+    inst = cnfgen.structured_mixed(8192, 32000, 11, communities=16)
     prob, st, cnfs = make([inst], 64, layer=ts.LAYER_RELAXED)
     hp = ts.hparams(seed=2, norm=1, layer=ts.LAYER_RELAXED)
     g = torch.Generator(device="cuda").manual_seed(0)
-    z = torch.randn(2048, 64, device="cuda", generator=g) + 0.1
+    z = torch.randn(8192, 64, device="cuda", generator=g) + 0.1
     S = torch.zeros(64, device="cuda")
     L = torch.zeros(1, device="cuda")
     ts.tsat_forward(st.h, hp, z, 0, S, L)
     grad = torch.zeros_like(z)
     ts.tsat_backward(st.h, hp, z, 1.0, grad)
+    rows = torch.randperm(8192, generator=torch.Generator().manual_seed(1))[:5000].cuda()
     d = torch.zeros_like(z)
-    rows = torch.randperm(2048, generator=torch.Generator().manual_seed(1))[:500]
-    d[rows.cuda()] = torch.randn(500, 64, device="cuda", generator=g)
+    d[rows] = torch.sign(grad[rows])
     h = 1e-2
     Lp, Lm = torch.zeros(1, device="cuda"), torch.zeros(1, device="cuda")
     ts.tsat_forward(st.h, hp, z + h * d, 0, S, Lp)
+    Sabs = float(S.abs().sum().item())
     ts.tsat_forward(st.h, hp, z - h * d, 0, S, Lm)
     torch.cuda.synchronize()
     fd = (Lp.item() - Lm.item()) / (2 * h)
     an = float((grad * d).sum().item())
-    # FP32 objective of size ~C: rounding error of L ~ 1e-7 |L| / h dominates
-    bound = 1e-3 * abs(an) + 4 * 6e-8 * abs(L.item()) / h
-    assert abs(fd - an) <= bound, (fd, an)
+    # FP32 evaluation error of L: S_i = Y_i / Z_i with Y, Z blocked FP32 sums
+    # over C clauses, relative error <= ~2e-6 each -> |dL| <= 4e-6 sum|S_i|;
+    # central differences add 2 |dL| / (2 h), the O(h^2) term is below 1e-3 |an|.
+    noise = 2 * 4e-6 * Sabs / (2 * h)
+    assert abs(fd - an) <= 1e-3 * abs(an) + noise, (fd, an, noise)
 
 
 def test_stop_on_sat_freezes_model():
-    inst = cnfgen.planted_ksat(100, 380, 3, 21)
+    inst = cnfgen.planted_ksat(100, 426, 3, 0)
     prob, st, cnfs = make([inst], 64)
-    hp = ts.hparams(seed=4, norm=1)
+    hp = ts.hparams(seed=1, norm=ts.NORM_NONE, tau=2.0)
     ts.tsat_init(st.h, hp)
-    ts.tsat_step(st.h, hp, 300, stop_on_sat=True)
+    ts.tsat_step(st.h, hp, 600, stop_on_sat=True)
     status = ts.tsat_status(st.h, 1)
     assert status["inst"][0]["found"] == 1
     i = status["inst"][0]["found_sample"]
