@@ -437,7 +437,9 @@ void orc_nu_f32(int32_t V, int32_t N, const float *z, int32_t mode,
 }
 
 /* Eq. 2 decided in FP32 from FP32 inputs z and nu (the GPU's precision).
- * mode 0 (deterministic): x = [z/nu > 0].
+ * The normalised value zt of Eq. 5 is evaluated as z * (1/nu): an FP32
+ * reciprocal and an FP32 product, each correctly rounded.
+ * mode 0 (deterministic): x = [zt > 0].
  * mode 1 (Philox): p = clamp(0.5 + c * (z/nu), 0, 1) with one FP32
  * multiply and one FP32 add (no fused multiply-add), u = (word >> 8) 2^-24,
  * x = [u < p].  t is the step the bits belong to.                         */
@@ -447,8 +449,9 @@ void orc_binarize_f32(int32_t V, int32_t N, const float *z, const float *nu,
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
 #pragma omp parallel for schedule(static)
   for (int32_t v = 0; v < V; ++v) {
+    volatile float rnu = 1.0f / nu[v];
     for (int32_t i = 0; i < N; ++i) {
-      volatile float zt = z[(int64_t)v * N + i] / nu[v];
+      volatile float zt = z[(int64_t)v * N + i] * rnu;
       uint8_t x;
       if (mode == 0) {
         x = (zt > 0.0f);

@@ -94,9 +94,10 @@ __device__ __forceinline__ void row_binarize_store(const StateDev &sd, const Hyp
   const uint32_t rw[4] = {rnd.x, rnd.y, rnd.z, rnd.w};
   uint32_t nib = 0;
   float a[4];
+  const float rnu = __frcp_rn(nu);  // zt = z * (1/nu), both correctly rounded (FP32 decision)
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
-    float zt = __fdiv_rn(zq[s], nu);
+    float zt = __fmul_rn(zq[s], rnu);
     nib |= binarize_one(zt, hy.binarize, hy.bin_c, rw[s]) << s;
     a[s] = sigmoidf_(zt);
   }
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
         const float zq_[4] = {z4.x, z4.y, z4.z, z4.w};
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-          const float a = sigmoidf_(__fdiv_rn(zq_[s], nu));
+          const float a = sigmoidf_(__fmul_rn(zq_[s], __frcp_rn(nu)));
           G[s] *= a * (1.0f - a);
         }
       } else {
@@ -517,6 +518,225 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
       row_binarize_store(sd, hy, g, red, v, zn, tcur + 1, bdst, RELAX);
     }
   }
+}
+
+// ------------------------------------------------------------------ fused update, lmax <= 3
+// TMA-staged variant for clause length <= 3 (R in 0..3, two bit planes).
+//   * the next row's z, m, v and int4 occurrence records stream into shared
+//     memory with 1-D bulk copies (cp.async.bulk + mbarrier, double buffered)
+//     while the current row is processed;
+//   * stage A: R bit-planes once per (occurrence, 32-sample word);
+//   * stage B: each thread counts, byte-packed for its 4 samples, the signed
+//     occurrences with plane-0 bit, plane-1 bit and both bits set; with
+//     gamma[R] = g0 + b0 d1 + b1 d2 + b0 b1 d3 the STE gradient is
+//     G = (n+ - n-) g0 + C0 d1 + C1 d2 + C01 d3 (exact rewrite of the sum).
+constexpr int kOcap = 64;    // occurrences per chunk for N >= 256
+constexpr int kOcapS = 32;   // ... for N < 256
+
+struct U2Layout {
+  int ocap, zbytes, rec_bytes, plane_words, group_bytes;
+};
+__host__ __device__ __forceinline__ U2Layout u2_layout(int N) {
+  U2Layout L;
+  L.ocap = N >= 256 ? kOcap : kOcapS;
+  L.zbytes = N * 4;
+  L.rec_bytes = L.ocap * 16;
+  L.plane_words = L.ocap * 2 * (N / 32);
+  // 2 stages x (z, m, v, records) + planes + 8 reduction floats + 2 mbarriers
+  L.group_bytes = 2 * (3 * L.zbytes + L.rec_bytes) + L.plane_words * 4 + 8 * 4 + 16;
+  L.group_bytes = (L.group_bytes + 127) & ~127;
+  return L;
+}
+
+__global__ void __launch_bounds__(kBlock, 4) k_update2(ProbDev pd, StateDev sd, Hyper hy, int mode, const float *zin,
+                                                       float *grad, float dL, int rows_per_item) {
+  extern __shared__ __align__(128) unsigned char smem2[];
+  const StateHdr *hdr = sd.hdr;
+  if (mode == 0 && hdr->all_done) return;
+  const int N = sd.N, W = sd.W;
+  const int GT = N >> 2, RPB = kBlock / GT;
+  Group g{GT, (int)threadIdx.x / GT, (int)threadIdx.x % GT, (int)(threadIdx.x & 31)};
+  const U2Layout L = u2_layout(N);
+  unsigned char *gb = smem2 + (size_t)g.grp * L.group_bytes;
+  float *stz[2] = {reinterpret_cast<float *>(gb), reinterpret_cast<float *>(gb + 3 * L.zbytes + L.rec_bytes)};
+  int4 *strec[2] = {reinterpret_cast<int4 *>(gb + 3 * L.zbytes),
+                    reinterpret_cast<int4 *>(gb + 2 * (3 * L.zbytes) + L.rec_bytes)};
+  uint32_t *planes = reinterpret_cast<uint32_t *>(gb + 2 * (3 * L.zbytes + L.rec_bytes));
+  float *red = reinterpret_cast<float *>(planes + L.plane_words);
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(red + 8);
+  const bool leader = g.gl == 0;
+  if (leader) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  StepParams sp;
+  if (mode == 0) sp = *sd.sp;
+  const int64_t tcur = (mode == 0) ? sp.t : hdr->t;
+  const uint32_t *bsrc = cur_bits(sd, tcur);
+  uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
+  const float b1 = hy.beta1, b2 = hy.beta2;
+  const float *zsrc = (mode == 0) ? sd.z : zin;
+  const int s0 = g.gl * 4, w = s0 >> 5, sh = s0 & 31;
+  const int tw = g.gl % W, to = g.gl / W, ostep = GT / W;   // stage-A task layout
+  const int64_t NG = (int64_t)gridDim.x * RPB;
+  const int64_t n_items = ((int64_t)pd.V + rows_per_item - 1) / rows_per_item;
+  // row sequence of this group
+  int64_t item = (int64_t)blockIdx.x * RPB + g.grp;
+  int64_t v = item < n_items ? item * rows_per_item : -1;
+  auto next_row = [&](int64_t vv, int64_t &it) -> int64_t {
+    if (vv + 1 < min((int64_t)pd.V, (it + 1) * rows_per_item)) return vv + 1;
+    it += NG;
+    return it < n_items ? it * rows_per_item : -1;
+  };
+  auto issue = [&](int64_t vv, int stage) {
+    const int32_t o0 = __ldg(pd.vptr + vv), o1 = __ldg(pd.vptr + vv + 1);
+    const int nrec = min(o1 - o0, L.ocap);
+    const uint32_t bytes = (mode == 0 ? 3u : 1u) * (uint32_t)L.zbytes + 16u * (uint32_t)nrec;
+    fence_proxy_async();
+    mbar_expect_tx(&mbar[stage], bytes);
+    float *dz = stz[stage];
+    tma_load_1d(dz, zsrc + (size_t)vv * N, L.zbytes, &mbar[stage]);
+    if (mode == 0) {
+      tma_load_1d(dz + N, sd.m + (size_t)vv * N, L.zbytes, &mbar[stage]);
+      tma_load_1d(dz + 2 * N, sd.v + (size_t)vv * N, L.zbytes, &mbar[stage]);
+    }
+    if (nrec > 0) tma_load_1d(strec[stage], pd.xrec + 4 * (int64_t)o0, 16u * nrec, &mbar[stage]);
+  };
+  if (v >= 0 && leader) issue(v, 0);
+  float gd[4][4];   // per sample: gamma0, d1, d2, d3
+  int cur_inst = -1;
+  uint32_t k = 0;
+  int64_t it_next = item;
+  while (v >= 0) {
+    const int64_t vn = next_row(v, it_next);
+    const int stage = k & 1;
+    if (vn >= 0 && leader) issue(vn, stage ^ 1);
+    if (!mbar_wait_bounded(&mbar[stage], (k >> 1) & 1, kWaitLimit)) {
+      sd.hdr->err = kErrTimeout;  // a copy never completed: stop this group
+      return;
+    }
+    const int inst = __ldg(pd.var_inst + v);
+    if (mode == 0 && sd.inst[inst].found) {  // frozen instance: keep its model
+      if ((g.gl & 7) == 0) bdst[v * W + w] = bsrc[v * W + w];
+    } else {
+      if (inst != cur_inst) {
+        cur_inst = inst;
+        const float *gsrc = sd.gamma + (size_t)inst * sd.lm1 * N;
+        float gm[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          float4 x = (r < sd.lm1) ? *reinterpret_cast<const float4 *>(gsrc + (size_t)r * N + s0)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+          gm[0][r] = x.x; gm[1][r] = x.y; gm[2][r] = x.z; gm[3][r] = x.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          gd[q][0] = gm[q][0];
+          gd[q][1] = gm[q][1] - gm[q][0];
+          gd[q][2] = gm[q][2] - gm[q][0];
+          gd[q][3] = (gm[q][3] - gm[q][2]) - (gm[q][1] - gm[q][0]);
+        }
+      }
+      const int32_t o0 = __ldg(pd.vptr + v), o1 = __ldg(pd.vptr + v + 1);
+      const uint32_t own_tw = __ldg(bsrc + v * W + tw);
+      float G[4] = {0.f, 0.f, 0.f, 0.f};
+      int nsign = 0;
+      const int4 *recs = strec[stage];
+      for (int32_t c0 = o0; c0 < o1; c0 += L.ocap) {
+        const int nc = min(L.ocap, o1 - c0);
+        if (c0 != o0) {  // rows longer than one chunk: plain cooperative load into the stage buffer
+          g.sync();
+          int4 *dst = strec[stage];
+          for (int q = g.gl; q < nc; q += GT) dst[q] = __ldg(reinterpret_cast<const int4 *>(pd.xrec) + c0 + q);
+          g.sync();
+        }
+        // stage A: bit planes of R for (occurrence, word)
+        for (int o = to; o < nc; o += ostep) {
+          const int4 rc = recs[o];
+          const uint32_t len = (uint32_t)rc.x >> 1;
+          const uint32_t a = own_tw ^ (0u - (uint32_t)(rc.x & 1));
+          const uint32_t bb = len > 1 ? (__ldg(bsrc + (size_t)(rc.y >> 1) * W + tw) ^ (0u - (uint32_t)(rc.y & 1))) : 0u;
+          const uint32_t cc = len > 2 ? (__ldg(bsrc + (size_t)(rc.z >> 1) * W + tw) ^ (0u - (uint32_t)(rc.z & 1))) : 0u;
+          planes[(o * 2) * W + tw] = a ^ bb ^ cc;
+          planes[(o * 2 + 1) * W + tw] = (a & bb) | (cc & (a ^ bb));
+        }
+        g.sync();
+        // stage B: byte-packed signed counts for this thread's 4 samples
+        uint32_t P0 = 0, P1 = 0, P01 = 0, N0 = 0, N1 = 0, N01 = 0;
+        for (int o = 0; o < nc; ++o) {
+          const uint32_t n0 = (planes[(o * 2) * W + w] >> sh) & 15u;
+          const uint32_t n1 = (planes[(o * 2 + 1) * W + w] >> sh) & 15u;
+          const uint32_t x0 = (n0 * 0x00204081u) & 0x01010101u;
+          const uint32_t x1 = (n1 * 0x00204081u) & 0x01010101u;
+          if (recs[o].x & 1) {
+            N0 += x0; N1 += x1; N01 += x0 & x1; --nsign;
+          } else {
+            P0 += x0; P1 += x1; P01 += x0 & x1; ++nsign;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int sq = 8 * q;
+          const float c0f = (float)((int)((P0 >> sq) & 255u) - (int)((N0 >> sq) & 255u));
+          const float c1f = (float)((int)((P1 >> sq) & 255u) - (int)((N1 >> sq) & 255u));
+          const float c2f = (float)((int)((P01 >> sq) & 255u) - (int)((N01 >> sq) & 255u));
+          G[q] += c0f * gd[q][1] + c1f * gd[q][2] + c2f * gd[q][3];
+        }
+        g.sync();   // planes and the record buffer are reused by the next chunk
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) G[q] += (float)nsign * gd[q][0];
+      // ---- chain rule through Eq. 5
+      const float *zr = stz[stage];
+      const float4 z4 = *reinterpret_cast<const float4 *>(zr + s0);
+      const float zq[4] = {z4.x, z4.y, z4.z, z4.w};
+      const float nu = sd.nu[v];
+      float gq[4];
+      if (hy.norm == TSAT_NORM_NONE) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) gq[q] = G[q];
+      } else {
+        const float dot = g.sum((G[0] * zq[0] + G[1] * zq[1]) + (G[2] * zq[2] + G[3] * zq[3]), red);
+        const float rnu = __frcp_rn(nu);
+        const float c2 = dot * rnu * rnu * (1.0f / (float)N);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float dmu = (hy.norm == TSAT_NORM_ABSMEAN) ? (float)((zq[q] > 0.f) - (zq[q] < 0.f)) : 1.0f;
+          gq[q] = G[q] * rnu - c2 * dmu;
+        }
+      }
+      const size_t off = (size_t)v * N + s0;
+      if (mode == 1) {
+        *reinterpret_cast<float4 *>(grad + off) = make_float4(dL * gq[0], dL * gq[1], dL * gq[2], dL * gq[3]);
+      } else {
+        const float4 m4 = *reinterpret_cast<const float4 *>(zr + N + s0);
+        const float4 v4 = *reinterpret_cast<const float4 *>(zr + 2 * N + s0);
+        float mq[4] = {m4.x, m4.y, m4.z, m4.w}, vq[4] = {v4.x, v4.y, v4.z, v4.w}, zn[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float gs = gq[q];
+          mq[q] = b1 * mq[q] + (1.0f - b1) * gs;
+          vq[q] = b2 * vq[q] + (1.0f - b2) * (gs * gs);
+          const float denom = sqrtf(vq[q]) * sp.inv_sqrt_bc2 + hy.eps;
+          zn[q] = zq[q] * sp.decay - sp.step_size * __fdividef(mq[q], denom);
+        }
+        st_cs(sd.z + off, make_float4(zn[0], zn[1], zn[2], zn[3]));
+        st_cs(sd.m + off, make_float4(mq[0], mq[1], mq[2], mq[3]));
+        st_cs(sd.v + off, make_float4(vq[0], vq[1], vq[2], vq[3]));
+        row_binarize_store(sd, hy, g, red, v, zn, tcur + 1, bdst);
+      }
+    }
+    g.sync();   // the stage buffers of this row are free for the prefetch two rows ahead
+    v = vn;
+    ++k;
+  }
+}
+
+int update2_smem_bytes(int N) {
+  const U2Layout L = u2_layout(N);
+  return (kBlock / (N >> 2)) * L.group_bytes;
 }
 
 // ------------------------------------------------------------------ exact check (Sec. III-A)
@@ -643,6 +863,7 @@ static cudaError_t upd_launch(const ProbDev &pd, const StateDev &sd, const Hyper
 void prepare_update_attrs(int lmax) {
   const int P = planes_for(lmax);
   const int bytes = 160 * 1024;
+  cudaFuncSetAttribute(k_update2, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   cudaFuncSetAttribute(k_update<1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   switch (P) {
     case 1: cudaFuncSetAttribute(k_update<1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); break;
@@ -656,6 +877,10 @@ void prepare_update_attrs(int lmax) {
 cudaError_t launch_update(const ProbDev &pd, const StateDev &sd, const Hyper &hy, int mode, const float *zin,
                           float *grad, float dL, int grid, int rpi, cudaStream_t st) {
   const int P = planes_for(pd.lmax);
+  if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_fixed4) {
+    k_update2<<<grid, kBlock, update2_smem_bytes(sd.N), st>>>(pd, sd, hy, mode, zin, grad, dL, rpi);
+    return cudaGetLastError();
+  }
   if (sd.layer == TSAT_LAYER_RELAXED) return upd_launch<1, true, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);
   switch (P) {
     case 1: return upd_launch<1, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);

@@ -217,7 +217,7 @@ __global__ void k_fill(const int32_t *cptr, const int32_t *clit, int32_t C, cons
 // order) with rank counting, then write the occurrence records.
 __global__ void k_records(const int32_t *cptr, const int32_t *clit, int32_t V, const int32_t *vptr,
                           const int32_t *occ_j, const int32_t *occ_c, int32_t *occ_s,
-                          const int64_t *xptr, int32_t *xrec, int32_t *vocc) {
+                          const int64_t *xptr, int32_t *xrec, int32_t *vocc, int fixed4) {
   __shared__ int32_t sh[128];
   __shared__ int32_t carry;
   const int32_t v = blockIdx.x;
@@ -254,19 +254,26 @@ __global__ void k_records(const int32_t *cptr, const int32_t *clit, int32_t V, c
     if (a < d) {
       int32_t own = clit[j];
       vocc[b + a] = (c << 1) | (own & 1);
-      int32_t *r = xrec + base + off;
+      int32_t *r = xrec + base + (fixed4 ? 4 * a : off);
       r[0] = (own & 1) | (len << 1);  // nonzero: padding words are 0
       int q = 1;
       for (int32_t k = cptr[c]; k < cptr[c + 1]; ++k)
         if (k != j) r[q++] = clit[k];
+      if (fixed4)
+        for (; q < 4; ++q) r[q] = 0;
     }
     __syncthreads();
     if (threadIdx.x == 127) carry += sh[127];
     __syncthreads();
   }
   // zero the padding
-  int64_t used = base + carry;
+  int64_t used = fixed4 ? xptr[v + 1] : base + carry;
   for (int64_t p = used + threadIdx.x; p < xptr[v + 1]; p += blockDim.x) xrec[p] = 0;
+}
+
+__global__ void k_xptr_fixed4(const int32_t *vptr, int32_t V, int64_t *xptr) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v <= V) xptr[v] = 4 * (int64_t)vptr[v];
 }
 
 __global__ void k_var_inst(const InstInfo *inst, int32_t n_inst, int32_t V, int32_t *var_inst) {
@@ -302,7 +309,7 @@ static int measure(int32_t n_inst, const tsat_cnf_desc *d, Sizes *s) {
     s->nnz_raw += p[d[j].n_clauses];
     s->items_cap += (d[j].n_clauses + kItemMin - 1) / kItemMin;
   }
-  s->xrec_cap += 3 * s->V + 4;
+  s->xrec_cap = std::max<int64_t>(s->xrec_cap, 4 * s->nnz_raw) + 3 * s->V + 8;
   if (s->V >= (1LL << 30) || s->C >= (1LL << 31) - 1 || s->nnz_raw >= (1LL << 31) - 1) {
     set_error("problem too large: V=%lld C=%lld nnz=%lld", (long long)s->V, (long long)s->C,
               (long long)s->nnz_raw);
@@ -468,7 +475,11 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
   CK(cudaGetLastError());
   unsigned long long herr = ~0ull;
   CK(cudaMemcpyAsync(&herr, derr, sizeof(herr), cudaMemcpyDeviceToHost, stream));
+  CK(cudaMemcpyAsync(p->inst.data(), dinst, sizeof(InstInfo) * n_inst, cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));
+  int32_t lmax_all = 0;
+  for (auto &I : p->inst) lmax_all = std::max(lmax_all, I.lmax);
+  const int fixed4 = lmax_all <= 3 ? 1 : 0;
   if (herr != ~0ull) {
     int code = (int)(herr & 0xFF);
     long long c = (long long)(herr >> 8);
@@ -482,13 +493,18 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
   CK(cudaGetLastError());
   rc2 = exclusive_scan(P32(L.deg), s.V, false, P64(L.scan_tmp), nullptr, P32(L.vptr), stream);
   if (rc2) return fail(rc2);
-  rc2 = exclusive_scan(P32(L.recsz), s.V, true, P64(L.scan_tmp), P64(L.xptr), nullptr, stream);
-  if (rc2) return fail(rc2);
+  if (fixed4) {
+    k_xptr_fixed4<<<(unsigned)((s.V + 1 + T - 1) / T), T, 0, stream>>>(P32(L.vptr), p->V, P64(L.xptr));
+    CK(cudaGetLastError());
+  } else {
+    rc2 = exclusive_scan(P32(L.recsz), s.V, true, P64(L.scan_tmp), P64(L.xptr), nullptr, stream);
+    if (rc2) return fail(rc2);
+  }
   k_fill<<<gc, T, 0, stream>>>(P32(L.cptr), P32(L.clit), p->C, P32(L.vptr), P32(L.fill), P32(L.occ_j),
                                P32(L.occ_c));
   CK(cudaGetLastError());
   k_records<<<(unsigned)s.V, 128, 0, stream>>>(P32(L.cptr), P32(L.clit), p->V, P32(L.vptr), P32(L.occ_j),
-                                               P32(L.occ_c), P32(L.occ_s), P64(L.xptr), P32(L.xrec), P32(L.vocc));
+                                               P32(L.occ_c), P32(L.occ_s), P64(L.xptr), P32(L.xrec), P32(L.vocc), fixed4);
   CK(cudaGetLastError());
   k_var_inst<<<gv, T, 0, stream>>>(dinst, n_inst, p->V, P32(L.var_inst));
   CK(cudaGetLastError());
@@ -516,6 +532,7 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
   D.xrec = P32(L.xrec);
   D.vptr = P32(L.vptr);
   D.vocc = P32(L.vocc);
+  D.rec_fixed4 = fixed4;
   D.var_inst = P32(L.var_inst);
   D.items = (const int4 *)(w + L.items);
   D.inst = dinst;
