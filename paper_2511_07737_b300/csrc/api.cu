@@ -11,7 +11,7 @@
 namespace tsat {
 
 struct StatePlan {
-  size_t hdr, inst, sp, z, m, v, bits, nu, hist, gamma, S, unsat;
+  size_t hdr, inst, sp, z, m, v, bits, nu, hist, gamma, gdelta, S, unsat;
   size_t ehist, eunsat, gcol, sel, digits, selstate, outbits, small, part_var, part_val, fwdS, hist1;
   size_t lit, rbuf, zy, zs;
   size_t total;
@@ -34,6 +34,7 @@ static StatePlan plan_state(const tsat_problem *p, int32_t N, int32_t layer, int
   S.nu = take(sizeof(float) * V);
   S.hist = take(sizeof(int32_t) * I * lm1 * N);
   S.gamma = take(sizeof(float) * I * lm1 * N);
+  S.gdelta = take(sizeof(float) * I * 4 * N);
   S.S = take(sizeof(float) * I * N);
   S.unsat = take(sizeof(int32_t) * I * N);
   S.ehist = take(sizeof(int32_t) * I * lm1 * N);
@@ -108,7 +109,11 @@ static int leave(tsat_state *s, cudaStream_t user) {
   return TSAT_OK;
 }
 
-static int upd_grid(const tsat_state *s) { return std::max(1, s->sm_count * s->upd_blocks_per_sm); }
+// Update grid: resident blocks per SM (occupancy API) unless tuned explicitly.
+static int upd_grid(const tsat_state *s) {
+  const int bps = s->upd_blocks_per_sm > 0 ? s->upd_blocks_per_sm : update_blocks_per_sm(s->prob->dev, s->dev);
+  return std::max(1, s->sm_count * bps);
+}
 
 // One optimisation step: forward histogram, gamma, fused update.
 static int issue_step(tsat_state *s, const Hyper &hy, const LrSched &ls, cudaStream_t st) {
@@ -204,6 +209,7 @@ int tsat_state_create(tsat_problem *p, void *d_state, size_t state_bytes, int32_
   D.nu = (float *)(b + P.nu);
   D.hist = (int32_t *)(b + P.hist);
   D.gamma = (float *)(b + P.gamma);
+  D.gdelta = (float *)(b + P.gdelta);
   D.S = (float *)(b + P.S);
   D.unsat = (int32_t *)(b + P.unsat);
   D.V = p->V;
@@ -573,7 +579,7 @@ int tsat_get_tuning(const tsat_state *s, int32_t h_tuning[4]) {
 
 int tsat_set_tuning(tsat_state *s, const int32_t h_tuning[4]) {
   if (!s || !h_tuning) return TSAT_EINVAL;
-  if (h_tuning[0] < kItemMin || h_tuning[1] != kBlock || h_tuning[2] < 1 || h_tuning[2] > 32 || h_tuning[3] < 1 ||
+  if (h_tuning[0] < kItemMin || h_tuning[1] != kBlock || h_tuning[2] < 0 || h_tuning[2] > 32 || h_tuning[3] < 1 ||
       h_tuning[3] > 4096) {
     set_error("tuning values out of range");
     return TSAT_EINVAL;

@@ -67,6 +67,7 @@ struct StateDev {
   float *nu;                   // [V]
   int32_t *hist;               // [n_inst][lm1][N]
   float *gamma;                // [n_inst][lm1][N]
+  float *gdelta;               // [n_inst][4][N] gamma0, g1-g0, g2-g0, g3-g2-g1+g0 (lmax <= 3)
   float *S;                    // [n_inst][N]
   int32_t *unsat;              // [n_inst][N]
   float *zy;                   // relaxed: [n_items][2][N] partial (Z, Y) sums
@@ -190,6 +191,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+// Ampere-style asynchronous 4-byte global -> shared copy (per-thread groups)
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 constexpr uint32_t kWaitLimit = 1u << 22;
 constexpr int32_t kErrTimeout = 1;

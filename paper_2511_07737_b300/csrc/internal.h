@@ -86,7 +86,7 @@ struct tsat_state {
   int32_t *small = nullptr;         // [64] misc ints
   float *fwd_scratch = nullptr;     // tsat_forward outputs staging
   // schedules
-  int32_t upd_blocks_per_sm = 4;
+  int32_t upd_blocks_per_sm = 0;   // 0: resident blocks per SM from the occupancy API
   int32_t upd_rows_per_item = 1;
   int32_t sm_count = 148;
   cudaStream_t stream = nullptr;

@@ -338,7 +338,19 @@ __global__ void __launch_bounds__(1024) k_gamma(ProbDev pd, StateDev sd, Hyper h
     const int32_t h0 = h[0];
     if (write_gamma) {
       float *gm = sd.gamma + (size_t)inst * lm1 * N + i;
-      for (int r = 0; r <= lmax; ++r) gm[(size_t)r * N] = -(etab[r] * invZ) * (1.0f - hy.tau * ((float)r - S));
+      float gr[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int r = 0; r <= lmax; ++r) {
+        const float gv = -(etab[r] * invZ) * (1.0f - hy.tau * ((float)r - S));
+        gm[(size_t)r * N] = gv;
+        if (r < 4) gr[r] = gv;
+      }
+      if (lm1 <= 4) {
+        float *gd = sd.gdelta + (size_t)inst * 4 * N + i;
+        gd[0] = gr[0];
+        gd[N] = gr[1] - gr[0];
+        gd[2 * N] = gr[2] - gr[0];
+        gd[3 * N] = (gr[3] - gr[2]) - (gr[1] - gr[0]);
+      }
     }
     if (step_mode)
       for (int r = 0; r <= lmax; ++r) h[(size_t)r * N] = 0;
@@ -522,23 +534,27 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
 
 // ------------------------------------------------------------------ fused update, lmax <= 3
 // TMA-staged variant for clause length <= 3 (R in 0..3, two bit planes).
+// A row group of N/8 threads owns one variable row; a thread owns 8 samples
+// (one byte of a 32-sample word).
 //   * the next row's z, m, v and int4 occurrence records stream into shared
 //     memory with 1-D bulk copies (cp.async.bulk + mbarrier, double buffered)
 //     while the current row is processed;
 //   * stage A: R bit-planes once per (occurrence, 32-sample word);
-//   * stage B: each thread counts, byte-packed for its 4 samples, the signed
-//     occurrences with plane-0 bit, plane-1 bit and both bits set; with
-//     gamma[R] = g0 + b0 d1 + b1 d2 + b0 b1 d3 the STE gradient is
-//     G = (n+ - n-) g0 + C0 d1 + C1 d2 + C01 d3 (exact rewrite of the sum).
-constexpr int kOcap = 64;    // occurrences per chunk for N >= 256
-constexpr int kOcapS = 32;   // ... for N < 256
+//   * stage B: each thread counts, byte-packed (bias 128) for its 8 samples,
+//     the signed occurrences with plane-0 bit, plane-1 bit and both bits
+//     set; with gamma[R] = g0 + b0 d1 + b1 d2 + b0 b1 d3 the STE gradient is
+//     G = (n+ - n-) g0 + C0 d1 + C1 d2 + C01 d3 (an exact rewrite of the sum).
+constexpr int kOcap = 32;    // occurrences per chunk (byte counters stay in 128 +- 32)
 
 struct U2Layout {
-  int ocap, zbytes, rec_bytes, plane_words, group_bytes;
+  int GT, RPB, threads, ocap, zbytes, rec_bytes, plane_words, group_bytes;
 };
 __host__ __device__ __forceinline__ U2Layout u2_layout(int N) {
   U2Layout L;
-  L.ocap = N >= 256 ? kOcap : kOcapS;
+  L.GT = N >> 3;
+  L.RPB = kBlock / L.GT < 16 ? kBlock / L.GT : 16;
+  L.threads = L.RPB * L.GT;
+  L.ocap = kOcap;
   L.zbytes = N * 4;
   L.rec_bytes = L.ocap * 16;
   L.plane_words = L.ocap * 2 * (N / 32);
@@ -548,26 +564,95 @@ __host__ __device__ __forceinline__ U2Layout u2_layout(int N) {
   return L;
 }
 
-__global__ void __launch_bounds__(kBlock, 4) k_update2(ProbDev pd, StateDev sd, Hyper hy, int mode, const float *zin,
+// Group of GT threads inside a block of `threads` threads.
+struct Group8 {
+  int GT, grp, gl, lane, threads;
+  __device__ __forceinline__ unsigned mask() const {
+    return (GT >= 32) ? 0xFFFFFFFFu : (((1u << GT) - 1u) << (lane & ~(GT - 1)));
+  }
+  __device__ __forceinline__ void sync() const {
+    if (GT <= 32) __syncwarp(mask());
+    else if (GT == threads) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(GT) : "memory");
+  }
+  __device__ __forceinline__ float sum(float x, float *red) const {
+    const int span = GT < 32 ? GT : 32;
+    const unsigned m = mask();
+    for (int o = 1; o < span; o <<= 1) x += __shfl_xor_sync(m, x, o);
+    if (GT <= 32) return x;
+    sync();
+    if ((gl & 31) == 0) red[gl >> 5] = x;
+    sync();
+    float s = 0.0f;
+    for (int k = 0; k < (GT >> 5); ++k) s += red[k];
+    return s;
+  }
+  // One barrier: the caller alternates `slot` between consecutive reductions,
+  // so a slot is never rewritten before every warp has read it.
+  __device__ __forceinline__ float sum1(float x, float *red, int slot) const {
+    const int span = GT < 32 ? GT : 32;
+    const unsigned m = mask();
+    for (int o = 1; o < span; o <<= 1) x += __shfl_xor_sync(m, x, o);
+    if (GT <= 32) return x;
+    float *r = red + 4 * slot;
+    if ((gl & 31) == 0) r[gl >> 5] = x;
+    sync();
+    float s = 0.0f;
+    for (int k = 0; k < (GT >> 5); ++k) s += r[k];
+    return s;
+  }
+};
+
+__device__ __forceinline__ uint32_t spread4(uint32_t n) { return (n * 0x00204081u) & 0x01010101u; }
+// (byte q of x) - 128 as an exact float: 2^23 + byte assembled in the mantissa
+__device__ __forceinline__ float biased_byte(uint32_t x, uint32_t q) {
+  return __int_as_float((int)__byte_perm(x, 0x4B000000u, 0x7440u | q)) - 8388736.0f;
+}
+
+// Per-group shared memory of the pipelined update (offsets in bytes).
+struct U3Layout {
+  int GT, RPB, threads, ocap, zmv, rec, gp, own, red, bar, group_bytes;
+};
+__host__ __device__ __forceinline__ U3Layout u3_layout(int N) {
+  U3Layout L;
+  L.GT = N >> 3;
+  L.RPB = kBlock / L.GT < 16 ? kBlock / L.GT : 16;
+  L.threads = L.RPB * L.GT;
+  L.ocap = kOcap;
+  const int W = N / 32;
+  int o = 0;
+  L.zmv = o;  o += 3 * N * 4;                       // z, m, v of the current row (single buffer)
+  L.rec = o;  o += 3 * L.ocap * 16;                 // records, three rows deep
+  L.gp = o;   o += 2 * L.ocap * 2 * W * 4;          // gathered words -> bit planes, two rows deep
+  L.own = o;  o += 2 * (L.GT / W) * W * 4;          // the row's own bits per task thread, two rows deep
+  o = (o + 15) & ~15;
+  L.red = o;  o += 8 * 4;
+  L.bar = o;  o += 4 * 8;                           // zmv barrier + 3 record barriers
+  L.group_bytes = (o + 127) & ~127;
+  return L;
+}
+
+__global__ void __launch_bounds__(kBlock, 3) k_update2(ProbDev pd, StateDev sd, Hyper hy, int mode, const float *zin,
                                                        float *grad, float dL, int rows_per_item) {
   extern __shared__ __align__(128) unsigned char smem2[];
   const StateHdr *hdr = sd.hdr;
   if (mode == 0 && hdr->all_done) return;
   const int N = sd.N, W = sd.W;
-  const int GT = N >> 2, RPB = kBlock / GT;
-  Group g{GT, (int)threadIdx.x / GT, (int)threadIdx.x % GT, (int)(threadIdx.x & 31)};
-  const U2Layout L = u2_layout(N);
+  const U3Layout L = u3_layout(N);
+  const int GT = L.GT, RPB = L.RPB, OC = L.ocap;
+  Group8 g{GT, (int)threadIdx.x / GT, (int)threadIdx.x % GT, (int)(threadIdx.x & 31), L.threads};
   unsigned char *gb = smem2 + (size_t)g.grp * L.group_bytes;
-  float *stz[2] = {reinterpret_cast<float *>(gb), reinterpret_cast<float *>(gb + 3 * L.zbytes + L.rec_bytes)};
-  int4 *strec[2] = {reinterpret_cast<int4 *>(gb + 3 * L.zbytes),
-                    reinterpret_cast<int4 *>(gb + 2 * (3 * L.zbytes) + L.rec_bytes)};
-  uint32_t *planes = reinterpret_cast<uint32_t *>(gb + 2 * (3 * L.zbytes + L.rec_bytes));
-  float *red = reinterpret_cast<float *>(planes + L.plane_words);
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(red + 8);
+  float *zmv = reinterpret_cast<float *>(gb + L.zmv);
+  int4 *recb = reinterpret_cast<int4 *>(gb + L.rec);
+  uint32_t *gpb = reinterpret_cast<uint32_t *>(gb + L.gp);
+  uint32_t *ownb = reinterpret_cast<uint32_t *>(gb + L.own);
+  float *red = reinterpret_cast<float *>(gb + L.red);
+  uint64_t *bar_z = reinterpret_cast<uint64_t *>(gb + L.bar);
+  uint64_t *bar_r = bar_z + 1;
   const bool leader = g.gl == 0;
   if (leader) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    mbar_init(bar_z, 1);
+    for (int q = 0; q < 3; ++q) mbar_init(&bar_r[q], 1);
     mbar_init_fence();
   }
   __syncthreads();
@@ -576,133 +661,186 @@ __global__ void __launch_bounds__(kBlock, 4) k_update2(ProbDev pd, StateDev sd, 
   const int64_t tcur = (mode == 0) ? sp.t : hdr->t;
   const uint32_t *bsrc = cur_bits(sd, tcur);
   uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
-  const float b1 = hy.beta1, b2 = hy.beta2;
+  const float b1 = hy.beta1, b2 = hy.beta2, omb1 = 1.0f - hy.beta1, omb2 = 1.0f - hy.beta2;
   const float *zsrc = (mode == 0) ? sd.z : zin;
-  const int s0 = g.gl * 4, w = s0 >> 5, sh = s0 & 31;
-  const int tw = g.gl % W, to = g.gl / W, ostep = GT / W;   // stage-A task layout
+  const int s0 = g.gl * 8, w = s0 >> 5, sh = s0 & 31;
+  const uint32_t bsel = 0x4440u | (uint32_t)(sh >> 3);   // byte sh/8 of a word -> low byte
+  const int tw = g.gl % W, to = g.gl / W, ostep = GT / W;   // (occurrence, word) task layout
   const int64_t NG = (int64_t)gridDim.x * RPB;
   const int64_t n_items = ((int64_t)pd.V + rows_per_item - 1) / rows_per_item;
-  // row sequence of this group
-  int64_t item = (int64_t)blockIdx.x * RPB + g.grp;
-  int64_t v = item < n_items ? item * rows_per_item : -1;
-  auto next_row = [&](int64_t vv, int64_t &it) -> int64_t {
-    if (vv + 1 < min((int64_t)pd.V, (it + 1) * rows_per_item)) return vv + 1;
-    it += NG;
-    return it < n_items ? it * rows_per_item : -1;
+  int64_t it_next = (int64_t)blockIdx.x * RPB + g.grp;
+  auto first_row = [&]() -> int64_t { return it_next < n_items ? it_next * rows_per_item : -1; };
+  auto next_row = [&](int64_t vv) -> int64_t {
+    if (vv < 0) return -1;
+    if (vv + 1 < min((int64_t)pd.V, (it_next + 1) * rows_per_item)) return vv + 1;
+    it_next += NG;
+    return it_next < n_items ? it_next * rows_per_item : -1;
   };
-  auto issue = [&](int64_t vv, int stage) {
+  // ---- asynchronous pieces
+  auto issue_rec = [&](int64_t vv, int slot) {
     const int32_t o0 = __ldg(pd.vptr + vv), o1 = __ldg(pd.vptr + vv + 1);
-    const int nrec = min(o1 - o0, L.ocap);
-    const uint32_t bytes = (mode == 0 ? 3u : 1u) * (uint32_t)L.zbytes + 16u * (uint32_t)nrec;
+    const int nrec = min(o1 - o0, OC);
     fence_proxy_async();
-    mbar_expect_tx(&mbar[stage], bytes);
-    float *dz = stz[stage];
-    tma_load_1d(dz, zsrc + (size_t)vv * N, L.zbytes, &mbar[stage]);
-    if (mode == 0) {
-      tma_load_1d(dz + N, sd.m + (size_t)vv * N, L.zbytes, &mbar[stage]);
-      tma_load_1d(dz + 2 * N, sd.v + (size_t)vv * N, L.zbytes, &mbar[stage]);
-    }
-    if (nrec > 0) tma_load_1d(strec[stage], pd.xrec + 4 * (int64_t)o0, 16u * nrec, &mbar[stage]);
+    mbar_expect_tx(&bar_r[slot], 16u * (uint32_t)nrec);
+    if (nrec > 0) tma_load_1d(recb + slot * OC, pd.xrec + 4 * (int64_t)o0, 16u * nrec, &bar_r[slot]);
   };
-  if (v >= 0 && leader) issue(v, 0);
-  float gd[4][4];   // per sample: gamma0, d1, d2, d3
+  auto issue_zmv = [&](int64_t vv) {
+    fence_proxy_async();
+    mbar_expect_tx(bar_z, (mode == 0 ? 3u : 1u) * (uint32_t)N * 4u);
+    tma_load_1d(zmv, zsrc + (size_t)vv * N, N * 4, bar_z);
+    if (mode == 0) {
+      tma_load_1d(zmv + N, sd.m + (size_t)vv * N, N * 4, bar_z);
+      tma_load_1d(zmv + 2 * N, sd.v + (size_t)vv * N, N * 4, bar_z);
+    }
+  };
+  // gathers of the other literals' words of row vv (first chunk) into gp slot
+  auto gather = [&](int64_t vv, const int4 *rc, int nc, uint32_t *gp, uint32_t *own) {
+    cp_async4(own + to * W + tw, bsrc + vv * W + tw);
+    for (int o = to; o < nc; o += ostep) {
+      const int4 r = rc[o];
+      const uint32_t len = (uint32_t)r.x >> 1;
+      uint32_t *d = gp + (o * 2) * W + tw;
+      if (len > 1) cp_async4(d, bsrc + (size_t)(r.y >> 1) * W + tw); else d[0] = 0u;
+      if (len > 2) cp_async4(d + W, bsrc + (size_t)(r.z >> 1) * W + tw); else d[W] = 0u;
+    }
+  };
+  // gathered words -> R bit planes, in place
+  auto planes_of = [&](const int4 *rc, int nc, uint32_t *gp, const uint32_t *own) {
+    const uint32_t ow = own[to * W + tw];
+    for (int o = to; o < nc; o += ostep) {
+      const int4 r = rc[o];
+      const uint32_t len = (uint32_t)r.x >> 1;
+      uint32_t *d = gp + (o * 2) * W + tw;
+      const uint32_t a = ow ^ (0u - (uint32_t)(r.x & 1));
+      const uint32_t bb = len > 1 ? d[0] ^ (0u - (uint32_t)(r.y & 1)) : 0u;
+      const uint32_t cc = len > 2 ? d[W] ^ (0u - (uint32_t)(r.z & 1)) : 0u;
+      d[0] = a ^ bb ^ cc;
+      d[W] = (a & bb) | (cc & (a ^ bb));
+    }
+  };
+  auto nocc = [&](int64_t vv) -> int { return vv < 0 ? 0 : min(__ldg(pd.vptr + vv + 1) - __ldg(pd.vptr + vv), OC); };
+  // ---- prologue: row 0 records + z/m/v, row 1 records; row 0 planes
+  int64_t v = first_row();
+  int64_t v1 = next_row(v);
+  if (v >= 0 && leader) {
+    issue_rec(v, 0);
+    issue_zmv(v);
+    if (v1 >= 0) issue_rec(v1, 1);
+  }
+  if (v >= 0) {
+    if (!mbar_wait_bounded(&bar_r[0], 0, kWaitLimit)) { sd.hdr->err = kErrTimeout; return; }
+    const int nc0 = nocc(v);
+    gather(v, recb, nc0, gpb, ownb);
+    cp_async_wait_all();
+    planes_of(recb, nc0, gpb, ownb);
+    g.sync();
+  }
   int cur_inst = -1;
+  bool frozen = false;
+  const float *gdp = nullptr;
   uint32_t k = 0;
-  int64_t it_next = item;
+  int64_t vn = v1;
   while (v >= 0) {
-    const int64_t vn = next_row(v, it_next);
-    const int stage = k & 1;
-    if (vn >= 0 && leader) issue(vn, stage ^ 1);
-    if (!mbar_wait_bounded(&mbar[stage], (k >> 1) & 1, kWaitLimit)) {
-      sd.hdr->err = kErrTimeout;  // a copy never completed: stop this group
-      return;
+    const int64_t vnn = next_row(vn);
+    const int rs = k % 3, rs1 = (k + 1) % 3, ps = k & 1;
+    if (vnn >= 0 && leader) issue_rec(vnn, (k + 2) % 3);
+    // start the gathers of row k+1 (their records arrived one row ago)
+    const int nc1 = nocc(vn);
+    if (vn >= 0) {
+      if (!mbar_wait_bounded(&bar_r[rs1], ((k + 1) / 3) & 1, kWaitLimit)) { sd.hdr->err = kErrTimeout; return; }
+      gather(vn, recb + rs1 * OC, nc1, gpb + (ps ^ 1) * OC * 2 * W, ownb + (ps ^ 1) * ostep * W);
     }
     const int inst = __ldg(pd.var_inst + v);
-    if (mode == 0 && sd.inst[inst].found) {  // frozen instance: keep its model
-      if ((g.gl & 7) == 0) bdst[v * W + w] = bsrc[v * W + w];
+    if (inst != cur_inst) {
+      cur_inst = inst;
+      frozen = (mode == 0) && sd.inst[inst].found;
+      gdp = sd.gdelta + (size_t)inst * 4 * N + s0;
+    }
+    const int32_t o0 = __ldg(pd.vptr + v), o1 = __ldg(pd.vptr + v + 1);
+    const float nu = sd.nu[v];
+    float G[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) G[q] = 0.f;
+    int nsign = 0;
+    if (!frozen) {
+      int4 *rc = recb + rs * OC;
+      uint32_t *gp = gpb + ps * OC * 2 * W;
+      for (int32_t c0 = o0; c0 < o1; c0 += OC) {
+        const int nc = min(OC, o1 - c0);
+        if (c0 != o0) {  // rows longer than one chunk: synchronous load, gather and planes
+          g.sync();
+          for (int q = g.gl; q < nc; q += GT) rc[q] = __ldg(reinterpret_cast<const int4 *>(pd.xrec) + c0 + q);
+          g.sync();
+          gather(v, rc, nc, gp, ownb + ps * ostep * W);
+          cp_async_wait_all();
+          planes_of(rc, nc, gp, ownb + ps * ostep * W);
+          g.sync();
+        }
+        // stage B: per-byte signed counts, bias 128 (|count| <= kOcap keeps bytes apart)
+        uint32_t A0 = 0x80808080u, A1 = 0x80808080u, A2 = 0x80808080u;   // samples 0-3
+        uint32_t B0 = 0x80808080u, B1 = 0x80808080u, B2 = 0x80808080u;   // samples 4-7
+        const uint32_t *pw = gp + w;
+        for (int o = 0; o < nc; ++o, pw += 2 * W) {
+          const uint32_t sg = (rc[o].x & 1) ? 0xFFFFFFFFu : 1u;     // -1 or +1 as a multiplier
+          const uint32_t y0 = __byte_perm(pw[0], 0, bsel);
+          const uint32_t y1 = __byte_perm(pw[W], 0, bsel);
+          const uint32_t x0l = spread4(y0 & 15u), x0h = spread4(y0 >> 4);
+          const uint32_t x1l = spread4(y1 & 15u), x1h = spread4(y1 >> 4);
+          A0 += x0l * sg; A1 += x1l * sg; A2 += (x0l & x1l) * sg;
+          B0 += x0h * sg; B1 += x1h * sg; B2 += (x0h & x1h) * sg;
+          nsign += (int)sg;
+        }
+        const float4 d1a = __ldg(reinterpret_cast<const float4 *>(gdp + N)), d1b = __ldg(reinterpret_cast<const float4 *>(gdp + N + 4));
+        const float4 d2a = __ldg(reinterpret_cast<const float4 *>(gdp + 2 * N)), d2b = __ldg(reinterpret_cast<const float4 *>(gdp + 2 * N + 4));
+        const float4 d3a = __ldg(reinterpret_cast<const float4 *>(gdp + 3 * N)), d3b = __ldg(reinterpret_cast<const float4 *>(gdp + 3 * N + 4));
+        const float dd1[8] = {d1a.x, d1a.y, d1a.z, d1a.w, d1b.x, d1b.y, d1b.z, d1b.w};
+        const float dd2[8] = {d2a.x, d2a.y, d2a.z, d2a.w, d2b.x, d2b.y, d2b.z, d2b.w};
+        const float dd3[8] = {d3a.x, d3a.y, d3a.z, d3a.w, d3b.x, d3b.y, d3b.z, d3b.w};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const uint32_t qq = (uint32_t)(q & 3);
+          const float c0f = biased_byte(q < 4 ? A0 : B0, qq);
+          const float c1f = biased_byte(q < 4 ? A1 : B1, qq);
+          const float c2f = biased_byte(q < 4 ? A2 : B2, qq);
+          G[q] = fmaf(c0f, dd1[q], fmaf(c1f, dd2[q], fmaf(c2f, dd3[q], G[q])));
+        }
+      }
+      const float4 g0a = __ldg(reinterpret_cast<const float4 *>(gdp)), g0b = __ldg(reinterpret_cast<const float4 *>(gdp + 4));
+      const float gg0[8] = {g0a.x, g0a.y, g0a.z, g0a.w, g0b.x, g0b.y, g0b.z, g0b.w};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) G[q] = fmaf((float)nsign, gg0[q], G[q]);
+    }
+    // ---- z, m, v of this row
+    if (!mbar_wait_bounded(bar_z, k & 1, kWaitLimit)) { sd.hdr->err = kErrTimeout; return; }
+    if (frozen) {  // frozen instance: keep its model
+      if ((g.gl & 3) == 0) bdst[v * W + w] = bsrc[v * W + w];
     } else {
-      if (inst != cur_inst) {
-        cur_inst = inst;
-        const float *gsrc = sd.gamma + (size_t)inst * sd.lm1 * N;
-        float gm[4][4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          float4 x = (r < sd.lm1) ? *reinterpret_cast<const float4 *>(gsrc + (size_t)r * N + s0)
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-          gm[0][r] = x.x; gm[1][r] = x.y; gm[2][r] = x.z; gm[3][r] = x.w;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          gd[q][0] = gm[q][0];
-          gd[q][1] = gm[q][1] - gm[q][0];
-          gd[q][2] = gm[q][2] - gm[q][0];
-          gd[q][3] = (gm[q][3] - gm[q][2]) - (gm[q][1] - gm[q][0]);
-        }
+      const float4 za = *reinterpret_cast<const float4 *>(zmv + s0), zb = *reinterpret_cast<const float4 *>(zmv + s0 + 4);
+      const float zq[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+      float mq[8], vq[8];
+      if (mode == 0) {
+        const float4 ma = *reinterpret_cast<const float4 *>(zmv + N + s0), mb = *reinterpret_cast<const float4 *>(zmv + N + s0 + 4);
+        const float4 va = *reinterpret_cast<const float4 *>(zmv + 2 * N + s0), vb = *reinterpret_cast<const float4 *>(zmv + 2 * N + s0 + 4);
+        mq[0] = ma.x; mq[1] = ma.y; mq[2] = ma.z; mq[3] = ma.w; mq[4] = mb.x; mq[5] = mb.y; mq[6] = mb.z; mq[7] = mb.w;
+        vq[0] = va.x; vq[1] = va.y; vq[2] = va.z; vq[3] = va.w; vq[4] = vb.x; vq[5] = vb.y; vq[6] = vb.z; vq[7] = vb.w;
       }
-      const int32_t o0 = __ldg(pd.vptr + v), o1 = __ldg(pd.vptr + v + 1);
-      const uint32_t own_tw = __ldg(bsrc + v * W + tw);
-      float G[4] = {0.f, 0.f, 0.f, 0.f};
-      int nsign = 0;
-      const int4 *recs = strec[stage];
-      for (int32_t c0 = o0; c0 < o1; c0 += L.ocap) {
-        const int nc = min(L.ocap, o1 - c0);
-        if (c0 != o0) {  // rows longer than one chunk: plain cooperative load into the stage buffer
-          g.sync();
-          int4 *dst = strec[stage];
-          for (int q = g.gl; q < nc; q += GT) dst[q] = __ldg(reinterpret_cast<const int4 *>(pd.xrec) + c0 + q);
-          g.sync();
-        }
-        // stage A: bit planes of R for (occurrence, word)
-        for (int o = to; o < nc; o += ostep) {
-          const int4 rc = recs[o];
-          const uint32_t len = (uint32_t)rc.x >> 1;
-          const uint32_t a = own_tw ^ (0u - (uint32_t)(rc.x & 1));
-          const uint32_t bb = len > 1 ? (__ldg(bsrc + (size_t)(rc.y >> 1) * W + tw) ^ (0u - (uint32_t)(rc.y & 1))) : 0u;
-          const uint32_t cc = len > 2 ? (__ldg(bsrc + (size_t)(rc.z >> 1) * W + tw) ^ (0u - (uint32_t)(rc.z & 1))) : 0u;
-          planes[(o * 2) * W + tw] = a ^ bb ^ cc;
-          planes[(o * 2 + 1) * W + tw] = (a & bb) | (cc & (a ^ bb));
-        }
-        g.sync();
-        // stage B: byte-packed signed counts for this thread's 4 samples
-        uint32_t P0 = 0, P1 = 0, P01 = 0, N0 = 0, N1 = 0, N01 = 0;
-        for (int o = 0; o < nc; ++o) {
-          const uint32_t n0 = (planes[(o * 2) * W + w] >> sh) & 15u;
-          const uint32_t n1 = (planes[(o * 2 + 1) * W + w] >> sh) & 15u;
-          const uint32_t x0 = (n0 * 0x00204081u) & 0x01010101u;
-          const uint32_t x1 = (n1 * 0x00204081u) & 0x01010101u;
-          if (recs[o].x & 1) {
-            N0 += x0; N1 += x1; N01 += x0 & x1; --nsign;
-          } else {
-            P0 += x0; P1 += x1; P01 += x0 & x1; ++nsign;
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int sq = 8 * q;
-          const float c0f = (float)((int)((P0 >> sq) & 255u) - (int)((N0 >> sq) & 255u));
-          const float c1f = (float)((int)((P1 >> sq) & 255u) - (int)((N1 >> sq) & 255u));
-          const float c2f = (float)((int)((P01 >> sq) & 255u) - (int)((N01 >> sq) & 255u));
-          G[q] += c0f * gd[q][1] + c1f * gd[q][2] + c2f * gd[q][3];
-        }
-        g.sync();   // planes and the record buffer are reused by the next chunk
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) G[q] += (float)nsign * gd[q][0];
+      // z, m, v are in registers: the buffer can take the next row now
+      g.sync();
+      if (vn >= 0 && leader) issue_zmv(vn);
       // ---- chain rule through Eq. 5
-      const float *zr = stz[stage];
-      const float4 z4 = *reinterpret_cast<const float4 *>(zr + s0);
-      const float zq[4] = {z4.x, z4.y, z4.z, z4.w};
-      const float nu = sd.nu[v];
-      float gq[4];
+      float gq[8];
       if (hy.norm == TSAT_NORM_NONE) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) gq[q] = G[q];
+        for (int q = 0; q < 8; ++q) gq[q] = G[q];
       } else {
-        const float dot = g.sum((G[0] * zq[0] + G[1] * zq[1]) + (G[2] * zq[2] + G[3] * zq[3]), red);
+        float part = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) part = fmaf(G[q], zq[q], part);
+        const float dot = g.sum1(part, red, 0);
         const float rnu = __frcp_rn(nu);
         const float c2 = dot * rnu * rnu * (1.0f / (float)N);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
           const float dmu = (hy.norm == TSAT_NORM_ABSMEAN) ? (float)((zq[q] > 0.f) - (zq[q] < 0.f)) : 1.0f;
           gq[q] = G[q] * rnu - c2 * dmu;
         }
@@ -710,34 +848,329 @@ __global__ void __launch_bounds__(kBlock, 4) k_update2(ProbDev pd, StateDev sd, 
       const size_t off = (size_t)v * N + s0;
       if (mode == 1) {
         *reinterpret_cast<float4 *>(grad + off) = make_float4(dL * gq[0], dL * gq[1], dL * gq[2], dL * gq[3]);
+        *reinterpret_cast<float4 *>(grad + off + 4) = make_float4(dL * gq[4], dL * gq[5], dL * gq[6], dL * gq[7]);
       } else {
-        const float4 m4 = *reinterpret_cast<const float4 *>(zr + N + s0);
-        const float4 v4 = *reinterpret_cast<const float4 *>(zr + 2 * N + s0);
-        float mq[4] = {m4.x, m4.y, m4.z, m4.w}, vq[4] = {v4.x, v4.y, v4.z, v4.w}, zn[4];
+        float zn[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
           const float gs = gq[q];
-          mq[q] = b1 * mq[q] + (1.0f - b1) * gs;
-          vq[q] = b2 * vq[q] + (1.0f - b2) * (gs * gs);
-          const float denom = sqrtf(vq[q]) * sp.inv_sqrt_bc2 + hy.eps;
+          mq[q] = b1 * mq[q] + omb1 * gs;
+          vq[q] = b2 * vq[q] + omb2 * (gs * gs);
+          const float sq = vq[q] > 0.f ? vq[q] * rsqrtf(vq[q]) : 0.f;
+          const float denom = sq * sp.inv_sqrt_bc2 + hy.eps;
           zn[q] = zq[q] * sp.decay - sp.step_size * __fdividef(mq[q], denom);
         }
         st_cs(sd.z + off, make_float4(zn[0], zn[1], zn[2], zn[3]));
+        st_cs(sd.z + off + 4, make_float4(zn[4], zn[5], zn[6], zn[7]));
         st_cs(sd.m + off, make_float4(mq[0], mq[1], mq[2], mq[3]));
+        st_cs(sd.m + off + 4, make_float4(mq[4], mq[5], mq[6], mq[7]));
         st_cs(sd.v + off, make_float4(vq[0], vq[1], vq[2], vq[3]));
-        row_binarize_store(sd, hy, g, red, v, zn, tcur + 1, bdst);
+        st_cs(sd.v + off + 4, make_float4(vq[4], vq[5], vq[6], vq[7]));
+        // ---- new normaliser and Eq. 2 / Philox for step t+1
+        float nun = 1.0f;
+        if (hy.norm != TSAT_NORM_NONE) {
+          float ps_ = 0.f;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) ps_ += (hy.norm == TSAT_NORM_ABSMEAN) ? fabsf(zn[q]) : zn[q];
+          nun = guard_nu(g.sum1(ps_, red, 1) / (float)N);
+        }
+        const float rnn = __frcp_rn(nun);
+        uint32_t byte = 0;
+        if (hy.binarize == TSAT_BIN_PHILOX) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)(s0 / 4 + h), (uint32_t)v, (uint32_t)(tcur + 1), kTagBin),
+                                          hy.key0, hy.key1);
+            const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              byte |= binarize_one(__fmul_rn(zn[4 * h + q], rnn), TSAT_BIN_PHILOX, hy.bin_c, rw[q]) << (4 * h + q);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) byte |= (__fmul_rn(zn[q], rnn) > 0.0f ? 1u : 0u) << q;
+        }
+        uint32_t val = byte << sh;
+        const unsigned gm = g.mask();
+        val |= __shfl_xor_sync(gm, val, 1);
+        val |= __shfl_xor_sync(gm, val, 2);
+        if ((g.gl & 3) == 0) bdst[v * W + w] = val;
+        if (g.gl == 0) sd.nu[v] = nun;
       }
     }
-    g.sync();   // the stage buffers of this row are free for the prefetch two rows ahead
+    // ---- planes of row k+1 from the words this thread gathered itself
+    cp_async_wait_all();
+    if (vn >= 0) planes_of(recb + rs1 * OC, nc1, gpb + (ps ^ 1) * OC * 2 * W, ownb + (ps ^ 1) * ostep * W);
+    if (frozen) {  // frozen rows skip the update: refill the z/m/v buffer here
+      g.sync();
+      if (vn >= 0 && leader) issue_zmv(vn);
+    }
+    g.sync();   // planes of row k+1 complete; reduction slots free
     v = vn;
+    vn = vnn;
     ++k;
   }
 }
 
 int update2_smem_bytes(int N) {
-  const U2Layout L = u2_layout(N);
-  return (kBlock / (N >> 2)) * L.group_bytes;
+  const U3Layout L = u3_layout(N);
+  return L.RPB * L.group_bytes;
 }
+int update2_threads(int N) { return u3_layout(N).threads; }
+
+// ------------------------------------------------------------------ fused update, word per lane
+// Clause length <= 3 (R in 0..3, two bit planes).  Counting phase: a lane owns
+// one 32-sample word of one variable row (W = N/32 lanes per row, 32/W rows
+// per warp), so
+//   * the occurrence records of a row are loaded by its W lanes in parallel
+//     and broadcast by shuffles; the other literals' words are gathered
+//     coalesced (W consecutive lanes read W consecutive words) and the R bit
+//     planes stay in registers;
+//   * the lane counts, byte-packed with bias 128 for its 32 samples, the
+//     signed occurrences whose R has plane-0 bit, plane-1 bit, both bits set;
+//     gamma[R] = g0 + b0 d1 + b1 d2 + b0 b1 d3 turns the STE sum into
+//     G = (n+ - n-) g0 + C0 d1 + C1 d2 + C01 d3 (exact rewrite).
+// Sample phase: G is transposed through shared memory so that each lane owns
+// 4 consecutive samples per pass (coalesced 16-byte accesses to z, m, v); row
+// reductions (Eq. 5 dot product, new normaliser) are shuffles across the row's
+// lanes; the lane of each word assembles and writes the new bits word.
+constexpr int kCntChunk = 127;   // occurrences per byte-counter chunk (|count| <= 127)
+constexpr int kGStride = 33;     // padded row of the [32 bits][32 lanes] transposition buffer
+
+__device__ __forceinline__ float seg_sum(float x, int W) {
+  for (int o = 1; o < W; o <<= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+  return x;
+}
+
+__global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, Hyper hy, int mode, const float *zin,
+                                                       float *grad, float dL) {
+  extern __shared__ __align__(16) float sm3[];
+  const StateHdr *hdr = sd.hdr;
+  if (mode == 0 && hdr->all_done) return;
+  const int N = sd.N, W = sd.W, RW = 32 / W;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rsub = lane / W, w = lane % W, rbase = rsub * W;   // row group: lanes rbase .. rbase + W - 1
+  float *gbuf = sm3 + warp * (32 * kGStride);                   // [32 bits][33]: (bit b, lane) -> b*33 + lane
+  uint32_t *cbuf = reinterpret_cast<uint32_t *>(sm3 + kWarps * 32 * kGStride) + warp * 768;  // [24][32]
+  float *tab = sm3 + kWarps * (32 * kGStride + 768);            // [4][32 bits][W words] delta table (one instance)
+  const bool one_inst = pd.n_inst == 1;
+  if (one_inst) {
+    for (int k = threadIdx.x; k < 4 * N; k += blockDim.x) {
+      const int kk = k / N, smp = k % N;
+      tab[(kk * 32 + (smp & 31)) * W + (smp >> 5)] = sd.gdelta[(size_t)kk * N + smp];
+    }
+  }
+  __syncthreads();
+  StepParams sp;
+  if (mode == 0) sp = *sd.sp;
+  const int64_t tcur = (mode == 0) ? sp.t : hdr->t;
+  const uint32_t *bsrc = cur_bits(sd, tcur);
+  uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
+  const float *zsrc = (mode == 0) ? sd.z : zin;
+  const int4 *xrec4 = reinterpret_cast<const int4 *>(pd.xrec);
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  // sample-phase layout: pass k (0..7) covers samples 4Wk .. 4W(k+1)-1 of the row,
+  // lane w of the row holds 4Wk + 4w + e, e = 0..3
+  for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * RW; base < pd.V; base += nwarps * RW) {
+    __syncwarp();   // the previous row's readers of gbuf / cbuf are done
+    const int64_t v = base + rsub;
+    const bool valid = v < pd.V;
+    int inst = 0;
+    bool frozen = false;
+    if (valid) {
+      inst = __ldg(pd.var_inst + v);
+      frozen = (mode == 0) && sd.inst[inst].found;
+    }
+    const bool act = valid && !frozen;
+    const float *gdp = sd.gdelta + (size_t)inst * 4 * N;
+    // ---- counting phase (lane = word w of row v)
+    int nsign = 0;
+    int32_t o0 = 0, o1 = 0;
+    if (act) {
+      o0 = __ldg(pd.vptr + v);
+      o1 = __ldg(pd.vptr + v + 1);
+    }
+    const uint32_t own = act ? __ldg(bsrc + v * W + w) : 0u;
+    bool first = true;
+    // every lane of the warp runs the same number of record rounds (shuffles)
+    int32_t deg = o1 - o0, maxdeg = deg;
+    for (int o = 16; o > 0; o >>= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xFFFFFFFFu, maxdeg, o));
+    for (int32_t c0 = 0; c0 < maxdeg || first; c0 += kCntChunk) {
+      const int32_t cn = act ? min(deg - c0, kCntChunk) : 0;   // this row's occurrences in the chunk
+      const int32_t cmax = min(maxdeg - c0, kCntChunk);
+      uint32_t cnt[4][6];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) cnt[q][j] = 0x80808080u;
+      for (int32_t r0 = 0; r0 < cmax; r0 += W) {
+        // W records of this row, one per lane, then broadcast within the row group
+        int4 myrec = make_int4(0, 0, 0, 0);
+        if (r0 + w < cn) myrec = __ldg(xrec4 + o0 + c0 + r0 + w);
+        const int nr = min(W, cmax - r0);
+#pragma unroll 4
+        for (int i = 0; i < nr; ++i) {
+          int4 rc;
+          rc.x = __shfl_sync(0xFFFFFFFFu, myrec.x, rbase + i);
+          rc.y = __shfl_sync(0xFFFFFFFFu, myrec.y, rbase + i);
+          rc.z = __shfl_sync(0xFFFFFFFFu, myrec.z, rbase + i);
+          if (r0 + i >= cn) continue;                 // this row has no occurrence here
+          const uint32_t len = (uint32_t)rc.x >> 1;
+          const uint32_t a = own ^ (0u - (uint32_t)(rc.x & 1));
+          const uint32_t bb = len > 1 ? (__ldg(bsrc + (size_t)(rc.y >> 1) * W + w) ^ (0u - (uint32_t)(rc.y & 1))) : 0u;
+          const uint32_t cc = len > 2 ? (__ldg(bsrc + (size_t)(rc.z >> 1) * W + w) ^ (0u - (uint32_t)(rc.z & 1))) : 0u;
+          const uint32_t p0 = a ^ bb ^ cc, p1 = (a & bb) | (cc & (a ^ bb));
+          const uint32_t sg = (rc.x & 1) ? 0xFFFFFFFFu : 1u;
+          nsign += (int)sg;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t y0 = __byte_perm(p0, 0, 0x4440u | q), y1 = __byte_perm(p1, 0, 0x4440u | q);
+            const uint32_t x0l = spread4(y0 & 15u), x0h = spread4(y0 >> 4);
+            const uint32_t x1l = spread4(y1 & 15u), x1h = spread4(y1 >> 4);
+            cnt[q][0] += x0l * sg; cnt[q][1] += x1l * sg; cnt[q][2] += (x0l & x1l) * sg;
+            cnt[q][3] += x0h * sg; cnt[q][4] += x1h * sg; cnt[q][5] += (x0h & x1h) * sg;
+          }
+        }
+      }
+      // fold this chunk into G (gbuf, bit-major): the counts pass through shared
+      // memory so the 24 counter registers die here; sample b = 8q + j of word w
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) cbuf[(q * 6 + j) * 32 + lane] = cnt[q][j];
+      if (act) {
+#pragma unroll 2
+        for (int b = 0; b < 32; ++b) {
+          const int q = b >> 3, j = b & 7, h = j < 4 ? 0 : 3;
+          const uint32_t bq = (uint32_t)(j & 3);
+          const float c0f = biased_byte(cbuf[(q * 6 + h + 0) * 32 + lane], bq);
+          const float c1f = biased_byte(cbuf[(q * 6 + h + 1) * 32 + lane], bq);
+          const float c2f = biased_byte(cbuf[(q * 6 + h + 2) * 32 + lane], bq);
+          float d1, d2, d3;
+          if (one_inst) {
+            d1 = tab[(1 * 32 + b) * W + w]; d2 = tab[(2 * 32 + b) * W + w]; d3 = tab[(3 * 32 + b) * W + w];
+          } else {
+            const int smp = 32 * w + b;
+            d1 = __ldg(gdp + N + smp); d2 = __ldg(gdp + 2 * N + smp); d3 = __ldg(gdp + 3 * N + smp);
+          }
+          const float add = fmaf(c0f, d1, fmaf(c1f, d2, c2f * d3));
+          gbuf[b * kGStride + lane] = first ? add : gbuf[b * kGStride + lane] + add;
+        }
+      }
+      first = false;
+    }
+    if (act) {
+#pragma unroll 4
+      for (int b = 0; b < 32; ++b) {
+        const float g0 = one_inst ? tab[b * W + w] : __ldg(gdp + 32 * w + b);
+        gbuf[b * kGStride + lane] = fmaf((float)nsign, g0, gbuf[b * kGStride + lane]);
+      }
+    }
+    __syncwarp();
+    // ---- sample phase: lane w holds samples s = 4Wk + 4w + e of row v
+    // G of sample s lives at gbuf[(s % 32) * 33 + rbase + s / 32]
+    const float nu = act ? sd.nu[v] : 1.0f;
+    const float rnu = __frcp_rn(nu);
+    const size_t rowoff = (size_t)v * N;
+    float part = 0.f;
+    if (act && hy.norm != TSAT_NORM_NONE) {
+#pragma unroll 2
+      for (int k = 0; k < 8; ++k) {
+        const int s = 4 * W * k + 4 * w;
+        const float4 z4 = __ldg(reinterpret_cast<const float4 *>(zsrc + rowoff + s));
+        const float *gp = gbuf + (s & 31) * kGStride + rbase + (s >> 5);
+        part = fmaf(gp[0], z4.x, part);
+        part = fmaf(gp[kGStride], z4.y, part);
+        part = fmaf(gp[2 * kGStride], z4.z, part);
+        part = fmaf(gp[3 * kGStride], z4.w, part);
+      }
+    }
+    const float dot = seg_sum(part, W);
+    const float c2 = dot * rnu * rnu * (1.0f / (float)N);
+    float psum = 0.f;
+    if (act) {
+#pragma unroll 2
+      for (int k = 0; k < 8; ++k) {
+        const int s = 4 * W * k + 4 * w;
+        const size_t off = rowoff + s;
+        float *gp = gbuf + (s & 31) * kGStride + rbase + (s >> 5);
+        const float4 z4 = __ldg(reinterpret_cast<const float4 *>(zsrc + off));
+        const float zq[4] = {z4.x, z4.y, z4.z, z4.w};
+        float gq[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float G = gp[e * kGStride];
+          if (hy.norm == TSAT_NORM_NONE) {
+            gq[e] = G;
+          } else {
+            const float dmu = (hy.norm == TSAT_NORM_ABSMEAN) ? (float)((zq[e] > 0.f) - (zq[e] < 0.f)) : 1.0f;
+            gq[e] = G * rnu - c2 * dmu;
+          }
+        }
+        if (mode == 1) {
+          *reinterpret_cast<float4 *>(grad + off) = make_float4(dL * gq[0], dL * gq[1], dL * gq[2], dL * gq[3]);
+          continue;
+        }
+        const float4 m4 = ld_cs(sd.m + off), v4 = ld_cs(sd.v + off);
+        float mq[4] = {m4.x, m4.y, m4.z, m4.w}, vq[4] = {v4.x, v4.y, v4.z, v4.w}, zn[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          mq[e] = hy.beta1 * mq[e] + (1.0f - hy.beta1) * gq[e];
+          vq[e] = hy.beta2 * vq[e] + (1.0f - hy.beta2) * (gq[e] * gq[e]);
+          const float sq = vq[e] > 0.f ? vq[e] * rsqrtf(vq[e]) : 0.f;
+          const float denom = sq * sp.inv_sqrt_bc2 + hy.eps;
+          zn[e] = zq[e] * sp.decay - sp.step_size * __fdividef(mq[e], denom);
+          gp[e * kGStride] = zn[e];
+          psum += (hy.norm == TSAT_NORM_ABSMEAN) ? fabsf(zn[e]) : zn[e];
+        }
+        st_cs(sd.z + off, make_float4(zn[0], zn[1], zn[2], zn[3]));
+        st_cs(sd.m + off, make_float4(mq[0], mq[1], mq[2], mq[3]));
+        st_cs(sd.v + off, make_float4(vq[0], vq[1], vq[2], vq[3]));
+      }
+    }
+    if (mode == 1) continue;
+    const float tot = seg_sum(psum, W);
+    __syncwarp();
+    // ---- Eq. 2 / Philox bits of step t+1: lane w assembles word w (bits b of gbuf)
+    if (valid && frozen) bdst[v * W + w] = bsrc[v * W + w];
+    if (act) {
+      const float nun = (hy.norm == TSAT_NORM_NONE) ? 1.0f : guard_nu(tot / (float)N);
+      const float rnn = __frcp_rn(nun);
+      uint32_t word = 0;
+      if (hy.binarize == TSAT_BIN_PHILOX) {
+#pragma unroll 2
+        for (int h = 0; h < 8; ++h) {
+          const uint4 r = philox4x32_10(make_uint4((uint32_t)(8 * w + h), (uint32_t)v, (uint32_t)(tcur + 1), kTagBin),
+                                        hy.key0, hy.key1);
+          const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            word |= binarize_one(__fmul_rn(gbuf[(4 * h + e) * kGStride + lane], rnn), TSAT_BIN_PHILOX, hy.bin_c, rw[e])
+                    << (4 * h + e);
+        }
+      } else {
+#pragma unroll 8
+        for (int b = 0; b < 32; ++b) word |= (__fmul_rn(gbuf[b * kGStride + lane], rnn) > 0.0f ? 1u : 0u) << b;
+      }
+      bdst[v * W + w] = word;
+      if (w == 0) sd.nu[v] = nun;
+    }
+    __syncwarp();
+  }
+}
+
+int update3_smem_bytes(int N);
+// Resident blocks per SM of the update kernel this problem uses (occupancy API).
+int update_blocks_per_sm(const ProbDev &pd, const StateDev &sd) {
+  int nb = 0;
+  if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_fixed4)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_update3, kBlock, update3_smem_bytes(sd.N));
+  else
+    nb = 3;
+  return nb > 0 ? nb : 1;
+}
+
+int update3_smem_bytes(int N) { return (kWarps * (32 * kGStride + 768) + 4 * N) * (int)sizeof(float); }
 
 // ------------------------------------------------------------------ exact check (Sec. III-A)
 // unsat_i = #clauses whose literal words OR to 0 at bit i.  Same warp
@@ -864,6 +1297,7 @@ void prepare_update_attrs(int lmax) {
   const int P = planes_for(lmax);
   const int bytes = 160 * 1024;
   cudaFuncSetAttribute(k_update2, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_update3, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   cudaFuncSetAttribute(k_update<1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   switch (P) {
     case 1: cudaFuncSetAttribute(k_update<1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); break;
@@ -878,7 +1312,8 @@ cudaError_t launch_update(const ProbDev &pd, const StateDev &sd, const Hyper &hy
                           float *grad, float dL, int grid, int rpi, cudaStream_t st) {
   const int P = planes_for(pd.lmax);
   if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_fixed4) {
-    k_update2<<<grid, kBlock, update2_smem_bytes(sd.N), st>>>(pd, sd, hy, mode, zin, grad, dL, rpi);
+    (void)rpi;
+    k_update3<<<grid, kBlock, update3_smem_bytes(sd.N), st>>>(pd, sd, hy, mode, zin, grad, dL);
     return cudaGetLastError();
   }
   if (sd.layer == TSAT_LAYER_RELAXED) return upd_launch<1, true, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);

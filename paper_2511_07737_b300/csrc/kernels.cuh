@@ -41,6 +41,7 @@ cudaError_t best_select(const ProbDev &pd, const StateDev &sd, int inst, int n_v
                         int32_t *small, int32_t *part_var, uint8_t *part_val, uint32_t *outbits,
                         cudaStream_t st);
 void prepare_update_attrs(int lmax);
+int update_blocks_per_sm(const ProbDev &pd, const StateDev &sd);
 
 int update_smem_bytes(int N, int lm1, bool greg);
 
