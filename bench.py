@@ -194,7 +194,9 @@ def reference_arm(args, w, rank, world):
     import oracle
     oracle.build()
     inst = gen(w, 0)
-    cols = min(ORACLE_COLS, w["N"])
+    # one sample column per host thread (the oracle parallelises over samples),
+    # so that each step is a bounded sample and K + W steps take minutes
+    cols = min(ORACLE_COLS, w["N"], max(1, oracle.num_threads()))
     oracle_run(inst, cols, max(1, args.warmup))            # warm-up (untimed)
     r = oracle_run(inst, cols, args.steps)
     val = r["evals"] / r["seconds"]

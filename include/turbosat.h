@@ -82,7 +82,9 @@ typedef struct tsat_hparams {
   float lr_floor;         /* lower bound, 1e-15 (Sec. IV-A "final learning rate") */
   int32_t decay_period;   /* iterations per decay, 30 (Sec. IV-A) */
   int32_t restart_period; /* iterations per restart, 360 (Sec. IV-A) */
-  float beta1, beta2, eps, weight_decay; /* AdamW; PyTorch defaults 0.9, 0.999, 1e-8, 0.01 */
+  double beta1, beta2;    /* AdamW moment decays (PyTorch defaults 0.9, 0.999); 1 - beta and the bias
+                             corrections are formed in double, as PyTorch does */
+  float eps, weight_decay; /* AdamW; PyTorch defaults 1e-8, 0.01 */
   int32_t norm;           /* TSAT_NORM_* (default TSAT_NORM_SIGNED_MEAN) */
   int32_t binarize;       /* TSAT_BIN_* (default TSAT_BIN_DET) */
   float bin_temp;         /* T of the Philox rule, c = 0.25 / T (default 1) */

@@ -62,8 +62,10 @@ static StatePlan plan_state(const tsat_problem *p, int32_t N, int32_t layer, int
 static Hyper make_hyper(const tsat_hparams &hp, int stop) {
   Hyper h{};
   h.tau = hp.tau;
-  h.beta1 = hp.beta1;
-  h.beta2 = hp.beta2;
+  h.beta1 = (float)hp.beta1;
+  h.beta2 = (float)hp.beta2;
+  h.omb1 = (float)(1.0 - hp.beta1);
+  h.omb2 = (float)(1.0 - hp.beta2);
   h.eps = hp.eps;
   h.bin_c = 0.25f / hp.bin_temp;
   h.norm = hp.norm;
@@ -90,7 +92,7 @@ static LrSched make_sched(const tsat_hparams &hp) {
 static int check_hp(const tsat_hparams *hp) {
   if (!hp) { set_error("hparams is NULL"); return TSAT_EINVAL; }
   if (!(hp->tau > 0.f) || hp->norm < 0 || hp->norm > 2 || hp->binarize < 0 || hp->binarize > 1 ||
-      !(hp->bin_temp > 0.f) || !(hp->beta1 >= 0.f && hp->beta1 < 1.f) || !(hp->beta2 >= 0.f && hp->beta2 < 1.f)) {
+      !(hp->bin_temp > 0.f) || !(hp->beta1 >= 0.0 && hp->beta1 < 1.0) || !(hp->beta2 >= 0.0 && hp->beta2 < 1.0)) {
     set_error("hparams out of range");
     return TSAT_EINVAL;
   }

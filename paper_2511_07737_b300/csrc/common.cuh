@@ -81,6 +81,7 @@ struct StateDev {
 // Hyper-parameters in the form the kernels use.
 struct Hyper {
   float tau, beta1, beta2, eps;
+  float omb1, omb2;            // 1 - beta1, 1 - beta2 formed in double on the host
   float bin_c;                 // 0.25 / T
   int32_t norm, binarize;
   uint32_t key0, key1;

@@ -289,8 +289,8 @@ __device__ void gamma_tail(const ProbDev &pd, const StateDev &sd, const Hyper &h
     const int64_t kdec = ls.period > 0 ? tt / ls.period : 0;
     double lr = (double)ls.lr0 * pow((double)ls.factor, (double)kdec);
     if (lr < (double)ls.floor) lr = ls.floor;
-    const double bc1 = 1.0 - pow((double)ls.beta1, (double)(t + 1));
-    const double bc2 = 1.0 - pow((double)ls.beta2, (double)(t + 1));
+    const double bc1 = 1.0 - pow(ls.beta1, (double)(t + 1));
+    const double bc2 = 1.0 - pow(ls.beta2, (double)(t + 1));
     StepParams sp;
     sp.t = t;
     sp.src = (int32_t)(t & 1);
@@ -518,8 +518,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
         const float gs = gq[s];
-        mq[s] = b1 * mq[s] + (1.0f - b1) * gs;
-        vq[s] = b2 * vq[s] + (1.0f - b2) * (gs * gs);
+        mq[s] = b1 * mq[s] + hy.omb1 * gs;
+        vq[s] = b2 * vq[s] + hy.omb2 * (gs * gs);
         const float denom = sqrtf(vq[s]) * sp.inv_sqrt_bc2 + hy.eps;
         zn[s] = zq[s] * sp.decay - sp.step_size * (mq[s] / denom);
       }
@@ -661,7 +661,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_update2(ProbDev pd, StateDev sd, 
   const int64_t tcur = (mode == 0) ? sp.t : hdr->t;
   const uint32_t *bsrc = cur_bits(sd, tcur);
   uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
-  const float b1 = hy.beta1, b2 = hy.beta2, omb1 = 1.0f - hy.beta1, omb2 = 1.0f - hy.beta2;
+  const float b1 = hy.beta1, b2 = hy.beta2, omb1 = hy.omb1, omb2 = hy.omb2;
   const float *zsrc = (mode == 0) ? sd.z : zin;
   const int s0 = g.gl * 8, w = s0 >> 5, sh = s0 & 31;
   const uint32_t bsel = 0x4440u | (uint32_t)(sh >> 3);   // byte sh/8 of a word -> low byte
@@ -1115,8 +1115,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
         float mq[4] = {m4.x, m4.y, m4.z, m4.w}, vq[4] = {v4.x, v4.y, v4.z, v4.w}, zn[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          mq[e] = hy.beta1 * mq[e] + (1.0f - hy.beta1) * gq[e];
-          vq[e] = hy.beta2 * vq[e] + (1.0f - hy.beta2) * (gq[e] * gq[e]);
+          mq[e] = hy.beta1 * mq[e] + (hy.omb1) * gq[e];
+          vq[e] = hy.beta2 * vq[e] + (hy.omb2) * (gq[e] * gq[e]);
           const float sq = vq[e] > 0.f ? vq[e] * rsqrtf(vq[e]) : 0.f;
           const float denom = sq * sp.inv_sqrt_bc2 + hy.eps;
           zn[e] = zq[e] * sp.decay - sp.step_size * __fdividef(mq[e], denom);

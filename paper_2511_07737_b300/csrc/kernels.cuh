@@ -7,7 +7,7 @@ namespace tsat {
 struct LrSched {
   float lr0, factor, floor, wd;
   int32_t period, restart;
-  float beta1, beta2;
+  double beta1, beta2;
 };
 
 // launch helpers (return cudaGetLastError of the launch)

@@ -36,7 +36,7 @@ class TsatError(RuntimeError):
 class tsat_hparams(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("lr0", ctypes.c_float), ("lr_factor", ctypes.c_float),
                 ("lr_floor", ctypes.c_float), ("decay_period", ctypes.c_int32),
-                ("restart_period", ctypes.c_int32), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("restart_period", ctypes.c_int32), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("eps", ctypes.c_float), ("weight_decay", ctypes.c_float), ("norm", ctypes.c_int32),
                 ("binarize", ctypes.c_int32), ("bin_temp", ctypes.c_float), ("layer", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]
