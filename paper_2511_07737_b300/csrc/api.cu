@@ -153,8 +153,8 @@ void tsat_hparams_default(tsat_hparams *hp) {
   hp->lr_floor = 1e-15f;
   hp->decay_period = 30;
   hp->restart_period = 360;
-  hp->beta1 = 0.9f;
-  hp->beta2 = 0.999f;
+  hp->beta1 = 0.9;
+  hp->beta2 = 0.999;
   hp->eps = 1e-8f;
   hp->weight_decay = 0.01f;
   hp->norm = TSAT_NORM_SIGNED_MEAN;
