@@ -187,6 +187,25 @@ int tsat_profile_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, fl
 int tsat_evaluate(tsat_state *s, const tsat_hparams *hp, int32_t *d_unsat, uint32_t *d_satmask,
                   float *d_loss, cudaStream_t stream);
 
+/* Evaluation without any device allocation.  The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc (code running inside a
+ * memory pool it does not own, or a process whose device memory another
+ * runtime reserved up front, where a late allocation could fail or stall).
+ * Same results as tsat_evaluate, but for a caller-supplied bit matrix d_bits
+ * (uint32 [n_vars][n_samples/32], bit i%32 of word i/32 = sample i's value)
+ * instead of a state: d_unsat int32 [n_inst][N] unsatisfied-clause counts,
+ * d_satmask uint32 [n_inst][N/32], d_loss (nullable) float [n_inst] with
+ * L = -sum_i S_i (Eq. 3, Eq. 4 with temperature tau).  The temporaries live
+ * in one fixed 4 MiB array inside the library's device image (each GPU that
+ * loads the library holds it until the process exits); a problem needs
+ * n_inst * N * (lmax + 3) + 64 ints of it, and larger requests fail with
+ * TSAT_ERANGE.  The first call on a device looks up that array's device
+ * address (make that first call before any stream capture).  Every call
+ * shares the array, so calls that overlap on the GPU (different streams, or
+ * different problems at once) race; serialise them.  Async on `stream`. */
+int tsat_evaluate_bits_noalloc(const tsat_problem *p, const uint32_t *d_bits, int32_t n_samples, float tau,
+                               int32_t *d_unsat, uint32_t *d_satmask, float *d_loss, cudaStream_t stream);
+
 /* Hand-off of instance `inst` (Sec. IV-B).  Chooses the sample with unsat = 0
  * (lowest index) or else the fewest unsatisfied clauses (lowest index on
  * ties), computes the STE gradient of its current bits, and returns the k

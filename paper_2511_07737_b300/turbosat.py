@@ -92,6 +92,7 @@ def lib():
             "tsat_get_tuning": (ctypes.c_int, [P, P]),
             "tsat_set_tuning": (ctypes.c_int, [P, P]),
             "tsat_launches_per_step": (i32, [P]),
+            "tsat_evaluate_bits_noalloc": (ctypes.c_int, [P, P, i32, f32, P, P, P, P]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -217,6 +218,13 @@ def tsat_profile_step(s, hp: tsat_hparams, n_steps: int) -> list:
 def tsat_evaluate(s, hp, unsat: torch.Tensor, satmask: torch.Tensor, loss: torch.Tensor | None = None, stream=None):
     _ck(lib().tsat_evaluate(s, ctypes.byref(hp), _ptr(unsat), _ptr(satmask), _ptr(loss), _stream(stream)),
         "tsat_evaluate")
+
+
+def tsat_evaluate_bits_noalloc(h, bits: torch.Tensor, n_samples: int, tau: float, unsat: torch.Tensor,
+                               satmask: torch.Tensor, loss: torch.Tensor | None = None, stream=None):
+    """Evaluation of a caller-supplied bit matrix with no device allocation (see the C header)."""
+    _ck(lib().tsat_evaluate_bits_noalloc(h, _ptr(bits), int(n_samples), float(tau), _ptr(unsat), _ptr(satmask),
+                                         _ptr(loss), _stream(stream)), "tsat_evaluate_bits_noalloc")
 
 
 def tsat_partial_k(n_vars: int) -> int:
