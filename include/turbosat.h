@@ -253,6 +253,30 @@ int tsat_autotune(tsat_state *s, const tsat_hparams *hp, cudaStream_t stream, in
 int tsat_get_tuning(const tsat_state *s, int32_t h_tuning[4]);
 int tsat_set_tuning(tsat_state *s, const int32_t h_tuning[4]);
 
+/* ---- learned proposer (a message-passing network proposing initial logits) ----
+ * The paper cites learned SAT models only as related work (Sec. II); this is
+ * an addition.  A 3-layer message-passing network (hidden 64, BF16 weights,
+ * FP32 accumulation) on the literal-clause bipartite graph of a loaded
+ * problem maps every variable to a logit; tsat_init(d_logits, scale) turns
+ * the logits into initial z (random init stays the fallback) and the exact
+ * check judges every proposal.  Parameters are a flat float array of
+ * tsat_mpnn_param_count() entries (FP32 master copy, owned by the caller).
+ * Workspace: tsat_mpnn_workspace_bytes (activations for the backward pass).
+ * tsat_mpnn_loss_grad: logits (float [V]), mean binary cross-entropy of the
+ * logits against d_targets (uint8 [V], a satisfying assignment per instance)
+ * summed over instances into d_loss[0], and its gradient d_grad (float
+ * [param_count]).  tsat_mpnn_adam: one Adam step (0.9, 0.999, 1e-8) with the
+ * 1-based step count.  All async on `stream`. */
+int32_t tsat_mpnn_param_count(void);
+int tsat_mpnn_workspace_bytes(const tsat_problem *p, size_t *bytes);
+int tsat_mpnn_init(float *d_params, uint64_t seed, cudaStream_t stream);
+int tsat_mpnn_forward(const tsat_problem *p, const float *d_params, void *d_ws, size_t ws_bytes, float *d_logits,
+                      cudaStream_t stream);
+int tsat_mpnn_loss_grad(const tsat_problem *p, const float *d_params, void *d_ws, size_t ws_bytes,
+                        const uint8_t *d_targets, float *d_logits, float *d_loss, float *d_grad, cudaStream_t stream);
+int tsat_mpnn_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int64_t step, float lr,
+                   cudaStream_t stream);
+
 /* Number of kernel launches one step issues (for launch accounting). */
 int32_t tsat_launches_per_step(const tsat_state *s);
 

@@ -1,0 +1,534 @@
+// mpnn.cu -- learned proposer of initial variable logits: a 3-layer message-
+// passing network on the literal-clause bipartite graph of a loaded problem
+// (the problem's clause-major CSR and variable-major occurrence index), with
+// BF16 weights and FP32 accumulation, forward and hand-written backward.
+//
+// Network (hidden H = 64, literal l, its negation l^1, clause c):
+//   f_l   = [1, log(1 + deg l), log(1 + deg l^1)]
+//   h0_l  = relu(W0 f_l + b0)
+//   for t = 1..3:
+//     m_c  = mean_{l in c} h_l                    (clause-major gather)
+//     e_c  = relu(Wc_t m_c + bc_t)
+//     a_l  = mean_{c owns l} e_c                  (variable-major gather)
+//     h_l  = relu(Wl_t [h_l ; a_l ; h_{l^1}] + bl_t)
+//   logit_v = wo [h_{2v} ; h_{2v+1}] + bo
+// Every gradient of a gather is the opposite gather (no atomics); weight
+// gradients reduce per-block partials in a fixed order.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace tsat {
+
+constexpr int kH = 64;
+constexpr int kLayers = 3;
+constexpr int kFeat = 3;
+// parameter layout (floats)
+constexpr int kOffW0 = 0;
+constexpr int kOffB0 = kOffW0 + kH * kFeat;
+constexpr int kOffLayer = kOffB0 + kH;
+constexpr int kLayerSize = kH * kH + kH + kH * 3 * kH + kH;   // Wc, bc, Wl, bl
+constexpr int kOffOut = kOffLayer + kLayers * kLayerSize;
+constexpr int kNParams = kOffOut + 2 * kH + 1;
+__host__ __device__ constexpr int off_wc(int t) { return kOffLayer + t * kLayerSize; }
+__host__ __device__ constexpr int off_bc(int t) { return off_wc(t) + kH * kH; }
+__host__ __device__ constexpr int off_wl(int t) { return off_bc(t) + kH; }
+__host__ __device__ constexpr int off_bl(int t) { return off_wl(t) + kH * 3 * kH; }
+
+struct MpWs {  // activations kept for the backward pass
+  float *feat;                     // [2V][3]
+  float *h[kLayers + 1];           // [2V][H]
+  float *m[kLayers], *e[kLayers];  // [C][H]
+  float *a[kLayers];               // [2V][H]
+  float *dh, *dh2, *da, *de, *dm;  // gradient buffers
+  float *part;                     // weight-gradient partials [kPartBlocks][64][193]
+  __nv_bfloat16 *wb;               // BF16 copy of the parameters
+  float *ldeg;                     // [2V] literal degrees
+  float *dlog, *lossv;             // [V] dL/dlogit and per-variable loss terms
+};
+constexpr int kPartBlocks = 256;
+
+static size_t mp_ws_bytes(int64_t V, int64_t C) {
+  const int64_t L = 2 * V;
+  size_t b = 0;
+  auto add = [&](size_t x) { b += align_up(x, 256); };
+  add(sizeof(float) * L * kFeat);
+  for (int t = 0; t <= kLayers; ++t) add(sizeof(float) * L * kH);
+  for (int t = 0; t < kLayers; ++t) {
+    add(sizeof(float) * C * kH);
+    add(sizeof(float) * C * kH);
+    add(sizeof(float) * L * kH);
+  }
+  add(sizeof(float) * L * kH * 3);   // dh, dh2, da
+  add(sizeof(float) * C * kH * 2);   // de, dm
+  add(sizeof(float) * kPartBlocks * kH * (3 * kH + 1));
+  add(sizeof(__nv_bfloat16) * kNParams);
+  add(sizeof(float) * L);
+  add(sizeof(float) * V);
+  add(sizeof(float) * V);
+  return b;
+}
+
+static MpWs mp_ws_plan(void *base, int64_t V, int64_t C) {
+  const int64_t L = 2 * V;
+  MpWs w{};
+  char *p = (char *)base;
+  auto take = [&](size_t x) { char *r = p; p += align_up(x, 256); return r; };
+  w.feat = (float *)take(sizeof(float) * L * kFeat);
+  for (int t = 0; t <= kLayers; ++t) w.h[t] = (float *)take(sizeof(float) * L * kH);
+  for (int t = 0; t < kLayers; ++t) {
+    w.m[t] = (float *)take(sizeof(float) * C * kH);
+    w.e[t] = (float *)take(sizeof(float) * C * kH);
+    w.a[t] = (float *)take(sizeof(float) * L * kH);
+  }
+  w.dh = (float *)take(sizeof(float) * L * kH);
+  w.dh2 = (float *)take(sizeof(float) * L * kH);
+  w.da = (float *)take(sizeof(float) * L * kH);
+  w.de = (float *)take(sizeof(float) * C * kH);
+  w.dm = (float *)take(sizeof(float) * C * kH);
+  w.part = (float *)take(sizeof(float) * kPartBlocks * kH * (3 * kH + 1));
+  w.wb = (__nv_bfloat16 *)take(sizeof(__nv_bfloat16) * kNParams);
+  w.ldeg = (float *)take(sizeof(float) * L);
+  w.dlog = (float *)take(sizeof(float) * V);
+  w.lossv = (float *)take(sizeof(float) * V);
+  return w;
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void k_mp_to_bf16(const float *p, __nv_bfloat16 *b, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = __float2bfloat16_rn(p[i]);
+}
+
+// literal degrees and input features
+__global__ void k_mp_feat(ProbDev pd, float *ldeg, float *feat) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < pd.V; v += (int64_t)gridDim.x * blockDim.x) {
+    int dp = 0, dn = 0;
+    for (int32_t o = pd.vptr[v]; o < pd.vptr[v + 1]; ++o) (pd.vocc[o] & 1) ? ++dn : ++dp;
+    ldeg[2 * v] = (float)dp;
+    ldeg[2 * v + 1] = (float)dn;
+    const float lp = logf(1.0f + (float)dp), ln = logf(1.0f + (float)dn);
+    float *f0 = feat + (2 * v) * kFeat, *f1 = feat + (2 * v + 1) * kFeat;
+    f0[0] = 1.f; f0[1] = lp; f0[2] = ln;
+    f1[0] = 1.f; f1[1] = ln; f1[2] = lp;
+  }
+}
+
+// Y[r][0:64] = act( sum_j X_j[r ^ xj][0:Kj] . W[:, offs_j]^T + b ),  W bf16 [64][Ktot]
+struct DIn {
+  const float *x;
+  int K, xr;
+};
+template <int NIN>
+__global__ void __launch_bounds__(256) k_mp_dense(DIn i0, DIn i1, DIn i2, int64_t M, const __nv_bfloat16 *W,
+                                                  const __nv_bfloat16 *bias, int relu, float *Y) {
+  extern __shared__ float ws[];   // [Ktot][64] (transposed weights)
+  const int Kt = i0.K + (NIN > 1 ? i1.K : 0) + (NIN > 2 ? i2.K : 0);
+  for (int k = threadIdx.x; k < Kt * kH; k += blockDim.x) {
+    const int o = k / Kt, kk = k % Kt;
+    ws[kk * kH + o] = __bfloat162float(W[o * Kt + kk]);
+  }
+  __syncthreads();
+  const int o = threadIdx.x & 63, rsub = threadIdx.x >> 6;   // 4 rows per pass
+  const float bo = __bfloat162float(bias[o]);
+  for (int64_t r = (int64_t)blockIdx.x * 4 + rsub; r < M; r += (int64_t)gridDim.x * 4) {
+    float acc = bo;
+    int koff = 0;
+    {
+      const float *x = i0.x + (r ^ i0.xr) * i0.K;
+      for (int k = 0; k < i0.K; ++k) acc = fmaf(x[k], ws[(koff + k) * kH + o], acc);
+      koff += i0.K;
+    }
+    if (NIN > 1) {
+      const float *x = i1.x + (r ^ i1.xr) * i1.K;
+      for (int k = 0; k < i1.K; ++k) acc = fmaf(x[k], ws[(koff + k) * kH + o], acc);
+      koff += i1.K;
+    }
+    if (NIN > 2) {
+      const float *x = i2.x + (r ^ i2.xr) * i2.K;
+      for (int k = 0; k < i2.K; ++k) acc = fmaf(x[k], ws[(koff + k) * kH + o], acc);
+    }
+    Y[r * kH + o] = relu ? fmaxf(acc, 0.f) : acc;
+  }
+}
+
+// m_c = mean_{l in c} h_l
+__global__ void k_mp_clause_mean(ProbDev pd, const float *h, float *m) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < pd.C;
+       c += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t b = pd.cptr[c], e = pd.cptr[c + 1];
+    float2 acc = make_float2(0.f, 0.f);
+    for (int32_t j = b; j < e; ++j) {
+      const float2 x = reinterpret_cast<const float2 *>(h + (int64_t)pd.clit[j] * kH)[lane];
+      acc.x += x.x;
+      acc.y += x.y;
+    }
+    const float s = 1.0f / (float)(e - b);
+    reinterpret_cast<float2 *>(m + c * kH)[lane] = make_float2(acc.x * s, acc.y * s);
+  }
+}
+
+// a_l = mean_{c owns l} e_c   (warp per variable: both literals)
+__global__ void k_mp_lit_mean(ProbDev pd, const float *e, const float *ldeg, float *a) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < pd.V;
+       v += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    float2 ap = make_float2(0.f, 0.f), an = ap;
+    for (int32_t o = pd.vptr[v]; o < pd.vptr[v + 1]; ++o) {
+      const int32_t oc = pd.vocc[o];
+      const float2 x = reinterpret_cast<const float2 *>(e + (int64_t)(oc >> 1) * kH)[lane];
+      if (oc & 1) { an.x += x.x; an.y += x.y; } else { ap.x += x.x; ap.y += x.y; }
+    }
+    const float sp = 1.0f / fmaxf(ldeg[2 * v], 1.f), sn = 1.0f / fmaxf(ldeg[2 * v + 1], 1.f);
+    reinterpret_cast<float2 *>(a + (2 * v) * kH)[lane] = make_float2(ap.x * sp, ap.y * sp);
+    reinterpret_cast<float2 *>(a + (2 * v + 1) * kH)[lane] = make_float2(an.x * sn, an.y * sn);
+  }
+}
+
+__global__ void k_mp_out(ProbDev pd, const float *h, const __nv_bfloat16 *wb, float *logits) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < pd.V;
+       v += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    float s = 0.f;
+    for (int k = lane; k < 2 * kH; k += 32) s += h[(2 * v) * kH + k] * __bfloat162float(wb[kOffOut + k]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if (lane == 0) logits[v] = s + __bfloat162float(wb[kOffOut + 2 * kH]);
+  }
+}
+
+// binary cross-entropy per variable, mean over the variables of each instance
+__global__ void k_mp_bce(ProbDev pd, const float *logits, const uint8_t *y, float *loss_v, float *dlog) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < pd.V; v += (int64_t)gridDim.x * blockDim.x) {
+    const float x = logits[v], t = (float)y[v];
+    const int inst = pd.var_inst[v];
+    const float inv = 1.0f / (float)pd.inst[inst].n_vars;
+    loss_v[v] = (fmaxf(x, 0.f) - x * t + log1pf(expf(-fabsf(x)))) * inv;
+    dlog[v] = (1.0f / (1.0f + expf(-x)) - t) * inv;
+  }
+}
+
+// output layer backward: dh3[2v .. 2v+1] = dlogit_v * wo
+__global__ void k_mp_out_bwd(ProbDev pd, const float *dlog, const __nv_bfloat16 *wb, float *dh) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)pd.V * 2 * kH;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = i / (2 * kH);
+    const int k = (int)(i % (2 * kH));
+    dh[2 * v * kH + k] = dlog[v] * __bfloat162float(wb[kOffOut + k]);
+  }
+}
+
+// in place: dZ = dY * [Y > 0]
+__global__ void k_mp_relu_bwd(const float *Y, float *dY, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!(Y[i] > 0.f)) dY[i] = 0.f;
+}
+
+// dX[r][0:K] = dZ[r][0:64] . W[0:64][koff : koff+K]   (one input slice)
+__global__ void __launch_bounds__(256) k_mp_dx(const float *dZ, int64_t M, const __nv_bfloat16 *W, int Ktot, int koff,
+                                               int K, float *dX, int accumulate, int xr) {
+  extern __shared__ float ws2[];   // [64][K]
+  for (int k = threadIdx.x; k < kH * K; k += blockDim.x) {
+    const int o = k / K, kk = k % K;
+    ws2[o * K + kk] = __bfloat162float(W[o * Ktot + koff + kk]);
+  }
+  __syncthreads();
+  const int per = blockDim.x / K;   // rows per pass
+  const int kk = threadIdx.x % K, rsub = threadIdx.x / K;
+  if (rsub >= per) return;
+  for (int64_t r = (int64_t)blockIdx.x * per + rsub; r < M; r += (int64_t)gridDim.x * per) {
+    const float *dz = dZ + r * kH;
+    float acc = 0.f;
+    for (int o = 0; o < kH; ++o) acc = fmaf(dz[o], ws2[o * K + kk], acc);
+    float *dst = dX + (r ^ xr) * K + kk;
+    *dst = accumulate ? *dst + acc : acc;
+  }
+}
+
+// partial weight gradients: part[b][o][k] = sum_{rows of block b} dZ[r][o] X[r^xr][k]; db in column K
+__global__ void __launch_bounds__(256) k_mp_wgrad(const float *dZ, int64_t M, DIn i0, DIn i1, DIn i2, int nin,
+                                                  float *part) {
+  const int Kt = i0.K + (nin > 1 ? i1.K : 0) + (nin > 2 ? i2.K : 0);
+  const int ncol = Kt + 1;                 // + bias column
+  float *out = part + (size_t)blockIdx.x * kH * ncol;
+  const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
+  for (int idx = threadIdx.x; idx < kH * ncol; idx += blockDim.x) {
+    const int o = idx / ncol, k = idx % ncol;
+    const float *xp;
+    int K, xr, kk;
+    if (k == Kt) { xp = nullptr; K = 0; xr = 0; kk = 0; }
+    else if (k < i0.K) { xp = i0.x; K = i0.K; xr = i0.xr; kk = k; }
+    else if (k < i0.K + i1.K) { xp = i1.x; K = i1.K; xr = i1.xr; kk = k - i0.K; }
+    else { xp = i2.x; K = i2.K; xr = i2.xr; kk = k - i0.K - i1.K; }
+    float acc = 0.f;
+    for (int64_t r = r0; r < r1; ++r) acc = fmaf(dZ[r * kH + o], xp ? xp[(r ^ xr) * K + kk] : 1.0f, acc);
+    out[idx] = acc;
+  }
+}
+
+// grad[W(o,k)] (+)= sum_b part[b][o][k], bias into gbias[o]
+__global__ void k_mp_wgrad_reduce(const float *part, int nb, int Kt, float *gW, float *gb) {
+  const int ncol = Kt + 1;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < kH * ncol; idx += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int b = 0; b < nb; ++b) s += part[(size_t)b * kH * ncol + idx];
+    const int o = idx / ncol, k = idx % ncol;
+    if (k == Kt) gb[o] = s; else gW[o * Kt + k] = s;
+  }
+}
+
+// de_c += sum_{l in c} da_l / deg_l ;  (transpose of the variable-major mean)
+__global__ void k_mp_clause_from_lit(ProbDev pd, const float *da, const float *ldeg, float *de) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < pd.C;
+       c += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int32_t j = pd.cptr[c]; j < pd.cptr[c + 1]; ++j) {
+      const int32_t l = pd.clit[j];
+      const float s = 1.0f / fmaxf(ldeg[l], 1.f);
+      const float2 x = reinterpret_cast<const float2 *>(da + (int64_t)l * kH)[lane];
+      acc.x += x.x * s;
+      acc.y += x.y * s;
+    }
+    reinterpret_cast<float2 *>(de + c * kH)[lane] = acc;
+  }
+}
+
+// dh_l += sum_{c owns l} dm_c / |c| ;  (transpose of the clause-major mean)
+__global__ void k_mp_lit_from_clause(ProbDev pd, const float *dm, float *dh) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < pd.V;
+       v += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    float2 ap = make_float2(0.f, 0.f), an = ap;
+    for (int32_t o = pd.vptr[v]; o < pd.vptr[v + 1]; ++o) {
+      const int32_t oc = pd.vocc[o], c = oc >> 1;
+      const float s = 1.0f / (float)(pd.cptr[c + 1] - pd.cptr[c]);
+      const float2 x = reinterpret_cast<const float2 *>(dm + (int64_t)c * kH)[lane];
+      if (oc & 1) { an.x += x.x * s; an.y += x.y * s; } else { ap.x += x.x * s; ap.y += x.y * s; }
+    }
+    float2 *p0 = reinterpret_cast<float2 *>(dh + (2 * v) * kH) + lane;
+    float2 *p1 = reinterpret_cast<float2 *>(dh + (2 * v + 1) * kH) + lane;
+    p0->x += ap.x; p0->y += ap.y;
+    p1->x += an.x; p1->y += an.y;
+  }
+}
+
+// output-layer weight gradient: gwo[k] = sum_v dlog_v h[2v*H + k], gbo = sum_v dlog_v
+__global__ void k_mp_out_wgrad(ProbDev pd, const float *h, const float *dlog, float *part) {
+  const int64_t r0 = (int64_t)pd.V * blockIdx.x / gridDim.x, r1 = (int64_t)pd.V * (blockIdx.x + 1) / gridDim.x;
+  for (int k = threadIdx.x; k <= 2 * kH; k += blockDim.x) {
+    float acc = 0.f;
+    for (int64_t v = r0; v < r1; ++v) acc = fmaf(dlog[v], k < 2 * kH ? h[2 * v * kH + k] : 1.f, acc);
+    part[(size_t)blockIdx.x * (2 * kH + 1) + k] = acc;
+  }
+}
+__global__ void k_mp_out_reduce(const float *part, int nb, float *g) {
+  for (int k = threadIdx.x; k <= 2 * kH; k += blockDim.x) {
+    float s = 0.f;
+    for (int b = 0; b < nb; ++b) s += part[(size_t)b * (2 * kH + 1) + k];
+    g[kOffOut + k] = s;
+  }
+}
+
+// parameter init: Xavier-uniform from Philox, zero biases
+__global__ void k_mp_init(float *p, uint32_t k0, uint32_t k1) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kNParams; i += gridDim.x * blockDim.x) {
+    float fan_in = 0.f, fan_out = kH;
+    bool bias = false;
+    if (i < kOffB0) fan_in = kFeat;
+    else if (i < kOffLayer) bias = true;
+    else if (i < kOffOut) {
+      const int j = (i - kOffLayer) % kLayerSize;
+      if (j < kH * kH) fan_in = kH;
+      else if (j < kH * kH + kH) bias = true;
+      else if (j < kH * kH + kH + 3 * kH * kH) fan_in = 3 * kH;
+      else bias = true;
+    } else if (i < kOffOut + 2 * kH) { fan_in = 2 * kH; fan_out = 1; }
+    else bias = true;
+    if (bias) { p[i] = 0.f; continue; }
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0, 0, 0x4D504E4Eu), k0, k1);
+    const float u = ((float)(r.x >> 8) + 0.5f) * (1.0f / 16777216.0f);
+    const float lim = sqrtf(6.0f / (fan_in + fan_out));
+    p[i] = (2.f * u - 1.f) * lim;
+  }
+}
+
+__global__ void k_mp_adam(float *p, const float *g, float *m, float *v, int n, float lr, float b1, float b2, float eps,
+                          float bc1, float bc2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    m[i] = b1 * m[i] + (1.f - b1) * gi;
+    v[i] = b2 * v[i] + (1.f - b2) * gi * gi;
+    p[i] -= lr * (m[i] / bc1) / (sqrtf(v[i] / bc2) + eps);
+  }
+}
+
+__global__ void k_mp_sum(const float *x, int64_t n, float *out) {  // one block, fixed order
+  __shared__ float sh[1024];
+  float s = 0.f;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// ------------------------------------------------------------------ host orchestration
+static int grid_for(int64_t work, int per_block) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(148 * 16, (work + per_block - 1) / per_block));
+}
+
+static cudaError_t dense(int nin, DIn a, DIn b, DIn c, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias,
+                         int relu, float *Y, cudaStream_t st) {
+  const int Kt = a.K + (nin > 1 ? b.K : 0) + (nin > 2 ? c.K : 0);
+  const size_t smem = sizeof(float) * Kt * kH;
+  const int g = grid_for(M, 4 * 16);
+  if (nin == 1) k_mp_dense<1><<<g, 256, smem, st>>>(a, b, c, M, W, bias, relu, Y);
+  else if (nin == 2) k_mp_dense<2><<<g, 256, smem, st>>>(a, b, c, M, W, bias, relu, Y);
+  else k_mp_dense<3><<<g, 256, smem, st>>>(a, b, c, M, W, bias, relu, Y);
+  return cudaGetLastError();
+}
+
+static int mp_forward(const tsat_problem *p, const float *params, MpWs &w, float *logits, cudaStream_t st) {
+  const ProbDev &pd = p->dev;
+  const int64_t L = 2 * (int64_t)p->V, C = p->C;
+  k_mp_to_bf16<<<64, 256, 0, st>>>(params, w.wb, kNParams);
+  k_mp_feat<<<grid_for(p->V, 256), 256, 0, st>>>(pd, w.ldeg, w.feat);
+  TSAT_LAUNCH_CHECK("mpnn features");
+  DIn none{nullptr, 0, 0};
+  cudaError_t e = dense(1, DIn{w.feat, kFeat, 0}, none, none, L, w.wb + kOffW0, w.wb + kOffB0, 1, w.h[0], st);
+  if (e != cudaSuccess) return cuda_fail(e, "mpnn input layer");
+  for (int t = 0; t < kLayers; ++t) {
+    k_mp_clause_mean<<<grid_for(C * 32, 256), 256, 0, st>>>(pd, w.h[t], w.m[t]);
+    if ((e = dense(1, DIn{w.m[t], kH, 0}, none, none, C, w.wb + off_wc(t), w.wb + off_bc(t), 1, w.e[t], st)) !=
+        cudaSuccess)
+      return cuda_fail(e, "mpnn clause layer");
+    k_mp_lit_mean<<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.e[t], w.ldeg, w.a[t]);
+    if ((e = dense(3, DIn{w.h[t], kH, 0}, DIn{w.a[t], kH, 0}, DIn{w.h[t], kH, 1}, L, w.wb + off_wl(t),
+                   w.wb + off_bl(t), 1, w.h[t + 1], st)) != cudaSuccess)
+      return cuda_fail(e, "mpnn literal layer");
+  }
+  if (logits) k_mp_out<<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.h[kLayers], w.wb, logits);
+  TSAT_LAUNCH_CHECK("mpnn forward");
+  return TSAT_OK;
+}
+
+static int wgrad(int nin, DIn a, DIn b, DIn c, const float *dZ, int64_t M, float *part, float *gW, float *gb,
+                 cudaStream_t st) {
+  const int Kt = a.K + (nin > 1 ? b.K : 0) + (nin > 2 ? c.K : 0);
+  const int nb = (int)std::min<int64_t>(kPartBlocks, std::max<int64_t>(1, M / 64));
+  k_mp_wgrad<<<nb, 256, 0, st>>>(dZ, M, a, b, c, nin, part);
+  k_mp_wgrad_reduce<<<(kH * (Kt + 1) + 255) / 256, 256, 0, st>>>(part, nb, Kt, gW, gb);
+  TSAT_LAUNCH_CHECK("mpnn weight gradient");
+  return TSAT_OK;
+}
+
+static int dx(const float *dZ, int64_t M, const __nv_bfloat16 *W, int Ktot, int koff, int K, float *dX, int acc,
+              int xr, cudaStream_t st) {
+  const int per = 256 / K;
+  k_mp_dx<<<grid_for(M, per * 8), 256, sizeof(float) * kH * K, st>>>(dZ, M, W, Ktot, koff, K, dX, acc, xr);
+  TSAT_LAUNCH_CHECK("mpnn input gradient");
+  return TSAT_OK;
+}
+
+static int mp_backward(const tsat_problem *p, MpWs &w, const float *dlog, float *grad, cudaStream_t st) {
+  const ProbDev &pd = p->dev;
+  const int64_t L = 2 * (int64_t)p->V, C = p->C;
+  DIn none{nullptr, 0, 0};
+  int rc;
+  // output layer
+  {
+    const int nb = (int)std::min<int64_t>(kPartBlocks, std::max<int64_t>(1, p->V / 64));
+    k_mp_out_wgrad<<<nb, 256, 0, st>>>(pd, w.h[kLayers], dlog, w.part);
+    k_mp_out_reduce<<<1, 256, 0, st>>>(w.part, nb, grad);
+    k_mp_out_bwd<<<grid_for(p->V * 2 * kH, 256), 256, 0, st>>>(pd, dlog, w.wb, w.dh);
+    TSAT_LAUNCH_CHECK("mpnn output backward");
+  }
+  for (int t = kLayers - 1; t >= 0; --t) {
+    // literal layer: h[t+1] = relu(Wl [h[t]; a[t]; h[t]^1] + bl)
+    k_mp_relu_bwd<<<grid_for(L * kH, 256), 256, 0, st>>>(w.h[t + 1], w.dh, L * kH);
+    if ((rc = wgrad(3, DIn{w.h[t], kH, 0}, DIn{w.a[t], kH, 0}, DIn{w.h[t], kH, 1}, w.dh, L, w.part,
+                    grad + off_wl(t), grad + off_bl(t), st)))
+      return rc;
+    const __nv_bfloat16 *Wl = w.wb + off_wl(t);
+    if ((rc = dx(w.dh, L, Wl, 3 * kH, 0, kH, w.dh2, 0, 0, st))) return rc;         // from h_l
+    if ((rc = dx(w.dh, L, Wl, 3 * kH, 2 * kH, kH, w.dh2, 1, 1, st))) return rc;    // from h_{l^1}
+    if ((rc = dx(w.dh, L, Wl, 3 * kH, kH, kH, w.da, 0, 0, st))) return rc;         // from a_l
+    // a = mean over owning clauses of e  ->  de
+    k_mp_clause_from_lit<<<grid_for(C * 32, 256), 256, 0, st>>>(pd, w.da, w.ldeg, w.de);
+    // clause layer: e = relu(Wc m + bc)
+    k_mp_relu_bwd<<<grid_for(C * kH, 256), 256, 0, st>>>(w.e[t], w.de, C * kH);
+    if ((rc = wgrad(1, DIn{w.m[t], kH, 0}, none, none, w.de, C, w.part, grad + off_wc(t), grad + off_bc(t), st)))
+      return rc;
+    if ((rc = dx(w.de, C, w.wb + off_wc(t), kH, 0, kH, w.dm, 0, 0, st))) return rc;
+    // m = mean of h over the clause's literals -> dh2 += ...
+    k_mp_lit_from_clause<<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.dm, w.dh2);
+    TSAT_LAUNCH_CHECK("mpnn layer backward");
+    std::swap(w.dh, w.dh2);
+  }
+  // input layer
+  k_mp_relu_bwd<<<grid_for(L * kH, 256), 256, 0, st>>>(w.h[0], w.dh, L * kH);
+  if ((rc = wgrad(1, DIn{w.feat, kFeat, 0}, none, none, w.dh, L, w.part, grad + kOffW0, grad + kOffB0, st))) return rc;
+  return TSAT_OK;
+}
+
+}  // namespace tsat
+
+using namespace tsat;
+
+extern "C" {
+
+int32_t tsat_mpnn_param_count(void) { return kNParams; }
+
+int tsat_mpnn_workspace_bytes(const tsat_problem *p, size_t *bytes) {
+  if (!p || !bytes) return TSAT_EINVAL;
+  *bytes = mp_ws_bytes(p->V, p->C);
+  return TSAT_OK;
+}
+
+int tsat_mpnn_init(float *d_params, uint64_t seed, cudaStream_t stream) {
+  if (!d_params) return TSAT_EINVAL;
+  k_mp_init<<<(kNParams + 255) / 256, 256, 0, stream>>>(d_params, (uint32_t)seed, (uint32_t)(seed >> 32));
+  TSAT_LAUNCH_CHECK("mpnn init");
+  return TSAT_OK;
+}
+
+int tsat_mpnn_forward(const tsat_problem *p, const float *d_params, void *d_ws, size_t ws_bytes, float *d_logits,
+                      cudaStream_t stream) {
+  if (!p || !d_params || !d_ws || !d_logits) return TSAT_EINVAL;
+  if (ws_bytes < mp_ws_bytes(p->V, p->C)) { set_error("mpnn workspace too small"); return TSAT_EWS; }
+  MpWs w = mp_ws_plan(d_ws, p->V, p->C);
+  return mp_forward(p, d_params, w, d_logits, stream);
+}
+
+int tsat_mpnn_loss_grad(const tsat_problem *p, const float *d_params, void *d_ws, size_t ws_bytes,
+                        const uint8_t *d_targets, float *d_logits, float *d_loss, float *d_grad, cudaStream_t stream) {
+  if (!p || !d_params || !d_ws || !d_targets || !d_logits || !d_loss || !d_grad) return TSAT_EINVAL;
+  if (ws_bytes < mp_ws_bytes(p->V, p->C)) { set_error("mpnn workspace too small"); return TSAT_EWS; }
+  MpWs w = mp_ws_plan(d_ws, p->V, p->C);
+  int rc = mp_forward(p, d_params, w, d_logits, stream);
+  if (rc) return rc;
+  k_mp_bce<<<grid_for(p->V, 256), 256, 0, stream>>>(p->dev, d_logits, d_targets, w.lossv, w.dlog);
+  k_mp_sum<<<1, 1024, 0, stream>>>(w.lossv, p->V, d_loss);
+  TSAT_LAUNCH_CHECK("mpnn loss");
+  return mp_backward(p, w, w.dlog, d_grad, stream);
+}
+
+int tsat_mpnn_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int64_t step, float lr,
+                   cudaStream_t stream) {
+  if (!d_params || !d_grad || !d_m || !d_v || step < 1) return TSAT_EINVAL;
+  const float bc1 = (float)(1.0 - std::pow(0.9, (double)step)), bc2 = (float)(1.0 - std::pow(0.999, (double)step));
+  k_mp_adam<<<(kNParams + 255) / 256, 256, 0, stream>>>(d_params, d_grad, d_m, d_v, kNParams, lr, 0.9f, 0.999f,
+                                                       1e-8f, bc1, bc2);
+  TSAT_LAUNCH_CHECK("mpnn adam");
+  return TSAT_OK;
+}
+
+}  // extern "C"

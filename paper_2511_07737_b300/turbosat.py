@@ -93,6 +93,12 @@ def lib():
             "tsat_set_tuning": (ctypes.c_int, [P, P]),
             "tsat_launches_per_step": (i32, [P]),
             "tsat_evaluate_bits_noalloc": (ctypes.c_int, [P, P, i32, f32, P, P, P, P]),
+            "tsat_mpnn_param_count": (i32, []),
+            "tsat_mpnn_workspace_bytes": (ctypes.c_int, [P, P]),
+            "tsat_mpnn_init": (ctypes.c_int, [P, ctypes.c_uint64, P]),
+            "tsat_mpnn_forward": (ctypes.c_int, [P, P, P, sz, P, P]),
+            "tsat_mpnn_loss_grad": (ctypes.c_int, [P, P, P, sz, P, P, P, P, P]),
+            "tsat_mpnn_adam": (ctypes.c_int, [P, P, P, P, i64, f32, P]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -294,6 +300,35 @@ def tsat_set_tuning(s, tuning: Sequence[int]):
 
 def tsat_launches_per_step(s) -> int:
     return int(lib().tsat_launches_per_step(s))
+
+
+def tsat_mpnn_param_count() -> int:
+    return int(lib().tsat_mpnn_param_count())
+
+
+def tsat_mpnn_workspace_bytes(h) -> int:
+    out = ctypes.c_size_t(0)
+    _ck(lib().tsat_mpnn_workspace_bytes(h, ctypes.byref(out)), "tsat_mpnn_workspace_bytes")
+    return int(out.value)
+
+
+def tsat_mpnn_init(params: torch.Tensor, seed: int, stream=None):
+    _ck(lib().tsat_mpnn_init(_ptr(params), int(seed), _stream(stream)), "tsat_mpnn_init")
+
+
+def tsat_mpnn_forward(h, params: torch.Tensor, ws: torch.Tensor, logits: torch.Tensor, stream=None):
+    _ck(lib().tsat_mpnn_forward(h, _ptr(params), _ptr(ws), ws.numel() * ws.element_size(), _ptr(logits),
+                                _stream(stream)), "tsat_mpnn_forward")
+
+
+def tsat_mpnn_loss_grad(h, params, ws, targets, logits, loss, grad, stream=None):
+    _ck(lib().tsat_mpnn_loss_grad(h, _ptr(params), _ptr(ws), ws.numel() * ws.element_size(), _ptr(targets),
+                                  _ptr(logits), _ptr(loss), _ptr(grad), _stream(stream)), "tsat_mpnn_loss_grad")
+
+
+def tsat_mpnn_adam(params, grad, m, v, step: int, lr: float, stream=None):
+    _ck(lib().tsat_mpnn_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr), _stream(stream)),
+        "tsat_mpnn_adam")
 
 
 # ---------------------------------------------------------------- lifetime holders

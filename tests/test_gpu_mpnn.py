@@ -1,0 +1,72 @@
+"""Learned proposer on the GPU: forward and gradient against the FP64 oracle,
+training decreases the loss, and the trained network beats random init."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mpnn
+from paper_2511_07737_b300 import cnfgen
+from paper_2511_07737_b300 import turbosat as ts
+from paper_2511_07737_b300.proposer import Proposer, compare, make_dataset
+from tests.conftest import rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    torch.cuda.set_device(0)
+
+
+def test_mpnn_forward_and_gradient_match_oracle():
+    insts = [cnfgen.planted_ksat(300, 1150, 3, 2), cnfgen.planted_ksat(200, 3800, 5, 3),
+             cnfgen.tiny_random(40, 120, 4, kmin=1, kmax=6)]
+    prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in insts])
+    pr = Proposer(seed=7)
+    y = np.concatenate([i.planted for i in insts]).astype(np.uint8)
+    ws = pr._ws(prob)
+    logits = torch.empty(prob.info["n_vars"], device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros_like(pr.params)
+    ts.tsat_mpnn_loss_grad(prob.h, pr.params, ws, torch.tensor(y, device="cuda"), logits, loss, grad)
+    torch.cuda.synchronize()
+    params = mpnn.bf16_round(pr.params.cpu().numpy())       # the kernels compute with BF16 weights
+    g = mpnn.Graph([oracle.CNF(i.n_vars, i.clause_ptr, i.lits) for i in insts])
+    l_ref, g_ref, lg_ref = mpnn.loss_and_grad(g, params, y)
+    assert rel_err(logits.cpu().numpy(), lg_ref) < 1e-5
+    assert abs(loss.item() - l_ref) < 1e-5 * abs(l_ref)
+    assert rel_err(grad.cpu().numpy(), g_ref) < 1e-4
+
+
+def test_training_lowers_loss_and_learned_init_beats_random():
+    # solver settings and ratios where the gradient solver finds models within
+    # the step cap (3-SAT at 0.9x, 5-SAT at 0.5x, 4-SAT at 0.6x of threshold)
+    hp = ts.hparams(seed=3, norm=ts.NORM_ABSMEAN, tau=2.0, lr0=0.5)
+    train = (cnfgen.batch_ksat(64, 101, n_lo=200, n_hi=600, ks=[3], ratio_scale=0.9)
+             + cnfgen.batch_ksat(48, 102, n_lo=200, n_hi=500, ks=[5], ratio_scale=0.5))
+    data, dropped = make_dataset(train, N=32, hp=hp, max_steps=1000)
+    assert len(data) >= 60, (len(data), dropped)
+    pr = Proposer(seed=1)
+    hist = pr.fit(data, epochs=8, batch=16, lr=3e-3)
+    assert np.mean(hist[-6:]) < np.mean(hist[:6])
+    test = cnfgen.batch_ksat(48, 202, n_lo=300, n_hi=600, ks=[4], ratio_scale=0.6)
+    # the proposal alone: fewer unsatisfied clauses than random init at step 0
+    prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in test])
+    lg = pr.logits(prob)
+    counts = []
+    for logits in (None, lg):
+        st = ts.State(prob, 32)
+        ts.tsat_init(st.h, hp, logits, 1.0)
+        unsat = torch.zeros(len(test) * 32, dtype=torch.int32, device="cuda")
+        sm = torch.zeros(len(test), dtype=torch.int32, device="cuda")
+        ts.tsat_evaluate(st.h, hp, unsat, sm)
+        counts.append(unsat.float().mean().item())
+    assert counts[1] < 0.9 * counts[0], counts
+    res = compare(test, pr, N=32, hp=hp, max_steps=1000)
+    assert res["learned"]["solved"] >= res["random"]["solved"] - 2, res
+    if res.get("matched_k", 0) >= 10:
+        m = res["matched_median_steps"]
+        assert m["learned"] <= m["random"], res
