@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--experiment", default="throughput",
+                    choices=["throughput", "time_to_sat", "batch", "relaxed", "proposer"],
+                    help="throughput (default, the driver's line) or one of the other workloads")
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the experiment workloads (quick runs)")
     return ap.parse_args()
 
 
@@ -352,12 +356,198 @@ def ours(args, w, rank, world, local):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- other workloads
+def _emit(d):
+    print(json.dumps(d), flush=True)
+
+
+def exp_time_to_sat(args):
+    """Planted 3-SAT n=100 m=426 (ratio 4.26), N=64, step cap 500: wall time
+    from init to the host seeing the found flag (status polled every 10 steps),
+    each instance solved alone; beside it the oracle's wall time to its first
+    satisfying sample on the first instances (same init, settings and
+    deterministic binarization), within a bounded budget."""
+    import torch
+    from paper_2511_07737_b300 import cnfgen
+    from paper_2511_07737_b300 import turbosat as ts
+    n_inst = max(4, int(32 * args.scale))
+    settings = {"signed_mean (Eq. 5 as printed), tau 1": dict(norm=0, tau=1.0),
+                "absmean, tau 2, lr0 0.5": dict(norm=1, tau=2.0, lr0=0.5),
+                "none, tau 2": dict(norm=2, tau=2.0)}
+    insts = [cnfgen.planted_ksat(100, 426, 3, j) for j in range(n_inst)]
+    out = {"experiment": "time_to_sat", "metric": "time-to-first-satisfying-assignment", "unit": "ms",
+           "workload": "planted 3-SAT n=100 m=426 (ratio 4.26), N=64, cap 500 steps, deterministic binarization",
+           "instances": n_inst, "results": {}}
+    for name, kw in settings.items():
+        walls, steps = [], []
+        for j, inst in enumerate(insts):
+            prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
+            st = ts.State(prob, 64)
+            hp = ts.hparams(seed=j + 1, **kw)
+            ts.tsat_step_prepare(st.h, hp, 10, stop_on_sat=True)      # graph capture, once per state
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ts.tsat_init(st.h, hp)
+            found, s_ = False, None
+            for _ in range(50):
+                ts.tsat_step(st.h, hp, 10, stop_on_sat=True)
+                s_ = ts.tsat_status(st.h, 1)
+                if s_["inst"][0]["found"]:
+                    found = True
+                    break
+            el = time.perf_counter() - t0
+            if found:
+                walls.append(el)
+                steps.append(s_["inst"][0]["found_step"])
+        out["results"][name] = {"solved": len(walls),
+                                "median_ms_to_sat": 1e3 * float(np.median(walls)) if walls else None,
+                                "median_steps_to_sat": float(np.median(steps)) if steps else None}
+    if not args.no_cpu:
+        import oracle
+        oracle.build()
+        kw = settings["absmean, tau 2, lr0 0.5"]
+        ohp = oracle.hparams(**kw)
+        walls, steps, tried, t_all = [], [], 0, time.perf_counter()
+        for j, inst in enumerate(insts):
+            if time.perf_counter() - t_all > 15.0:
+                break
+            tried += 1
+            cnf = oracle.CNF(inst.n_vars, inst.clause_ptr, inst.lits)
+            t0 = time.perf_counter()
+            z = oracle.init_normal(inst.n_vars, 64, j + 1).astype(np.float64)
+            m, v = np.zeros_like(z), np.zeros_like(z)
+            for t in range(500):
+                r = oracle.step(cnf, ohp, t, z, m, v)
+                if (r["unsat"] == 0).any():
+                    walls.append(time.perf_counter() - t0)
+                    steps.append(t)
+                    break
+        out["cpu_baseline"] = {"kind": "oracle", "cores": oracle.num_threads(), "unit": "ms",
+                               "value": 1e3 * float(np.median(walls)) if walls else None,
+                               "median_steps_to_sat": float(np.median(steps)) if steps else None,
+                               "solved": len(walls),
+                               "sample": f"first {tried} instances, setting 'absmean, tau 2, lr0 0.5', FP64"}
+    _emit(out)
+
+
+def exp_batch(args):
+    """512 planted k-SAT instances (k uniform 3..7, n log-uniform 200-50,000,
+    ratio 0.9 x threshold), 64 restarts each, one launch per kernel per step
+    for the whole batch, replayed as a CUDA graph; autotuned launch shapes."""
+    import torch
+    from paper_2511_07737_b300 import cnfgen
+    from paper_2511_07737_b300 import turbosat as ts
+    n_inst = max(8, int(512 * args.scale))
+    t0 = time.perf_counter()
+    n_hi = 50_000 if args.scale >= 0.25 else max(1000, int(200_000 * args.scale))
+    insts = cnfgen.batch_ksat(n_inst, 3, n_lo=200, n_hi=n_hi)
+    gen_s = time.perf_counter() - t0
+    prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in insts])
+    info = prob.info
+    st = ts.State(prob, 64)
+    hp = ts.hparams(seed=2, norm=1, tau=2.0, lr0=0.5)
+    ts.tsat_init(st.h, hp)
+    tun = ts.tsat_autotune(st.h, hp)
+    K = max(3, args.steps // 4)
+    ts.tsat_step(st.h, hp, 3, stop_on_sat=False)
+    ts.tsat_step_prepare(st.h, hp, K, stop_on_sat=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ts.tsat_step(st.h, hp, K, stop_on_sat=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kms = ts.tsat_profile_step(st.h, hp, 2)
+    status = ts.tsat_status(st.h, n_inst)
+    found = [x for x in status["inst"] if x["found"]]
+    _emit({"experiment": "batch", "instances": n_inst, "samples_per_instance": 64, "n_vars": info["n_vars"],
+           "n_clauses": info["n_clauses"], "nnz": info["nnz"], "lmax": info["lmax"], "steps": K,
+           "ms_per_step": ms / K, "evals_per_s": info["nnz"] * 64 * K / (ms / 1e3), "kernel_ms": kms,
+           "tuning": tun, "solved_within_steps": len(found),
+           "median_found_step": float(np.median([x["found_step"] for x in found])) if found else None,
+           "generation_s": gen_s})
+
+
+def exp_relaxed(args):
+    """Structured mixed-length planted SAT n=2e6 m=8e6 (lengths 2-16, power-law
+    occurrences in 64 communities), N=256, relaxed layer with FP32 vs BF16
+    literal storage (FP32 sums)."""
+    import torch
+    from paper_2511_07737_b300 import cnfgen
+    from paper_2511_07737_b300 import turbosat as ts
+    n = int(2_000_000 * args.scale)
+    inst = cnfgen.structured_mixed(n, 4 * n, 5)
+    prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
+    info = prob.info
+    res = {"experiment": "relaxed", "n_vars": info["n_vars"], "n_clauses": info["n_clauses"], "nnz": info["nnz"],
+           "lmax": info["lmax"], "samples": 256, "results": {}}
+    for name, dt in (("fp32", ts.DTYPE_F32), ("bf16", ts.DTYPE_BF16)):
+        st = ts.State(prob, 256, ts.LAYER_RELAXED, dt)
+        hp = ts.hparams(seed=3, norm=1, layer=ts.LAYER_RELAXED)
+        ts.tsat_init(st.h, hp)
+        K = max(3, args.steps // 10)
+        ts.tsat_step(st.h, hp, 2, stop_on_sat=False)
+        ts.tsat_step_prepare(st.h, hp, K, stop_on_sat=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ts.tsat_step(st.h, hp, K, stop_on_sat=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kms = ts.tsat_profile_step(st.h, hp, 2)
+        res["results"][name] = {"ms_per_step": ms / K, "evals_per_s": info["nnz"] * 256 * K / (ms / 1e3),
+                                "kernel_ms": {"check": kms[3], "forward": kms[0], "gamma": kms[1], "update": kms[2]},
+                                "loss": ts.tsat_status(st.h, 1)["inst"][0]["loss"]}
+        del st
+        torch.cuda.empty_cache()
+    _emit(res)
+
+
+def exp_proposer(args):
+    """Learned proposer: train on models the gradient solver found for planted
+    3-SAT (0.9 x threshold) and 5-SAT (0.5 x threshold), n 500-5,000; compare
+    learned vs random init on held-out planted 4-SAT n=20,000 at ratio 9.0
+    (time to 99 % satisfied, remaining unsatisfied clauses) and at 0.6 x
+    threshold (time to SAT, solve-rate matched)."""
+    from paper_2511_07737_b300 import cnfgen
+    from paper_2511_07737_b300 import turbosat as ts
+    from paper_2511_07737_b300.proposer import Proposer, compare, make_dataset
+    hp = ts.hparams(seed=3, norm=1, tau=2.0, lr0=0.5)
+    n_train = max(32, int(10_000 * args.scale))
+    t0 = time.perf_counter()
+    train = (cnfgen.batch_ksat(n_train // 2, 11, n_lo=500, n_hi=5000, ks=[3], ratio_scale=0.9)
+             + cnfgen.batch_ksat(n_train // 2, 12, n_lo=500, n_hi=5000, ks=[5], ratio_scale=0.5))
+    data, dropped = make_dataset(train, N=32, hp=hp, max_steps=1000)
+    t_data = time.perf_counter() - t0
+    pr = Proposer(seed=1)
+    t1 = time.perf_counter()
+    hist = pr.fit(data, epochs=4, batch=16, lr=3e-3)
+    t_fit = time.perf_counter() - t1
+    n_eval = max(8, int(200 * args.scale))
+    nv = max(2000, int(20_000 * min(1.0, args.scale * 4)))
+    hard = [cnfgen.planted_ksat(nv, int(round(9.0 * nv)), 4, 5000 + j) for j in range(n_eval)]
+    easy = cnfgen.batch_ksat(n_eval, 13, n_lo=nv, n_hi=nv, ks=[4], ratio_scale=0.6)
+    r_hard = compare(hard, pr, N=32, hp=hp, max_steps=1000, chunk=10)
+    r_easy = compare(easy, pr, N=32, hp=hp, max_steps=1000, chunk=10)
+    _emit({"experiment": "proposer", "train_instances": len(train), "train_kept": len(data), "train_dropped": dropped,
+           "data_seconds": t_data, "fit_seconds": t_fit, "loss_first": float(np.mean(hist[:10])),
+           "loss_last": float(np.mean(hist[-10:])), "eval_n_vars": nv,
+           "eval_4sat_ratio_9.0": r_hard, "eval_4sat_0.6x_threshold": r_easy})
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         reference_arm(args, w, rank, world)
+        return
+    if args.experiment != "throughput":
+        if rank == 0:
+            {"time_to_sat": exp_time_to_sat, "batch": exp_batch, "relaxed": exp_relaxed,
+             "proposer": exp_proposer}[args.experiment](args)
         return
     ours(args, w, rank, world, local)
 

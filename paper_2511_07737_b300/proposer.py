@@ -38,12 +38,17 @@ def solve(instances, N: int = 32, hp=None, max_steps: int = 500, logits: torch.T
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ts.tsat_init(st.h, hp, logits, scale)
+    ncl = np.array([i.n_clauses for i in instances], np.float64)
+    t99 = np.full(len(instances), -1, np.int64)
     done_steps = 0
     while done_steps < max_steps:
         k = min(chunk, max_steps - done_steps)
         ts.tsat_step(st.h, hp, k, stop_on_sat=True)
         done_steps += k
         status = ts.tsat_status(st.h, len(instances))
+        mu = np.array([x["min_unsat"] if not x["found"] else 0 for x in status["inst"]], np.float64)
+        hit = ((ncl - mu) / ncl > 0.99) & (t99 < 0)
+        t99[hit] = done_steps
         if status["all_done"]:
             break
     torch.cuda.synchronize()
@@ -61,7 +66,7 @@ def solve(instances, N: int = 32, hp=None, max_steps: int = 500, logits: torch.T
         else:
             assign.append(None)
     return dict(found=np.array(found), steps=np.array(steps), assign=assign, min_unsat=np.array(min_unsat),
-                wall=wall, total_steps=status["step"], ms_per_step=1e3 * wall / max(1, status["step"]))
+                t99=t99, wall=wall, total_steps=status["step"], ms_per_step=1e3 * wall / max(1, status["step"]))
 
 
 class Proposer:
@@ -132,7 +137,8 @@ def make_dataset(instances, N: int = 32, hp=None, max_steps: int = 500, batch: i
     return data, dropped
 
 
-def compare(instances, proposer: Proposer, N: int = 32, hp=None, max_steps: int = 1000, scale: float = 1.0) -> dict:
+def compare(instances, proposer: Proposer, N: int = 32, hp=None, max_steps: int = 1000, scale: float = 1.0,
+            chunk: int = 50) -> dict:
     """Learned vs random initialisation on the same batch and solver settings."""
     prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in instances])
     torch.cuda.synchronize()
@@ -140,14 +146,16 @@ def compare(instances, proposer: Proposer, N: int = 32, hp=None, max_steps: int 
     lg = proposer.logits(prob)
     torch.cuda.synchronize()
     t_prop = time.perf_counter() - t0
-    rnd = solve(instances, N=N, hp=hp, max_steps=max_steps)
-    lrn = solve(instances, N=N, hp=hp, max_steps=max_steps, logits=lg, scale=scale)
+    rnd = solve(instances, N=N, hp=hp, max_steps=max_steps, chunk=chunk)
+    lrn = solve(instances, N=N, hp=hp, max_steps=max_steps, logits=lg, scale=scale, chunk=chunk)
 
     def summ(r, extra=0.0):
         s = r["steps"][r["found"]]
+        t99 = r["t99"][r["t99"] >= 0]
         return dict(solved=int(r["found"].sum()), rate=float(r["found"].mean()),
                     median_steps=float(np.median(s)) if s.size else None,
                     median_seconds=(float(np.median(s)) * r["ms_per_step"] / 1e3 + extra) if s.size else None,
+                    reached99=int(t99.size), median_steps_to_99=float(np.median(t99)) if t99.size else None,
                     ms_per_step=r["ms_per_step"], mean_min_unsat=float(r["min_unsat"].mean()))
 
     out = dict(random=summ(rnd), learned=summ(lrn, t_prop), proposal_seconds=t_prop, n=len(instances))
