@@ -384,6 +384,7 @@ def exp_time_to_sat(args):
             prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
             st = ts.State(prob, 64)
             hp = ts.hparams(seed=j + 1, **kw)
+            ts.tsat_init(st.h, hp)
             ts.tsat_step_prepare(st.h, hp, 10, stop_on_sat=True)      # graph capture, once per state
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -417,7 +418,9 @@ def exp_time_to_sat(args):
             z = oracle.init_normal(inst.n_vars, 64, j + 1).astype(np.float64)
             m, v = np.zeros_like(z), np.zeros_like(z)
             for t in range(500):
-                r = oracle.step(cnf, ohp, t, z, m, v)
+                zf = z.astype(np.float32)
+                X = oracle.binarize_f32(zf, oracle.nu_f32(zf, kw["norm"]), 0)    # Eq. 2
+                r = oracle.step(cnf, ohp, t, z, m, v, X=X)
                 if (r["unsat"] == 0).any():
                     walls.append(time.perf_counter() - t0)
                     steps.append(t)
@@ -459,13 +462,35 @@ def exp_batch(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     kms = ts.tsat_profile_step(st.h, hp, 2)
+    # solve phase: fresh init, up to 1000 steps with solved instances frozen
+    ts.tsat_init(st.h, hp)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    done = 0
+    while done < 1000:
+        ts.tsat_step(st.h, hp, 100, stop_on_sat=True)
+        done += 100
+        if ts.tsat_status(st.h, n_inst)["all_done"]:
+            break
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t1
     status = ts.tsat_status(st.h, n_inst)
-    found = [x for x in status["inst"] if x["found"]]
-    _emit({"experiment": "batch", "instances": n_inst, "samples_per_instance": 64, "n_vars": info["n_vars"],
-           "n_clauses": info["n_clauses"], "nnz": info["nnz"], "lmax": info["lmax"], "steps": K,
-           "ms_per_step": ms / K, "evals_per_s": info["nnz"] * 64 * K / (ms / 1e3), "kernel_ms": kms,
-           "tuning": tun, "solved_within_steps": len(found),
-           "median_found_step": float(np.median([x["found_step"] for x in found])) if found else None,
+    by_k = {}
+    for inst, x in zip(insts, status["inst"]):
+        k = int(np.diff(inst.clause_ptr).max())
+        d = by_k.setdefault(k, {"instances": 0, "solved": 0, "steps": []})
+        d["instances"] += 1
+        if x["found"]:
+            d["solved"] += 1
+            d["steps"].append(x["found_step"])
+    for d in by_k.values():
+        d["median_found_step"] = float(np.median(d.pop("steps"))) if d["solved"] else None
+    _emit({"experiment": "batch", "metric": "literal-clause evals/s (fwd+bwd step), batched", "instances": n_inst,
+           "samples_per_instance": 64, "n_vars": info["n_vars"], "n_clauses": info["n_clauses"], "nnz": info["nnz"],
+           "lmax": info["lmax"], "steps": K, "ms_per_step": ms / K, "evals_per_s": info["nnz"] * 64 * K / (ms / 1e3),
+           "kernel_ms": {"forward": kms[0], "gamma": kms[1], "update": kms[2]}, "tuning": tun,
+           "solve": {"steps_cap": 1000, "steps_run": done, "seconds": solve_s,
+                     "solved": sum(d["solved"] for d in by_k.values()), "by_k": by_k},
            "generation_s": gen_s})
 
 

@@ -930,59 +930,84 @@ int update2_threads(int N) { return u3_layout(N).threads; }
 //     signed occurrences whose R has plane-0 bit, plane-1 bit, both bits set;
 //     gamma[R] = g0 + b0 d1 + b1 d2 + b0 b1 d3 turns the STE sum into
 //     G = (n+ - n-) g0 + C0 d1 + C1 d2 + C01 d3 (exact rewrite).
-// Sample phase: G is transposed through shared memory so that each lane owns
-// 4 consecutive samples per pass (coalesced 16-byte accesses to z, m, v); row
-// reductions (Eq. 5 dot product, new normaliser) are shuffles across the row's
-// lanes; the lane of each word assembles and writes the new bits word.
+// Sample phase: each counter register holds 4 consecutive samples, so the
+// counts go to shared memory as words indexed by sample/4 and each lane reads
+// back the words of its own 4 consecutive samples per pass (8 passes), with
+// coalesced 16-byte accesses to z, m, v (z is read in both passes; the second
+// read hits L2).  Row reductions (Eq. 5 dot product, new normaliser) are
+// shuffles across the row's lanes; each lane binarises its 4 samples into a
+// nibble and lane w assembles bits word w from the eight nibbles of its
+// samples.  The passes are rolled (unroll 2) to keep the kernel's code small:
+// with 24 warps per SM in different phases, instruction-cache misses cost
+// more than the loop overhead.
 constexpr int kCntChunk = 127;   // occurrences per byte-counter chunk (|count| <= 127)
-constexpr int kGStride = 33;     // padded row of the [32 bits][32 lanes] transposition buffer
 
 __device__ __forceinline__ float seg_sum(float x, int W) {
   for (int o = 1; o < W; o <<= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
   return x;
 }
 
-__global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, Hyper hy, int mode, const float *zin,
-                                                       float *grad, float dL) {
+// Word i (0..255) of a per-warp word array lives at cswz(i): i XOR g(i / 32),
+// g = {0, 29, 26, 7, 20, 9, 14, 19}.  Both access patterns of the kernel,
+// word 8 * lane + c (counting layout) and word 8 W r + W k + w (sample layout),
+// then hit 32 distinct banks for every W in {1, 2, ..., 32}.
+__device__ __forceinline__ int cswz(int i) {
+  const int u = (i >> 5) & 7;
+  return i ^ (((9 * u) ^ (20 * u)) & 31);
+}
+
+// C0 d1 + C1 d2 + C01 d3 for 4 samples from their count words (biased bytes)
+__device__ __forceinline__ float4 fold_counts(uint32_t w0, uint32_t w1, uint32_t w2, float4 d1, float4 d2, float4 d3) {
+  float4 r;
+  r.x = fmaf(biased_byte(w0, 0), d1.x, fmaf(biased_byte(w1, 0), d2.x, biased_byte(w2, 0) * d3.x));
+  r.y = fmaf(biased_byte(w0, 1), d1.y, fmaf(biased_byte(w1, 1), d2.y, biased_byte(w2, 1) * d3.y));
+  r.z = fmaf(biased_byte(w0, 2), d1.z, fmaf(biased_byte(w1, 2), d2.z, biased_byte(w2, 2) * d3.z));
+  r.w = fmaf(biased_byte(w0, 3), d1.w, fmaf(biased_byte(w1, 3), d2.w, biased_byte(w2, 3) * d3.w));
+  return r;
+}
+
+__device__ __forceinline__ float4 f4_add(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// MODE 0: optimisation step; MODE 1: autograd backward (gradient out, no
+// update).  BIN and NORM are the binarisation and Eq. 5 modes: one kernel per
+// combination keeps each kernel's code small and free of mode branches.
+template <int MODE, int BIN, int NORM>
+__global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, Hyper hy, const float *zin, float *grad,
+                                                       float dL) {
   extern __shared__ __align__(16) float sm3[];
   const StateHdr *hdr = sd.hdr;
-  if (mode == 0 && hdr->all_done) return;
+  if (MODE == 0 && hdr->all_done) return;
   const int N = sd.N, W = sd.W, RW = 32 / W;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rsub = lane / W, w = lane % W, rbase = rsub * W;   // row group: lanes rbase .. rbase + W - 1
-  float *gbuf = sm3 + warp * (32 * kGStride);                   // [32 bits][33]: (bit b, lane) -> b*33 + lane
-  uint32_t *cbuf = reinterpret_cast<uint32_t *>(sm3 + kWarps * 32 * kGStride) + warp * 768;  // [24][32]
-  float *tab = sm3 + kWarps * (32 * kGStride + 768);            // [4][32 bits][W words] delta table (one instance)
-  const bool one_inst = pd.n_inst == 1;
-  if (one_inst) {
-    for (int k = threadIdx.x; k < 4 * N; k += blockDim.x) {
-      const int kk = k / N, smp = k % N;
-      tab[(kk * 32 + (smp & 31)) * W + (smp >> 5)] = sd.gdelta[(size_t)kk * N + smp];
-    }
-  }
-  __syncthreads();
+  float4 *gbuf = reinterpret_cast<float4 *>(sm3) + warp * 448;                     // [8 passes][32 lanes]: G, then z(t+1)
+  uint32_t *cbuf = reinterpret_cast<uint32_t *>(gbuf + 256);                         // [3 counts][256 words]
+  uint32_t *nbuf = cbuf;                                                             // [256 nibbles] after the counts
   StepParams sp;
-  if (mode == 0) sp = *sd.sp;
-  const int64_t tcur = (mode == 0) ? sp.t : hdr->t;
+  if (MODE == 0) sp = *sd.sp;
+  const int64_t tcur = (MODE == 0) ? sp.t : hdr->t;
   const uint32_t *bsrc = cur_bits(sd, tcur);
   uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
-  const float *zsrc = (mode == 0) ? sd.z : zin;
+  const float *zsrc = (MODE == 0) ? sd.z : zin;
   const int4 *xrec4 = reinterpret_cast<const int4 *>(pd.xrec);
   const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-  // sample-phase layout: pass k (0..7) covers samples 4Wk .. 4W(k+1)-1 of the row,
-  // lane w of the row holds 4Wk + 4w + e, e = 0..3
+  const int ist = 8 * lane;          // count words this lane stores: its 32 samples
+  const int isam = rsub * 8 * W + w; // + W k: the word of this lane's samples in pass k
   for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * RW; base < pd.V; base += nwarps * RW) {
-    __syncwarp();   // the previous row's readers of gbuf / cbuf are done
+    __syncwarp();   // the previous row's readers of gbuf / zbuf are done
     const int64_t v = base + rsub;
     const bool valid = v < pd.V;
     int inst = 0;
     bool frozen = false;
     if (valid) {
       inst = __ldg(pd.var_inst + v);
-      frozen = (mode == 0) && sd.inst[inst].found;
+      frozen = (MODE == 0) && sd.inst[inst].found;
     }
     const bool act = valid && !frozen;
-    const float *gdp = sd.gdelta + (size_t)inst * 4 * N;
+    const float4 *gd4 = reinterpret_cast<const float4 *>(sd.gdelta + (size_t)inst * 4 * N);   // [4][N/4]
+    const int n4 = N >> 2;
     // ---- counting phase (lane = word w of row v)
     int nsign = 0;
     int32_t o0 = 0, o1 = 0;
@@ -991,11 +1016,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
       o1 = __ldg(pd.vptr + v + 1);
     }
     const uint32_t own = act ? __ldg(bsrc + v * W + w) : 0u;
-    bool first = true;
+    bool first = true;   // no earlier chunk folded into gbuf
     // every lane of the warp runs the same number of record rounds (shuffles)
     int32_t deg = o1 - o0, maxdeg = deg;
     for (int o = 16; o > 0; o >>= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xFFFFFFFFu, maxdeg, o));
-    for (int32_t c0 = 0; c0 < maxdeg || first; c0 += kCntChunk) {
+    for (int32_t c0 = 0;; c0 += kCntChunk) {
       const int32_t cn = act ? min(deg - c0, kCntChunk) : 0;   // this row's occurrences in the chunk
       const int32_t cmax = min(maxdeg - c0, kCntChunk);
       uint32_t cnt[4][6];
@@ -1008,7 +1033,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
         int4 myrec = make_int4(0, 0, 0, 0);
         if (r0 + w < cn) myrec = __ldg(xrec4 + o0 + c0 + r0 + w);
         const int nr = min(W, cmax - r0);
-#pragma unroll 4
+#pragma unroll 2
         for (int i = 0; i < nr; ++i) {
           int4 rc;
           rc.x = __shfl_sync(0xFFFFFFFFu, myrec.x, rbase + i);
@@ -1032,82 +1057,73 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
           }
         }
       }
-      // fold this chunk into G (gbuf, bit-major): the counts pass through shared
-      // memory so the 24 counter registers die here; sample b = 8q + j of word w
+      // cnt[q][3h + t] holds count t of samples 8q + 4h .. 8q + 4h + 3 of word w,
+      // i.e. count word (32 w + 8 q + 4 h) / 4 of the row
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int j = 0; j < 6; ++j) cbuf[(q * 6 + j) * 32 + lane] = cnt[q][j];
+        for (int j = 0; j < 6; ++j) cbuf[(j % 3) * 256 + cswz(ist + 2 * q + j / 3)] = cnt[q][j];
+      __syncwarp();
+      if (c0 + kCntChunk >= maxdeg) break;   // the last chunk is folded in pass 1 below
       if (act) {
-#pragma unroll 2
-        for (int b = 0; b < 32; ++b) {
-          const int q = b >> 3, j = b & 7, h = j < 4 ? 0 : 3;
-          const uint32_t bq = (uint32_t)(j & 3);
-          const float c0f = biased_byte(cbuf[(q * 6 + h + 0) * 32 + lane], bq);
-          const float c1f = biased_byte(cbuf[(q * 6 + h + 1) * 32 + lane], bq);
-          const float c2f = biased_byte(cbuf[(q * 6 + h + 2) * 32 + lane], bq);
-          float d1, d2, d3;
-          if (one_inst) {
-            d1 = tab[(1 * 32 + b) * W + w]; d2 = tab[(2 * 32 + b) * W + w]; d3 = tab[(3 * 32 + b) * W + w];
-          } else {
-            const int smp = 32 * w + b;
-            d1 = __ldg(gdp + N + smp); d2 = __ldg(gdp + 2 * N + smp); d3 = __ldg(gdp + 3 * N + smp);
-          }
-          const float add = fmaf(c0f, d1, fmaf(c1f, d2, c2f * d3));
-          gbuf[b * kGStride + lane] = first ? add : gbuf[b * kGStride + lane] + add;
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k) {
+          const int ci = cswz(isam + W * k), s4 = W * k + w;
+          const float4 add = fold_counts(cbuf[ci], cbuf[256 + ci], cbuf[512 + ci], __ldg(gd4 + n4 + s4),
+                                         __ldg(gd4 + 2 * n4 + s4), __ldg(gd4 + 3 * n4 + s4));
+          gbuf[k * 32 + lane] = first ? add : f4_add(gbuf[k * 32 + lane], add);
         }
       }
       first = false;
+      __syncwarp();   // the count words are read before the next chunk stores
     }
-    if (act) {
-#pragma unroll 4
-      for (int b = 0; b < 32; ++b) {
-        const float g0 = one_inst ? tab[b * W + w] : __ldg(gdp + 32 * w + b);
-        gbuf[b * kGStride + lane] = fmaf((float)nsign, g0, gbuf[b * kGStride + lane]);
-      }
-    }
-    __syncwarp();
-    // ---- sample phase: lane w holds samples s = 4Wk + 4w + e of row v
-    // G of sample s lives at gbuf[(s % 32) * 33 + rbase + s / 32]
+    // ---- sample phase, pass 1: G of samples s = 4Wk + 4w + e, Eq. 5 dot product
     const float nu = act ? sd.nu[v] : 1.0f;
     const float rnu = __frcp_rn(nu);
     const size_t rowoff = (size_t)v * N;
+    const float4 *z4p = reinterpret_cast<const float4 *>(zsrc + rowoff);
     float part = 0.f;
-    if (act && hy.norm != TSAT_NORM_NONE) {
-#pragma unroll 2
+    if (act) {
+      const float ns = (float)nsign;
+#pragma unroll 1
       for (int k = 0; k < 8; ++k) {
-        const int s = 4 * W * k + 4 * w;
-        const float4 z4 = __ldg(reinterpret_cast<const float4 *>(zsrc + rowoff + s));
-        const float *gp = gbuf + (s & 31) * kGStride + rbase + (s >> 5);
-        part = fmaf(gp[0], z4.x, part);
-        part = fmaf(gp[kGStride], z4.y, part);
-        part = fmaf(gp[2 * kGStride], z4.z, part);
-        part = fmaf(gp[3 * kGStride], z4.w, part);
+        const int s4 = W * k + w, ci = cswz(isam + W * k);
+        const float4 z4 = __ldg(z4p + s4);
+        const float4 add = fold_counts(cbuf[ci], cbuf[256 + ci], cbuf[512 + ci], __ldg(gd4 + n4 + s4),
+                                       __ldg(gd4 + 2 * n4 + s4), __ldg(gd4 + 3 * n4 + s4));
+        float4 g = first ? add : f4_add(gbuf[k * 32 + lane], add);
+        const float4 g0 = __ldg(gd4 + s4);
+        g = make_float4(fmaf(ns, g0.x, g.x), fmaf(ns, g0.y, g.y), fmaf(ns, g0.z, g.z), fmaf(ns, g0.w, g.w));
+        gbuf[k * 32 + lane] = g;
+        part = fmaf(g.x, z4.x, part);
+        part = fmaf(g.y, z4.y, part);
+        part = fmaf(g.z, z4.z, part);
+        part = fmaf(g.w, z4.w, part);
       }
     }
+    if (NORM == TSAT_NORM_NONE) part = 0.f;
     const float dot = seg_sum(part, W);
     const float c2 = dot * rnu * rnu * (1.0f / (float)N);
+    // ---- pass 2: Eq. 5 chain rule and AdamW (or the gradient for the autograd backward)
     float psum = 0.f;
     if (act) {
-#pragma unroll 2
+#pragma unroll 1
       for (int k = 0; k < 8; ++k) {
-        const int s = 4 * W * k + 4 * w;
-        const size_t off = rowoff + s;
-        float *gp = gbuf + (s & 31) * kGStride + rbase + (s >> 5);
-        const float4 z4 = __ldg(reinterpret_cast<const float4 *>(zsrc + off));
+        const size_t off = rowoff + 4 * (W * k + w);
+        const float4 g4 = gbuf[k * 32 + lane], z4 = __ldg(z4p + W * k + w);
         const float zq[4] = {z4.x, z4.y, z4.z, z4.w};
+        const float Gq[4] = {g4.x, g4.y, g4.z, g4.w};
         float gq[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const float G = gp[e * kGStride];
-          if (hy.norm == TSAT_NORM_NONE) {
-            gq[e] = G;
+          if constexpr (NORM == TSAT_NORM_NONE) {
+            gq[e] = Gq[e];
           } else {
-            const float dmu = (hy.norm == TSAT_NORM_ABSMEAN) ? (float)((zq[e] > 0.f) - (zq[e] < 0.f)) : 1.0f;
-            gq[e] = G * rnu - c2 * dmu;
+            const float dmu = (NORM == TSAT_NORM_ABSMEAN) ? (float)((zq[e] > 0.f) - (zq[e] < 0.f)) : 1.0f;
+            gq[e] = Gq[e] * rnu - c2 * dmu;
           }
         }
-        if (mode == 1) {
+        if constexpr (MODE == 1) {
           *reinterpret_cast<float4 *>(grad + off) = make_float4(dL * gq[0], dL * gq[1], dL * gq[2], dL * gq[3]);
           continue;
         }
@@ -1120,42 +1136,51 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
           const float sq = vq[e] > 0.f ? vq[e] * rsqrtf(vq[e]) : 0.f;
           const float denom = sq * sp.inv_sqrt_bc2 + hy.eps;
           zn[e] = zq[e] * sp.decay - sp.step_size * __fdividef(mq[e], denom);
-          gp[e * kGStride] = zn[e];
-          psum += (hy.norm == TSAT_NORM_ABSMEAN) ? fabsf(zn[e]) : zn[e];
+          psum += (NORM == TSAT_NORM_ABSMEAN) ? fabsf(zn[e]) : zn[e];
         }
-        st_cs(sd.z + off, make_float4(zn[0], zn[1], zn[2], zn[3]));
+        const float4 z1 = make_float4(zn[0], zn[1], zn[2], zn[3]);
+        gbuf[k * 32 + lane] = z1;   // G of this pass is consumed
+        st_cs(sd.z + off, z1);
         st_cs(sd.m + off, make_float4(mq[0], mq[1], mq[2], mq[3]));
         st_cs(sd.v + off, make_float4(vq[0], vq[1], vq[2], vq[3]));
       }
     }
-    if (mode == 1) continue;
+    if constexpr (MODE == 1) continue;
     const float tot = seg_sum(psum, W);
-    __syncwarp();
-    // ---- Eq. 2 / Philox bits of step t+1: lane w assembles word w (bits b of gbuf)
+    __syncwarp();   // every lane's count words are consumed: their space takes the nibbles
+    // ---- Eq. 2 / Philox bits of step t+1: the lane's samples of pass k form
+    // nibble (Wk + w) of the row, stored at word isam + W k; lane w then joins
+    // nibbles 8w .. 8w + 7 (its counting-layout words) into bits word w
     if (valid && frozen) bdst[v * W + w] = bsrc[v * W + w];
+    const float nun = (NORM == TSAT_NORM_NONE) ? 1.0f : guard_nu(tot / (float)N);
+    const float rnn = __frcp_rn(nun);
     if (act) {
-      const float nun = (hy.norm == TSAT_NORM_NONE) ? 1.0f : guard_nu(tot / (float)N);
-      const float rnn = __frcp_rn(nun);
-      uint32_t word = 0;
-      if (hy.binarize == TSAT_BIN_PHILOX) {
-#pragma unroll 2
-        for (int h = 0; h < 8; ++h) {
-          const uint4 r = philox4x32_10(make_uint4((uint32_t)(8 * w + h), (uint32_t)v, (uint32_t)(tcur + 1), kTagBin),
+#pragma unroll 1
+      for (int k = 0; k < 8; ++k) {
+        const float4 z4 = gbuf[k * 32 + lane];
+        const float zq[4] = {z4.x, z4.y, z4.z, z4.w};
+        uint32_t nib = 0;
+        if constexpr (BIN == TSAT_BIN_PHILOX) {
+          const uint4 r = philox4x32_10(make_uint4((uint32_t)(W * k + w), (uint32_t)v, (uint32_t)(tcur + 1), kTagBin),
                                         hy.key0, hy.key1);
           const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            word |= binarize_one(__fmul_rn(gbuf[(4 * h + e) * kGStride + lane], rnn), TSAT_BIN_PHILOX, hy.bin_c, rw[e])
-                    << (4 * h + e);
+          for (int e = 0; e < 4; ++e) nib |= binarize_one(__fmul_rn(zq[e], rnn), TSAT_BIN_PHILOX, hy.bin_c, rw[e]) << e;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) nib |= (__fmul_rn(zq[e], rnn) > 0.0f ? 1u : 0u) << e;
         }
-      } else {
-#pragma unroll 8
-        for (int b = 0; b < 32; ++b) word |= (__fmul_rn(gbuf[b * kGStride + lane], rnn) > 0.0f ? 1u : 0u) << b;
+        nbuf[cswz(isam + W * k)] = nib;
       }
+    }
+    __syncwarp();
+    if (act) {
+      uint32_t word = 0;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) word |= nbuf[cswz(ist + c)] << (4 * c);
       bdst[v * W + w] = word;
       if (w == 0) sd.nu[v] = nun;
     }
-    __syncwarp();
   }
 }
 
@@ -1164,13 +1189,14 @@ int update3_smem_bytes(int N);
 int update_blocks_per_sm(const ProbDev &pd, const StateDev &sd) {
   int nb = 0;
   if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_fixed4)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_update3, kBlock, update3_smem_bytes(sd.N));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_update3<0, TSAT_BIN_PHILOX, TSAT_NORM_SIGNED_MEAN>, kBlock,
+                                                  update3_smem_bytes(sd.N));
   else
     nb = 3;
   return nb > 0 ? nb : 1;
 }
 
-int update3_smem_bytes(int N) { return (kWarps * (32 * kGStride + 768) + 4 * N) * (int)sizeof(float); }
+int update3_smem_bytes(int N) { return kWarps * 1792 * (int)sizeof(float); }
 
 // ------------------------------------------------------------------ exact check (Sec. III-A)
 // unsat_i = #clauses whose literal words OR to 0 at bit i.  Same warp
@@ -1293,11 +1319,49 @@ static cudaError_t upd_launch(const ProbDev &pd, const StateDev &sd, const Hyper
   return cudaGetLastError();
 }
 
+template <typename F>
+static void for_each_update3(F f) {
+  f(k_update3<0, TSAT_BIN_DET, TSAT_NORM_SIGNED_MEAN>);
+  f(k_update3<0, TSAT_BIN_DET, TSAT_NORM_ABSMEAN>);
+  f(k_update3<0, TSAT_BIN_DET, TSAT_NORM_NONE>);
+  f(k_update3<0, TSAT_BIN_PHILOX, TSAT_NORM_SIGNED_MEAN>);
+  f(k_update3<0, TSAT_BIN_PHILOX, TSAT_NORM_ABSMEAN>);
+  f(k_update3<0, TSAT_BIN_PHILOX, TSAT_NORM_NONE>);
+  f(k_update3<1, TSAT_BIN_DET, TSAT_NORM_SIGNED_MEAN>);
+  f(k_update3<1, TSAT_BIN_DET, TSAT_NORM_ABSMEAN>);
+  f(k_update3<1, TSAT_BIN_DET, TSAT_NORM_NONE>);
+}
+
+template <int MODE, int BIN>
+static cudaError_t launch_update3_n(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const float *zin,
+                                    float *grad, float dL, int grid, cudaStream_t st) {
+  const int smem = update3_smem_bytes(sd.N);
+  switch (hy.norm) {
+    case TSAT_NORM_SIGNED_MEAN:
+      k_update3<MODE, BIN, TSAT_NORM_SIGNED_MEAN><<<grid, kBlock, smem, st>>>(pd, sd, hy, zin, grad, dL);
+      break;
+    case TSAT_NORM_ABSMEAN:
+      k_update3<MODE, BIN, TSAT_NORM_ABSMEAN><<<grid, kBlock, smem, st>>>(pd, sd, hy, zin, grad, dL);
+      break;
+    default:
+      k_update3<MODE, BIN, TSAT_NORM_NONE><<<grid, kBlock, smem, st>>>(pd, sd, hy, zin, grad, dL);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_update3(const ProbDev &pd, const StateDev &sd, const Hyper &hy, int mode, const float *zin,
+                                  float *grad, float dL, int grid, cudaStream_t st) {
+  if (mode == 1) return launch_update3_n<1, TSAT_BIN_DET>(pd, sd, hy, zin, grad, dL, grid, st);
+  if (hy.binarize == TSAT_BIN_PHILOX) return launch_update3_n<0, TSAT_BIN_PHILOX>(pd, sd, hy, zin, grad, dL, grid, st);
+  return launch_update3_n<0, TSAT_BIN_DET>(pd, sd, hy, zin, grad, dL, grid, st);
+}
+
 void prepare_update_attrs(int lmax) {
   const int P = planes_for(lmax);
   const int bytes = 160 * 1024;
   cudaFuncSetAttribute(k_update2, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_update3, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  for_each_update3([bytes](auto fn) { cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
   cudaFuncSetAttribute(k_update<1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   switch (P) {
     case 1: cudaFuncSetAttribute(k_update<1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); break;
@@ -1313,8 +1377,7 @@ cudaError_t launch_update(const ProbDev &pd, const StateDev &sd, const Hyper &hy
   const int P = planes_for(pd.lmax);
   if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_fixed4) {
     (void)rpi;
-    k_update3<<<grid, kBlock, update3_smem_bytes(sd.N), st>>>(pd, sd, hy, mode, zin, grad, dL);
-    return cudaGetLastError();
+    return launch_update3(pd, sd, hy, mode, zin, grad, dL, grid, st);
   }
   if (sd.layer == TSAT_LAYER_RELAXED) return upd_launch<1, true, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);
   switch (P) {
