@@ -1007,6 +1007,14 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
     }
     const bool act = valid && !frozen;
     const float4 *gd4 = reinterpret_cast<const float4 *>(sd.gdelta + (size_t)inst * 4 * N);   // [4][N/4]
+    if (MODE == 0 && act && w == 0) {
+      // the row's z, m, v stream into L2 while the occurrences are counted
+      const size_t ro = (size_t)v * N;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(zsrc + ro), "r"(N * 4) : "memory");
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sd.m + ro), "r"(N * 4) : "memory");
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sd.v + ro), "r"(N * 4) : "memory");
+    }
+
     const int n4 = N >> 2;
     // ---- counting phase (lane = word w of row v)
     int nsign = 0;
