@@ -484,7 +484,8 @@ def exp_batch(args):
             d["solved"] += 1
             d["steps"].append(x["found_step"])
     for d in by_k.values():
-        d["median_found_step"] = float(np.median(d.pop("steps"))) if d["solved"] else None
+        steps = d.pop("steps")
+        d["median_found_step"] = float(np.median(steps)) if steps else None
     _emit({"experiment": "batch", "metric": "literal-clause evals/s (fwd+bwd step), batched", "instances": n_inst,
            "samples_per_instance": 64, "n_vars": info["n_vars"], "n_clauses": info["n_clauses"], "nnz": info["nnz"],
            "lmax": info["lmax"], "steps": K, "ms_per_step": ms / K, "evals_per_s": info["nnz"] * 64 * K / (ms / 1e3),

@@ -91,7 +91,7 @@ __global__ void k_gcol(ProbDev pd, StateDev sd, Hyper hy, int inst, const int32_
         r += (int)(((bits[(size_t)(lit >> 1) * sd.W + word] >> bit) & 1u) ^ (uint32_t)(lit & 1));
       }
       G += (h & 1) ? -gt[r] : gt[r];
-      p += pd.rec_fixed4 ? 4 : len;
+      p += pd.rec_stride ? pd.rec_stride : len;
     }
     gcol[vl] = G;
   }

@@ -22,7 +22,8 @@ struct ProbDev {
   int32_t n_inst, V, C, lmax;
   int64_t nnz;
   int32_t n_items;
-  int32_t rec_fixed4;      // 1: records are int4 {hdr, lit, lit, 0} at xptr[v] = 4 vptr[v] (lmax <= 3)
+  int32_t rec_stride;      // 4: {hdr, lit, lit, 0} per occurrence (lmax <= 3); 8: {hdr, lit x 6, 0} (lmax <= 7);
+                           // 0: variable length; fixed records sit at xptr[v] = stride * vptr[v]
   const int32_t *cptr;     // [C+1] clause offsets into clit
   const int32_t *clit;     // [nnz] (global var << 1) | negated
   const int64_t *xptr;     // [V+1] offsets (int32 words) into xrec, multiples of 4
@@ -156,51 +157,11 @@ __device__ __forceinline__ uint32_t binarize_one(float zt, int mode, float c, ui
 
 __device__ __forceinline__ int32_t load_nc(const int32_t *p) { return __ldg(p); }
 
-// ---------------------------------------------------------------- TMA (1-D bulk) + mbarrier
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+// ---------------------------------------------------------------- L2 prefetch
+// Bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) into L2; a hint
+// only: no shared memory, no barrier, nothing waits on it.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void mbar_init_fence() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-// 1-D bulk copy global -> shared (16-byte aligned addresses, size multiple of 16)
-__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: gives up after `limit` polls (each poll may suspend briefly).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t it = 0; it < limit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-// Ampere-style asynchronous 4-byte global -> shared copy (per-thread groups)
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-}
-constexpr uint32_t kWaitLimit = 1u << 22;
-constexpr int32_t kErrTimeout = 1;
 
 }  // namespace tsat

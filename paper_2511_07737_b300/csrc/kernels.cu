@@ -532,391 +532,12 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
   }
 }
 
-// ------------------------------------------------------------------ fused update, lmax <= 3
-// TMA-staged variant for clause length <= 3 (R in 0..3, two bit planes).
-// A row group of N/8 threads owns one variable row; a thread owns 8 samples
-// (one byte of a 32-sample word).
-//   * the next row's z, m, v and int4 occurrence records stream into shared
-//     memory with 1-D bulk copies (cp.async.bulk + mbarrier, double buffered)
-//     while the current row is processed;
-//   * stage A: R bit-planes once per (occurrence, 32-sample word);
-//   * stage B: each thread counts, byte-packed (bias 128) for its 8 samples,
-//     the signed occurrences with plane-0 bit, plane-1 bit and both bits
-//     set; with gamma[R] = g0 + b0 d1 + b1 d2 + b0 b1 d3 the STE gradient is
-//     G = (n+ - n-) g0 + C0 d1 + C1 d2 + C01 d3 (an exact rewrite of the sum).
-constexpr int kOcap = 32;    // occurrences per chunk (byte counters stay in 128 +- 32)
-
-struct U2Layout {
-  int GT, RPB, threads, ocap, zbytes, rec_bytes, plane_words, group_bytes;
-};
-__host__ __device__ __forceinline__ U2Layout u2_layout(int N) {
-  U2Layout L;
-  L.GT = N >> 3;
-  L.RPB = kBlock / L.GT < 16 ? kBlock / L.GT : 16;
-  L.threads = L.RPB * L.GT;
-  L.ocap = kOcap;
-  L.zbytes = N * 4;
-  L.rec_bytes = L.ocap * 16;
-  L.plane_words = L.ocap * 2 * (N / 32);
-  // 2 stages x (z, m, v, records) + planes + 8 reduction floats + 2 mbarriers
-  L.group_bytes = 2 * (3 * L.zbytes + L.rec_bytes) + L.plane_words * 4 + 8 * 4 + 16;
-  L.group_bytes = (L.group_bytes + 127) & ~127;
-  return L;
-}
-
-// Group of GT threads inside a block of `threads` threads.
-struct Group8 {
-  int GT, grp, gl, lane, threads;
-  __device__ __forceinline__ unsigned mask() const {
-    return (GT >= 32) ? 0xFFFFFFFFu : (((1u << GT) - 1u) << (lane & ~(GT - 1)));
-  }
-  __device__ __forceinline__ void sync() const {
-    if (GT <= 32) __syncwarp(mask());
-    else if (GT == threads) __syncthreads();
-    else asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(GT) : "memory");
-  }
-  __device__ __forceinline__ float sum(float x, float *red) const {
-    const int span = GT < 32 ? GT : 32;
-    const unsigned m = mask();
-    for (int o = 1; o < span; o <<= 1) x += __shfl_xor_sync(m, x, o);
-    if (GT <= 32) return x;
-    sync();
-    if ((gl & 31) == 0) red[gl >> 5] = x;
-    sync();
-    float s = 0.0f;
-    for (int k = 0; k < (GT >> 5); ++k) s += red[k];
-    return s;
-  }
-  // One barrier: the caller alternates `slot` between consecutive reductions,
-  // so a slot is never rewritten before every warp has read it.
-  __device__ __forceinline__ float sum1(float x, float *red, int slot) const {
-    const int span = GT < 32 ? GT : 32;
-    const unsigned m = mask();
-    for (int o = 1; o < span; o <<= 1) x += __shfl_xor_sync(m, x, o);
-    if (GT <= 32) return x;
-    float *r = red + 4 * slot;
-    if ((gl & 31) == 0) r[gl >> 5] = x;
-    sync();
-    float s = 0.0f;
-    for (int k = 0; k < (GT >> 5); ++k) s += r[k];
-    return s;
-  }
-};
-
+// 0/1 bytes from the 4 bits of n (bit b -> byte b)
 __device__ __forceinline__ uint32_t spread4(uint32_t n) { return (n * 0x00204081u) & 0x01010101u; }
 // (byte q of x) - 128 as an exact float: 2^23 + byte assembled in the mantissa
 __device__ __forceinline__ float biased_byte(uint32_t x, uint32_t q) {
   return __int_as_float((int)__byte_perm(x, 0x4B000000u, 0x7440u | q)) - 8388736.0f;
 }
-
-// Per-group shared memory of the pipelined update (offsets in bytes).
-struct U3Layout {
-  int GT, RPB, threads, ocap, zmv, rec, gp, own, red, bar, group_bytes;
-};
-__host__ __device__ __forceinline__ U3Layout u3_layout(int N) {
-  U3Layout L;
-  L.GT = N >> 3;
-  L.RPB = kBlock / L.GT < 16 ? kBlock / L.GT : 16;
-  L.threads = L.RPB * L.GT;
-  L.ocap = kOcap;
-  const int W = N / 32;
-  int o = 0;
-  L.zmv = o;  o += 3 * N * 4;                       // z, m, v of the current row (single buffer)
-  L.rec = o;  o += 3 * L.ocap * 16;                 // records, three rows deep
-  L.gp = o;   o += 2 * L.ocap * 2 * W * 4;          // gathered words -> bit planes, two rows deep
-  L.own = o;  o += 2 * (L.GT / W) * W * 4;          // the row's own bits per task thread, two rows deep
-  o = (o + 15) & ~15;
-  L.red = o;  o += 8 * 4;
-  L.bar = o;  o += 4 * 8;                           // zmv barrier + 3 record barriers
-  L.group_bytes = (o + 127) & ~127;
-  return L;
-}
-
-__global__ void __launch_bounds__(kBlock, 3) k_update2(ProbDev pd, StateDev sd, Hyper hy, int mode, const float *zin,
-                                                       float *grad, float dL, int rows_per_item) {
-  extern __shared__ __align__(128) unsigned char smem2[];
-  const StateHdr *hdr = sd.hdr;
-  if (mode == 0 && hdr->all_done) return;
-  const int N = sd.N, W = sd.W;
-  const U3Layout L = u3_layout(N);
-  const int GT = L.GT, RPB = L.RPB, OC = L.ocap;
-  Group8 g{GT, (int)threadIdx.x / GT, (int)threadIdx.x % GT, (int)(threadIdx.x & 31), L.threads};
-  unsigned char *gb = smem2 + (size_t)g.grp * L.group_bytes;
-  float *zmv = reinterpret_cast<float *>(gb + L.zmv);
-  int4 *recb = reinterpret_cast<int4 *>(gb + L.rec);
-  uint32_t *gpb = reinterpret_cast<uint32_t *>(gb + L.gp);
-  uint32_t *ownb = reinterpret_cast<uint32_t *>(gb + L.own);
-  float *red = reinterpret_cast<float *>(gb + L.red);
-  uint64_t *bar_z = reinterpret_cast<uint64_t *>(gb + L.bar);
-  uint64_t *bar_r = bar_z + 1;
-  const bool leader = g.gl == 0;
-  if (leader) {
-    mbar_init(bar_z, 1);
-    for (int q = 0; q < 3; ++q) mbar_init(&bar_r[q], 1);
-    mbar_init_fence();
-  }
-  __syncthreads();
-  StepParams sp;
-  if (mode == 0) sp = *sd.sp;
-  const int64_t tcur = (mode == 0) ? sp.t : hdr->t;
-  const uint32_t *bsrc = cur_bits(sd, tcur);
-  uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
-  const float b1 = hy.beta1, b2 = hy.beta2, omb1 = hy.omb1, omb2 = hy.omb2;
-  const float *zsrc = (mode == 0) ? sd.z : zin;
-  const int s0 = g.gl * 8, w = s0 >> 5, sh = s0 & 31;
-  const uint32_t bsel = 0x4440u | (uint32_t)(sh >> 3);   // byte sh/8 of a word -> low byte
-  const int tw = g.gl % W, to = g.gl / W, ostep = GT / W;   // (occurrence, word) task layout
-  const int64_t NG = (int64_t)gridDim.x * RPB;
-  const int64_t n_items = ((int64_t)pd.V + rows_per_item - 1) / rows_per_item;
-  int64_t it_next = (int64_t)blockIdx.x * RPB + g.grp;
-  auto first_row = [&]() -> int64_t { return it_next < n_items ? it_next * rows_per_item : -1; };
-  auto next_row = [&](int64_t vv) -> int64_t {
-    if (vv < 0) return -1;
-    if (vv + 1 < min((int64_t)pd.V, (it_next + 1) * rows_per_item)) return vv + 1;
-    it_next += NG;
-    return it_next < n_items ? it_next * rows_per_item : -1;
-  };
-  // ---- asynchronous pieces
-  auto issue_rec = [&](int64_t vv, int slot) {
-    const int32_t o0 = __ldg(pd.vptr + vv), o1 = __ldg(pd.vptr + vv + 1);
-    const int nrec = min(o1 - o0, OC);
-    fence_proxy_async();
-    mbar_expect_tx(&bar_r[slot], 16u * (uint32_t)nrec);
-    if (nrec > 0) tma_load_1d(recb + slot * OC, pd.xrec + 4 * (int64_t)o0, 16u * nrec, &bar_r[slot]);
-  };
-  auto issue_zmv = [&](int64_t vv) {
-    fence_proxy_async();
-    mbar_expect_tx(bar_z, (mode == 0 ? 3u : 1u) * (uint32_t)N * 4u);
-    tma_load_1d(zmv, zsrc + (size_t)vv * N, N * 4, bar_z);
-    if (mode == 0) {
-      tma_load_1d(zmv + N, sd.m + (size_t)vv * N, N * 4, bar_z);
-      tma_load_1d(zmv + 2 * N, sd.v + (size_t)vv * N, N * 4, bar_z);
-    }
-  };
-  // gathers of the other literals' words of row vv (first chunk) into gp slot
-  auto gather = [&](int64_t vv, const int4 *rc, int nc, uint32_t *gp, uint32_t *own) {
-    cp_async4(own + to * W + tw, bsrc + vv * W + tw);
-    for (int o = to; o < nc; o += ostep) {
-      const int4 r = rc[o];
-      const uint32_t len = (uint32_t)r.x >> 1;
-      uint32_t *d = gp + (o * 2) * W + tw;
-      if (len > 1) cp_async4(d, bsrc + (size_t)(r.y >> 1) * W + tw); else d[0] = 0u;
-      if (len > 2) cp_async4(d + W, bsrc + (size_t)(r.z >> 1) * W + tw); else d[W] = 0u;
-    }
-  };
-  // gathered words -> R bit planes, in place
-  auto planes_of = [&](const int4 *rc, int nc, uint32_t *gp, const uint32_t *own) {
-    const uint32_t ow = own[to * W + tw];
-    for (int o = to; o < nc; o += ostep) {
-      const int4 r = rc[o];
-      const uint32_t len = (uint32_t)r.x >> 1;
-      uint32_t *d = gp + (o * 2) * W + tw;
-      const uint32_t a = ow ^ (0u - (uint32_t)(r.x & 1));
-      const uint32_t bb = len > 1 ? d[0] ^ (0u - (uint32_t)(r.y & 1)) : 0u;
-      const uint32_t cc = len > 2 ? d[W] ^ (0u - (uint32_t)(r.z & 1)) : 0u;
-      d[0] = a ^ bb ^ cc;
-      d[W] = (a & bb) | (cc & (a ^ bb));
-    }
-  };
-  auto nocc = [&](int64_t vv) -> int { return vv < 0 ? 0 : min(__ldg(pd.vptr + vv + 1) - __ldg(pd.vptr + vv), OC); };
-  // ---- prologue: row 0 records + z/m/v, row 1 records; row 0 planes
-  int64_t v = first_row();
-  int64_t v1 = next_row(v);
-  if (v >= 0 && leader) {
-    issue_rec(v, 0);
-    issue_zmv(v);
-    if (v1 >= 0) issue_rec(v1, 1);
-  }
-  if (v >= 0) {
-    if (!mbar_wait_bounded(&bar_r[0], 0, kWaitLimit)) { sd.hdr->err = kErrTimeout; return; }
-    const int nc0 = nocc(v);
-    gather(v, recb, nc0, gpb, ownb);
-    cp_async_wait_all();
-    planes_of(recb, nc0, gpb, ownb);
-    g.sync();
-  }
-  int cur_inst = -1;
-  bool frozen = false;
-  const float *gdp = nullptr;
-  uint32_t k = 0;
-  int64_t vn = v1;
-  while (v >= 0) {
-    const int64_t vnn = next_row(vn);
-    const int rs = k % 3, rs1 = (k + 1) % 3, ps = k & 1;
-    if (vnn >= 0 && leader) issue_rec(vnn, (k + 2) % 3);
-    // start the gathers of row k+1 (their records arrived one row ago)
-    const int nc1 = nocc(vn);
-    if (vn >= 0) {
-      if (!mbar_wait_bounded(&bar_r[rs1], ((k + 1) / 3) & 1, kWaitLimit)) { sd.hdr->err = kErrTimeout; return; }
-      gather(vn, recb + rs1 * OC, nc1, gpb + (ps ^ 1) * OC * 2 * W, ownb + (ps ^ 1) * ostep * W);
-    }
-    const int inst = __ldg(pd.var_inst + v);
-    if (inst != cur_inst) {
-      cur_inst = inst;
-      frozen = (mode == 0) && sd.inst[inst].found;
-      gdp = sd.gdelta + (size_t)inst * 4 * N + s0;
-    }
-    const int32_t o0 = __ldg(pd.vptr + v), o1 = __ldg(pd.vptr + v + 1);
-    const float nu = sd.nu[v];
-    float G[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) G[q] = 0.f;
-    int nsign = 0;
-    if (!frozen) {
-      int4 *rc = recb + rs * OC;
-      uint32_t *gp = gpb + ps * OC * 2 * W;
-      for (int32_t c0 = o0; c0 < o1; c0 += OC) {
-        const int nc = min(OC, o1 - c0);
-        if (c0 != o0) {  // rows longer than one chunk: synchronous load, gather and planes
-          g.sync();
-          for (int q = g.gl; q < nc; q += GT) rc[q] = __ldg(reinterpret_cast<const int4 *>(pd.xrec) + c0 + q);
-          g.sync();
-          gather(v, rc, nc, gp, ownb + ps * ostep * W);
-          cp_async_wait_all();
-          planes_of(rc, nc, gp, ownb + ps * ostep * W);
-          g.sync();
-        }
-        // stage B: per-byte signed counts, bias 128 (|count| <= kOcap keeps bytes apart)
-        uint32_t A0 = 0x80808080u, A1 = 0x80808080u, A2 = 0x80808080u;   // samples 0-3
-        uint32_t B0 = 0x80808080u, B1 = 0x80808080u, B2 = 0x80808080u;   // samples 4-7
-        const uint32_t *pw = gp + w;
-        for (int o = 0; o < nc; ++o, pw += 2 * W) {
-          const uint32_t sg = (rc[o].x & 1) ? 0xFFFFFFFFu : 1u;     // -1 or +1 as a multiplier
-          const uint32_t y0 = __byte_perm(pw[0], 0, bsel);
-          const uint32_t y1 = __byte_perm(pw[W], 0, bsel);
-          const uint32_t x0l = spread4(y0 & 15u), x0h = spread4(y0 >> 4);
-          const uint32_t x1l = spread4(y1 & 15u), x1h = spread4(y1 >> 4);
-          A0 += x0l * sg; A1 += x1l * sg; A2 += (x0l & x1l) * sg;
-          B0 += x0h * sg; B1 += x1h * sg; B2 += (x0h & x1h) * sg;
-          nsign += (int)sg;
-        }
-        const float4 d1a = __ldg(reinterpret_cast<const float4 *>(gdp + N)), d1b = __ldg(reinterpret_cast<const float4 *>(gdp + N + 4));
-        const float4 d2a = __ldg(reinterpret_cast<const float4 *>(gdp + 2 * N)), d2b = __ldg(reinterpret_cast<const float4 *>(gdp + 2 * N + 4));
-        const float4 d3a = __ldg(reinterpret_cast<const float4 *>(gdp + 3 * N)), d3b = __ldg(reinterpret_cast<const float4 *>(gdp + 3 * N + 4));
-        const float dd1[8] = {d1a.x, d1a.y, d1a.z, d1a.w, d1b.x, d1b.y, d1b.z, d1b.w};
-        const float dd2[8] = {d2a.x, d2a.y, d2a.z, d2a.w, d2b.x, d2b.y, d2b.z, d2b.w};
-        const float dd3[8] = {d3a.x, d3a.y, d3a.z, d3a.w, d3b.x, d3b.y, d3b.z, d3b.w};
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const uint32_t qq = (uint32_t)(q & 3);
-          const float c0f = biased_byte(q < 4 ? A0 : B0, qq);
-          const float c1f = biased_byte(q < 4 ? A1 : B1, qq);
-          const float c2f = biased_byte(q < 4 ? A2 : B2, qq);
-          G[q] = fmaf(c0f, dd1[q], fmaf(c1f, dd2[q], fmaf(c2f, dd3[q], G[q])));
-        }
-      }
-      const float4 g0a = __ldg(reinterpret_cast<const float4 *>(gdp)), g0b = __ldg(reinterpret_cast<const float4 *>(gdp + 4));
-      const float gg0[8] = {g0a.x, g0a.y, g0a.z, g0a.w, g0b.x, g0b.y, g0b.z, g0b.w};
-#pragma unroll
-      for (int q = 0; q < 8; ++q) G[q] = fmaf((float)nsign, gg0[q], G[q]);
-    }
-    // ---- z, m, v of this row
-    if (!mbar_wait_bounded(bar_z, k & 1, kWaitLimit)) { sd.hdr->err = kErrTimeout; return; }
-    if (frozen) {  // frozen instance: keep its model
-      if ((g.gl & 3) == 0) bdst[v * W + w] = bsrc[v * W + w];
-    } else {
-      const float4 za = *reinterpret_cast<const float4 *>(zmv + s0), zb = *reinterpret_cast<const float4 *>(zmv + s0 + 4);
-      const float zq[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
-      float mq[8], vq[8];
-      if (mode == 0) {
-        const float4 ma = *reinterpret_cast<const float4 *>(zmv + N + s0), mb = *reinterpret_cast<const float4 *>(zmv + N + s0 + 4);
-        const float4 va = *reinterpret_cast<const float4 *>(zmv + 2 * N + s0), vb = *reinterpret_cast<const float4 *>(zmv + 2 * N + s0 + 4);
-        mq[0] = ma.x; mq[1] = ma.y; mq[2] = ma.z; mq[3] = ma.w; mq[4] = mb.x; mq[5] = mb.y; mq[6] = mb.z; mq[7] = mb.w;
-        vq[0] = va.x; vq[1] = va.y; vq[2] = va.z; vq[3] = va.w; vq[4] = vb.x; vq[5] = vb.y; vq[6] = vb.z; vq[7] = vb.w;
-      }
-      // z, m, v are in registers: the buffer can take the next row now
-      g.sync();
-      if (vn >= 0 && leader) issue_zmv(vn);
-      // ---- chain rule through Eq. 5
-      float gq[8];
-      if (hy.norm == TSAT_NORM_NONE) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) gq[q] = G[q];
-      } else {
-        float part = 0.f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) part = fmaf(G[q], zq[q], part);
-        const float dot = g.sum1(part, red, 0);
-        const float rnu = __frcp_rn(nu);
-        const float c2 = dot * rnu * rnu * (1.0f / (float)N);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float dmu = (hy.norm == TSAT_NORM_ABSMEAN) ? (float)((zq[q] > 0.f) - (zq[q] < 0.f)) : 1.0f;
-          gq[q] = G[q] * rnu - c2 * dmu;
-        }
-      }
-      const size_t off = (size_t)v * N + s0;
-      if (mode == 1) {
-        *reinterpret_cast<float4 *>(grad + off) = make_float4(dL * gq[0], dL * gq[1], dL * gq[2], dL * gq[3]);
-        *reinterpret_cast<float4 *>(grad + off + 4) = make_float4(dL * gq[4], dL * gq[5], dL * gq[6], dL * gq[7]);
-      } else {
-        float zn[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float gs = gq[q];
-          mq[q] = b1 * mq[q] + omb1 * gs;
-          vq[q] = b2 * vq[q] + omb2 * (gs * gs);
-          const float sq = vq[q] > 0.f ? vq[q] * rsqrtf(vq[q]) : 0.f;
-          const float denom = sq * sp.inv_sqrt_bc2 + hy.eps;
-          zn[q] = zq[q] * sp.decay - sp.step_size * __fdividef(mq[q], denom);
-        }
-        st_cs(sd.z + off, make_float4(zn[0], zn[1], zn[2], zn[3]));
-        st_cs(sd.z + off + 4, make_float4(zn[4], zn[5], zn[6], zn[7]));
-        st_cs(sd.m + off, make_float4(mq[0], mq[1], mq[2], mq[3]));
-        st_cs(sd.m + off + 4, make_float4(mq[4], mq[5], mq[6], mq[7]));
-        st_cs(sd.v + off, make_float4(vq[0], vq[1], vq[2], vq[3]));
-        st_cs(sd.v + off + 4, make_float4(vq[4], vq[5], vq[6], vq[7]));
-        // ---- new normaliser and Eq. 2 / Philox for step t+1
-        float nun = 1.0f;
-        if (hy.norm != TSAT_NORM_NONE) {
-          float ps_ = 0.f;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) ps_ += (hy.norm == TSAT_NORM_ABSMEAN) ? fabsf(zn[q]) : zn[q];
-          nun = guard_nu(g.sum1(ps_, red, 1) / (float)N);
-        }
-        const float rnn = __frcp_rn(nun);
-        uint32_t byte = 0;
-        if (hy.binarize == TSAT_BIN_PHILOX) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)(s0 / 4 + h), (uint32_t)v, (uint32_t)(tcur + 1), kTagBin),
-                                          hy.key0, hy.key1);
-            const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              byte |= binarize_one(__fmul_rn(zn[4 * h + q], rnn), TSAT_BIN_PHILOX, hy.bin_c, rw[q]) << (4 * h + q);
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) byte |= (__fmul_rn(zn[q], rnn) > 0.0f ? 1u : 0u) << q;
-        }
-        uint32_t val = byte << sh;
-        const unsigned gm = g.mask();
-        val |= __shfl_xor_sync(gm, val, 1);
-        val |= __shfl_xor_sync(gm, val, 2);
-        if ((g.gl & 3) == 0) bdst[v * W + w] = val;
-        if (g.gl == 0) sd.nu[v] = nun;
-      }
-    }
-    // ---- planes of row k+1 from the words this thread gathered itself
-    cp_async_wait_all();
-    if (vn >= 0) planes_of(recb + rs1 * OC, nc1, gpb + (ps ^ 1) * OC * 2 * W, ownb + (ps ^ 1) * ostep * W);
-    if (frozen) {  // frozen rows skip the update: refill the z/m/v buffer here
-      g.sync();
-      if (vn >= 0 && leader) issue_zmv(vn);
-    }
-    g.sync();   // planes of row k+1 complete; reduction slots free
-    v = vn;
-    vn = vnn;
-    ++k;
-  }
-}
-
-int update2_smem_bytes(int N) {
-  const U3Layout L = u3_layout(N);
-  return L.RPB * L.group_bytes;
-}
-int update2_threads(int N) { return u3_layout(N).threads; }
 
 // ------------------------------------------------------------------ fused update, word per lane
 // Clause length <= 3 (R in 0..3, two bit planes).  Counting phase: a lane owns
@@ -1010,9 +631,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
     if (MODE == 0 && act && w == 0) {
       // the row's z, m, v stream into L2 while the occurrences are counted
       const size_t ro = (size_t)v * N;
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(zsrc + ro), "r"(N * 4) : "memory");
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sd.m + ro), "r"(N * 4) : "memory");
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sd.v + ro), "r"(N * 4) : "memory");
+      prefetch_l2(zsrc + ro, N * 4);
+      prefetch_l2(sd.m + ro, N * 4);
+      prefetch_l2(sd.v + ro, N * 4);
     }
 
     const int n4 = N >> 2;
@@ -1192,13 +813,220 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
   }
 }
 
+// ------------------------------------------------------------------ fused update, clause length 4..7
+// Word per lane like k_update3, with fixed 8-int records {hdr, lit x 6, 0}.
+// Counting phase: for every occurrence the lane gathers the other literals'
+// words, forms the bit-sliced R planes (3 planes, R <= 7) and adds
+// sign * gamma_i[R_i] to one FP32 accumulator per sample, looking gamma up in
+// a per-warp shared-memory table laid out [sample][8] with an 8-float skew per
+// word so that the 32 lanes of one lookup (same bit position, any words, any
+// R) hit distinct banks or the same address when W <= 4 (N <= 128); larger N
+// reads the table through L1.  The accumulators go to shared memory
+// bit-major ([32][33]) and the sample phase (Eq. 5, AdamW, bits) reads them
+// back with each lane owning 4 consecutive samples per pass.  A row group
+// whose rows span several instances is processed once per instance.
+constexpr int kGS = 33;   // padded row of the [32 bits][32 lanes] buffer
+
+__device__ __forceinline__ int ltab_off(int s) { return 8 * s + 8 * ((s >> 5) & 3); }
+__host__ __device__ __forceinline__ int updateL_tab_floats(int N) { return N <= 128 ? 8 * N + 32 : 0; }
+
+template <int MODE, int BIN, int NORM, bool STAB>
+__global__ void __launch_bounds__(kBlock, 3) k_updateL(ProbDev pd, StateDev sd, Hyper hy, const float *zin, float *grad,
+                                                       float dL) {
+  extern __shared__ __align__(16) float smL[];
+  const StateHdr *hdr = sd.hdr;
+  if (MODE == 0 && hdr->all_done) return;
+  const int N = sd.N, W = sd.W, RW = 32 / W, lm1 = sd.lm1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rsub = lane / W, w = lane % W, rbase = rsub * W;
+  const int tabf = updateL_tab_floats(N);
+  float *gbuf = smL + warp * (32 * kGS + tabf);   // [32 bits][33]: G, then z(t+1)
+  float *tab = gbuf + 32 * kGS;                   // [N][8] + skew: gamma of the warp's current instance
+  int tinst = -1;
+  StepParams sp;
+  if (MODE == 0) sp = *sd.sp;
+  const int64_t tcur = (MODE == 0) ? sp.t : hdr->t;
+  const uint32_t *bsrc = cur_bits(sd, tcur);
+  uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
+  const float *zsrc = (MODE == 0) ? sd.z : zin;
+  const int4 *xrec8 = reinterpret_cast<const int4 *>(pd.xrec);   // two int4 per occurrence
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int tlane = ltab_off(32 * w);   // this lane's word in the table (bit position added per sample)
+  for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * RW; base < pd.V; base += nwarps * RW) {
+    const int64_t v = base + rsub;
+    const bool valid = v < pd.V;
+    const int inst = valid ? __ldg(pd.var_inst + v) : INT_MAX;
+    bool todo = valid;
+    while (__any_sync(0xFFFFFFFFu, todo)) {
+      // the lowest instance among the rows not yet done
+      int cur = todo ? inst : INT_MAX;
+      for (int o = 16; o > 0; o >>= 1) cur = min(cur, __shfl_xor_sync(0xFFFFFFFFu, cur, o));
+      const bool mine = todo && inst == cur;
+      todo = todo && !mine;
+      __syncwarp();   // readers of the previous table / gbuf are done
+      const bool frozen = mine && MODE == 0 && sd.inst[cur].found;
+      const bool act = mine && !frozen;
+      if (STAB && cur != tinst) {
+        const float *gsrc = sd.gamma + (size_t)cur * lm1 * N;
+        for (int k = lane; k < 8 * N; k += 32) {
+          const int ss = k >> 3, r = k & 7;
+          tab[ltab_off(ss) + r] = r < lm1 ? gsrc[(size_t)r * N + ss] : 0.f;
+        }
+        tinst = cur;
+        __syncwarp();
+      }
+      const float *gglob = sd.gamma + (size_t)cur * lm1 * N + 32 * w;
+      if (MODE == 0 && act && w == 0) {
+        const size_t ro = (size_t)v * N;
+        prefetch_l2(zsrc + ro, N * 4);
+        prefetch_l2(sd.m + ro, N * 4);
+        prefetch_l2(sd.v + ro, N * 4);
+      }
+      // ---- counting phase: G of the lane's 32 samples, bit position 8b + j in acc[8b + j]
+      float acc[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+      int32_t o0 = 0, deg = 0;
+      if (act) {
+        o0 = __ldg(pd.vptr + v);
+        deg = __ldg(pd.vptr + v + 1) - o0;
+      }
+      const uint32_t own = act ? __ldg(bsrc + v * W + w) : 0u;
+#pragma unroll 1
+      for (int32_t i = 0; i < deg; ++i) {
+        const int4 ra = __ldg(xrec8 + 2 * (int64_t)(o0 + i)), rb = __ldg(xrec8 + 2 * (int64_t)(o0 + i) + 1);
+        const int len = ra.x >> 1;
+        const int lits[6] = {ra.y, ra.z, ra.w, rb.x, rb.y, rb.z};
+        uint32_t pl[3] = {own ^ (0u - (uint32_t)(ra.x & 1)), 0u, 0u};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          if (q + 1 < len) {
+            const uint32_t x = __ldg(bsrc + (size_t)(lits[q] >> 1) * W + w) ^ (0u - (uint32_t)(lits[q] & 1));
+            bitslice_add<3>(pl, x);
+          }
+        }
+        const float sg = (ra.x & 1) ? -1.0f : 1.0f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          // R of the samples at bit positions j, 8 + j, 16 + j, 24 + j, one per byte
+          const uint32_t r4 = ((pl[0] >> j) & 0x01010101u) + 2u * ((pl[1] >> j) & 0x01010101u) +
+                              4u * ((pl[2] >> j) & 0x01010101u);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int r = (int)((r4 >> (8 * b)) & 0xFFu);
+            float gv;
+            if constexpr (STAB) gv = tab[tlane + 8 * (8 * b + j) + r];
+            else gv = __ldg(gglob + (size_t)r * N + 8 * b + j);
+            acc[8 * b + j] = fmaf(sg, gv, acc[8 * b + j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) gbuf[i * kGS + lane] = acc[i];
+      __syncwarp();
+      // ---- sample phase: lane w holds samples s = 4Wk + 4w + e; G of sample s
+      // lives at gbuf[(s % 32) * 33 + rbase + s / 32]
+      const float nu = act ? sd.nu[v] : 1.0f;
+      const float rnu = __frcp_rn(nu);
+      const size_t rowoff = (size_t)v * N;
+      float part = 0.f;
+      if (NORM != TSAT_NORM_NONE && act) {
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k) {
+          const int s = 4 * W * k + 4 * w;
+          const float4 z4 = __ldg(reinterpret_cast<const float4 *>(zsrc + rowoff + s));
+          const float *gp = gbuf + (s & 31) * kGS + rbase + (s >> 5);
+          part = fmaf(gp[0], z4.x, part);
+          part = fmaf(gp[kGS], z4.y, part);
+          part = fmaf(gp[2 * kGS], z4.z, part);
+          part = fmaf(gp[3 * kGS], z4.w, part);
+        }
+      }
+      const float dot = seg_sum(part, W);
+      const float c2 = dot * rnu * rnu * (1.0f / (float)N);
+      float psum = 0.f;
+      if (act) {
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k) {
+          const int s = 4 * W * k + 4 * w;
+          const size_t off = rowoff + s;
+          float *gp = gbuf + (s & 31) * kGS + rbase + (s >> 5);
+          const float4 z4 = __ldg(reinterpret_cast<const float4 *>(zsrc + off));
+          const float zq[4] = {z4.x, z4.y, z4.z, z4.w};
+          float gq[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float G = gp[e * kGS];
+            if constexpr (NORM == TSAT_NORM_NONE) {
+              gq[e] = G;
+            } else {
+              const float dmu = (NORM == TSAT_NORM_ABSMEAN) ? (float)((zq[e] > 0.f) - (zq[e] < 0.f)) : 1.0f;
+              gq[e] = G * rnu - c2 * dmu;
+            }
+          }
+          if constexpr (MODE == 1) {
+            *reinterpret_cast<float4 *>(grad + off) = make_float4(dL * gq[0], dL * gq[1], dL * gq[2], dL * gq[3]);
+            continue;
+          }
+          const float4 m4 = ld_cs(sd.m + off), v4 = ld_cs(sd.v + off);
+          float mq[4] = {m4.x, m4.y, m4.z, m4.w}, vq[4] = {v4.x, v4.y, v4.z, v4.w}, zn[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            mq[e] = hy.beta1 * mq[e] + (hy.omb1) * gq[e];
+            vq[e] = hy.beta2 * vq[e] + (hy.omb2) * (gq[e] * gq[e]);
+            const float sq = vq[e] > 0.f ? vq[e] * rsqrtf(vq[e]) : 0.f;
+            const float denom = sq * sp.inv_sqrt_bc2 + hy.eps;
+            zn[e] = zq[e] * sp.decay - sp.step_size * __fdividef(mq[e], denom);
+            gp[e * kGS] = zn[e];
+            psum += (NORM == TSAT_NORM_ABSMEAN) ? fabsf(zn[e]) : zn[e];
+          }
+          st_cs(sd.z + off, make_float4(zn[0], zn[1], zn[2], zn[3]));
+          st_cs(sd.m + off, make_float4(mq[0], mq[1], mq[2], mq[3]));
+          st_cs(sd.v + off, make_float4(vq[0], vq[1], vq[2], vq[3]));
+        }
+      }
+      if constexpr (MODE == 1) continue;
+      const float tot = seg_sum(psum, W);
+      __syncwarp();
+      // ---- Eq. 2 / Philox bits of step t+1: lane w assembles word w (bits b of gbuf)
+      if (frozen) bdst[v * W + w] = bsrc[v * W + w];
+      if (act) {
+        const float nun = (NORM == TSAT_NORM_NONE) ? 1.0f : guard_nu(tot / (float)N);
+        const float rnn = __frcp_rn(nun);
+        uint32_t word = 0;
+        if constexpr (BIN == TSAT_BIN_PHILOX) {
+#pragma unroll 1
+          for (int h = 0; h < 8; ++h) {
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)(8 * w + h), (uint32_t)v, (uint32_t)(tcur + 1), kTagBin),
+                                          hy.key0, hy.key1);
+            const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              word |= binarize_one(__fmul_rn(gbuf[(4 * h + e) * kGS + lane], rnn), TSAT_BIN_PHILOX, hy.bin_c, rw[e])
+                      << (4 * h + e);
+          }
+        } else {
+#pragma unroll 8
+          for (int b = 0; b < 32; ++b) word |= (__fmul_rn(gbuf[b * kGS + lane], rnn) > 0.0f ? 1u : 0u) << b;
+        }
+        bdst[v * W + w] = word;
+        if (w == 0) sd.nu[v] = nun;
+      }
+    }
+  }
+}
+
 int update3_smem_bytes(int N);
+int updateL_smem_bytes(int N) { return kWarps * (32 * kGS + updateL_tab_floats(N)) * (int)sizeof(float); }
 // Resident blocks per SM of the update kernel this problem uses (occupancy API).
 int update_blocks_per_sm(const ProbDev &pd, const StateDev &sd) {
   int nb = 0;
-  if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_fixed4)
+  if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_stride == 4)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_update3<0, TSAT_BIN_PHILOX, TSAT_NORM_SIGNED_MEAN>, kBlock,
                                                   update3_smem_bytes(sd.N));
+  else if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_stride == 8)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_updateL<0, TSAT_BIN_PHILOX, TSAT_NORM_SIGNED_MEAN, true>,
+                                                  kBlock, updateL_smem_bytes(sd.N));
   else
     nb = 3;
   return nb > 0 ? nb : 1;
@@ -1365,11 +1193,66 @@ static cudaError_t launch_update3(const ProbDev &pd, const StateDev &sd, const H
   return launch_update3_n<0, TSAT_BIN_DET>(pd, sd, hy, zin, grad, dL, grid, st);
 }
 
+template <typename F>
+static void for_each_updateL(F f) {
+  f(k_updateL<0, TSAT_BIN_DET, TSAT_NORM_SIGNED_MEAN, true>);
+  f(k_updateL<0, TSAT_BIN_DET, TSAT_NORM_ABSMEAN, true>);
+  f(k_updateL<0, TSAT_BIN_DET, TSAT_NORM_NONE, true>);
+  f(k_updateL<0, TSAT_BIN_PHILOX, TSAT_NORM_SIGNED_MEAN, true>);
+  f(k_updateL<0, TSAT_BIN_PHILOX, TSAT_NORM_ABSMEAN, true>);
+  f(k_updateL<0, TSAT_BIN_PHILOX, TSAT_NORM_NONE, true>);
+  f(k_updateL<1, TSAT_BIN_DET, TSAT_NORM_SIGNED_MEAN, true>);
+  f(k_updateL<1, TSAT_BIN_DET, TSAT_NORM_ABSMEAN, true>);
+  f(k_updateL<1, TSAT_BIN_DET, TSAT_NORM_NONE, true>);
+  f(k_updateL<0, TSAT_BIN_DET, TSAT_NORM_SIGNED_MEAN, false>);
+  f(k_updateL<0, TSAT_BIN_DET, TSAT_NORM_ABSMEAN, false>);
+  f(k_updateL<0, TSAT_BIN_DET, TSAT_NORM_NONE, false>);
+  f(k_updateL<0, TSAT_BIN_PHILOX, TSAT_NORM_SIGNED_MEAN, false>);
+  f(k_updateL<0, TSAT_BIN_PHILOX, TSAT_NORM_ABSMEAN, false>);
+  f(k_updateL<0, TSAT_BIN_PHILOX, TSAT_NORM_NONE, false>);
+  f(k_updateL<1, TSAT_BIN_DET, TSAT_NORM_SIGNED_MEAN, false>);
+  f(k_updateL<1, TSAT_BIN_DET, TSAT_NORM_ABSMEAN, false>);
+  f(k_updateL<1, TSAT_BIN_DET, TSAT_NORM_NONE, false>);
+}
+
+template <int MODE, int BIN, bool STAB>
+static cudaError_t launch_updateL_n(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const float *zin,
+                                    float *grad, float dL, int grid, cudaStream_t st) {
+  const int smem = updateL_smem_bytes(sd.N);
+  switch (hy.norm) {
+    case TSAT_NORM_SIGNED_MEAN:
+      k_updateL<MODE, BIN, TSAT_NORM_SIGNED_MEAN, STAB><<<grid, kBlock, smem, st>>>(pd, sd, hy, zin, grad, dL);
+      break;
+    case TSAT_NORM_ABSMEAN:
+      k_updateL<MODE, BIN, TSAT_NORM_ABSMEAN, STAB><<<grid, kBlock, smem, st>>>(pd, sd, hy, zin, grad, dL);
+      break;
+    default:
+      k_updateL<MODE, BIN, TSAT_NORM_NONE, STAB><<<grid, kBlock, smem, st>>>(pd, sd, hy, zin, grad, dL);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+template <bool STAB>
+static cudaError_t launch_updateL_s(const ProbDev &pd, const StateDev &sd, const Hyper &hy, int mode,
+                                    const float *zin, float *grad, float dL, int grid, cudaStream_t st) {
+  if (mode == 1) return launch_updateL_n<1, TSAT_BIN_DET, STAB>(pd, sd, hy, zin, grad, dL, grid, st);
+  if (hy.binarize == TSAT_BIN_PHILOX)
+    return launch_updateL_n<0, TSAT_BIN_PHILOX, STAB>(pd, sd, hy, zin, grad, dL, grid, st);
+  return launch_updateL_n<0, TSAT_BIN_DET, STAB>(pd, sd, hy, zin, grad, dL, grid, st);
+}
+
+static cudaError_t launch_updateL(const ProbDev &pd, const StateDev &sd, const Hyper &hy, int mode, const float *zin,
+                                  float *grad, float dL, int grid, cudaStream_t st) {
+  if (updateL_tab_floats(sd.N) > 0) return launch_updateL_s<true>(pd, sd, hy, mode, zin, grad, dL, grid, st);
+  return launch_updateL_s<false>(pd, sd, hy, mode, zin, grad, dL, grid, st);
+}
+
 void prepare_update_attrs(int lmax) {
   const int P = planes_for(lmax);
   const int bytes = 160 * 1024;
-  cudaFuncSetAttribute(k_update2, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   for_each_update3([bytes](auto fn) { cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
+  for_each_updateL([bytes](auto fn) { cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
   cudaFuncSetAttribute(k_update<1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   switch (P) {
     case 1: cudaFuncSetAttribute(k_update<1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); break;
@@ -1383,10 +1266,8 @@ void prepare_update_attrs(int lmax) {
 cudaError_t launch_update(const ProbDev &pd, const StateDev &sd, const Hyper &hy, int mode, const float *zin,
                           float *grad, float dL, int grid, int rpi, cudaStream_t st) {
   const int P = planes_for(pd.lmax);
-  if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_fixed4) {
-    (void)rpi;
-    return launch_update3(pd, sd, hy, mode, zin, grad, dL, grid, st);
-  }
+  if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_stride == 4) return launch_update3(pd, sd, hy, mode, zin, grad, dL, grid, st);
+  if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_stride == 8) return launch_updateL(pd, sd, hy, mode, zin, grad, dL, grid, st);
   if (sd.layer == TSAT_LAYER_RELAXED) return upd_launch<1, true, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);
   switch (P) {
     case 1: return upd_launch<1, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);

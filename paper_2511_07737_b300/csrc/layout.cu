@@ -217,7 +217,7 @@ __global__ void k_fill(const int32_t *cptr, const int32_t *clit, int32_t C, cons
 // order) with rank counting, then write the occurrence records.
 __global__ void k_records(const int32_t *cptr, const int32_t *clit, int32_t V, const int32_t *vptr,
                           const int32_t *occ_j, const int32_t *occ_c, int32_t *occ_s,
-                          const int64_t *xptr, int32_t *xrec, int32_t *vocc, int fixed4) {
+                          const int64_t *xptr, int32_t *xrec, int32_t *vocc, int stride) {
   __shared__ int32_t sh[128];
   __shared__ int32_t carry;
   const int32_t v = blockIdx.x;
@@ -254,26 +254,26 @@ __global__ void k_records(const int32_t *cptr, const int32_t *clit, int32_t V, c
     if (a < d) {
       int32_t own = clit[j];
       vocc[b + a] = (c << 1) | (own & 1);
-      int32_t *r = xrec + base + (fixed4 ? 4 * a : off);
+      int32_t *r = xrec + base + (stride ? stride * a : off);
       r[0] = (own & 1) | (len << 1);  // nonzero: padding words are 0
       int q = 1;
       for (int32_t k = cptr[c]; k < cptr[c + 1]; ++k)
         if (k != j) r[q++] = clit[k];
-      if (fixed4)
-        for (; q < 4; ++q) r[q] = 0;
+      if (stride)
+        for (; q < stride; ++q) r[q] = 0;
     }
     __syncthreads();
     if (threadIdx.x == 127) carry += sh[127];
     __syncthreads();
   }
   // zero the padding
-  int64_t used = fixed4 ? xptr[v + 1] : base + carry;
+  int64_t used = stride ? xptr[v + 1] : base + carry;
   for (int64_t p = used + threadIdx.x; p < xptr[v + 1]; p += blockDim.x) xrec[p] = 0;
 }
 
-__global__ void k_xptr_fixed4(const int32_t *vptr, int32_t V, int64_t *xptr) {
+__global__ void k_xptr_fixed(const int32_t *vptr, int32_t V, int64_t *xptr, int stride) {
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v <= V) xptr[v] = 4 * (int64_t)vptr[v];
+  if (v <= V) xptr[v] = stride * (int64_t)vptr[v];
 }
 
 __global__ void k_var_inst(const InstInfo *inst, int32_t n_inst, int32_t V, int32_t *var_inst) {
@@ -284,13 +284,13 @@ __global__ void k_var_inst(const InstInfo *inst, int32_t n_inst, int32_t V, int3
 // ------------------------------------------------------------------ host side
 struct Sizes {
   int32_t n_inst;
-  int64_t V, C, nnz_raw, xrec_cap, items_cap;
+  int64_t V, C, nnz_raw, xrec_cap, items_cap, lraw;
 };
 
 static int measure(int32_t n_inst, const tsat_cnf_desc *d, Sizes *s) {
   if (n_inst <= 0 || !d) { set_error("n_inst must be positive and descs non-NULL"); return TSAT_EINVAL; }
   s->n_inst = n_inst;
-  s->V = s->C = s->nnz_raw = s->xrec_cap = s->items_cap = 0;
+  s->V = s->C = s->nnz_raw = s->xrec_cap = s->items_cap = s->lraw = 0;
   for (int32_t j = 0; j < n_inst; ++j) {
     if (d[j].n_vars <= 0 || d[j].n_clauses <= 0 || !d[j].h_clause_ptr || !d[j].h_lits) {
       set_error("instance %d: empty or NULL arrays", j);
@@ -303,13 +303,15 @@ static int measure(int32_t n_inst, const tsat_cnf_desc *d, Sizes *s) {
       if (len < 0) { set_error("instance %d: clause_ptr decreases at %d", j, c); return TSAT_EINVAL; }
       int64_t eff = std::min<int64_t>(len, TSAT_MAX_CLAUSE_LEN);
       s->xrec_cap += eff * eff;
+      s->lraw = std::max<int64_t>(s->lraw, len);
     }
     s->V += d[j].n_vars;
     s->C += d[j].n_clauses;
     s->nnz_raw += p[d[j].n_clauses];
     s->items_cap += (d[j].n_clauses + kItemMin - 1) / kItemMin;
   }
-  s->xrec_cap = std::max<int64_t>(s->xrec_cap, 4 * s->nnz_raw) + 3 * s->V + 8;
+  // fixed records: 4 ints per occurrence up to length 3, 8 up to length 7
+  s->xrec_cap = std::max<int64_t>(s->xrec_cap, (s->lraw <= 7 ? 8 : 4) * s->nnz_raw) + 3 * s->V + 8;
   if (s->V >= (1LL << 30) || s->C >= (1LL << 31) - 1 || s->nnz_raw >= (1LL << 31) - 1) {
     set_error("problem too large: V=%lld C=%lld nnz=%lld", (long long)s->V, (long long)s->C,
               (long long)s->nnz_raw);
@@ -479,7 +481,7 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
   CK(cudaStreamSynchronize(stream));
   int32_t lmax_all = 0;
   for (auto &I : p->inst) lmax_all = std::max(lmax_all, I.lmax);
-  const int fixed4 = lmax_all <= 3 ? 1 : 0;
+  const int stride = lmax_all <= 3 ? 4 : (lmax_all <= 7 && 8 * s.nnz_raw <= L.xrec_cap) ? 8 : 0;
   if (herr != ~0ull) {
     int code = (int)(herr & 0xFF);
     long long c = (long long)(herr >> 8);
@@ -493,8 +495,8 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
   CK(cudaGetLastError());
   rc2 = exclusive_scan(P32(L.deg), s.V, false, P64(L.scan_tmp), nullptr, P32(L.vptr), stream);
   if (rc2) return fail(rc2);
-  if (fixed4) {
-    k_xptr_fixed4<<<(unsigned)((s.V + 1 + T - 1) / T), T, 0, stream>>>(P32(L.vptr), p->V, P64(L.xptr));
+  if (stride) {
+    k_xptr_fixed<<<(unsigned)((s.V + 1 + T - 1) / T), T, 0, stream>>>(P32(L.vptr), p->V, P64(L.xptr), stride);
     CK(cudaGetLastError());
   } else {
     rc2 = exclusive_scan(P32(L.recsz), s.V, true, P64(L.scan_tmp), P64(L.xptr), nullptr, stream);
@@ -504,7 +506,7 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
                                P32(L.occ_c));
   CK(cudaGetLastError());
   k_records<<<(unsigned)s.V, 128, 0, stream>>>(P32(L.cptr), P32(L.clit), p->V, P32(L.vptr), P32(L.occ_j),
-                                               P32(L.occ_c), P32(L.occ_s), P64(L.xptr), P32(L.xrec), P32(L.vocc), fixed4);
+                                               P32(L.occ_c), P32(L.occ_s), P64(L.xptr), P32(L.xrec), P32(L.vocc), stride);
   CK(cudaGetLastError());
   k_var_inst<<<gv, T, 0, stream>>>(dinst, n_inst, p->V, P32(L.var_inst));
   CK(cudaGetLastError());
@@ -532,7 +534,7 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
   D.xrec = P32(L.xrec);
   D.vptr = P32(L.vptr);
   D.vocc = P32(L.vocc);
-  D.rec_fixed4 = fixed4;
+  D.rec_stride = stride;
   D.var_inst = P32(L.var_inst);
   D.items = (const int4 *)(w + L.items);
   D.inst = dinst;

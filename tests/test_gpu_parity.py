@@ -80,6 +80,13 @@ CASES = [
     ("mixed-k", lambda: [cnfgen.structured_mixed(2048, 8000, 7, communities=8)], 128, dict(norm=1, binarize=1), 3),
     ("k7", lambda: [cnfgen.planted_ksat(400, 14000, 7, 8)], 64, dict(norm=0, binarize=0), 2),
     ("batch", lambda: cnfgen.batch_ksat(5, 9, n_lo=60, n_hi=900), 64, dict(norm=1, binarize=1), 3),
+    # clause length 4..7 (fixed 8-int records): gamma table in shared memory (N <= 128) or through L1
+    ("k5-N256", lambda: [cnfgen.planted_ksat(600, 6000, 5, 31)], 256, dict(norm=2, binarize=1), 3),
+    ("k4-N1024", lambda: [cnfgen.planted_ksat(300, 2400, 4, 32)], 1024, dict(norm=1, binarize=0), 2),
+    ("k6-N128", lambda: [cnfgen.planted_ksat(500, 12000, 6, 35)], 128, dict(norm=0, binarize=1), 2),
+    # many small instances per warp (row groups span several instances)
+    ("batch-N32", lambda: cnfgen.batch_ksat(12, 33, n_lo=20, n_hi=80, k_lo=4, k_hi=6), 32, dict(norm=0, binarize=1), 3),
+    ("batch-N128", lambda: cnfgen.batch_ksat(6, 34, n_lo=40, n_hi=300), 128, dict(norm=1, binarize=0), 3),
 ]
 
 
@@ -117,13 +124,14 @@ def test_lockstep_ste(name, gen, N, kw, steps):
     assert ts.tsat_status(st.h, len(insts))["step"] == steps
 
 
-@pytest.mark.parametrize("norm", [0, 1, 2])
-def test_autograd_hooks_match_oracle_gradient(norm):
-    inst = cnfgen.planted_ksat(500, 2130, 3, 3)
-    prob, st, cnfs = make([inst], 128)
+@pytest.mark.parametrize("norm,k,N", [(0, 3, 128), (1, 3, 128), (2, 3, 128), (1, 5, 64), (0, 6, 256)])
+def test_autograd_hooks_match_oracle_gradient(norm, k, N):
+    m = 2130 if k == 3 else int(round(0.8 * cnfgen.KSAT_THRESHOLD[k] * 500))
+    inst = cnfgen.planted_ksat(500, m, k, 3)
+    prob, st, cnfs = make([inst], N)
     hp = ts.hparams(seed=3, norm=norm, tau=0.8)
-    z = torch.randn(500, 128, device="cuda", generator=torch.Generator(device="cuda").manual_seed(4)) + 0.5
-    S = torch.zeros(128, device="cuda")
+    z = torch.randn(500, N, device="cuda", generator=torch.Generator(device="cuda").manual_seed(4)) + 0.5
+    S = torch.zeros(N, device="cuda")
     L = torch.zeros(1, device="cuda")
     ts.tsat_forward(st.h, hp, z, 0, S, L)
     grad = torch.zeros_like(z)
