@@ -395,7 +395,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
   uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
   const float b1 = hy.beta1, b2 = hy.beta2;
   float gam[4][4];
-  float Zr[4], Sr[4];
   int cur_inst = -1;
   const int64_t NG = (int64_t)gridDim.x * RPB;
   const int64_t n_items = ((int64_t)pd.V + rows_per_item - 1) / rows_per_item;
@@ -411,10 +410,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
         cur_inst = inst;
         const float *gsrc = sd.gamma + (size_t)inst * lm1 * N;
         if constexpr (RELAX) {
-          const float4 zz = *reinterpret_cast<const float4 *>(sd.zs + (size_t)inst * 2 * N + s0);
-          const float4 ss = *reinterpret_cast<const float4 *>(sd.zs + ((size_t)inst * 2 + 1) * N + s0);
-          Zr[0] = zz.x; Zr[1] = zz.y; Zr[2] = zz.z; Zr[3] = zz.w;
-          Sr[0] = ss.x; Sr[1] = ss.y; Sr[2] = ss.z; Sr[3] = ss.w;
         } else if constexpr (GREG) {
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
@@ -436,16 +431,34 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
       const float nu = sd.nu[v];
       float G[4] = {0.f, 0.f, 0.f, 0.f};
       if constexpr (RELAX) {
-        // ---- relaxed backward: dL/dR_ci = -(e^{-tau R}/Z_i)(1 - tau (R - S_i)) from the stored R
-        for (int32_t o = __ldg(pd.vptr + v); o < __ldg(pd.vptr + v + 1); ++o) {
-          const int32_t e = __ldg(pd.vocc + o);
-          const float4 R4 = __ldg(reinterpret_cast<const float4 *>(sd.rbuf + (size_t)(e >> 1) * N + s0));
-          const float Rq[4] = {R4.x, R4.y, R4.z, R4.w};
+        // ---- relaxed backward: sum of +-dL/dR_ci over the row's occurrences; the
+        // buffer holds dL/dR (k_relaxed_dr), 8 occurrences' loads in flight
+        const int32_t ob = __ldg(pd.vptr + v), oe = __ldg(pd.vptr + v + 1);
+        int32_t o = ob;
+        for (; o + 8 <= oe; o += 8) {
+          int32_t e[8];
+          float4 D[8];
 #pragma unroll
-          for (int s = 0; s < 4; ++s) {
-            const float gr = -(expf(-hy.tau * Rq[s]) / Zr[s]) * (1.0f - hy.tau * (Rq[s] - Sr[s]));
-            G[s] += (e & 1) ? -gr : gr;
+          for (int q = 0; q < 8; ++q) e[q] = __ldg(pd.vocc + o + q);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) D[q] = __ldg(reinterpret_cast<const float4 *>(sd.rbuf + (size_t)(e[q] >> 1) * N + s0));
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float sg = (e[q] & 1) ? -1.0f : 1.0f;
+            G[0] = fmaf(sg, D[q].x, G[0]);
+            G[1] = fmaf(sg, D[q].y, G[1]);
+            G[2] = fmaf(sg, D[q].z, G[2]);
+            G[3] = fmaf(sg, D[q].w, G[3]);
           }
+        }
+        for (; o < oe; ++o) {
+          const int32_t e = __ldg(pd.vocc + o);
+          const float4 D = __ldg(reinterpret_cast<const float4 *>(sd.rbuf + (size_t)(e >> 1) * N + s0));
+          const float sg = (e & 1) ? -1.0f : 1.0f;
+          G[0] = fmaf(sg, D.x, G[0]);
+          G[1] = fmaf(sg, D.y, G[1]);
+          G[2] = fmaf(sg, D.z, G[2]);
+          G[3] = fmaf(sg, D.w, G[3]);
         }
         const float zq_[4] = {z4.x, z4.y, z4.z, z4.w};
 #pragma unroll
@@ -1356,8 +1369,62 @@ __global__ void __launch_bounds__(kBlock) k_relaxed_fwd(ProbDev pd, StateDev sd,
   }
 }
 
-// One block: S_i = Y_i / Z_i per (instance, sample) from the item partials in
-// a fixed order, loss (Eq. 3), and the step bookkeeping.  Found detection uses
+// dL/dR_ci = -(e^{-tau R_ci} / Z_i)(1 - tau (R_ci - S_i)) (Eq. 4 differentiated),
+// in place over the stored R, once per (clause, sample): the update then only
+// gathers and adds it per occurrence.
+__global__ void __launch_bounds__(kBlock) k_relaxed_dr(ProbDev pd, StateDev sd, Hyper hy, int skip_frozen) {
+  if (skip_frozen && sd.hdr->all_done) return;
+  const int4 it = pd.items[blockIdx.x];
+  const int inst = it.x;
+  if (skip_frozen && sd.inst[inst].found) return;
+  const int N = sd.N, GT = N >> 2, CPB = kBlock / GT;
+  const int cs = threadIdx.x / GT, s0 = (threadIdx.x % GT) * 4;
+  const float4 zz = *reinterpret_cast<const float4 *>(sd.zs + (size_t)inst * 2 * N + s0);
+  const float4 ss = *reinterpret_cast<const float4 *>(sd.zs + ((size_t)inst * 2 + 1) * N + s0);
+  const float Zr[4] = {zz.x, zz.y, zz.z, zz.w}, Sr[4] = {ss.x, ss.y, ss.z, ss.w};
+  for (int c = it.y + cs; c < it.z; c += CPB) {
+    float4 *p = reinterpret_cast<float4 *>(sd.rbuf + (size_t)c * N + s0);
+    const float4 R4 = *p;
+    const float Rq[4] = {R4.x, R4.y, R4.z, R4.w};
+    float D[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) D[s] = -(expf(-hy.tau * Rq[s]) / Zr[s]) * (1.0f - hy.tau * (Rq[s] - Sr[s]));
+    *p = make_float4(D[0], D[1], D[2], D[3]);
+  }
+}
+
+// Z_i, S_i = Y_i / Z_i per (instance, sample) from the item partials, summed
+// over items in a fixed order by 32 lanes (strided) and then across the lanes.
+// Block (instance, 32-sample chunk), 32 x 32 threads.
+__global__ void __launch_bounds__(1024) k_relaxed_zs(ProbDev pd, StateDev sd, int step_mode, float *S_out) {
+  __shared__ float shZ[32][33], shY[32][33];
+  const int N = sd.N;
+  const int inst = blockIdx.x, i = blockIdx.y * 32 + threadIdx.x, q0 = threadIdx.y;
+  if (step_mode && (sd.hdr->all_done || sd.inst[inst].found)) return;
+  const InstInfo I = pd.inst[inst];
+  float Z = 0.f, Y = 0.f;
+  if (i < N)
+    for (int q = q0; q < I.n_items; q += 32) {
+      Z += sd.zy[((size_t)(I.item_off + q) * 2) * N + i];
+      Y += sd.zy[((size_t)(I.item_off + q) * 2 + 1) * N + i];
+    }
+  shZ[q0][threadIdx.x] = Z;
+  shY[q0][threadIdx.x] = Y;
+  __syncthreads();
+  if (q0 == 0 && i < N) {
+    float z = 0.f, y = 0.f;
+    for (int k = 0; k < 32; ++k) {
+      z += shZ[k][threadIdx.x];
+      y += shY[k][threadIdx.x];
+    }
+    const float S = y / z;
+    sd.zs[((size_t)inst * 2) * N + i] = z;
+    sd.zs[((size_t)inst * 2 + 1) * N + i] = S;
+    (S_out ? S_out : sd.S)[(size_t)inst * N + i] = S;
+  }
+}
+
+// One block: loss (Eq. 3) and the step bookkeeping from S (k_relaxed_zs).  Found detection uses
 // the exact unsatisfied counts of the current bits (sd.unsat, filled by the
 // exact check earlier in the step).
 __global__ void __launch_bounds__(1024) k_relaxed_gamma(ProbDev pd, StateDev sd, Hyper hy, LrSched ls, int step_mode,
@@ -1365,23 +1432,7 @@ __global__ void __launch_bounds__(1024) k_relaxed_gamma(ProbDev pd, StateDev sd,
   StateHdr *hdr = sd.hdr;
   if (step_mode && hdr->all_done) return;
   const int64_t t = hdr->t;
-  const int N = sd.N;
   float *Sb = S_out ? S_out : sd.S;
-  const int64_t total = (int64_t)pd.n_inst * N;
-  for (int64_t p = threadIdx.x; p < total; p += blockDim.x) {
-    const int inst = (int)(p / N), i = (int)(p - (int64_t)inst * N);
-    if (step_mode && sd.inst[inst].found) continue;
-    const InstInfo I = pd.inst[inst];
-    float Z = 0.f, Y = 0.f;
-    for (int q = 0; q < I.n_items; ++q) {
-      Z += sd.zy[((size_t)(I.item_off + q) * 2) * N + i];
-      Y += sd.zy[((size_t)(I.item_off + q) * 2 + 1) * N + i];
-    }
-    const float S = Y / Z;
-    sd.zs[((size_t)inst * 2) * N + i] = Z;
-    sd.zs[((size_t)inst * 2 + 1) * N + i] = S;
-    Sb[(size_t)inst * N + i] = S;
-  }
   gamma_tail(pd, sd, hy, ls, step_mode, loss_out, Sb, t);
 }
 
@@ -1392,8 +1443,12 @@ cudaError_t launch_relaxed_fwd(const ProbDev &pd, const StateDev &sd, const Hype
   return cudaGetLastError();
 }
 
+// S and Z (k_relaxed_zs), the loss and step bookkeeping (k_relaxed_gamma), then
+// dL/dR in place over the stored R (k_relaxed_dr) for the backward.
 cudaError_t launch_relaxed_gamma(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls,
                                  int step_mode, float *loss_out, float *S_out, cudaStream_t st) {
+  k_relaxed_zs<<<dim3(pd.n_inst, (sd.N + 31) / 32), dim3(32, 32), 0, st>>>(pd, sd, step_mode, S_out);
+  k_relaxed_dr<<<pd.n_items, kBlock, 0, st>>>(pd, sd, hy, step_mode);
   k_relaxed_gamma<<<1, 1024, 0, st>>>(pd, sd, hy, ls, step_mode, loss_out, S_out);
   return cudaGetLastError();
 }
