@@ -67,12 +67,14 @@ def parse():
 
 
 def dist_env():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+    from paper_2511_07737_b300.replicas import rank_env
+    return rank_env()
 
 
 def gen(w, rank):
     from paper_2511_07737_b300 import cnfgen
-    return cnfgen.planted_ksat(w["n"], w["m"], w["k"], w["seed"] + 1000 * rank)
+    from paper_2511_07737_b300.replicas import replica_seed
+    return cnfgen.planted_ksat(w["n"], w["m"], w["k"], replica_seed(w["seed"], rank))
 
 
 def hp_for(ts, seed):
@@ -221,27 +223,20 @@ def ours(args, w, rank, world, local):
     import torch
     from paper_2511_07737_b300 import turbosat as ts
 
+    from paper_2511_07737_b300.replicas import Replicas, whole_job_rate
+
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+    rep = Replicas(world, "nccl", dev)
     inst = gen(w, rank)
     N, K, Wm = w["N"], args.steps, args.warmup
     hp = hp_for(ts, seed=w["seed"] + rank)
 
     def barrier():
         torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
+        rep.barrier()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = rep.max
 
     # ---- device-resident run
     prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)], device=dev)
@@ -265,7 +260,7 @@ def ours(args, w, rank, world, local):
     status = ts.tsat_status(st.h, 1)
     launches_per_step = ts.tsat_launches_per_step(st.h)
     evals_step = info["nnz"] * N
-    value = evals_step * K * world / (ms / 1e3)
+    value = whole_job_rate(evals_step, K, world, ms)
     # ---- per-kernel device times (individual launches, CUDA events on the launch stream)
     kms = ts.tsat_profile_step(st.h, hp, 5)
     t_fwd, t_gamma, t_upd = kms[0], kms[1], kms[2]
@@ -352,8 +347,7 @@ def ours(args, w, rank, world, local):
                 "gpu_launches": K * launches_per_step,
                 "impl": "ours"}
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    rep.close()
 
 
 # ---------------------------------------------------------------- other workloads

@@ -665,11 +665,12 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
     for (int32_t c0 = 0;; c0 += kCntChunk) {
       const int32_t cn = act ? min(deg - c0, kCntChunk) : 0;   // this row's occurrences in the chunk
       const int32_t cmax = min(maxdeg - c0, kCntChunk);
-      uint32_t cnt[4][6];
+      // strided byte counters: byte b of sc[t][j] counts sample 8 b + j of word w
+      uint32_t sc[3][8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int t = 0; t < 3; ++t)
 #pragma unroll
-        for (int j = 0; j < 6; ++j) cnt[q][j] = 0x80808080u;
+        for (int j = 0; j < 8; ++j) sc[t][j] = 0x80808080u;
       for (int32_t r0 = 0; r0 < cmax; r0 += W) {
         // W records of this row, one per lane, then broadcast within the row group
         int4 myrec = make_int4(0, 0, 0, 0);
@@ -690,21 +691,28 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
           const uint32_t sg = (rc.x & 1) ? 0xFFFFFFFFu : 1u;
           nsign += (int)sg;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const uint32_t y0 = __byte_perm(p0, 0, 0x4440u | q), y1 = __byte_perm(p1, 0, 0x4440u | q);
-            const uint32_t x0l = spread4(y0 & 15u), x0h = spread4(y0 >> 4);
-            const uint32_t x1l = spread4(y1 & 15u), x1h = spread4(y1 >> 4);
-            cnt[q][0] += x0l * sg; cnt[q][1] += x1l * sg; cnt[q][2] += (x0l & x1l) * sg;
-            cnt[q][3] += x0h * sg; cnt[q][4] += x1h * sg; cnt[q][5] += (x0h & x1h) * sg;
+          for (int j = 0; j < 8; ++j) {
+            const uint32_t t0 = (p0 >> j) & 0x01010101u, t1 = (p1 >> j) & 0x01010101u;
+            sc[0][j] += t0 * sg;
+            sc[1][j] += t1 * sg;
+            sc[2][j] += (t0 & t1) * sg;
           }
         }
       }
-      // cnt[q][3h + t] holds count t of samples 8q + 4h .. 8q + 4h + 3 of word w,
-      // i.e. count word (32 w + 8 q + 4 h) / 4 of the row
+      // 4x4 byte transposes: cnt word (q, h) of count t holds samples 8q + 4h + e
+      // (byte e), i.e. count word (32 w + 8 q + 4 h) / 4 of the row
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int t = 0; t < 3; ++t)
 #pragma unroll
-        for (int j = 0; j < 6; ++j) cbuf[(j % 3) * 256 + cswz(ist + 2 * q + j / 3)] = cnt[q][j];
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t A = sc[t][4 * h], B = sc[t][4 * h + 1], C = sc[t][4 * h + 2], D = sc[t][4 * h + 3];
+          const uint32_t abl = __byte_perm(A, B, 0x5140u), abh = __byte_perm(A, B, 0x7362u);
+          const uint32_t cdl = __byte_perm(C, D, 0x5140u), cdh = __byte_perm(C, D, 0x7362u);
+          cbuf[t * 256 + cswz(ist + 0 + h)] = __byte_perm(abl, cdl, 0x5410u);
+          cbuf[t * 256 + cswz(ist + 2 + h)] = __byte_perm(abl, cdl, 0x7632u);
+          cbuf[t * 256 + cswz(ist + 4 + h)] = __byte_perm(abh, cdh, 0x5410u);
+          cbuf[t * 256 + cswz(ist + 6 + h)] = __byte_perm(abh, cdh, 0x7632u);
+        }
       __syncwarp();
       if (c0 + kCntChunk >= maxdeg) break;   // the last chunk is folded in pass 1 below
       if (act) {
