@@ -163,5 +163,7 @@ __device__ __forceinline__ int32_t load_nc(const int32_t *p) { return __ldg(p); 
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
+// The cache line holding p into L2 (a hint).
+__device__ __forceinline__ void prefetch_l2_line(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 }  // namespace tsat

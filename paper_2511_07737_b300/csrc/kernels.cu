@@ -629,6 +629,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
   const int64_t nwarps = (int64_t)gridDim.x * kWarps;
   const int ist = 8 * lane;          // count words this lane stores: its 32 samples
   const int isam = rsub * 8 * W + w; // + W k: the word of this lane's samples in pass k
+  // first record round of the row group's current row, loaded during the previous row
+  int4 crec = make_int4(0, 0, 0, 0);
+  bool have_crec = false;
   for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * RW; base < pd.V; base += nwarps * RW) {
     __syncwarp();   // the previous row's readers of gbuf / zbuf are done
     const int64_t v = base + rsub;
@@ -649,6 +652,15 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
       prefetch_l2(sd.v + ro, N * 4);
     }
 
+    // the row group's next row: its vptr entries now, its first record round
+    // before pass 1, and an L2 prefetch of the bits rows its occurrences will
+    // gather after pass 2 (the bits array is larger than L2 at scale)
+    const int64_t vn = v + nwarps * RW;
+    int32_t o0n = 0, dn = 0;
+    if (vn < pd.V) {
+      o0n = __ldg(pd.vptr + vn);
+      dn = __ldg(pd.vptr + vn + 1) - o0n;
+    }
     const int n4 = N >> 2;
     // ---- counting phase (lane = word w of row v)
     int nsign = 0;
@@ -674,7 +686,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
       for (int32_t r0 = 0; r0 < cmax; r0 += W) {
         // W records of this row, one per lane, then broadcast within the row group
         int4 myrec = make_int4(0, 0, 0, 0);
-        if (r0 + w < cn) myrec = __ldg(xrec4 + o0 + c0 + r0 + w);
+        if (c0 == 0 && r0 == 0 && have_crec) myrec = crec;
+        else if (r0 + w < cn) myrec = __ldg(xrec4 + o0 + c0 + r0 + w);
         const int nr = min(W, cmax - r0);
 #pragma unroll 2
         for (int i = 0; i < nr; ++i) {
@@ -727,6 +740,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
       first = false;
       __syncwarp();   // the count words are read before the next chunk stores
     }
+    int4 nrec = make_int4(0, 0, 0, 0);
+    if (w < dn) nrec = __ldg(xrec4 + o0n + w);
+    crec = nrec;
+    have_crec = true;
     // ---- sample phase, pass 1: G of samples s = 4Wk + 4w + e, Eq. 5 dot product
     const float nu = act ? sd.nu[v] : 1.0f;
     const float rnu = __frcp_rn(nu);
@@ -794,6 +811,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
         st_cs(sd.m + off, make_float4(mq[0], mq[1], mq[2], mq[3]));
         st_cs(sd.v + off, make_float4(vq[0], vq[1], vq[2], vq[3]));
       }
+    }
+    if (w < dn) {
+      prefetch_l2_line(bsrc + (size_t)(nrec.y >> 1) * W);
+      if ((nrec.x >> 1) > 2) prefetch_l2_line(bsrc + (size_t)(nrec.z >> 1) * W);
     }
     if constexpr (MODE == 1) continue;
     const float tot = seg_sum(psum, W);
