@@ -114,7 +114,10 @@ static int leave(tsat_state *s, cudaStream_t user) {
 // Update grid: resident blocks per SM (occupancy API) unless tuned explicitly.
 static int upd_grid(const tsat_state *s) {
   const int bps = s->upd_blocks_per_sm > 0 ? s->upd_blocks_per_sm : update_blocks_per_sm(s->prob->dev, s->dev);
-  return std::max(1, s->sm_count * bps);
+  // no more blocks than row groups of a block (8 warps x 32/W rows)
+  const int64_t rows_per_block = (int64_t)kWarps * (32 / s->dev.W);
+  const int64_t need = (s->prob->dev.V + rows_per_block - 1) / rows_per_block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)s->sm_count * bps, need));
 }
 
 // One optimisation step: forward histogram, gamma, fused update.
@@ -602,7 +605,7 @@ int tsat_autotune(tsat_state *s, const tsat_hparams *hp, cudaStream_t stream, in
   // Each candidate runs one step from a fresh init (the init is repeated at the
   // end, so the state is left as tsat_init(hp) leaves it).
   const int items[] = {1024, 2048, 4096, 8192};
-  const int bps[] = {2, 3, 4, 6, 8};
+  const int bps[] = {3, 6, 12, 24, 32};
   const int rpi[] = {1, 8, 64};
   cudaEvent_t a, b;
   TSAT_CUDA(cudaEventCreate(&a));
