@@ -1064,8 +1064,8 @@ int updateL_smem_bytes(int N) { return kWarps * (32 * kGS + updateL_tab_floats(N
 // an oversubscription factor.  The word-per-lane kernels take rows grid-strided
 // per warp; with several waves of blocks the hardware scheduler fills the SMs
 // that finish early (rows differ in degree, and in cost between instances),
-// measured 5 % (clause length <= 3) and 19 % (batched 3..7) faster than one
-// wave.
+// measured 5 % (clause length <= 3), 19 % (batched 3..7) and 15 % (relaxed)
+// faster than one wave.
 int update_blocks_per_sm(const ProbDev &pd, const StateDev &sd) {
   int nb = 0;
   if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_stride == 4) {
@@ -1077,7 +1077,7 @@ int update_blocks_per_sm(const ProbDev &pd, const StateDev &sd) {
                                                   kBlock, updateL_smem_bytes(sd.N));
     nb *= 4;
   } else {
-    nb = 3;
+    nb = 24;   // general / relaxed kernel: 3 resident, 8 waves (relaxed n=1e6 N=256: 6.8 -> 5.8 ms)
   }
   return nb > 0 ? (nb < 32 ? nb : 32) : 1;
 }
