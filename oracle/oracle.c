@@ -388,7 +388,8 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
 /* Counter layout (both sides use this definition):
  *   key     = (seed low 32 bits, seed high 32 bits)
  *   init    : counter = (i, v, j, 0x494E4954) for j = 0,1,2  -> 12 words
- *   binarize: counter = (i / 4, v, t, 0x42494E41), word i mod 4         */
+ *   binarize: counter = (i / 8, v, t, 0x42494E41); sample i takes the
+ *             16-bit half i mod 8 (word (i mod 8) / 2, low half first)  */
 #define ORC_TAG_INIT 0x494E4954u
 #define ORC_TAG_BIN 0x42494E41u
 
@@ -441,7 +442,8 @@ void orc_nu_f32(int32_t V, int32_t N, const float *z, int32_t mode,
  * reciprocal and an FP32 product, each correctly rounded.
  * mode 0 (deterministic): x = [zt > 0].
  * mode 1 (Philox): p = clamp(0.5 + c * (z/nu), 0, 1) with one FP32
- * multiply and one FP32 add (no fused multiply-add), u = (word >> 8) 2^-24,
+ * multiply and one FP32 add (no fused multiply-add), u = half 2^-16 with
+ * half the 16-bit Philox output of the sample (counter layout above),
  * x = [u < p].  t is the step the bits belong to.                         */
 void orc_binarize_f32(int32_t V, int32_t N, const float *z, const float *nu,
                       int32_t mode, float c, uint64_t seed, int64_t t,
@@ -456,11 +458,12 @@ void orc_binarize_f32(int32_t V, int32_t N, const float *z, const float *nu,
       if (mode == 0) {
         x = (zt > 0.0f);
       } else {
-        uint32_t ctr[4] = {(uint32_t)(i / 4), (uint32_t)v, (uint32_t)t,
+        uint32_t ctr[4] = {(uint32_t)(i / 8), (uint32_t)v, (uint32_t)t,
                            ORC_TAG_BIN},
                  o[4];
         orc_philox4x32_10(ctr, key, o);
-        float u = (float)(o[i % 4] >> 8) * (1.0f / 16777216.0f);
+        uint32_t half = (o[(i % 8) / 2] >> (16 * (i % 2))) & 0xFFFFu;
+        float u = (float)half * (1.0f / 65536.0f);
         volatile float prod = c * zt;
         volatile float p = 0.5f + prod;
         if (p < 0.0f) p = 0.0f;

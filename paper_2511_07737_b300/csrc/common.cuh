@@ -11,6 +11,11 @@ constexpr int kBlock = 256;              // threads per block of the step kernel
 constexpr int kWarps = kBlock / 32;
 constexpr uint32_t kTagInit = 0x494E4954u;  // Philox counter word 3 for the init draw
 constexpr uint32_t kTagBin = 0x42494E41u;   // Philox counter word 3 for sampled binarisation
+// 16-bit half h (0..3) of two Philox output words (w0, w1): low half first
+__device__ __forceinline__ uint32_t half16(uint32_t w0, uint32_t w1, int h) {
+  const uint32_t x = (h & 2) ? w1 : w0;
+  return (h & 1) ? (x >> 16) : (x & 0xFFFFu);
+}
 
 struct InstInfo {
   int32_t v_off, n_vars, c_off, n_clauses;
@@ -147,9 +152,11 @@ __device__ __forceinline__ float guard_nu(float mu) {
 }
 
 // Eq. 2 / Philox rule on one value, decided in FP32 without contraction.
-__device__ __forceinline__ uint32_t binarize_one(float zt, int mode, float c, uint32_t word) {
+// half: the sample's 16-bit Philox output (counter (i / 8, v, t, kTagBin),
+// half i mod 8 of the four output words, low half first); u = half 2^-16.
+__device__ __forceinline__ uint32_t binarize_one(float zt, int mode, float c, uint32_t half) {
   if (mode == TSAT_BIN_DET) return zt > 0.0f ? 1u : 0u;
-  float u = __uint2float_rn(word >> 8) * (1.0f / 16777216.0f);
+  float u = __uint2float_rn(half) * (1.0f / 65536.0f);
   float p = __fadd_rn(0.5f, __fmul_rn(c, zt));
   p = fminf(fmaxf(p, 0.0f), 1.0f);
   return u < p ? 1u : 0u;

@@ -88,17 +88,18 @@ __device__ __forceinline__ void row_binarize_store(const StateDev &sd, const Hyp
     nu = guard_nu(g.sum(part, red) / (float)N);
   }
   const int s0 = g.gl * 4;
+  // samples s0 .. s0+3 are halves 0..3 or 4..7 of the block s0 / 8
   uint4 rnd = make_uint4(0, 0, 0, 0);
   if (hy.binarize == TSAT_BIN_PHILOX)
-    rnd = philox4x32_10(make_uint4((uint32_t)g.gl, (uint32_t)v, (uint32_t)t, kTagBin), hy.key0, hy.key1);
-  const uint32_t rw[4] = {rnd.x, rnd.y, rnd.z, rnd.w};
+    rnd = philox4x32_10(make_uint4((uint32_t)(g.gl >> 1), (uint32_t)v, (uint32_t)t, kTagBin), hy.key0, hy.key1);
+  const uint32_t w0 = (g.gl & 1) ? rnd.z : rnd.x, w1 = (g.gl & 1) ? rnd.w : rnd.y;
   uint32_t nib = 0;
   float a[4];
   const float rnu = __frcp_rn(nu);  // zt = z * (1/nu), both correctly rounded (FP32 decision)
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     float zt = __fmul_rn(zq[s], rnu);
-    nib |= binarize_one(zt, hy.binarize, hy.bin_c, rw[s]) << s;
+    nib |= binarize_one(zt, hy.binarize, hy.bin_c, half16(w0, w1, s)) << s;
     a[s] = sigmoidf_(zt);
   }
   if (want_lits) store_lits(sd, (size_t)v * N + s0, a);
@@ -825,23 +826,44 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
     if (valid && frozen) bdst[v * W + w] = bsrc[v * W + w];
     const float nun = (NORM == TSAT_NORM_NONE) ? 1.0f : guard_nu(tot / (float)N);
     const float rnn = __frcp_rn(nun);
-    if (act) {
+    // Philox: samples 4(Wk + w) .. +3 are halves 0..3 (w even) or 4..7 (w odd)
+    // of block (Wk + w) / 2.  Over a pair of passes (2kk, 2kk + 1) the even lane
+    // of a lane pair draws the block of pass 2kk and the odd lane that of pass
+    // 2kk + 1, and they swap the two words the other needs: one draw per lane
+    // per two passes.  With W = 1 both passes share one block of the lane.
 #pragma unroll 1
-      for (int k = 0; k < 8; ++k) {
-        const float4 z4 = gbuf[k * 32 + lane];
-        const float zq[4] = {z4.x, z4.y, z4.z, z4.w};
-        uint32_t nib = 0;
-        if constexpr (BIN == TSAT_BIN_PHILOX) {
-          const uint4 r = philox4x32_10(make_uint4((uint32_t)(W * k + w), (uint32_t)v, (uint32_t)(tcur + 1), kTagBin),
-                                        hy.key0, hy.key1);
-          const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) nib |= binarize_one(__fmul_rn(zq[e], rnn), TSAT_BIN_PHILOX, hy.bin_c, rw[e]) << e;
-        } else {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) nib |= (__fmul_rn(zq[e], rnn) > 0.0f ? 1u : 0u) << e;
+    for (int kk = 0; kk < 4; ++kk) {
+      uint32_t own0 = 0, own1 = 0, oth0 = 0, oth1 = 0;
+      if constexpr (BIN == TSAT_BIN_PHILOX) {
+        const uint32_t blk = (uint32_t)((W * (2 * kk + (w & 1)) + (w & ~1)) >> 1);
+        const uint4 r = philox4x32_10(make_uint4(blk, (uint32_t)v, (uint32_t)(tcur + 1), kTagBin), hy.key0, hy.key1);
+        const uint32_t s0 = (w & 1) ? r.x : r.z, s1 = (w & 1) ? r.y : r.w;   // the partner's words
+        const uint32_t g0 = __shfl_xor_sync(0xFFFFFFFFu, s0, 1), g1 = __shfl_xor_sync(0xFFFFFFFFu, s1, 1);
+        if (W == 1) {                   // pass 2kk: words 0, 1; pass 2kk + 1: words 2, 3
+          own0 = r.x; own1 = r.y; oth0 = r.z; oth1 = r.w;
+        } else if (w & 1) {             // pass 2kk: even lane's words 2, 3; pass 2kk + 1: own words 2, 3
+          own0 = g0; own1 = g1; oth0 = r.z; oth1 = r.w;
+        } else {                        // pass 2kk: own words 0, 1; pass 2kk + 1: odd lane's words 0, 1
+          own0 = r.x; own1 = r.y; oth0 = g0; oth1 = g1;
         }
-        nbuf[cswz(isam + W * k)] = nib;
+      }
+#pragma unroll
+      for (int pp = 0; pp < 2; ++pp) {
+        const int k = 2 * kk + pp;
+        if (act) {
+          const float4 z4 = gbuf[k * 32 + lane];
+          const float zq[4] = {z4.x, z4.y, z4.z, z4.w};
+          const uint32_t q0 = pp ? oth0 : own0, q1 = pp ? oth1 : own1;
+          uint32_t nib = 0;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if constexpr (BIN == TSAT_BIN_PHILOX)
+              nib |= binarize_one(__fmul_rn(zq[e], rnn), TSAT_BIN_PHILOX, hy.bin_c, half16(q0, q1, e)) << e;
+            else
+              nib |= (__fmul_rn(zq[e], rnn) > 0.0f ? 1u : 0u) << e;
+          }
+          nbuf[cswz(isam + W * k)] = nib;
+        }
       }
     }
     __syncwarp();
@@ -1038,14 +1060,14 @@ __global__ void __launch_bounds__(kBlock, 3) k_updateL(ProbDev pd, StateDev sd, 
         uint32_t word = 0;
         if constexpr (BIN == TSAT_BIN_PHILOX) {
 #pragma unroll 1
-          for (int h = 0; h < 8; ++h) {
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)(8 * w + h), (uint32_t)v, (uint32_t)(tcur + 1), kTagBin),
+          for (int h = 0; h < 4; ++h) {   // samples 32 w + 8 h + e: block 4 w + h, half e
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)(4 * w + h), (uint32_t)v, (uint32_t)(tcur + 1), kTagBin),
                                           hy.key0, hy.key1);
-            const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-              word |= binarize_one(__fmul_rn(gbuf[(4 * h + e) * kGS + lane], rnn), TSAT_BIN_PHILOX, hy.bin_c, rw[e])
-                      << (4 * h + e);
+            for (int e = 0; e < 8; ++e)
+              word |= binarize_one(__fmul_rn(gbuf[(8 * h + e) * kGS + lane], rnn), TSAT_BIN_PHILOX, hy.bin_c,
+                                   half16(e < 4 ? r.x : r.z, e < 4 ? r.y : r.w, e & 3))
+                      << (8 * h + e);
           }
         } else {
 #pragma unroll 8

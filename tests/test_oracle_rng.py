@@ -98,3 +98,33 @@ def test_best_sample_and_topk_bruteforce():
     assert oracle.partial_k(1_000_000) == 100
     assert oracle.partial_k(1_000_001) == 101
     assert oracle.partial_k(7) == 7
+
+
+def test_binarize_philox_counter_layout_and_halves():
+    # sample i of variable v at step t uses the 16-bit half i mod 8 of the
+    # Philox output for counter (i / 8, v, t, 0x42494E41) (low half of word 0
+    # first); with p fixed, x = [half / 2^16 < p]
+    V, N, t, seed = 5, 64, 7, 0x1234_5678_9ABC
+    z = np.zeros((V, N), np.float32)          # p = 0.5 + c * 0 = 0.5
+    nu = np.ones(V, np.float32)
+    X = oracle.binarize_f32(z, nu, 1, c=0.25, seed=seed, t=t)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for v in range(V):
+        for i in range(N):
+            o = oracle.philox4x32_10((i // 8, v, t, 0x42494E41), key)
+            half = (int(o[(i % 8) // 2]) >> (16 * (i % 2))) & 0xFFFF
+            assert X[v, i] == (1 if half / 65536.0 < 0.5 else 0), (v, i)
+
+
+def test_binarize_philox_halves_are_independent():
+    # the eight samples that share one draw get distinct 16-bit halves: at
+    # p = 1/2 neighbours agree half the time and every sample is a fair coin
+    V, N = 256, 1024
+    z = np.zeros((V, N), np.float32)
+    nu = np.ones(V, np.float32)
+    X = oracle.binarize_f32(z, nu, 1, c=0.25, seed=11, t=1).astype(np.int8)
+    n = X.size
+    assert abs(X.mean() - 0.5) < 5 * np.sqrt(0.25 / n)
+    for d in (1, 2, 4):                        # same draw, other half / word
+        agree = (X[:, :-d] == X[:, d:]).mean()
+        assert abs(agree - 0.5) < 5 * np.sqrt(0.25 / (V * (N - d)))
