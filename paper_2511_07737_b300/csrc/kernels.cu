@@ -198,24 +198,37 @@ __global__ void __launch_bounds__(kBlock) k_fwd_hist(ProbDev pd, StateDev sd, in
 #pragma unroll
         for (int p = 0; p < P; ++p) pl[q][p] = 0;
       if (active) {
+        // literals in chunks of 4: the chunk's literal loads, then its gathers,
+        // are issued together (one dependent-load round each per chunk)
         const int32_t b = __ldg(pd.cptr + c), e = __ldg(pd.cptr + c + 1);
-        for (int32_t j = b; j < e; ++j) {
-          const int32_t lit = __ldg(pd.clit + j);
-          const uint32_t negm = 0u - (uint32_t)(lit & 1);
-          const uint32_t *row = bits + (size_t)(lit >> 1) * W + wb * WB;
-          if constexpr (WB == 4) {
-            uint4 x = __ldg(reinterpret_cast<const uint4 *>(row));
-            bitslice_add<P>(pl[0], x.x ^ negm);
-            bitslice_add<P>(pl[1], x.y ^ negm);
-            bitslice_add<P>(pl[2], x.z ^ negm);
-            bitslice_add<P>(pl[3], x.w ^ negm);
-          } else if constexpr (WB == 2) {
-            uint2 x = __ldg(reinterpret_cast<const uint2 *>(row));
-            bitslice_add<P>(pl[0], x.x ^ negm);
-            bitslice_add<P>(pl[1], x.y ^ negm);
-          } else {
-            bitslice_add<P>(pl[0], __ldg(row) ^ negm);
+        for (int32_t j0 = b; j0 < e; j0 += 4) {
+          int32_t lit[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) lit[u] = (j0 + u < e) ? __ldg(pd.clit + j0 + u) : -1;
+          uint32_t x[4][WB];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t negm = 0u - (uint32_t)(lit[u] & 1);
+            const uint32_t *row = bits + (size_t)(lit[u] >> 1) * W + wb * WB;
+            if (lit[u] < 0) {
+#pragma unroll
+              for (int q = 0; q < WB; ++q) x[u][q] = 0u;
+            } else if constexpr (WB == 4) {
+              const uint4 y = __ldg(reinterpret_cast<const uint4 *>(row));
+              x[u][0] = y.x ^ negm; x[u][1] = y.y ^ negm; x[u][2] = y.z ^ negm; x[u][3] = y.w ^ negm;
+            } else if constexpr (WB == 2) {
+              const uint2 y = __ldg(reinterpret_cast<const uint2 *>(row));
+              x[u][0] = y.x ^ negm; x[u][1] = y.y ^ negm;
+            } else {
+              x[u][0] = __ldg(row) ^ negm;
+            }
           }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (lit[u] >= 0) {
+#pragma unroll
+              for (int q = 0; q < WB; ++q) bitslice_add<P>(pl[q], x[u][q]);
+            }
         }
       }
       const uint32_t valid = __ballot_sync(0xFFFFFFFFu, active);
@@ -1131,12 +1144,19 @@ __global__ void __launch_bounds__(kBlock) k_check(ProbDev pd, StateDev sd, int32
 #pragma unroll
       for (int q = 0; q < WB; ++q) orw[q] = 0;
       if (active) {
-        for (int32_t j = __ldg(pd.cptr + c); j < __ldg(pd.cptr + c + 1); ++j) {
-          const int32_t lit = __ldg(pd.clit + j);
-          const uint32_t negm = 0u - (uint32_t)(lit & 1);
-          const uint32_t *row = bits + (size_t)(lit >> 1) * W + wb * WB;
+        const int32_t b = __ldg(pd.cptr + c), e = __ldg(pd.cptr + c + 1);
+        for (int32_t j0 = b; j0 < e; j0 += 4) {   // chunks of 4 literals, loads issued together
+          int32_t lit[4];
 #pragma unroll
-          for (int q = 0; q < WB; ++q) orw[q] |= __ldg(row + q) ^ negm;
+          for (int u = 0; u < 4; ++u) lit[u] = (j0 + u < e) ? __ldg(pd.clit + j0 + u) : -1;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (lit[u] >= 0) {
+              const uint32_t negm = 0u - (uint32_t)(lit[u] & 1);
+              const uint32_t *row = bits + (size_t)(lit[u] >> 1) * W + wb * WB;
+#pragma unroll
+              for (int q = 0; q < WB; ++q) orw[q] |= __ldg(row + q) ^ negm;
+            }
         }
       }
       const uint32_t valid = __ballot_sync(0xFFFFFFFFu, active);
