@@ -604,7 +604,7 @@ int tsat_autotune(tsat_state *s, const tsat_hparams *hp, cudaStream_t stream, in
   TSAT_CUDA(cudaStreamSynchronize(stream));
   // Each candidate runs one step from a fresh init (the init is repeated at the
   // end, so the state is left as tsat_init(hp) leaves it).
-  const int items[] = {1024, 2048, 4096, 8192};
+  const int items[] = {512, 1024, 2048, 4096};
   const int bps[] = {3, 6, 12, 24, 32};
   const int rpi[] = {1, 8, 64};
   cudaEvent_t a, b;

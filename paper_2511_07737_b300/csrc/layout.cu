@@ -538,7 +538,7 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
   D.var_inst = P32(L.var_inst);
   D.items = (const int4 *)(w + L.items);
   D.inst = dinst;
-  int rc3 = p->set_items(2048, stream);
+  int rc3 = p->set_items(1024, stream);   // forward work items of 1024 clauses (measured 512..4096: near the best)
   if (rc3) return fail(rc3);
   *out = p;
   return TSAT_OK;
