@@ -90,6 +90,12 @@ typedef struct tsat_hparams {
   float bin_temp;         /* T of the Philox rule, c = 0.25 / T (default 1) */
   int32_t layer;          /* TSAT_LAYER_* (default TSAT_LAYER_STE) */
   uint64_t seed;          /* Philox key (init and sampled binarisation) */
+  int32_t mix_restart;    /* 1: assignment mixing at each lr restart (t = k * restart_period, k >= 1):
+                             the instance's sample with the fewest unsatisfied clauses, i*, is kept,
+                             every other sample's z becomes (z + z_i*) / 2, m = v = 0, and the AdamW
+                             step count restarts; that step takes no gradient step.  A variant the
+                             paper describes and leaves disabled (Sec. IV-A); default 0 */
+  int32_t reserved;       /* must be 0 */
 } tsat_hparams;
 
 /* One CNF in DIMACS form: clause c holds h_lits[h_clause_ptr[c] .. h_clause_ptr[c+1]),

@@ -255,13 +255,14 @@ class HParams(ctypes.Structure):
                 ("decay_period", ctypes.c_int32), ("restart_period", ctypes.c_int32),
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("eps", ctypes.c_double), ("weight_decay", ctypes.c_double),
-                ("norm", ctypes.c_int32), ("relaxed", ctypes.c_int32)]
+                ("norm", ctypes.c_int32), ("relaxed", ctypes.c_int32),
+                ("mix", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 def hparams(**kw) -> HParams:
     d = dict(tau=1.0, lr0=0.1, lr_factor=0.1, lr_floor=1e-15, decay_period=30,
              restart_period=360, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.01,
-             norm=NORM_SIGNED_MEAN, relaxed=0)
+             norm=NORM_SIGNED_MEAN, relaxed=0, mix=0)
     d.update(kw)
     return HParams(**d)
 

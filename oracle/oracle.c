@@ -481,6 +481,8 @@ void orc_binarize_f32(int32_t V, int32_t N, const float *z, const float *nu,
 /*   objective and gradient at the given assignments (X for the STE     */
 /*   layer, sigmoid(zt) for the relaxed layer)                          */
 /*   chain rule through Eq. 5, AdamW with lr(t), step count s = t + 1   */
+/*   (with mix: at t = k R, k >= 1, assignment mixing instead, and the  */
+/*   step count restarts: s = t mod R after the first restart)          */
 /*   nu_{t+1} from the updated z.                                       */
 /* z, m, v are updated in place.  Outputs: S[N], *L, G[V*N] (nullable), */
 /* g[V*N] (nullable), nu_next[V] (nullable), unsat[N] (nullable).       */
@@ -491,6 +493,8 @@ typedef struct {
   double beta1, beta2, eps, weight_decay;
   int32_t norm;
   int32_t relaxed;
+  int32_t mix;      /* assignment mixing at each lr restart (see orc_step) */
+  int32_t pad;
 } orc_hparams;
 
 int orc_step(int32_t V, int32_t C, const int64_t *cptr, const int32_t *var,
@@ -511,16 +515,39 @@ int orc_step(int32_t V, int32_t C, const int64_t *cptr, const int32_t *var,
       for (int32_t i = 0; i < N; ++i)
         zt[(int64_t)r * N + i] = z[(int64_t)r * N + i] / nu[r];
   }
+  int32_t *us = unsat ? unsat : (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+  if (!us) return ORC_ENOMEM;
   int rc = orc_objective(V, C, cptr, var, neg, N, hp->relaxed, X, zt, hp->tau,
-                         S, L, G, unsat);
-  if (rc == ORC_OK) {
+                         S, L, G, us);
+  const int32_t R = hp->restart_period;
+  if (rc == ORC_OK && hp->mix && R > 0 && t > 0 && t % R == 0) {
+    /* assignment mixing at an lr restart (the paper's commented-out variant):
+     * the sample with the most satisfied clauses, i*, is kept; every other
+     * sample becomes the mean of itself and i*; the optimizer is reset.  No
+     * gradient step is taken at this step. */
+    int32_t best = 0;
+    for (int32_t i = 1; i < N; ++i)
+      if (us[i] < us[best]) best = i;
+    for (int32_t r = 0; r < V; ++r)
+      for (int32_t i = 0; i < N; ++i) {
+        int64_t k = (int64_t)r * N + i;
+        if (i != best) z[k] = 0.5 * (z[k] + z[(int64_t)r * N + best]);
+        m[k] = 0.0;
+        v[k] = 0.0;
+      }
+    for (size_t k = 0; k < n; ++k) g[k] = 0.0;
+    if (nu_next) orc_normalize(V, N, z, hp->norm, nu_next, NULL);
+  } else if (rc == ORC_OK) {
     orc_normalize_backward(V, N, z, nu, G, hp->norm, g);
     double lr = orc_lr(t, hp->lr0, hp->lr_factor, hp->decay_period,
                        hp->restart_period, hp->lr_floor);
-    orc_adamw((int64_t)n, z, m, v, g, t + 1, lr, hp->beta1, hp->beta2,
+    /* AdamW step count: global, or counted from the last mixing restart */
+    int64_t cnt = (hp->mix && R > 0 && t >= R) ? t % R : t + 1;
+    orc_adamw((int64_t)n, z, m, v, g, cnt, lr, hp->beta1, hp->beta2,
               hp->eps, hp->weight_decay);
     if (nu_next) orc_normalize(V, N, z, hp->norm, nu_next, NULL);
   }
+  if (!unsat) free(us);
   free(nu);
   free(zt);
   if (!G_out) free(G);

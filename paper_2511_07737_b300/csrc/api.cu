@@ -86,13 +86,15 @@ static LrSched make_sched(const tsat_hparams &hp) {
   l.restart = hp.restart_period;
   l.beta1 = hp.beta1;
   l.beta2 = hp.beta2;
+  l.mix = hp.mix_restart;
   return l;
 }
 
 static int check_hp(const tsat_hparams *hp) {
   if (!hp) { set_error("hparams is NULL"); return TSAT_EINVAL; }
   if (!(hp->tau > 0.f) || hp->norm < 0 || hp->norm > 2 || hp->binarize < 0 || hp->binarize > 1 ||
-      !(hp->bin_temp > 0.f) || !(hp->beta1 >= 0.0 && hp->beta1 < 1.0) || !(hp->beta2 >= 0.0 && hp->beta2 < 1.0)) {
+      !(hp->bin_temp > 0.f) || !(hp->beta1 >= 0.0 && hp->beta1 < 1.0) || !(hp->beta2 >= 0.0 && hp->beta2 < 1.0) ||
+      hp->mix_restart < 0 || hp->mix_restart > 1 || hp->reserved != 0) {
     set_error("hparams out of range");
     return TSAT_EINVAL;
   }
@@ -136,6 +138,7 @@ static int issue_step(tsat_state *s, const Hyper &hy, const LrSched &ls, cudaStr
     if ((e = launch_gamma(pd, s->dev, hy, ls, s->dev.hist, 1, 1, nullptr, nullptr, st)) != cudaSuccess)
       return cuda_fail(e, "gamma");
   }
+  if (ls.mix && (e = launch_mix(pd, s->dev, hy, upd_grid(s), st)) != cudaSuccess) return cuda_fail(e, "mix");
   if ((e = launch_update(pd, s->dev, hy, 0, nullptr, nullptr, 0.f, upd_grid(s), s->upd_rows_per_item, st)) !=
       cudaSuccess)
     return cuda_fail(e, "update");
@@ -165,6 +168,8 @@ void tsat_hparams_default(tsat_hparams *hp) {
   hp->bin_temp = 1.0f;
   hp->layer = TSAT_LAYER_STE;
   hp->seed = 0;
+  hp->mix_restart = 0;
+  hp->reserved = 0;
 }
 
 int tsat_state_bytes(const tsat_problem *p, int32_t N, int32_t layer, int32_t dt, size_t *bytes) {
@@ -397,6 +402,7 @@ int tsat_profile_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, fl
       if (e == cudaSuccess) e = launch_gamma(pd, s->dev, hy, ls, s->dev.hist, 1, 1, nullptr, nullptr, st);
     }
     TSAT_CUDA(cudaEventRecord(ev[2], st));
+    if (e == cudaSuccess && ls.mix) e = launch_mix(pd, s->dev, hy, upd_grid(s), st);
     if (e == cudaSuccess)
       e = launch_update(pd, s->dev, hy, 0, nullptr, nullptr, 0.f, upd_grid(s), s->upd_rows_per_item, st);
     TSAT_CUDA(cudaEventRecord(ev[3], st));

@@ -59,7 +59,7 @@ struct InstState {
 struct StepParams {
   int64_t t;          // step being executed
   int32_t src;        // bits buffer read this step (t & 1)
-  int32_t pad;
+  int32_t mix_now;    // this step mixes assignments instead of the gradient update
   float lr, step_size, inv_sqrt_bc2, decay;
 };
 

@@ -141,6 +141,46 @@ __global__ void __launch_bounds__(kBlock) k_init(ProbDev pd, StateDev sd, Hyper 
   }
 }
 
+// Assignment mixing at an lr restart (the step's sp.mix_now): per instance the
+// sample i* with the fewest unsatisfied clauses (gamma's best_sample) is kept,
+// every other sample's z becomes (z + z_i*) / 2, m = v = 0, and the new
+// normaliser and bits of step t + 1 follow from the mixed z (the update
+// kernels skip this step).  Frozen instances keep their bits.
+__global__ void __launch_bounds__(kBlock) k_mix(ProbDev pd, StateDev sd, Hyper hy) {
+  __shared__ float red[64];
+  const StepParams sp = *sd.sp;
+  if (!sp.mix_now || sd.hdr->all_done) return;
+  const int GT = sd.N >> 2, RPB = kBlock / GT;
+  Group g{GT, (int)threadIdx.x / GT, (int)threadIdx.x % GT, (int)(threadIdx.x & 31)};
+  const int64_t NG = (int64_t)gridDim.x * RPB;
+  const int64_t rows_round = ((int64_t)pd.V + NG - 1) / NG * NG;
+  const uint32_t *bsrc = cur_bits(sd, sp.t);
+  uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, sp.t + 1));
+  for (int64_t v = (int64_t)blockIdx.x * RPB + g.grp; v < rows_round; v += NG) {
+    if (v >= pd.V) continue;  // whole group skips together (group-uniform v)
+    const int inst = __ldg(pd.var_inst + v);
+    const int s0 = g.gl * 4;
+    if (sd.inst[inst].found) {
+      if ((g.gl & 7) == 0) bdst[v * sd.W + (s0 >> 5)] = bsrc[v * sd.W + (s0 >> 5)];
+      continue;
+    }
+    const int best = sd.inst[inst].best_sample;
+    const size_t off = (size_t)v * sd.N + s0;
+    const float zb = sd.z[(size_t)v * sd.N + best];
+    const float4 z4 = *reinterpret_cast<const float4 *>(sd.z + off);
+    float zq[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (s0 + e != best) zq[e] = 0.5f * (zq[e] + zb);
+    g.sync();   // every thread of the row has read z_i* before it is stored (unchanged, but ordered)
+    *reinterpret_cast<float4 *>(sd.z + off) = make_float4(zq[0], zq[1], zq[2], zq[3]);
+    *reinterpret_cast<float4 *>(sd.m + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4 *>(sd.v + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+    row_binarize_store(sd, hy, g, red + (GT > 32 ? g.grp * 8 : 0), v, zq, sp.t + 1, bdst,
+                       sd.layer == TSAT_LAYER_RELAXED);
+  }
+}
+
 // Binarise an external z (autograd forward) into the current bits buffer.
 __global__ void __launch_bounds__(kBlock) k_binarize(ProbDev pd, StateDev sd, Hyper hy, const float *zin,
                                                      int64_t t_bin, int want_lits) {
@@ -303,12 +343,14 @@ __device__ void gamma_tail(const ProbDev &pd, const StateDev &sd, const Hyper &h
     const int64_t kdec = ls.period > 0 ? tt / ls.period : 0;
     double lr = (double)ls.lr0 * pow((double)ls.factor, (double)kdec);
     if (lr < (double)ls.floor) lr = ls.floor;
-    const double bc1 = 1.0 - pow(ls.beta1, (double)(t + 1));
-    const double bc2 = 1.0 - pow(ls.beta2, (double)(t + 1));
+    // AdamW step count: global, or counted from the last mixing restart
+    const int64_t cnt = (ls.mix && ls.restart > 0 && t >= ls.restart) ? t % ls.restart : t + 1;
+    const double bc1 = 1.0 - pow(ls.beta1, (double)cnt);
+    const double bc2 = 1.0 - pow(ls.beta2, (double)cnt);
     StepParams sp;
     sp.t = t;
     sp.src = (int32_t)(t & 1);
-    sp.pad = 0;
+    sp.mix_now = (ls.mix && ls.restart > 0 && t > 0 && t % ls.restart == 0) ? 1 : 0;
     sp.lr = (float)lr;
     sp.step_size = (float)(lr / bc1);
     sp.inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
@@ -404,6 +446,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
   const int s0 = g.gl * 4, w = s0 >> 5, sh = s0 & 31;
   StepParams sp;
   if (mode == 0) sp = *sd.sp;
+  if (mode == 0 && sp.mix_now) return;   // this step mixes assignments (k_mix)
   const int64_t tcur = (mode == 0) ? sp.t : hdr->t;
   const uint32_t *bsrc = cur_bits(sd, tcur);
   uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
@@ -635,6 +678,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
   uint32_t *nbuf = cbuf;                                                             // [256 nibbles] after the counts
   StepParams sp;
   if (MODE == 0) sp = *sd.sp;
+  if (MODE == 0 && sp.mix_now) return;   // this step mixes assignments (k_mix)
   const int64_t tcur = (MODE == 0) ? sp.t : hdr->t;
   const uint32_t *bsrc = cur_bits(sd, tcur);
   uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
@@ -922,6 +966,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_updateL(ProbDev pd, StateDev sd, 
   int tinst = -1;
   StepParams sp;
   if (MODE == 0) sp = *sd.sp;
+  if (MODE == 0 && sp.mix_now) return;   // this step mixes assignments (k_mix)
   const int64_t tcur = (MODE == 0) ? sp.t : hdr->t;
   const uint32_t *bsrc = cur_bits(sd, tcur);
   uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
@@ -1191,6 +1236,11 @@ static int planes_for(int lmax) {
 cudaError_t launch_init(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const float *logits, float scale,
                         int grid, cudaStream_t st) {
   k_init<<<grid, kBlock, 0, st>>>(pd, sd, hy, logits, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mix(const ProbDev &pd, const StateDev &sd, const Hyper &hy, int grid, cudaStream_t st) {
+  k_mix<<<grid, kBlock, 0, st>>>(pd, sd, hy);
   return cudaGetLastError();
 }
 

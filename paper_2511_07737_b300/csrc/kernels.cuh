@@ -8,11 +8,13 @@ struct LrSched {
   float lr0, factor, floor, wd;
   int32_t period, restart;
   double beta1, beta2;
+  int32_t mix;   // assignment mixing at each restart
 };
 
 // launch helpers (return cudaGetLastError of the launch)
 cudaError_t launch_init(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const float *logits,
                         float scale, int grid, cudaStream_t st);
+cudaError_t launch_mix(const ProbDev &pd, const StateDev &sd, const Hyper &hy, int grid, cudaStream_t st);
 cudaError_t launch_binarize(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const float *zin,
                             int64_t t_bin, int grid, cudaStream_t st);
 cudaError_t launch_fwd_hist(const ProbDev &pd, const StateDev &sd, int32_t *hist, int skip_frozen,

@@ -39,7 +39,7 @@ class tsat_hparams(ctypes.Structure):
                 ("restart_period", ctypes.c_int32), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("eps", ctypes.c_float), ("weight_decay", ctypes.c_float), ("norm", ctypes.c_int32),
                 ("binarize", ctypes.c_int32), ("bin_temp", ctypes.c_float), ("layer", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("mix_restart", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class tsat_cnf_desc(ctypes.Structure):

@@ -30,7 +30,7 @@ def oracle_hp(hp: ts.tsat_hparams) -> oracle.HParams:
     return oracle.hparams(tau=hp.tau, lr0=hp.lr0, lr_factor=hp.lr_factor, lr_floor=hp.lr_floor,
                           decay_period=hp.decay_period, restart_period=hp.restart_period, beta1=hp.beta1,
                           beta2=hp.beta2, eps=hp.eps, weight_decay=hp.weight_decay, norm=hp.norm,
-                          relaxed=hp.layer)
+                          relaxed=hp.layer, mix=hp.mix_restart)
 
 
 def lockstep(cnfs, offsets, hp, t, snap):
@@ -58,7 +58,7 @@ def make(instances, N, layer=ts.LAYER_STE, dtype=ts.DTYPE_F32):
     return prob, st, cnfs
 
 
-def assert_adamw_z(z_gpu, z_ref, m_gpu, m_ref, v_gpu, v_ref, t, hp, tol=TOL_F32):
+def assert_adamw_z(z_gpu, z_ref, m_gpu, m_ref, v_gpu, v_ref, t, hp, tol=TOL_F32, cnt=None):
     """z after AdamW, element by element, within a bound propagated from the
     measured m / v differences (which are themselves held to `tol`).
 
@@ -72,8 +72,9 @@ def assert_adamw_z(z_gpu, z_ref, m_gpu, m_ref, v_gpu, v_ref, t, hp, tol=TOL_F32)
     assert rel_err(m_gpu, m_ref) < tol
     assert rel_err(v_gpu, v_ref) < tol
     lr = oracle.lr_at(t, hp.lr0, hp.lr_factor, hp.decay_period, hp.restart_period, hp.lr_floor)
-    bc1 = 1.0 - float(hp.beta1) ** (t + 1)
-    bc2 = 1.0 - float(hp.beta2) ** (t + 1)
+    cnt = t + 1 if cnt is None else cnt        # AdamW step count (restarts with assignment mixing)
+    bc1 = 1.0 - float(hp.beta1) ** cnt
+    bc2 = 1.0 - float(hp.beta2) ** cnt
     vh = np.maximum(v_ref / bc2, 0.0)
     sq = np.sqrt(vh)
     eps = float(hp.eps)

@@ -124,6 +124,36 @@ def test_lockstep_ste(name, gen, N, kw, steps):
     assert ts.tsat_status(st.h, len(insts))["step"] == steps
 
 
+def test_lockstep_assignment_mixing_at_restarts():
+    # restart period 3: steps 3 and 6 mix assignments per instance (best sample
+    # kept, the others averaged with it, moments zeroed), the AdamW step count
+    # restarts after each; both layouts of instance rows in a warp (N = 64)
+    insts = [cnfgen.planted_ksat(90, 380, 3, 41), cnfgen.planted_ksat(70, 290, 3, 42)]
+    prob, st, cnfs = make(insts, 64)
+    hp = ts.hparams(seed=5, tau=1.5, norm=1, binarize=1, restart_period=3, decay_period=1, mix_restart=1)
+    ts.tsat_init(st.h, hp)
+    offs = prob.var_offsets
+    for t in range(8):
+        s0 = snapshot(st)
+        ts.tsat_step(st.h, hp, 1, stop_on_sat=False)
+        s1 = snapshot(st)
+        z, m, v, res = lockstep(cnfs, offs, hp, t, s0)
+        status = ts.tsat_status(st.h, len(insts))
+        for j, r in enumerate(res):
+            assert status["inst"][j]["min_unsat"] == int(r["unsat"].min())
+            assert status["inst"][j]["best_sample"] == int(np.argmin(r["unsat"]))
+        if t > 0 and t % 3 == 0:
+            assert rel_err(s1["z"], z) < 1e-6
+            assert not s1["m"].any() and not s1["v"].any()
+        else:
+            cnt = t % 3 if t >= 3 else t + 1
+            assert_adamw_z(s1["z"], z, s1["m"], m, s1["v"], v, t, hp, cnt=cnt)
+        X = oracle.binarize_f32(s1["z"], s1["nu"], hp.binarize, c=0.25 / hp.bin_temp, seed=hp.seed, t=t + 1)
+        np.testing.assert_array_equal(s1["X"], X)
+        nu_ref = oracle.nu_f32(s1["z"], hp.norm)
+        assert np.all(np.abs(s1["nu"] - nu_ref) <= 2e-6 * np.abs(s1["z"]).mean(axis=1) + 2e-6 * np.abs(nu_ref))
+
+
 @pytest.mark.parametrize("norm,k,N", [(0, 3, 128), (1, 3, 128), (2, 3, 128), (1, 5, 64), (0, 6, 256)])
 def test_autograd_hooks_match_oracle_gradient(norm, k, N):
     m = 2130 if k == 3 else int(round(0.8 * cnfgen.KSAT_THRESHOLD[k] * 500))

@@ -216,3 +216,53 @@ def test_oracle_solves_small_planted():
             found = True
             break
     assert found
+
+
+def _mix_case(seed=0, V=12, N=16, R=3):
+    from paper_2511_07737_b300 import cnfgen
+    inst = cnfgen.planted_ksat(V, 40, 3, seed)
+    cnf = oracle.CNF(inst.n_vars, inst.clause_ptr, inst.lits)
+    rng = np.random.default_rng(seed)
+    z = rng.normal(size=(V, N))
+    m = rng.normal(size=(V, N)) * 0.1
+    v = rng.random((V, N)) * 0.1
+    X = (rng.random((V, N)) < 0.5).astype(np.uint8)
+    return cnf, z, m, v, X, R
+
+
+def test_mixing_step_keeps_best_and_averages_the_rest():
+    # at an lr restart t = R with mixing on: i* = the sample with the fewest
+    # unsatisfied clauses (lowest index on ties) keeps its z, every other
+    # sample moves half way to it, the moments are zeroed, no gradient step
+    cnf, z, m, v, X, R = _mix_case()
+    hp = oracle.hparams(norm=1, restart_period=R, mix=1)
+    unsat, _ = oracle.check(cnf, X)
+    best = int(np.argmin(unsat))
+    z0 = z.copy()
+    out = oracle.step(cnf, hp, R, z, m, v, X=X)
+    np.testing.assert_array_equal(out["unsat"], unsat)
+    np.testing.assert_array_equal(z[:, best], z0[:, best])
+    others = np.arange(z.shape[1]) != best
+    np.testing.assert_allclose(z[:, others], 0.5 * (z0[:, others] + z0[:, [best]]), rtol=0, atol=0)
+    assert not m.any() and not v.any()
+    # not a restart step, or mixing off: an ordinary AdamW step
+    for t, mix in ((R + 1, 1), (R, 0)):
+        cnf, z, m, v, X, R = _mix_case(1)
+        z0 = z.copy()
+        oracle.step(cnf, oracle.hparams(norm=1, restart_period=R, mix=mix), t, z, m, v, X=X)
+        assert m.any() and not np.array_equal(z, z0)
+
+
+def test_first_step_after_a_mixing_restart_is_a_fresh_adam_step():
+    # after the reset m = v = 0 and the step count restarts at 1, so the bias
+    # corrected update is g / (|g| + eps) per element (closed form of AdamW's
+    # first step): z' = z (1 - lr wd) - lr g / (|g| + eps)
+    cnf, z, m, v, X, R = _mix_case(2)
+    hp = oracle.hparams(norm=1, restart_period=R, mix=1, weight_decay=0.01)
+    oracle.step(cnf, hp, R, z, m, v, X=X)               # mixing step: m = v = 0
+    z1 = z.copy()
+    out = oracle.step(cnf, hp, R + 1, z, m, v, X=X)
+    g = out["g"]
+    lr = oracle.lr_at(R + 1, hp.lr0, hp.lr_factor, hp.decay_period, hp.restart_period, hp.lr_floor)
+    ref = z1 * (1 - lr * hp.weight_decay) - lr * g / (np.abs(g) + hp.eps)
+    np.testing.assert_allclose(z, ref, rtol=1e-12, atol=1e-15)
