@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--experiment", default="throughput",
-                    choices=["throughput", "time_to_sat", "batch", "relaxed", "proposer"],
+                    choices=["throughput", "time_to_sat", "batch", "relaxed", "proposer", "mixing"],
                     help="throughput (default, the driver's line) or one of the other workloads")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the experiment workloads (quick runs)")
     return ap.parse_args()
@@ -557,6 +557,42 @@ def exp_proposer(args):
            "eval_4sat_ratio_9.0": r_hard, "eval_4sat_0.6x_threshold": r_easy})
 
 
+def exp_mixing(args):
+    """Assignment mixing at lr restarts on or off, same schedule (restart 360,
+    decay 30): 32 planted 3-SAT instances n=1000 m=4000 (ratio 4.0) solved as
+    one batch, N=64, absmean, tau 2, lr0 0.5, cap 1440 steps (4 restarts)."""
+    import torch
+    from paper_2511_07737_b300 import cnfgen
+    from paper_2511_07737_b300 import turbosat as ts
+    n_inst = max(4, int(32 * args.scale))
+    insts = [cnfgen.planted_ksat(1000, 4000, 3, 700 + j) for j in range(n_inst)]
+    prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in insts])
+    out = {"experiment": "mixing", "workload": f"{n_inst} x planted 3-SAT n=1000 m=4000, N=64, cap 1440 steps",
+           "results": {}}
+    for mix in (0, 1):
+        st = ts.State(prob, 64)
+        hp = ts.hparams(seed=9, norm=1, tau=2.0, lr0=0.5, mix_restart=mix)
+        ts.tsat_init(st.h, hp)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = 0
+        while done < 1440:
+            ts.tsat_step(st.h, hp, 120, stop_on_sat=True)
+            done += 120
+            if ts.tsat_status(st.h, n_inst)["all_done"]:
+                break
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        status = ts.tsat_status(st.h, n_inst)
+        steps = [x["found_step"] for x in status["inst"] if x["found"]]
+        out["results"]["mix" if mix else "no_mix"] = {
+            "solved": len(steps), "median_found_step": float(np.median(steps)) if steps else None,
+            "mean_min_unsat_unsolved": float(np.mean([x["min_unsat"] for x in status["inst"] if not x["found"]] or [0])),
+            "seconds": el}
+        del st
+    _emit(out)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -567,7 +603,7 @@ def main():
     if args.experiment != "throughput":
         if rank == 0:
             {"time_to_sat": exp_time_to_sat, "batch": exp_batch, "relaxed": exp_relaxed,
-             "proposer": exp_proposer}[args.experiment](args)
+             "proposer": exp_proposer, "mixing": exp_mixing}[args.experiment](args)
         return
     ours(args, w, rank, world, local)
 
