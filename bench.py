@@ -63,6 +63,7 @@ def parse():
                     choices=["throughput", "time_to_sat", "batch", "relaxed", "proposer", "mixing"],
                     help="throughput (default, the driver's line) or one of the other workloads")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the experiment workloads (quick runs)")
+    ap.add_argument("--solve-steps", type=int, default=1000, help="step cap of the batch experiment's solve phase")
     return ap.parse_args()
 
 
@@ -461,7 +462,7 @@ def exp_batch(args):
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     done = 0
-    while done < 1000:
+    while done < args.solve_steps:
         ts.tsat_step(st.h, hp, 100, stop_on_sat=True)
         done += 100
         if ts.tsat_status(st.h, n_inst)["all_done"]:
@@ -484,7 +485,7 @@ def exp_batch(args):
            "samples_per_instance": 64, "n_vars": info["n_vars"], "n_clauses": info["n_clauses"], "nnz": info["nnz"],
            "lmax": info["lmax"], "steps": K, "ms_per_step": ms / K, "evals_per_s": info["nnz"] * 64 * K / (ms / 1e3),
            "kernel_ms": {"forward": kms[0], "gamma": kms[1], "update": kms[2]}, "tuning": tun,
-           "solve": {"steps_cap": 1000, "steps_run": done, "seconds": solve_s,
+           "solve": {"steps_cap": args.solve_steps, "steps_run": done, "seconds": solve_s,
                      "solved": sum(d["solved"] for d in by_k.values()), "by_k": by_k},
            "generation_s": gen_s})
 
