@@ -193,6 +193,14 @@ int tsat_profile_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, fl
 int tsat_evaluate(tsat_state *s, const tsat_hparams *hp, int32_t *d_unsat, uint32_t *d_satmask,
                   float *d_loss, cudaStream_t stream);
 
+/* The forward product of the current bits as per-sample histograms (Sec.
+ * III-A, Eq. 1): d_hist int32 [n_inst][lmax+1][N] (lmax = the longest clause
+ * of the batch, tsat_problem_info), d_hist[j][r][i] = number of clauses of
+ * instance j whose R_ci = r, the count of true literals of clause c in sample
+ * i (r = 0: unsatisfied).  Integer exact.  The caller owns d_hist; it is
+ * overwritten.  Async on `stream`. */
+int tsat_histogram(tsat_state *s, int32_t *d_hist, cudaStream_t stream);
+
 /* Evaluation without any device allocation.  The paper has no counterpart:
  * this exists for callers that cannot call cudaMalloc (code running inside a
  * memory pool it does not own, or a process whose device memory another

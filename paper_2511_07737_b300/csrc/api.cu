@@ -449,6 +449,18 @@ int tsat_evaluate(tsat_state *s, const tsat_hparams *hp, int32_t *d_unsat, uint3
   return leave(s, stream);
 }
 
+int tsat_histogram(tsat_state *s, int32_t *d_hist, cudaStream_t stream) {
+  if (!s || !d_hist) { set_error("NULL argument"); return TSAT_EINVAL; }
+  if (!s->initialised) { set_error("state not initialised"); return TSAT_ESTATE; }
+  int rc;
+  if ((rc = enter(s, stream))) return rc;
+  const ProbDev &pd = s->prob->dev;
+  TSAT_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(int32_t) * (size_t)pd.n_inst * s->dev.lm1 * s->N, s->stream));
+  cudaError_t e = launch_fwd_hist(pd, s->dev, d_hist, 0, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "forward");
+  return leave(s, stream);
+}
+
 int tsat_best(tsat_state *s, const tsat_hparams *hp, int32_t inst, int32_t k, uint32_t *h_bits, int32_t *h_unsat,
               int32_t *h_sample, int32_t *h_part_var, uint8_t *h_part_val, int32_t *h_ready, cudaStream_t stream) {
   if (!s || !h_bits || !h_unsat || !h_sample || !h_part_var || !h_part_val) {

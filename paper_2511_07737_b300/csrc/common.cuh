@@ -38,6 +38,11 @@ struct ProbDev {
   const int32_t *var_inst; // [V]
   const int4 *items;       // [n_items] {inst, clause begin, clause end, 0}
   const InstInfo *inst;    // [n_inst]
+  const int4 *crec;        // [C] clause records {var0, var1, var2, flags} when every clause has <= 3
+                           // literals, else NULL; flags byte u = 0xFF if literal u is negated, byte 3 =
+                           // clause length; a missing literal repeats var0 (the kernels mask it)
+  int32_t full3;           // every clause has exactly 3 literals
+  int32_t pad_;
 };
 
 // Device header of a state buffer.

@@ -34,7 +34,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 constexpr int kItemMin = 512;
 
 struct Layout {  // byte offsets inside the problem workspace
-  size_t cptr, clit, xptr, xrec, vptr, vocc, var_inst, items, inst, err;
+  size_t cptr, clit, xptr, xrec, vptr, vocc, var_inst, items, inst, err, crec;
   size_t raw_cptr, raw_lits, tmp, clen, deg, recsz, fill, occ_j, occ_c, occ_s, scan_tmp;
   size_t total;
   int64_t xrec_cap, items_cap, scan_blocks;

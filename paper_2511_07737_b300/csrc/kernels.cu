@@ -291,6 +291,164 @@ __global__ void __launch_bounds__(kBlock) k_fwd_hist(ProbDev pd, StateDev sd, in
   }
 }
 
+// ------------------------------------------------------------------ forward histogram, word per lane
+// Clause length <= 3 and N >= 512 (W >= 16 words per row).  A row group of W
+// lanes takes one clause at a time: lane w gathers word w of the clause's three
+// literal rows (W consecutive words, one 128-byte line per literal when W = 32)
+// and forms R's bit planes for its 32 samples, p0 = [R odd], p1 = [R >= 2].
+// The masks p0, p1 and p0 & p1 are added into vertical (bit-sliced) counters
+// with carry-save adders (Harley-Seal: seven CSAs per mask per 8 clauses, the
+// eights rippled into a 5-plane counter).  Their sums are C0 = h1 + h3,
+// C1 = h2 + h3 and C01 = h3, so over n clauses
+//   h3 = C01, h2 = C1 - C01, h1 = C0 - C01, h0 = (n - C0) - h2.
+// Every <= 248 clauses a lane turns its counters into per-sample byte counts
+// and adds them to the block's histogram in shared memory; at the end the
+// block adds its histogram to the global one.  Compared with k_fwd_hist (lane
+// = clause, 32x32 warp transposes) this issues about a third of the
+// instructions per clause and gathers whole lines instead of 16-byte pieces.
+constexpr int kFwdUnitsPerFlush = 31;   // 8-clause units between flushes: counts <= 248 fit a byte
+
+// lo + b + c = 2 hi + lo' (one carry-save adder, two 3-input logic ops)
+__device__ __forceinline__ void csa(uint32_t &hi, uint32_t &lo, uint32_t b, uint32_t c) {
+  const uint32_t u = lo ^ b;
+  hi = (lo & b) | (u & c);
+  lo = u ^ c;
+}
+
+// Column j of a vertical counter (planes pl[0..7], weights 1..128) as strided
+// byte counts: byte q = the count of sample 8 q + j of the word.
+__device__ __forceinline__ uint32_t vertical_column(const uint32_t (&pl)[8], int j) {
+  uint32_t a = 0;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) a += ((pl[b] >> j) & 0x01010101u) << b;
+  return a;
+}
+
+// The three masks of one clause for this lane's 32 samples.  MASKED: the clause
+// may lie past the item's end (valid = 0) or be shorter than 3 literals.
+template <bool MASKED>
+__device__ __forceinline__ void clause_masks(const ProbDev &pd, const uint32_t *bw, int W, int c, bool valid,
+                                             uint32_t &m0, uint32_t &m1, uint32_t &m2) {
+  const int4 cr = __ldg(pd.crec + c);
+  uint32_t a = __ldg(bw + (size_t)cr.x * W) ^ __byte_perm((uint32_t)cr.w, 0u, 0x0000u);
+  uint32_t b = __ldg(bw + (size_t)cr.y * W) ^ __byte_perm((uint32_t)cr.w, 0u, 0x1111u);
+  uint32_t d = __ldg(bw + (size_t)cr.z * W) ^ __byte_perm((uint32_t)cr.w, 0u, 0x2222u);
+  if constexpr (MASKED) {
+    const uint32_t len = valid ? ((uint32_t)cr.w >> 24) : 0u;
+    a = len > 0 ? a : 0u;
+    b = len > 1 ? b : 0u;
+    d = len > 2 ? d : 0u;
+  }
+  m0 = a ^ b ^ d;
+  m1 = (a & b) | (d & (a ^ b));
+  m2 = m0 & m1;
+}
+
+// One unit: 8 clauses of this row group (c, c + RW, ..., c + 7 RW), their
+// masks added into the vertical counters pl[mask][plane].
+template <bool MASKED>
+__device__ __forceinline__ void fwd_unit(const ProbDev &pd, const uint32_t *bw, int W, int RW, int c, int cend,
+                                         uint32_t (&pl)[3][8]) {
+  uint32_t fA[3];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t m[3][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int ck = c + (4 * h + k) * RW;
+      const bool ok = !MASKED || ck < cend;
+      clause_masks<MASKED>(pd, bw, W, ok ? ck : cend - 1, ok, m[0][k], m[1][k], m[2][k]);
+    }
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      uint32_t tA, tB, fX;
+      csa(tA, pl[s][0], m[s][0], m[s][1]);
+      csa(tB, pl[s][0], m[s][2], m[s][3]);
+      csa(fX, pl[s][1], tA, tB);
+      if (h == 0) {
+        fA[s] = fX;
+      } else {
+        uint32_t e;
+        csa(e, pl[s][2], fA[s], fX);
+#pragma unroll
+        for (int q = 3; q < 8; ++q) {
+          const uint32_t cy = pl[s][q] & e;
+          pl[s][q] ^= e;
+          e = cy;
+        }
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock, 4) k_fwd_w3(ProbDev pd, StateDev sd, int32_t *hist, int skip_frozen) {
+  extern __shared__ int32_t shh[];   // [nr][N] block histogram; sample 32 w + i at 32 w + ((i + w) & 31)
+  const StateHdr *hdr = sd.hdr;
+  if (skip_frozen && hdr->all_done) return;
+  const int4 it = pd.items[blockIdx.x];
+  const int inst = it.x;
+  if (skip_frozen && sd.inst[inst].found) return;
+  const int W = sd.W, N = sd.N, RW = 32 / W, lm1 = sd.lm1;
+  const int nr = min(pd.inst[inst].lmax, 3) + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rsub = lane / W, w = lane % W;
+  for (int i = threadIdx.x; i < nr * N; i += kBlock) shh[i] = 0;
+  __syncthreads();
+  const uint32_t *bw = cur_bits(sd, hdr->t) + w;
+  const int U = 8 * RW;
+  const int nunits = (it.z - it.y + U - 1) / U;
+  uint32_t pl[3][8];
+#pragma unroll
+  for (int s = 0; s < 3; ++s)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pl[s][q] = 0u;
+  int n = 0, since = 0;
+  for (int u = warp; u < nunits; u += kWarps) {
+    const int c = it.y + u * U + rsub;
+    if (pd.full3 && it.y + (u + 1) * U <= it.z) {   // a whole unit of 3-literal clauses
+      fwd_unit<false>(pd, bw, W, RW, c, it.z, pl);
+      n += 8;
+    } else {
+      fwd_unit<true>(pd, bw, W, RW, c, it.z, pl);
+      n += max(0, min(8, (it.z - c + RW - 1) / RW));
+    }
+    ++since;
+    const bool last = u + kWarps >= nunits;
+    if (since == kFwdUnitsPerFlush || last) {
+      // per-sample byte counts of the three masks, then h0..h3 (no byte borrows: all are >= 0)
+      const uint32_t nrep = (uint32_t)n * 0x01010101u;
+#pragma unroll 1
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t c0 = vertical_column(pl[0], j), c1 = vertical_column(pl[1], j);
+        const uint32_t c01 = vertical_column(pl[2], j);
+        const uint32_t h3 = c01, h2 = c1 - c01, h1 = c0 - c01, h0 = (nrep - c0) - h2;
+        const uint32_t hv[4] = {h0, h1, h2, h3};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int idx = 32 * w + ((8 * q + j + w) & 31);
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (r < nr) atomicAdd(shh + r * N + idx, (int32_t)((hv[r] >> (8 * q)) & 0xFFu));
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) pl[s][q] = 0u;
+      n = 0;
+      since = 0;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nr * N; i += kBlock) {
+    const int val = shh[i];
+    if (!val) continue;
+    const int r = i / N, k = i - r * N, wd = k >> 5;
+    const int sample = 32 * wd + (((k & 31) - wd) & 31);
+    atomicAdd(hist + ((size_t)inst * lm1 + r) * N + sample, val);
+  }
+}
+
 // Per-instance loss / best sample / exact-SAT freeze, then (step mode) the
 // step scalars: lr(t) of Sec. IV-A, AdamW bias corrections, t <- t + 1.
 __device__ void gamma_tail(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls,
@@ -1261,6 +1419,11 @@ cudaError_t launch_relaxed_lits(const ProbDev &pd, const StateDev &sd, const Hyp
 cudaError_t launch_fwd_hist(const ProbDev &pd, const StateDev &sd, int32_t *hist, int skip_frozen, cudaStream_t st) {
   const int P = planes_for(pd.lmax);
   const int W = sd.W;
+  if (pd.crec && pd.lmax <= 3 && W >= 16) {   // word per lane (clause records, vertical counters)
+    const int smem = (int)sizeof(int32_t) * 4 * sd.N;
+    k_fwd_w3<<<pd.n_items, kBlock, smem, st>>>(pd, sd, hist, skip_frozen);
+    return cudaGetLastError();
+  }
   const int WB = (P >= 4) ? 1 : (W >= 4 ? 4 : W);
   dim3 grid(pd.n_items), block(kBlock);
 #define FWD(PP, WW) k_fwd_hist<PP, WW><<<grid, block, 0, st>>>(pd, sd, hist, skip_frozen)

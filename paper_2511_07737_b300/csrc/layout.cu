@@ -201,6 +201,23 @@ __global__ void k_compact_count(const int64_t *raw_cptr, const int32_t *tmp, con
   }
 }
 
+// Fixed clause records for clause length <= 3: {var0, var1, var2, flags},
+// flags byte u = 0xFF when literal u is negated, byte 3 = the clause length; a
+// missing literal repeats var0 with flag byte 0 (the kernels mask it by length).
+__global__ void k_crec(const int32_t *cptr, const int32_t *clit, int32_t C, int4 *crec) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const int32_t b = cptr[c], n = cptr[c + 1] - b;
+  int32_t v[3];
+  uint32_t fl = (uint32_t)n << 24;
+  for (int u = 0; u < 3; ++u) {
+    const int32_t lit = clit[b + (u < n ? u : 0)];
+    v[u] = lit >> 1;
+    if (u < n && (lit & 1)) fl |= 0xFFu << (8 * u);
+  }
+  crec[c] = make_int4(v[0], v[1], v[2], (int32_t)fl);
+}
+
 __global__ void k_fill(const int32_t *cptr, const int32_t *clit, int32_t C, const int32_t *vptr,
                        int32_t *fill, int32_t *occ_j, int32_t *occ_c) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -338,6 +355,7 @@ static Layout plan(const Sizes &s) {
   L.items = take(sizeof(int4) * s.items_cap);
   L.inst = take(sizeof(InstInfo) * s.n_inst);
   L.err = take(64);
+  L.crec = s.lraw <= 3 ? take(sizeof(int4) * s.C) : 0;   // fixed clause records (clause length <= 3)
   L.raw_cptr = take(sizeof(int64_t) * (s.C + 1));
   L.raw_lits = take(sizeof(int32_t) * (s.nnz_raw + 1));
   L.tmp = take(sizeof(int32_t) * (s.nnz_raw + 1));
@@ -510,6 +528,10 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
   CK(cudaGetLastError());
   k_var_inst<<<gv, T, 0, stream>>>(dinst, n_inst, p->V, P32(L.var_inst));
   CK(cudaGetLastError());
+  if (L.crec) {
+    k_crec<<<gc, T, 0, stream>>>(P32(L.cptr), P32(L.clit), p->C, (int4 *)(w + L.crec));
+    CK(cudaGetLastError());
+  }
   int32_t nnz32 = 0;
   int64_t xlen = 0;
   CK(cudaMemcpyAsync(&nnz32, P32(L.cptr) + s.C, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
@@ -538,6 +560,8 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
   D.var_inst = P32(L.var_inst);
   D.items = (const int4 *)(w + L.items);
   D.inst = dinst;
+  D.crec = L.crec ? (const int4 *)(w + L.crec) : nullptr;
+  D.full3 = (L.crec && p->nnz == 3LL * p->C) ? 1 : 0;
   int rc3 = p->set_items(1024, stream);   // forward work items of 1024 clauses (measured 512..4096: near the best)
   if (rc3) return fail(rc3);
   *out = p;

@@ -82,6 +82,7 @@ def lib():
             "tsat_step_prepare": (ctypes.c_int, [P, P, i32, i32]),
             "tsat_profile_step": (ctypes.c_int, [P, P, i32, P]),
             "tsat_evaluate": (ctypes.c_int, [P, P, P, P, P, P]),
+            "tsat_histogram": (ctypes.c_int, [P, P, P]),
             "tsat_best": (ctypes.c_int, [P, P, i32, i32, P, P, P, P, P, P, P]),
             "tsat_partial_k": (i32, [i32]),
             "tsat_status": (ctypes.c_int, [P, P, P, P, P]),
@@ -224,6 +225,11 @@ def tsat_profile_step(s, hp: tsat_hparams, n_steps: int) -> list:
 def tsat_evaluate(s, hp, unsat: torch.Tensor, satmask: torch.Tensor, loss: torch.Tensor | None = None, stream=None):
     _ck(lib().tsat_evaluate(s, ctypes.byref(hp), _ptr(unsat), _ptr(satmask), _ptr(loss), _stream(stream)),
         "tsat_evaluate")
+
+
+def tsat_histogram(s, hist: torch.Tensor, stream=None):
+    """Per-sample histograms of R = P A at the current bits, int32 [n_inst][lmax+1][N]."""
+    _ck(lib().tsat_histogram(s, _ptr(hist), _stream(stream)), "tsat_histogram")
 
 
 def tsat_evaluate_bits_noalloc(h, bits: torch.Tensor, n_samples: int, tau: float, unsat: torch.Tensor,
