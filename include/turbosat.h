@@ -262,7 +262,8 @@ int tsat_backward(tsat_state *s, const tsat_hparams *hp, const float *d_z, float
  * Launch shapes of the forward and update kernels.  tsat_autotune times the
  * candidate shapes on this state with hp (state contents are restored) and
  * keeps the fastest; tsat_get_tuning / tsat_set_tuning read or force them.
- * h_tuning = {fwd_chunk_clauses, fwd_block_threads, upd_blocks_per_sm, upd_rows_per_item}. */
+ * h_tuning = {fwd_chunk_clauses, fwd_block_threads, upd_blocks_per_sm, upd_rows_per_item};
+ * upd_blocks_per_sm in [0, 128], 0 = the default (resident blocks x 8 waves). */
 int tsat_autotune(tsat_state *s, const tsat_hparams *hp, cudaStream_t stream, int32_t h_tuning[4]);
 int tsat_get_tuning(const tsat_state *s, int32_t h_tuning[4]);
 int tsat_set_tuning(tsat_state *s, const int32_t h_tuning[4]);

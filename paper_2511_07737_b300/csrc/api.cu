@@ -116,8 +116,8 @@ static int leave(tsat_state *s, cudaStream_t user) {
 // Update grid: resident blocks per SM (occupancy API) unless tuned explicitly.
 static int upd_grid(const tsat_state *s) {
   const int bps = s->upd_blocks_per_sm > 0 ? s->upd_blocks_per_sm : update_blocks_per_sm(s->prob->dev, s->dev);
-  // no more blocks than row groups of a block (8 warps x 32/W rows)
-  const int64_t rows_per_block = (int64_t)kWarps * (32 / s->dev.W);
+  // no more blocks than needed to give every warp a row group (32/W rows)
+  const int64_t rows_per_block = (int64_t)update_warps_per_block(s->prob->dev, s->dev) * (32 / s->dev.W);
   const int64_t need = (s->prob->dev.V + rows_per_block - 1) / rows_per_block;
   return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)s->sm_count * bps, need));
 }
@@ -602,7 +602,7 @@ int tsat_get_tuning(const tsat_state *s, int32_t h_tuning[4]) {
 
 int tsat_set_tuning(tsat_state *s, const int32_t h_tuning[4]) {
   if (!s || !h_tuning) return TSAT_EINVAL;
-  if (h_tuning[0] < kItemMin || h_tuning[1] != kBlock || h_tuning[2] < 0 || h_tuning[2] > 32 || h_tuning[3] < 1 ||
+  if (h_tuning[0] < kItemMin || h_tuning[1] != kBlock || h_tuning[2] < 0 || h_tuning[2] > 128 || h_tuning[3] < 1 ||
       h_tuning[3] > 4096) {
     set_error("tuning values out of range");
     return TSAT_EINVAL;
@@ -623,7 +623,9 @@ int tsat_autotune(tsat_state *s, const tsat_hparams *hp, cudaStream_t stream, in
   // Each candidate runs one step from a fresh init (the init is repeated at the
   // end, so the state is left as tsat_init(hp) leaves it).
   const int items[] = {512, 1024, 2048, 4096};
-  const int bps[] = {3, 6, 12, 24, 32};
+  // blocks per SM around the default (resident blocks x 8 waves): 1, 2, 4, 8 and 10 waves
+  const int bdef = update_blocks_per_sm(s->prob->dev, s->dev);
+  const int bps[] = {std::max(1, bdef / 8), std::max(1, bdef / 4), std::max(1, bdef / 2), bdef, bdef * 5 / 4};
   const int rpi[] = {1, 8, 64};
   cudaEvent_t a, b;
   TSAT_CUDA(cudaEventCreate(&a));

@@ -786,10 +786,15 @@ __device__ __forceinline__ float biased_byte(uint32_t x, uint32_t q) {
 // read hits L2).  Row reductions (Eq. 5 dot product, new normaliser) are
 // shuffles across the row's lanes; each lane binarises its 4 samples into a
 // nibble and lane w assembles bits word w from the eight nibbles of its
-// samples.  The passes are rolled (unroll 2) to keep the kernel's code small:
-// with 24 warps per SM in different phases, instruction-cache misses cost
-// more than the loop overhead.
+// samples.  The counting loop and the two sample passes are unrolled by 2
+// (two passes' z, m, v loads in flight: 6.24 -> 6.01 ms at n = 1e6); full
+// unrolling loses: with 24 warps per SM in different phases,
+// instruction-cache misses cost more than the loop overhead.
 constexpr int kCntChunk = 127;   // occurrences per byte-counter chunk (|count| <= 127)
+// Blocks of 4 warps at <= 73 registers: 7 blocks (28 warps) per SM.  Measured
+// at n = 1e6, N = 1024: 5.97 ms, against 6.02 ms for 8-warp blocks at 80
+// registers (24 warps per SM) and 6.42 ms at 64 registers (spills).
+constexpr int kUpd3Block = 128, kUpd3Warps = 4, kUpd3MinB = 7;
 
 __device__ __forceinline__ float seg_sum(float x, int W) {
   for (int o = 1; o < W; o <<= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
@@ -823,7 +828,7 @@ __device__ __forceinline__ float4 f4_add(float4 a, float4 b) {
 // update).  BIN and NORM are the binarisation and Eq. 5 modes: one kernel per
 // combination keeps each kernel's code small and free of mode branches.
 template <int MODE, int BIN, int NORM>
-__global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, Hyper hy, const float *zin, float *grad,
+__global__ void __launch_bounds__(kUpd3Block, kUpd3MinB) k_update3(ProbDev pd, StateDev sd, Hyper hy, const float *zin, float *grad,
                                                        float dL) {
   extern __shared__ __align__(16) float sm3[];
   const StateHdr *hdr = sd.hdr;
@@ -842,13 +847,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
   uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
   const float *zsrc = (MODE == 0) ? sd.z : zin;
   const int4 *xrec4 = reinterpret_cast<const int4 *>(pd.xrec);
-  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int64_t nwarps = (int64_t)gridDim.x * kUpd3Warps;
   const int ist = 8 * lane;          // count words this lane stores: its 32 samples
   const int isam = rsub * 8 * W + w; // + W k: the word of this lane's samples in pass k
   // first record round of the row group's current row, loaded during the previous row
   int4 crec = make_int4(0, 0, 0, 0);
   bool have_crec = false;
-  for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * RW; base < pd.V; base += nwarps * RW) {
+  for (int64_t base = ((int64_t)blockIdx.x * kUpd3Warps + warp) * RW; base < pd.V; base += nwarps * RW) {
     __syncwarp();   // the previous row's readers of gbuf / zbuf are done
     const int64_t v = base + rsub;
     const bool valid = v < pd.V;
@@ -968,7 +973,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
     float part = 0.f;
     if (act) {
       const float ns = (float)nsign;
-#pragma unroll 1
+#pragma unroll 2
       for (int k = 0; k < 8; ++k) {
         const int s4 = W * k + w, ci = cswz(isam + W * k);
         const float4 z4 = __ldg(z4p + s4);
@@ -990,7 +995,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_update3(ProbDev pd, StateDev sd, 
     // ---- pass 2: Eq. 5 chain rule and AdamW (or the gradient for the autograd backward)
     float psum = 0.f;
     if (act) {
-#pragma unroll 1
+#pragma unroll 2
       for (int k = 0; k < 8; ++k) {
         const size_t off = rowoff + 4 * (W * k + w);
         const float4 g4 = gbuf[k * 32 + lane], z4 = __ldg(z4p + W * k + w);
@@ -1307,7 +1312,7 @@ int updateL_smem_bytes(int N) { return kWarps * (32 * kGS + updateL_tab_floats(N
 int update_blocks_per_sm(const ProbDev &pd, const StateDev &sd) {
   int nb = 0;
   if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_stride == 4) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_update3<0, TSAT_BIN_PHILOX, TSAT_NORM_SIGNED_MEAN>, kBlock,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_update3<0, TSAT_BIN_PHILOX, TSAT_NORM_SIGNED_MEAN>, kUpd3Block,
                                                   update3_smem_bytes(sd.N));
     nb *= 8;
   } else if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_stride == 8) {
@@ -1317,10 +1322,14 @@ int update_blocks_per_sm(const ProbDev &pd, const StateDev &sd) {
   } else {
     nb = 24;   // general / relaxed kernel: 3 resident, 8 waves (relaxed n=1e6 N=256: 6.8 -> 5.8 ms)
   }
-  return nb > 0 ? (nb < 32 ? nb : 32) : 1;
+  return nb > 0 ? (nb < 64 ? nb : 64) : 1;
 }
 
-int update3_smem_bytes(int N) { return kWarps * 1792 * (int)sizeof(float); }
+int update3_smem_bytes(int N) { return kUpd3Warps * 1792 * (int)sizeof(float); }
+// Warps per block of the update kernel that launch_update picks.
+int update_warps_per_block(const ProbDev &pd, const StateDev &sd) {
+  return (sd.layer != TSAT_LAYER_RELAXED && pd.rec_stride == 4) ? kUpd3Warps : kWarps;
+}
 
 // ------------------------------------------------------------------ exact check (Sec. III-A)
 // unsat_i = #clauses whose literal words OR to 0 at bit i.  Same warp
@@ -1479,13 +1488,13 @@ static cudaError_t launch_update3_n(const ProbDev &pd, const StateDev &sd, const
   const int smem = update3_smem_bytes(sd.N);
   switch (hy.norm) {
     case TSAT_NORM_SIGNED_MEAN:
-      k_update3<MODE, BIN, TSAT_NORM_SIGNED_MEAN><<<grid, kBlock, smem, st>>>(pd, sd, hy, zin, grad, dL);
+      k_update3<MODE, BIN, TSAT_NORM_SIGNED_MEAN><<<grid, kUpd3Block, smem, st>>>(pd, sd, hy, zin, grad, dL);
       break;
     case TSAT_NORM_ABSMEAN:
-      k_update3<MODE, BIN, TSAT_NORM_ABSMEAN><<<grid, kBlock, smem, st>>>(pd, sd, hy, zin, grad, dL);
+      k_update3<MODE, BIN, TSAT_NORM_ABSMEAN><<<grid, kUpd3Block, smem, st>>>(pd, sd, hy, zin, grad, dL);
       break;
     default:
-      k_update3<MODE, BIN, TSAT_NORM_NONE><<<grid, kBlock, smem, st>>>(pd, sd, hy, zin, grad, dL);
+      k_update3<MODE, BIN, TSAT_NORM_NONE><<<grid, kUpd3Block, smem, st>>>(pd, sd, hy, zin, grad, dL);
       break;
   }
   return cudaGetLastError();

@@ -44,6 +44,7 @@ cudaError_t best_select(const ProbDev &pd, const StateDev &sd, int inst, int n_v
                         cudaStream_t st);
 void prepare_update_attrs(int lmax);
 int update_blocks_per_sm(const ProbDev &pd, const StateDev &sd);
+int update_warps_per_block(const ProbDev &pd, const StateDev &sd);
 
 int update_smem_bytes(int N, int lm1, bool greg);
 
