@@ -150,6 +150,20 @@ __device__ __forceinline__ uint32_t bitslice_eq(const uint32_t (&t)[P], int r) {
   return m;
 }
 
+// AdamW's 1 / (sqrt(v / bc2) + eps), given 1 / sqrt(bc2): the hardware
+// approximations sqrt.approx and rcp.approx (about 1 ulp each) with denormal
+// inputs flushed to zero.  v >= 0 and the denominator is >= eps, so only a
+// denormal v is affected (its square root is far below eps either way);
+// skipping the denormal range fix-ups of sqrtf and of the division saves
+// about 2 % of the fused update's time.
+__device__ __forceinline__ float adam_inv_denom(float v, float inv_sqrt_bc2, float eps) {
+  float s, r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(v));
+  const float d = fmaf(s, inv_sqrt_bc2, eps);
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return r;
+}
+
 __device__ __forceinline__ float guard_nu(float mu) {
   const float g = 1e-12f;
   if (fabsf(mu) < g) return (mu < 0.0f) ? -g : g;

@@ -748,8 +748,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
         const float gs = gq[s];
         mq[s] = b1 * mq[s] + hy.omb1 * gs;
         vq[s] = b2 * vq[s] + hy.omb2 * (gs * gs);
-        const float denom = sqrtf(vq[s]) * sp.inv_sqrt_bc2 + hy.eps;
-        zn[s] = zq[s] * sp.decay - sp.step_size * (mq[s] / denom);
+        zn[s] = zq[s] * sp.decay - sp.step_size * (mq[s] * adam_inv_denom(vq[s], sp.inv_sqrt_bc2, hy.eps));
       }
       st_cs(sd.z + off, make_float4(zn[0], zn[1], zn[2], zn[3]));
       st_cs(sd.m + off, make_float4(mq[0], mq[1], mq[2], mq[3]));
@@ -1021,9 +1020,7 @@ __global__ void __launch_bounds__(kUpd3Block, kUpd3MinB) k_update3(ProbDev pd, S
         for (int e = 0; e < 4; ++e) {
           mq[e] = hy.beta1 * mq[e] + (hy.omb1) * gq[e];
           vq[e] = hy.beta2 * vq[e] + (hy.omb2) * (gq[e] * gq[e]);
-          const float sq = vq[e] > 0.f ? vq[e] * rsqrtf(vq[e]) : 0.f;
-          const float denom = sq * sp.inv_sqrt_bc2 + hy.eps;
-          zn[e] = zq[e] * sp.decay - sp.step_size * __fdividef(mq[e], denom);
+          zn[e] = zq[e] * sp.decay - sp.step_size * (mq[e] * adam_inv_denom(vq[e], sp.inv_sqrt_bc2, hy.eps));
           psum += (NORM == TSAT_NORM_ABSMEAN) ? fabsf(zn[e]) : zn[e];
         }
         const float4 z1 = make_float4(zn[0], zn[1], zn[2], zn[3]);
@@ -1259,9 +1256,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_updateL(ProbDev pd, StateDev sd, 
           for (int e = 0; e < 4; ++e) {
             mq[e] = hy.beta1 * mq[e] + (hy.omb1) * gq[e];
             vq[e] = hy.beta2 * vq[e] + (hy.omb2) * (gq[e] * gq[e]);
-            const float sq = vq[e] > 0.f ? vq[e] * rsqrtf(vq[e]) : 0.f;
-            const float denom = sq * sp.inv_sqrt_bc2 + hy.eps;
-            zn[e] = zq[e] * sp.decay - sp.step_size * __fdividef(mq[e], denom);
+            zn[e] = zq[e] * sp.decay - sp.step_size * (mq[e] * adam_inv_denom(vq[e], sp.inv_sqrt_bc2, hy.eps));
             gp[e * kGS] = zn[e];
             psum += (NORM == TSAT_NORM_ABSMEAN) ? fabsf(zn[e]) : zn[e];
           }
