@@ -358,10 +358,13 @@ def _emit(d):
 
 def exp_time_to_sat(args):
     """Planted 3-SAT n=100 m=426 (ratio 4.26), N=64, step cap 500: wall time
-    from init to the host seeing the found flag (status polled every 10 steps),
-    each instance solved alone; beside it the oracle's wall time to its first
-    satisfying sample on the first instances (same init, settings and
-    deterministic binarization), within a bounded budget."""
+    from init to the host seeing the found flag, each instance solved alone,
+    on the multi-kernel path (10-step graph replays, status polled after each)
+    and on the persistent solver (one launch that stops at the first model);
+    then all instances as one batch in one persistent launch.  Beside them
+    the oracle's wall time to its first satisfying sample on the first
+    instances (same init, settings and deterministic binarization), within a
+    bounded budget."""
     import torch
     from paper_2511_07737_b300 import cnfgen
     from paper_2511_07737_b300 import turbosat as ts
@@ -395,9 +398,45 @@ def exp_time_to_sat(args):
             if found:
                 walls.append(el)
                 steps.append(s_["inst"][0]["found_step"])
+        # the persistent solver: one launch of up to 500 steps (the block stops at
+        # the first model), then one status read
+        walls_p, steps_p = [], []
+        for j, inst in enumerate(insts):
+            prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
+            st = ts.State(prob, 64)
+            hp = ts.hparams(seed=j + 1, **kw)
+            ts.tsat_init(st.h, hp)
+            ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)     # first launch: kernel attributes
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ts.tsat_init(st.h, hp)
+            ts.tsat_step_persistent(st.h, hp, 500, stop_on_sat=True)
+            s_ = ts.tsat_status(st.h, 1)
+            el = time.perf_counter() - t0
+            if s_["inst"][0]["found"]:
+                walls_p.append(el)
+                steps_p.append(s_["inst"][0]["found_step"])
+        # all instances as one batch in one persistent launch
+        prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in insts])
+        st = ts.State(prob, 64)
+        hp = ts.hparams(seed=1, **kw)
+        ts.tsat_init(st.h, hp)
+        ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ts.tsat_init(st.h, hp)
+        ts.tsat_step_persistent(st.h, hp, 500, stop_on_sat=True)
+        sb = ts.tsat_status(st.h, n_inst)
+        batch_s = time.perf_counter() - t0
         out["results"][name] = {"solved": len(walls),
                                 "median_ms_to_sat": 1e3 * float(np.median(walls)) if walls else None,
-                                "median_steps_to_sat": float(np.median(steps)) if steps else None}
+                                "median_steps_to_sat": float(np.median(steps)) if steps else None,
+                                "persistent": {"solved": len(walls_p),
+                                               "median_ms_to_sat": 1e3 * float(np.median(walls_p)) if walls_p else None,
+                                               "median_steps_to_sat": float(np.median(steps_p)) if steps_p else None},
+                                "persistent_batch": {"instances": n_inst,
+                                                     "solved": int(sum(x["found"] for x in sb["inst"])),
+                                                     "ms_all_instances": 1e3 * batch_s, "steps": sb["step"]}}
     if not args.no_cpu:
         import oracle
         oracle.build()

@@ -175,6 +175,24 @@ int tsat_init(tsat_state *s, const tsat_hparams *hp, const float *d_logits, floa
 int tsat_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
               cudaStream_t stream);
 
+/* The same n_steps steps as tsat_step for a batch of small instances, in one
+ * launch: each instance is owned by one thread block, which runs its steps
+ * (Eq. 1 forward, Eq. 4, the STE backward, Eq. 5, AdamW, re-binarisation;
+ * Sec. III-B, IV-A) with block barriers between the phases and no wait on any
+ * other block.  Results follow tsat_step: per-instance freezing at the first
+ * zero-unsat sample, the status records, the step counter and, with
+ * stop_on_sat, the stop once every instance is frozen; FP32 sums may differ
+ * from tsat_step in rounding order, integers and bits agree given the same
+ * FP32 state.  Each block keeps its instance's bits (both step parities) in
+ * shared memory.  Requirements: the STE layer, hp->mix_restart = 0, clauses
+ * of at most 7 literals, clauses x longest clause x samples <= 2^26 per
+ * instance, and 4 (16.25 N + 2 n_vars N / 32) bytes of shared memory <= 200
+ * KiB for the largest instance (about 25,000 variables at N = 32, 12,500 at
+ * N = 64, 540 at N = 1024); else TSAT_EINVAL / TSAT_ERANGE.  Async on
+ * `stream`. */
+int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
+                         cudaStream_t stream);
+
 /* Capture and instantiate the graph tsat_step(hp, n_steps, stop_on_sat) would
  * replay, without running it (keeps graph building out of timed regions). */
 int tsat_step_prepare(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat);

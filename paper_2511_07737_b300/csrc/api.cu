@@ -273,6 +273,7 @@ __global__ void k_reset(StateDev sd, int n_inst) {
     sd.hdr->all_done = 0;
     sd.hdr->err = 0;
     sd.hdr->n_active = n_inst;
+    sd.hdr->blocks_done = 0;
   }
   if (j < n_inst) {
     InstState is{};
@@ -371,6 +372,42 @@ int tsat_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t st
   cudaGraphExec_t exec = nullptr;
   if ((rc = get_graph(s, hp, n_steps, stop_on_sat, &exec))) return rc;
   TSAT_CUDA(cudaGraphLaunch(exec, s->stream));
+  return leave(s, stream);
+}
+
+int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
+                         cudaStream_t stream) {
+  int rc = check_step_args(s, hp, n_steps);
+  if (rc) return rc;
+  const tsat_problem *p = s->prob;
+  if (s->layer != TSAT_LAYER_STE || hp->mix_restart) {
+    set_error("the persistent solver runs the STE layer without assignment mixing");
+    return TSAT_EINVAL;
+  }
+  if (p->lmax > 7 || (p->dev.rec_stride != 4 && p->dev.rec_stride != 8)) {
+    set_error("the persistent solver needs clauses of at most 7 literals (longest: %d)", p->lmax);
+    return TSAT_EINVAL;
+  }
+  int32_t vmax = 0;
+  for (const InstInfo &I : p->inst) {
+    vmax = std::max(vmax, I.n_vars);
+    if ((int64_t)I.n_clauses * I.lmax * s->N > kPersistMaxWork) {
+      set_error("instance too large for one block: %d clauses x %d literals x %d samples > %lld", I.n_clauses,
+                I.lmax, s->N, (long long)kPersistMaxWork);
+      return TSAT_ERANGE;
+    }
+  }
+  if (persist_smem_bytes(s->N, vmax, false) > kPersistMaxSmem) {
+    set_error("instance too large for one block: %d variables x %d samples need %lld bytes of shared memory",
+              vmax, s->N, (long long)persist_smem_bytes(s->N, vmax, false));
+    return TSAT_ERANGE;
+  }
+  const bool resident = persist_smem_bytes(s->N, vmax, true) <= kPersistMaxSmem;
+  if ((rc = enter(s, stream))) return rc;
+  const Hyper hy = make_hyper(*hp, stop_on_sat ? 1 : 0);
+  const LrSched ls = make_sched(*hp);
+  cudaError_t e = launch_persist(p->dev, s->dev, hy, ls, n_steps, vmax, resident, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent solver");
   return leave(s, stream);
 }
 

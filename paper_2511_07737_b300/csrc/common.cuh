@@ -51,7 +51,8 @@ struct StateHdr {
   int32_t all_done;   // every instance frozen and stop requested
   int32_t err;
   int32_t n_active;   // instances still being optimised
-  int32_t pad[11];
+  int32_t blocks_done;   // persistent solver: blocks finished in the current launch (the last resets it)
+  int32_t pad[10];
 };
 
 struct InstState {
@@ -162,6 +163,13 @@ __device__ __forceinline__ float adam_inv_denom(float v, float inv_sqrt_bc2, flo
   const float d = fmaf(s, inv_sqrt_bc2, eps);
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
   return r;
+}
+
+// Sum over the W consecutive lanes of a row group (W a power of two dividing
+// 32); every lane of the warp takes part.
+__device__ __forceinline__ float seg_sum(float x, int W) {
+  for (int o = 1; o < W; o <<= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+  return x;
 }
 
 __device__ __forceinline__ float guard_nu(float mu) {

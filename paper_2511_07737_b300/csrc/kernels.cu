@@ -497,23 +497,7 @@ __device__ void gamma_tail(const ProbDev &pd, const StateDev &sd, const Hyper &h
       hdr->all_done = 1;
       return;
     }
-    const int64_t tt = ls.restart > 0 ? t % ls.restart : t;
-    const int64_t kdec = ls.period > 0 ? tt / ls.period : 0;
-    double lr = (double)ls.lr0 * pow((double)ls.factor, (double)kdec);
-    if (lr < (double)ls.floor) lr = ls.floor;
-    // AdamW step count: global, or counted from the last mixing restart
-    const int64_t cnt = (ls.mix && ls.restart > 0 && t >= ls.restart) ? t % ls.restart : t + 1;
-    const double bc1 = 1.0 - pow(ls.beta1, (double)cnt);
-    const double bc2 = 1.0 - pow(ls.beta2, (double)cnt);
-    StepParams sp;
-    sp.t = t;
-    sp.src = (int32_t)(t & 1);
-    sp.mix_now = (ls.mix && ls.restart > 0 && t > 0 && t % ls.restart == 0) ? 1 : 0;
-    sp.lr = (float)lr;
-    sp.step_size = (float)(lr / bc1);
-    sp.inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
-    sp.decay = (float)(1.0 - lr * (double)ls.wd);
-    *sd.sp = sp;
+    *sd.sp = step_params(ls, t);
     hdr->t = t + 1;
   }
 }
@@ -795,10 +779,6 @@ constexpr int kCntChunk = 127;   // occurrences per byte-counter chunk (|count| 
 // registers (24 warps per SM) and 6.42 ms at 64 registers (spills).
 constexpr int kUpd3Block = 128, kUpd3Warps = 4, kUpd3MinB = 7;
 
-__device__ __forceinline__ float seg_sum(float x, int W) {
-  for (int o = 1; o < W; o <<= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-  return x;
-}
 
 // Word i (0..255) of a per-warp word array lives at cswz(i): i XOR g(i / 32),
 // g = {0, 29, 26, 7, 20, 9, 14, 19}.  Both access patterns of the kernel,

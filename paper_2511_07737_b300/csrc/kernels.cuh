@@ -11,6 +11,29 @@ struct LrSched {
   int32_t mix;   // assignment mixing at each restart
 };
 
+// Scalars of step t (Sec. IV-A): lr(t) = max(lr0 factor^floor((t mod restart) / period), floor),
+// AdamW bias corrections with the 1-based step count (counted from the last
+// restart when assignments are mixed), decoupled weight decay.  Formed in
+// double, stored as float.
+__device__ __forceinline__ StepParams step_params(const LrSched &ls, int64_t t) {
+  const int64_t tt = ls.restart > 0 ? t % ls.restart : t;
+  const int64_t kdec = ls.period > 0 ? tt / ls.period : 0;
+  double lr = (double)ls.lr0 * pow((double)ls.factor, (double)kdec);
+  if (lr < (double)ls.floor) lr = ls.floor;
+  const int64_t cnt = (ls.mix && ls.restart > 0 && t >= ls.restart) ? t % ls.restart : t + 1;
+  const double bc1 = 1.0 - pow(ls.beta1, (double)cnt);
+  const double bc2 = 1.0 - pow(ls.beta2, (double)cnt);
+  StepParams sp;
+  sp.t = t;
+  sp.src = (int32_t)(t & 1);
+  sp.mix_now = (ls.mix && ls.restart > 0 && t > 0 && t % ls.restart == 0) ? 1 : 0;
+  sp.lr = (float)lr;
+  sp.step_size = (float)(lr / bc1);
+  sp.inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
+  sp.decay = (float)(1.0 - lr * (double)ls.wd);
+  return sp;
+}
+
 // launch helpers (return cudaGetLastError of the launch)
 cudaError_t launch_init(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const float *logits,
                         float scale, int grid, cudaStream_t st);
@@ -47,5 +70,12 @@ int update_blocks_per_sm(const ProbDev &pd, const StateDev &sd);
 int update_warps_per_block(const ProbDev &pd, const StateDev &sd);
 
 int update_smem_bytes(int N, int lm1, bool greg);
+
+// persistent solver (persist.cu): one block per instance, n_steps steps per launch
+constexpr int64_t kPersistMaxWork = 1LL << 26;   // clauses x longest clause x samples of one instance
+constexpr int64_t kPersistMaxSmem = 200 * 1024;   // shared memory of one block (bits of both parities included)
+int64_t persist_smem_bytes(int N, int32_t vmax, bool resident);
+cudaError_t launch_persist(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls, int32_t K,
+                           int32_t vmax, bool resident, cudaStream_t st);
 
 }  // namespace tsat

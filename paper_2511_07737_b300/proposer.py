@@ -28,9 +28,12 @@ def _unpack_column(words: np.ndarray, col: int) -> np.ndarray:
 
 
 def solve(instances, N: int = 32, hp=None, max_steps: int = 500, logits: torch.Tensor | None = None,
-          scale: float = 1.0, chunk: int = 50, device="cuda") -> dict:
+          scale: float = 1.0, chunk: int = 50, device="cuda", persistent: bool = False) -> dict:
     """Run the gradient solver on a batch; returns found flags, steps-to-SAT,
-    assignments (for solved instances), min-unsat trajectory and timings."""
+    assignments (for solved instances), min-unsat trajectory and timings.
+    ``persistent`` runs each chunk as one launch with a block per instance
+    (tsat_step_persistent, for instances small enough for one block) instead
+    of replaying the multi-kernel step graph."""
     if hp is None:
         hp = ts.hparams(seed=1, norm=ts.NORM_NONE, tau=2.0)
     prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in instances], device=device)
@@ -43,7 +46,10 @@ def solve(instances, N: int = 32, hp=None, max_steps: int = 500, logits: torch.T
     done_steps = 0
     while done_steps < max_steps:
         k = min(chunk, max_steps - done_steps)
-        ts.tsat_step(st.h, hp, k, stop_on_sat=True)
+        if persistent:
+            ts.tsat_step_persistent(st.h, hp, k, stop_on_sat=True)
+        else:
+            ts.tsat_step(st.h, hp, k, stop_on_sat=True)
         done_steps += k
         status = ts.tsat_status(st.h, len(instances))
         mu = np.array([x["min_unsat"] if not x["found"] else 0 for x in status["inst"]], np.float64)

@@ -83,6 +83,7 @@ def lib():
             "tsat_profile_step": (ctypes.c_int, [P, P, i32, P]),
             "tsat_evaluate": (ctypes.c_int, [P, P, P, P, P, P]),
             "tsat_histogram": (ctypes.c_int, [P, P, P]),
+            "tsat_step_persistent": (ctypes.c_int, [P, P, i32, i32, P]),
             "tsat_best": (ctypes.c_int, [P, P, i32, i32, P, P, P, P, P, P, P]),
             "tsat_partial_k": (i32, [i32]),
             "tsat_status": (ctypes.c_int, [P, P, P, P, P]),
@@ -210,6 +211,12 @@ def tsat_init(s, hp: tsat_hparams, logits: torch.Tensor | None = None, scale: fl
 
 def tsat_step(s, hp: tsat_hparams, n_steps: int, stop_on_sat: bool = True, stream=None):
     _ck(lib().tsat_step(s, ctypes.byref(hp), int(n_steps), int(bool(stop_on_sat)), _stream(stream)), "tsat_step")
+
+
+def tsat_step_persistent(s, hp: tsat_hparams, n_steps: int, stop_on_sat: bool = True, stream=None):
+    """n_steps steps of a batch of small instances in one launch (one block per instance)."""
+    _ck(lib().tsat_step_persistent(s, ctypes.byref(hp), int(n_steps), int(bool(stop_on_sat)), _stream(stream)),
+        "tsat_step_persistent")
 
 
 def tsat_step_prepare(s, hp: tsat_hparams, n_steps: int, stop_on_sat: bool = True):

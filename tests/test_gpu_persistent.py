@@ -1,0 +1,124 @@
+"""Persistent solver (tsat_step_persistent: one block per instance, many steps
+per launch) against the FP64 oracle, one step at a time from the GPU's FP32
+state, and its stopping semantics against the multi-kernel path."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2511_07737_b300 import cnfgen
+from paper_2511_07737_b300 import turbosat as ts
+from tests.gpu_util import TOL_F32, assert_adamw_z, lockstep, make, snapshot, unpack_bits
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    torch.cuda.set_device(0)
+
+
+CASES = [
+    ("3sat-N64", lambda: [cnfgen.planted_ksat(100, 426, 3, 0)], 64, dict(norm=0, binarize=0)),
+    ("3sat-N64-philox", lambda: [cnfgen.planted_ksat(100, 426, 3, 1)], 64, dict(norm=1, binarize=1, bin_temp=0.5)),
+    ("3sat-N32-none", lambda: [cnfgen.planted_ksat(700, 2982, 3, 6)], 32, dict(norm=2, binarize=1)),
+    ("3sat-N1024", lambda: [cnfgen.planted_ksat(300, 1278, 3, 5)], 1024, dict(norm=1, binarize=1)),
+    ("k7-N128", lambda: [cnfgen.planted_ksat(300, 9000, 7, 8)], 128, dict(norm=0, binarize=0)),
+    ("short-dup-N256", lambda: [cnfgen.tiny_random(200, 1500, 9, kmin=1, kmax=5)], 256, dict(norm=1, binarize=1)),
+    ("batch-k3..7-N64", lambda: cnfgen.batch_ksat(9, 10, n_lo=40, n_hi=600), 64, dict(norm=1, binarize=1)),
+]
+
+
+@pytest.mark.parametrize("name,gen,N,kw", CASES, ids=[c[0] for c in CASES])
+def test_persistent_lockstep(name, gen, N, kw):
+    insts = gen()
+    prob, st, cnfs = make(insts, N)
+    hp = ts.hparams(seed=33, tau=1.3, **kw)
+    ts.tsat_init(st.h, hp)
+    offs = prob.var_offsets
+    steps = 4
+    for t in range(steps):
+        s0 = snapshot(st)
+        # alternate the persistent launch with the multi-kernel step: both leave the same state layout
+        if t == 2:
+            ts.tsat_step(st.h, hp, 1, stop_on_sat=False)
+        else:
+            ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=False)
+        s1 = snapshot(st)
+        z, m, v, res = lockstep(cnfs, offs, hp, t, s0)
+        status = ts.tsat_status(st.h, len(insts))
+        frozen = np.zeros(prob.info["n_vars"], bool)
+        for j, r in enumerate(res):
+            if status["inst"][j]["found"]:
+                frozen[offs[j]:offs[j + 1]] = True
+            if status["inst"][j]["found"] and status["inst"][j]["found_step"] < t:
+                continue
+            assert status["inst"][j]["min_unsat"] == int(r["unsat"].min())
+            assert status["inst"][j]["best_sample"] == oracle.best_sample(r["unsat"])
+            assert abs(status["inst"][j]["loss"] - r["L"]) <= TOL_F32 * abs(r["L"])
+        live = ~frozen
+        assert_adamw_z(s1["z"][live], z[live], s1["m"][live], m[live], s1["v"][live], v[live], t, hp)
+        X = oracle.binarize_f32(s1["z"], s1["nu"], hp.binarize, c=0.25 / hp.bin_temp, seed=hp.seed, t=t + 1)
+        np.testing.assert_array_equal(s1["X"][live], X[live])
+        np.testing.assert_array_equal(s1["X"][frozen], s0["X"][frozen])
+        nu_ref = oracle.nu_f32(s1["z"], hp.norm)
+        assert np.all(np.abs(s1["nu"] - nu_ref) <= 2e-6 * np.abs(s1["z"]).mean(axis=1) + 2e-6 * np.abs(nu_ref))
+        assert status["step"] == t + 1
+
+
+def test_persistent_solves_and_stops_like_the_graph_path():
+    """A batch solved to the end: every instance frozen on a model of its own
+    formula, the step counter at the step that froze the last one, no further
+    work once stopped; the same launch with stop_on_sat off keeps counting."""
+    insts = [cnfgen.planted_ksat(100, 400, 3, j) for j in range(12)]
+    prob, st, cnfs = make(insts, 64)
+    hp = ts.hparams(seed=3, norm=ts.NORM_ABSMEAN, tau=2.0, lr0=0.5)
+    ts.tsat_init(st.h, hp)
+    ts.tsat_step_persistent(st.h, hp, 600, stop_on_sat=True)
+    status = ts.tsat_status(st.h, len(insts))
+    found = [x["found"] for x in status["inst"]]
+    assert sum(found) >= 9
+    X = snapshot(st)["X"]
+    offs = prob.var_offsets
+    for j, x in enumerate(status["inst"]):
+        if x["found"]:
+            u, _ = oracle.check(cnfs[j], X[offs[j]:offs[j + 1]])
+            assert u[x["found_sample"]] == 0 and x["min_unsat"] == 0
+    if all(found):
+        assert status["all_done"]
+        assert status["step"] == max(x["found_step"] for x in status["inst"])
+        before = snapshot(st)
+        ts.tsat_step_persistent(st.h, hp, 50, stop_on_sat=True)   # stopped: nothing changes
+        after = snapshot(st)
+        assert ts.tsat_status(st.h, len(insts))["step"] == status["step"]
+        np.testing.assert_array_equal(before["z"], after["z"])
+    else:
+        assert status["step"] == 600 and not status["all_done"]
+    # without the stop the counter advances by the launch's steps
+    st2 = ts.State(prob, 64)
+    ts.tsat_init(st2.h, hp)
+    ts.tsat_step_persistent(st2.h, hp, 37, stop_on_sat=False)
+    ts.tsat_step_persistent(st2.h, hp, 5, stop_on_sat=False)
+    assert ts.tsat_status(st2.h, len(insts))["step"] == 42
+
+
+def test_persistent_rejects_what_it_does_not_run():
+    inst = cnfgen.planted_ksat(100, 426, 3, 0)
+    prob, st, _ = make([inst], 64)
+    hp = ts.hparams(seed=1)
+    ts.tsat_init(st.h, hp)
+    with pytest.raises(ts.TsatError) as e:
+        ts.tsat_step_persistent(st.h, ts.hparams(seed=1, mix_restart=1), 1)
+    assert e.value.status == -1
+    long = cnfgen.planted_ksat(60, 200, 9, 2)
+    prob2, st2, _ = make([long], 64)
+    ts.tsat_init(st2.h, hp)
+    with pytest.raises(ts.TsatError):
+        ts.tsat_step_persistent(st2.h, hp, 1)
+    rel = ts.State(prob, 64, ts.LAYER_RELAXED)
+    hr = ts.hparams(seed=1, layer=ts.LAYER_RELAXED)
+    ts.tsat_init(rel.h, hr)
+    with pytest.raises(ts.TsatError):
+        ts.tsat_step_persistent(rel.h, hr, 1)
