@@ -87,3 +87,40 @@ def assert_adamw_z(z_gpu, z_ref, m_gpu, m_ref, v_gpu, v_ref, t, hp, tol=TOL_F32,
     err = np.abs(z_gpu.astype(np.float64) - z_ref)
     bad = err > bound
     assert not bad.any(), (int(bad.sum()), float(err[bad].max()), float(bound[bad].min()))
+
+
+def run_lockstep(insts, N, hp, steps, step_fn=None):
+    """Run `steps` steps of `insts` (one call of step_fn per step, tsat_step by
+    default) and check every step against one oracle step taken from the GPU's
+    FP32 state: status records, z / m / v after AdamW, the bits of the next
+    step and the new normaliser.  Returns the last status."""
+    if step_fn is None:
+        step_fn = lambda st: ts.tsat_step(st.h, hp, 1, stop_on_sat=False)   # noqa: E731
+    prob, st, cnfs = make(insts, N)
+    ts.tsat_init(st.h, hp)
+    offs = prob.var_offsets
+    status = None
+    for t in range(steps):
+        s0 = snapshot(st)
+        step_fn(st)
+        s1 = snapshot(st)
+        z, m, v, res = lockstep(cnfs, offs, hp, t, s0)
+        status = ts.tsat_status(st.h, len(insts))
+        frozen = np.zeros(prob.info["n_vars"], bool)
+        for j, r in enumerate(res):
+            x = status["inst"][j]
+            if x["found"]:
+                frozen[offs[j]:offs[j + 1]] = True
+                if x["found_step"] < t:
+                    continue
+            assert x["min_unsat"] == int(r["unsat"].min())
+            assert abs(x["loss"] - r["L"]) <= TOL_F32 * max(abs(r["L"]), 1e-30)
+        live = ~frozen
+        if live.any():
+            assert_adamw_z(s1["z"][live], z[live], s1["m"][live], m[live], s1["v"][live], v[live], t, hp)
+        X = oracle.binarize_f32(s1["z"], s1["nu"], hp.binarize, c=0.25 / hp.bin_temp, seed=hp.seed, t=t + 1)
+        np.testing.assert_array_equal(s1["X"][live], X[live])
+        np.testing.assert_array_equal(s1["X"][frozen], s0["X"][frozen])
+        nu_ref = oracle.nu_f32(s1["z"], hp.norm)
+        assert np.all(np.abs(s1["nu"] - nu_ref) <= 2e-6 * np.abs(s1["z"]).mean(axis=1) + 2e-6 * np.abs(nu_ref))
+    return status, prob, st, cnfs
