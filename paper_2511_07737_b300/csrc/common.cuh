@@ -165,6 +165,13 @@ __device__ __forceinline__ float adam_inv_denom(float v, float inv_sqrt_bc2, flo
   return r;
 }
 
+// 0/1 bytes from the 4 bits of n (bit b -> byte b)
+__device__ __forceinline__ uint32_t spread4(uint32_t n) { return (n * 0x00204081u) & 0x01010101u; }
+// (byte q of x) - 128 as an exact float: 2^23 + byte assembled in the mantissa
+__device__ __forceinline__ float biased_byte(uint32_t x, uint32_t q) {
+  return __int_as_float((int)__byte_perm(x, 0x4B000000u, 0x7440u | q)) - 8388736.0f;
+}
+
 // Sum over the W consecutive lanes of a row group (W a power of two dividing
 // 32); every lane of the warp takes part.
 __device__ __forceinline__ float seg_sum(float x, int W) {

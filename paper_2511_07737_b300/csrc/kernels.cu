@@ -743,12 +743,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
   }
 }
 
-// 0/1 bytes from the 4 bits of n (bit b -> byte b)
-__device__ __forceinline__ uint32_t spread4(uint32_t n) { return (n * 0x00204081u) & 0x01010101u; }
-// (byte q of x) - 128 as an exact float: 2^23 + byte assembled in the mantissa
-__device__ __forceinline__ float biased_byte(uint32_t x, uint32_t q) {
-  return __int_as_float((int)__byte_perm(x, 0x4B000000u, 0x7440u | q)) - 8388736.0f;
-}
 
 // ------------------------------------------------------------------ fused update, word per lane
 // Clause length <= 3 (R in 0..3, two bit planes).  Counting phase: a lane owns

@@ -17,30 +17,48 @@
 
 namespace tsat {
 
-constexpr int kPsBlock = 256, kPsWarps = kPsBlock / 32;
+constexpr int kPsSched = 256;   // steps whose scalars are formed at once (one per thread)
 
 // dL/dR table of one sample: 8 floats (r = 0..7); each word's 32 samples are
 // followed by 8 floats of padding (264 floats per word), so that the lanes of
 // one lookup (same bit, rows at different words) start on different banks
 __device__ __forceinline__ int ps_tab(int s) { return 8 * s + 8 * (s >> 5); }
 
+// In place: c[m] = sum over m' subset of m of (-1)^{|m| - |m'|} g[m'] (R's three
+// bit planes b0, b1, b2 as the bits of m), so that g[R] = sum over the
+// subsets m of the bits set in R of c[m]
+__device__ __forceinline__ void ps_moebius(float (&c)[8]) {
+#pragma unroll
+  for (int bit = 1; bit < 8; bit <<= 1)
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+      if (m & bit) c[m] -= c[m ^ bit];
+}
+
+constexpr int kPsChunk = 127;   // occurrences per byte-counter chunk (|count| <= 127)
+
 __device__ __forceinline__ uint32_t *ps_bits(const StateDev &sd, int64_t t) {
   return sd.bits + (size_t)(t & 1) * (size_t)sd.V * sd.W;
 }
 
 // RES: the instance's z, m, v and normaliser stay in shared memory for the
-// whole launch (layout [row][word][33]: a lane's 32 samples start on their
-// own bank) and are written back once at the end; otherwise they are read and
-// written in global memory at every step.
-template <int BIN, int NORM, bool RES>
-__global__ void __launch_bounds__(kPsBlock, 2) k_persist(ProbDev pd, StateDev sd, Hyper hy, LrSched ls, int32_t K,
-                                                         int32_t vmax) {
+// whole launch (layout [row][word][33]: the samples of one lane start on
+// their own bank) and are written back once at the end; otherwise they are
+// read and written in global memory at every step.
+// SPT: samples per thread in the update.  With SPT = 8 (N <= 256) four
+// threads share a 32-sample word and a block has 1024 threads: four times the
+// threads of SPT = 32 (N >= 512, 256 threads), each with a quarter of the
+// per-sample work, so a small instance's step has more warps in flight.
+template <int BIN, int NORM, bool RES, int SPT>
+__global__ void __launch_bounds__(SPT == 8 ? 1024 : 256, SPT == 8 ? 1 : 2)
+    k_persist(ProbDev pd, StateDev sd, Hyper hy, LrSched ls, int32_t K, int32_t vmax) {
+  constexpr int BS = SPT == 8 ? 1024 : 256, NW = BS / 32, Q = 32 / SPT;
   extern __shared__ __align__(16) float smP[];
   __shared__ int64_t sh_t0;
   __shared__ int sh_skip, sh_found;
-  __shared__ float sh_ls[kPsWarps], etab[8];
-  __shared__ int sh_mu[kPsWarps], sh_mi[kPsWarps];
-  __shared__ StepParams sh_sps[kPsBlock];   // step scalars of the next kPsBlock steps, one per thread
+  __shared__ float sh_ls[NW], etab[8];
+  __shared__ int sh_mu[NW], sh_mi[NW];
+  __shared__ StepParams sh_sps[kPsSched];   // step scalars of the next kPsSched steps
   StateHdr *hdr = sd.hdr;
   const int inst = blockIdx.x;
   const int N = sd.N, W = sd.W;
@@ -62,36 +80,36 @@ __global__ void __launch_bounds__(kPsBlock, 2) k_persist(ProbDev pd, StateDev sd
   // first variable: every gather of the forward and the backward reads them here
   uint32_t *sbits = reinterpret_cast<uint32_t *>(tab + 264 * W);   // [2][vmax][W]
   const size_t vw = (size_t)vmax * W;
-  for (int64_t i = tid; i < (int64_t)I.n_vars * W; i += kPsBlock)
+  for (int64_t i = tid; i < (int64_t)I.n_vars * W; i += BS)
     sbits[(t0 & 1) * vw + i] = ps_bits(sd, t0)[(size_t)I.v_off * W + i];
   float *smz = reinterpret_cast<float *>(sbits + 2 * vw);   // RES: z, m, v [vmax][W][33], then nu [vmax]
   float *smm = smz + vw * 33, *smv = smm + vw * 33, *snu = smv + vw * 33;
   const size_t g0 = (size_t)I.v_off * N;
   if (RES && !sh_found) {
-    for (int64_t i = tid; i < (int64_t)I.n_vars * N; i += kPsBlock) {
+    for (int64_t i = tid; i < (int64_t)I.n_vars * N; i += BS) {
       const size_t si = (size_t)(i / 32) * 33 + (i & 31);   // [row][word][33]: word index i / 32 of the row-major array
       smz[si] = sd.z[g0 + i];
       smm[si] = sd.m[g0 + i];
       smv[si] = sd.v[g0 + i];
     }
-    for (int i = tid; i < I.n_vars; i += kPsBlock) snu[i] = sd.nu[I.v_off + i];
+    for (int i = tid; i < I.n_vars; i += BS) snu[i] = sd.nu[I.v_off + i];
   }
   __syncthreads();
   int found = sh_found;
   const bool ran = !found;   // the instance is live at the start of the launch
   int64_t t = t0;
   for (int32_t k = 0; k < K && !found; ++k, ++t) {
-    if (k % kPsBlock == 0) {   // the double-precision schedule of the next kPsBlock steps, in parallel
-      sh_sps[tid] = step_params(ls, t + tid);
+    if (k % kPsSched == 0) {   // the double-precision schedule of the next kPsSched steps, in parallel
+      if (tid < kPsSched) sh_sps[tid] = step_params(ls, t + tid);
       __syncthreads();
     }
     // ---- forward (Eq. 1): lane = clause, 32 samples of word w; bit-sliced R,
     // warp transpose, popcounts of the R = r masks into the block histogram
-    for (int i = tid; i < (lmax + 1) * N; i += kPsBlock) hist[i] = 0;
+    for (int i = tid; i < (lmax + 1) * N; i += BS) hist[i] = 0;
     __syncthreads();
     const uint32_t *bsrc = sbits + (t & 1) * vw;
     const int ngroups = (I.n_clauses + 31) >> 5;
-    for (int task = warp; task < ngroups * W; task += kPsWarps) {
+    for (int task = warp; task < ngroups * W; task += NW) {
       const int g = task / W, w = task - g * W;
       const bool active = 32 * g + lane < I.n_clauses;
       uint32_t pl[3] = {0u, 0u, 0u};
@@ -116,7 +134,7 @@ __global__ void __launch_bounds__(kPsBlock, 2) k_persist(ProbDev pd, StateDev sd
     // ---- Eq. 4 per sample, the dL/dR table, loss, fewest-unsatisfied sample
     float lsum = 0.f;
     int mu = 0x7FFFFFFF, mi = 0x7FFFFFFF;
-    for (int i = tid; i < N; i += kPsBlock) {
+    for (int i = tid; i < N; i += BS) {
       float Z = 0.f, Y = 0.f;
       for (int r = 0; r <= lmax; ++r) {
         const float hv = (float)hist[r * N + i];
@@ -125,9 +143,12 @@ __global__ void __launch_bounds__(kPsBlock, 2) k_persist(ProbDev pd, StateDev sd
       }
       const float S = Y / Z;
       const float invZ = 1.0f / Z;
+      float c[8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
-        tab[ps_tab(i) + r] = r <= lmax ? -(etab[r] * invZ) * (1.0f - hy.tau * ((float)r - S)) : 0.f;
+      for (int r = 0; r < 8; ++r) c[r] = r <= lmax ? -(etab[r] * invZ) * (1.0f - hy.tau * ((float)r - S)) : 0.f;
+      ps_moebius(c);   // the update counts product masks of R's bit planes
+#pragma unroll
+      for (int r = 0; r < 8; ++r) tab[ps_tab(i) + r] = c[r];
       const int h0 = hist[i];
       lsum += S;
       if (h0 < mu || (h0 == mu && i < mi)) { mu = h0; mi = i; }
@@ -143,7 +164,7 @@ __global__ void __launch_bounds__(kPsBlock, 2) k_persist(ProbDev pd, StateDev sd
     __syncthreads();
     if (tid == 0) {
       float L = 0.f;
-      for (int q = 0; q < kPsWarps; ++q) {
+      for (int q = 0; q < NW; ++q) {
         L += sh_ls[q];
         if (sh_mu[q] < mu || (sh_mu[q] == mu && sh_mi[q] < mi)) { mu = sh_mu[q]; mi = sh_mi[q]; }
       }
@@ -164,52 +185,105 @@ __global__ void __launch_bounds__(kPsBlock, 2) k_persist(ProbDev pd, StateDev sd
     // ---- fused update: thread = (row, word w); G of its 32 samples summed over
     // the row's occurrences in record order, then Eq. 5, AdamW, the new
     // normaliser and the bits of step t + 1
-    const StepParams sp = sh_sps[k % kPsBlock];
+    const StepParams sp = sh_sps[k % kPsSched];
     uint32_t *bdst = ps_bits(sd, t + 1), *sdst = sbits + ((t + 1) & 1) * vw;
-    const int rpp = kPsBlock / W;
+    const int WQ = W * Q;                 // threads of one row: W words x Q parts
+    const int rpp = BS / WQ;              // rows per pass
+    const int rl = tid % WQ, w = rl / Q, sb = SPT * (rl % Q);   // word, first bit of this thread's samples
     for (int vb = 0; vb < I.n_vars; vb += rpp) {
-      const int vl = vb + tid / W, w = tid % W;
+      const int vl = vb + tid / WQ;
       const bool act = vl < I.n_vars;
       const int64_t v = (int64_t)I.v_off + vl;
-      float acc[32];
+      // G of this thread's samples: signed byte counts of the product masks of
+      // R's bit planes (mask m of the subset m of {b0, b1, b2}), folded with
+      // the Moebius coefficients of the dL/dR table (an exact rewrite of the
+      // per-sample sum over the occurrences).  Word u of a mask holds samples
+      // sb + 4u .. sb + 4u + 3, one byte each with bias 128.
+      constexpr int NWD = SPT / 4;
+      float acc[SPT];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+      for (int j = 0; j < SPT; ++j) acc[j] = 0.f;
       if (act) {
         const uint32_t own = bsrc[(size_t)vl * W + w];
         const int32_t o0 = __ldg(pd.vptr + v), o1 = __ldg(pd.vptr + v + 1);
-        const int tb = ps_tab(32 * w);
-        for (int32_t o = o0; o < o1; ++o) {
-          const int32_t *rec = pd.xrec + (size_t)pd.rec_stride * o;
-          const int32_t h = __ldg(rec);
-          const int len = h >> 1;
-          uint32_t pl[3] = {own ^ (0u - (uint32_t)(h & 1)), 0u, 0u};
-          for (int q = 1; q < len; ++q) {
-            const int32_t lit = __ldg(rec + q);
-            bitslice_add<3>(pl, bsrc[(size_t)((lit >> 1) - I.v_off) * W + w] ^ (0u - (uint32_t)(lit & 1)));
-          }
-          const float sg = (h & 1) ? -1.0f : 1.0f;
+        const int tb = ps_tab(32 * w + sb);
+        const bool two = pd.rec_stride == 4;   // clause length <= 3: R <= 3, masks b0, b1, b0 b1
+        int nsign = 0;
+        for (int32_t c0 = o0; c0 < o1; c0 += kPsChunk) {
+          const int32_t c1 = min(o1, c0 + kPsChunk);
+          uint32_t sc[7][NWD];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int r = (int)(((pl[0] >> j) & 1u) | (((pl[1] >> j) & 1u) << 1) | (((pl[2] >> j) & 1u) << 2));
-            acc[j] = fmaf(sg, tab[tb + 8 * j + r], acc[j]);
+          for (int mk = 0; mk < 7; ++mk)
+#pragma unroll
+            for (int u = 0; u < NWD; ++u) sc[mk][u] = 0x80808080u;
+#pragma unroll 2
+          for (int32_t o = c0; o < c1; ++o) {
+            // the fixed record {hdr, lit x 2, 0} (clause length <= 3) or {hdr, lit x 6, 0}, in one or two loads
+            const int4 *rp = reinterpret_cast<const int4 *>(pd.xrec) + (two ? o : 2 * (int64_t)o);
+            const int4 ra = __ldg(rp), rb = two ? make_int4(0, 0, 0, 0) : __ldg(rp + 1);
+            const int h = ra.x, len = h >> 1;
+            const int lits[6] = {ra.y, ra.z, ra.w, rb.x, rb.y, rb.z};
+            uint32_t pl[3] = {own ^ (0u - (uint32_t)(h & 1)), 0u, 0u};
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+              if (q + 1 < len)
+                bitslice_add<3>(pl, bsrc[(size_t)((lits[q] >> 1) - I.v_off) * W + w] ^ (0u - (uint32_t)(lits[q] & 1)));
+            }
+            const uint32_t sg = (h & 1) ? 0xFFFFFFFFu : 1u;
+            nsign += (int)sg;
+            const uint32_t b0 = pl[0] >> sb, b1 = pl[1] >> sb, b01 = b0 & b1;
+#pragma unroll
+            for (int u = 0; u < NWD; ++u) {
+              sc[0][u] += spread4((b0 >> (4 * u)) & 15u) * sg;
+              sc[1][u] += spread4((b1 >> (4 * u)) & 15u) * sg;
+              sc[2][u] += spread4((b01 >> (4 * u)) & 15u) * sg;
+            }
+            if (!two) {
+              const uint32_t b2 = pl[2] >> sb;
+#pragma unroll
+              for (int u = 0; u < NWD; ++u) {
+                sc[3][u] += spread4((b2 >> (4 * u)) & 15u) * sg;
+                sc[4][u] += spread4(((b0 & b2) >> (4 * u)) & 15u) * sg;
+                sc[5][u] += spread4(((b1 & b2) >> (4 * u)) & 15u) * sg;
+                sc[6][u] += spread4(((b01 & b2) >> (4 * u)) & 15u) * sg;
+              }
+            }
           }
+          // fold the chunk: acc[j] += sum over masks of count * coefficient
+#pragma unroll
+          for (int u = 0; u < NWD; ++u)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float *cf = tab + tb + 8 * (4 * u + e);
+              float g = acc[4 * u + e];
+              g = fmaf(biased_byte(sc[0][u], e), cf[1], g);
+              g = fmaf(biased_byte(sc[1][u], e), cf[2], g);
+              g = fmaf(biased_byte(sc[2][u], e), cf[3], g);
+              if (!two) {
+#pragma unroll
+                for (int mk = 3; mk < 7; ++mk) g = fmaf(biased_byte(sc[mk][u], e), cf[mk + 1], g);
+              }
+              acc[4 * u + e] = g;
+            }
         }
+#pragma unroll
+        for (int j = 0; j < SPT; ++j) acc[j] = fmaf((float)nsign, tab[tb + 8 * j], acc[j]);
       }
-      const size_t off = RES ? ((size_t)vl * W + w) * 33 : (size_t)v * N + 32 * w;
+      const size_t off = RES ? ((size_t)vl * W + w) * 33 + sb : (size_t)v * N + 32 * w + sb;
       float *zp = RES ? smz : sd.z, *mp = RES ? smm : sd.m, *vp = RES ? smv : sd.v;
       const float nu = act ? (RES ? snu[vl] : sd.nu[v]) : 1.0f;
       const float rnu = __frcp_rn(nu);
       float part = 0.f;
       if (act && NORM != TSAT_NORM_NONE) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) part = fmaf(acc[j], zp[off + j], part);
+        for (int j = 0; j < SPT; ++j) part = fmaf(acc[j], zp[off + j], part);
       }
-      const float dot = seg_sum(part, W);
+      const float dot = seg_sum(part, WQ);
       const float c2 = dot * rnu * rnu * (1.0f / (float)N);
       float psum = 0.f;
       if (act) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < SPT; ++j) {
           const float z = zp[off + j];
           float g;
           if constexpr (NORM == TSAT_NORM_NONE) {
@@ -229,26 +303,32 @@ __global__ void __launch_bounds__(kPsBlock, 2) k_persist(ProbDev pd, StateDev sd
           psum += (NORM == TSAT_NORM_ABSMEAN) ? fabsf(zn) : zn;
         }
       }
-      const float tot = seg_sum(psum, W);
+      const float tot = seg_sum(psum, WQ);
+      const float nun = (NORM == TSAT_NORM_NONE) ? 1.0f : guard_nu(tot / (float)N);
+      uint32_t part_bits = 0;
       if (act) {
-        const float nun = (NORM == TSAT_NORM_NONE) ? 1.0f : guard_nu(tot / (float)N);
         const float rnn = __frcp_rn(nun);
-        uint32_t word = 0;
         if constexpr (BIN == TSAT_BIN_PHILOX) {
 #pragma unroll
-          for (int h = 0; h < 4; ++h) {   // samples 32 w + 8 h + e: block 4 w + h, half e
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)(4 * w + h), (uint32_t)v, (uint32_t)(t + 1), kTagBin),
-                                          hy.key0, hy.key1);
+          for (int hb = 0; hb < SPT / 8; ++hb) {   // samples 32 w + sb + 8 hb + e: block 4 w + sb / 8 + hb, half e
+            const uint4 r = philox4x32_10(
+                make_uint4((uint32_t)(4 * w + (sb >> 3) + hb), (uint32_t)v, (uint32_t)(t + 1), kTagBin), hy.key0, hy.key1);
 #pragma unroll
             for (int e = 0; e < 8; ++e)
-              word |= binarize_one(__fmul_rn(acc[8 * h + e], rnn), TSAT_BIN_PHILOX, hy.bin_c,
-                                   half16(e < 4 ? r.x : r.z, e < 4 ? r.y : r.w, e & 3))
-                      << (8 * h + e);
+              part_bits |= binarize_one(__fmul_rn(acc[8 * hb + e], rnn), TSAT_BIN_PHILOX, hy.bin_c,
+                                        half16(e < 4 ? r.x : r.z, e < 4 ? r.y : r.w, e & 3))
+                           << (8 * hb + e);
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) word |= (__fmul_rn(acc[j], rnn) > 0.0f ? 1u : 0u) << j;
+          for (int j = 0; j < SPT; ++j) part_bits |= (__fmul_rn(acc[j], rnn) > 0.0f ? 1u : 0u) << j;
         }
+      }
+      // the Q parts of word w are consecutive lanes: join their bits
+      uint32_t word = (SPT == 32) ? part_bits : (part_bits << sb);
+#pragma unroll
+      for (int o = 1; o < Q; o <<= 1) word |= __shfl_xor_sync(0xFFFFFFFFu, word, o);
+      if (act && sb == 0) {
         if (!RES) bdst[v * W + w] = word;
         sdst[(size_t)vl * W + w] = word;
         if (w == 0) {
@@ -264,21 +344,21 @@ __global__ void __launch_bounds__(kPsBlock, 2) k_persist(ProbDev pd, StateDev sd
   __syncthreads();
   if (found && ran) {
     const int64_t tf = sd.inst[inst].found_step;
-    for (int64_t i = tid; i < (int64_t)I.n_vars * W; i += kPsBlock) {
+    for (int64_t i = tid; i < (int64_t)I.n_vars * W; i += BS) {
       if (RES) sbits[((tf + 1) & 1) * vw + i] = sbits[(tf & 1) * vw + i];
       else ps_bits(sd, tf + 1)[(size_t)I.v_off * W + i] = ps_bits(sd, tf)[(size_t)I.v_off * W + i];
     }
   }
   if (RES && ran) {   // write the resident state back
     __syncthreads();
-    for (int64_t i = tid; i < (int64_t)I.n_vars * N; i += kPsBlock) {
+    for (int64_t i = tid; i < (int64_t)I.n_vars * N; i += BS) {
       const size_t si = (size_t)(i / 32) * 33 + (i & 31);
       sd.z[g0 + i] = smz[si];
       sd.m[g0 + i] = smm[si];
       sd.v[g0 + i] = smv[si];
     }
-    for (int i = tid; i < I.n_vars; i += kPsBlock) sd.nu[I.v_off + i] = snu[i];
-    for (int64_t i = tid; i < (int64_t)I.n_vars * W; i += kPsBlock) {
+    for (int i = tid; i < I.n_vars; i += BS) sd.nu[I.v_off + i] = snu[i];
+    for (int64_t i = tid; i < (int64_t)I.n_vars * W; i += BS) {
       ps_bits(sd, 0)[(size_t)I.v_off * W + i] = sbits[i];
       ps_bits(sd, 1)[(size_t)I.v_off * W + i] = sbits[vw + i];
     }
@@ -324,14 +404,17 @@ int64_t persist_smem_bytes(int N, int32_t vmax, bool resident) {
 cudaError_t launch_persist(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls, int32_t K,
                            int32_t vmax, bool resident, cudaStream_t st) {
   const int smem = (int)persist_smem_bytes(sd.N, vmax, resident);
-  auto go = [&](auto kern) {
+  auto go = [&](auto kern, int block) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<pd.n_inst, kPsBlock, smem, st>>>(pd, sd, hy, ls, K, vmax);
+    kern<<<pd.n_inst, block, smem, st>>>(pd, sd, hy, ls, K, vmax);
     return cudaGetLastError();
   };
   const bool ph = hy.binarize == TSAT_BIN_PHILOX;
-#define PS_GO(B, M) (resident ? go(k_persist<B, M, true>) : go(k_persist<B, M, false>))
+  const bool small = sd.N <= 256;   // 8 samples per thread, 1024-thread blocks
+#define PS_GO(B, M)                                                                          \
+  (small ? (resident ? go(k_persist<B, M, true, 8>, 1024) : go(k_persist<B, M, false, 8>, 1024)) \
+         : (resident ? go(k_persist<B, M, true, 32>, 256) : go(k_persist<B, M, false, 32>, 256)))
   switch (hy.norm) {
     case TSAT_NORM_SIGNED_MEAN:
       return ph ? PS_GO(TSAT_BIN_PHILOX, TSAT_NORM_SIGNED_MEAN) : PS_GO(TSAT_BIN_DET, TSAT_NORM_SIGNED_MEAN);
