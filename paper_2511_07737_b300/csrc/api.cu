@@ -13,7 +13,7 @@ namespace tsat {
 struct StatePlan {
   size_t hdr, inst, sp, z, m, v, bits, nu, hist, gamma, gdelta, S, unsat;
   size_t ehist, eunsat, gcol, sel, digits, selstate, outbits, small, part_var, part_val, fwdS, hist1;
-  size_t lit, rbuf, zy, zs;
+  size_t lit, rbuf, dr16, zy, zs;
   size_t total;
 };
 
@@ -52,6 +52,7 @@ static StatePlan plan_state(const tsat_problem *p, int32_t N, int32_t layer, int
   if (layer == TSAT_LAYER_RELAXED) {
     S.lit = take((dt == TSAT_DTYPE_BF16 ? 2 : 4) * V * N);
     S.rbuf = take(sizeof(float) * (size_t)p->C * N);
+    if (dt == TSAT_DTYPE_BF16) S.dr16 = take(sizeof(uint16_t) * (size_t)p->C * N);
     S.zy = take(sizeof(float) * 2 * (size_t)p->lay.items_cap * N);
     S.zs = take(sizeof(float) * 2 * I * N);
   }
@@ -226,6 +227,7 @@ int tsat_state_create(tsat_problem *p, void *d_state, size_t state_bytes, int32_
   if (layer == TSAT_LAYER_RELAXED) {
     D.lit = b + P.lit;
     D.rbuf = (float *)(b + P.rbuf);
+    D.dr16 = dt == TSAT_DTYPE_BF16 ? (uint32_t *)(b + P.dr16) : nullptr;
     D.zy = (float *)(b + P.zy);
     D.zs = (float *)(b + P.zs);
     D.lit_bf16 = dt == TSAT_DTYPE_BF16;

@@ -571,7 +571,7 @@ __device__ __forceinline__ float sel4(int r, float g0, float g1, float g2, float
   return (r & 2) ? b : a;
 }
 
-template <int P, bool GREG, bool RELAX>
+template <int P, bool GREG, bool RELAX, bool DR16 = false>
 __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, Hyper hy, int mode,
                                                       const float *zin, float *grad, float dL,
                                                       int rows_per_item) {
@@ -634,13 +634,24 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
         // buffer holds dL/dR (k_relaxed_dr), 8 occurrences' loads in flight
         const int32_t ob = __ldg(pd.vptr + v), oe = __ldg(pd.vptr + v + 1);
         int32_t o = ob;
+        // dL/dR of clause c for this thread's 4 samples (FP32 or bf16 storage)
+        auto dR = [&](int32_t c) -> float4 {
+          if constexpr (DR16) {
+            const uint2 u = __ldg(reinterpret_cast<const uint2 *>(sd.dr16 + ((size_t)c * N + s0) / 2));
+            const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+            const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+            return make_float4(lo.x, lo.y, hi.x, hi.y);
+          } else {
+            return __ldg(reinterpret_cast<const float4 *>(sd.rbuf + (size_t)c * N + s0));
+          }
+        };
         for (; o + 8 <= oe; o += 8) {
           int32_t e[8];
           float4 D[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) e[q] = __ldg(pd.vocc + o + q);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) D[q] = __ldg(reinterpret_cast<const float4 *>(sd.rbuf + (size_t)(e[q] >> 1) * N + s0));
+          for (int q = 0; q < 8; ++q) D[q] = dR(e[q] >> 1);
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const float sg = (e[q] & 1) ? -1.0f : 1.0f;
@@ -652,7 +663,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
         }
         for (; o < oe; ++o) {
           const int32_t e = __ldg(pd.vocc + o);
-          const float4 D = __ldg(reinterpret_cast<const float4 *>(sd.rbuf + (size_t)(e >> 1) * N + s0));
+          const float4 D = dR(e >> 1);
           const float sg = (e & 1) ? -1.0f : 1.0f;
           G[0] = fmaf(sg, D.x, G[0]);
           G[1] = fmaf(sg, D.y, G[1]);
@@ -1430,11 +1441,11 @@ cudaError_t launch_gamma(const ProbDev &pd, const StateDev &sd, const Hyper &hy,
   return cudaGetLastError();
 }
 
-template <int P, bool GREG, bool RELAX = false>
+template <int P, bool GREG, bool RELAX = false, bool DR16 = false>
 static cudaError_t upd_launch(const ProbDev &pd, const StateDev &sd, const Hyper &hy, int mode, const float *zin,
                               float *grad, float dL, int grid, int rpi, cudaStream_t st) {
   const int smem = update_smem_bytes(sd.N, sd.lm1, GREG);
-  k_update<P, GREG, RELAX><<<grid, kBlock, smem, st>>>(pd, sd, hy, mode, zin, grad, dL, rpi);
+  k_update<P, GREG, RELAX, DR16><<<grid, kBlock, smem, st>>>(pd, sd, hy, mode, zin, grad, dL, rpi);
   return cudaGetLastError();
 }
 
@@ -1537,6 +1548,7 @@ void prepare_update_attrs(int lmax) {
   for_each_update3([bytes](auto fn) { cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
   for_each_updateL([bytes](auto fn) { cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
   cudaFuncSetAttribute(k_update<1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_update<1, true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   switch (P) {
     case 1: cudaFuncSetAttribute(k_update<1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); break;
     case 2: cudaFuncSetAttribute(k_update<2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); break;
@@ -1551,7 +1563,9 @@ cudaError_t launch_update(const ProbDev &pd, const StateDev &sd, const Hyper &hy
   const int P = planes_for(pd.lmax);
   if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_stride == 4) return launch_update3(pd, sd, hy, mode, zin, grad, dL, grid, st);
   if (sd.layer != TSAT_LAYER_RELAXED && pd.rec_stride == 8) return launch_updateL(pd, sd, hy, mode, zin, grad, dL, grid, st);
-  if (sd.layer == TSAT_LAYER_RELAXED) return upd_launch<1, true, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);
+  if (sd.layer == TSAT_LAYER_RELAXED)
+    return sd.dr16 ? upd_launch<1, true, true, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st)
+                   : upd_launch<1, true, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);
   switch (P) {
     case 1: return upd_launch<1, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);
     case 2: return upd_launch<2, true>(pd, sd, hy, mode, zin, grad, dL, grid, rpi, st);
@@ -1640,8 +1654,10 @@ __global__ void __launch_bounds__(kBlock) k_relaxed_fwd(ProbDev pd, StateDev sd,
 }
 
 // dL/dR_ci = -(e^{-tau R_ci} / Z_i)(1 - tau (R_ci - S_i)) (Eq. 4 differentiated),
-// in place over the stored R, once per (clause, sample): the update then only
-// gathers and adds it per occurrence.
+// once per (clause, sample): the update then only gathers and adds it per
+// occurrence.  FP32 storage: in place over the stored R; BF16 storage: into
+// the bf16 buffer, so that the update gathers half the bytes (the sums stay
+// FP32).
 __global__ void __launch_bounds__(kBlock) k_relaxed_dr(ProbDev pd, StateDev sd, Hyper hy, int skip_frozen) {
   if (skip_frozen && sd.hdr->all_done) return;
   const int4 it = pd.items[blockIdx.x];
@@ -1659,7 +1675,13 @@ __global__ void __launch_bounds__(kBlock) k_relaxed_dr(ProbDev pd, StateDev sd, 
     float D[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) D[s] = -(expf(-hy.tau * Rq[s]) / Zr[s]) * (1.0f - hy.tau * (Rq[s] - Sr[s]));
-    *p = make_float4(D[0], D[1], D[2], D[3]);
+    if (sd.dr16) {
+      const __nv_bfloat162 lo = __floats2bfloat162_rn(D[0], D[1]), hi = __floats2bfloat162_rn(D[2], D[3]);
+      *reinterpret_cast<uint2 *>(sd.dr16 + ((size_t)c * N + s0) / 2) =
+          make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
+    } else {
+      *p = make_float4(D[0], D[1], D[2], D[3]);
+    }
   }
 }
 
