@@ -173,6 +173,15 @@ __device__ __forceinline__ float biased_byte(uint32_t x, uint32_t q) {
   return __int_as_float((int)__byte_perm(x, 0x4B000000u, 0x7440u | q)) - 8388736.0f;
 }
 
+// Byte-wise sum of two words of biased byte counts: bytes 128 + a and 128 + b
+// give 128 + a + b, with no carry between bytes (valid while |a + b| <= 127):
+// the low 7 bits add without leaving the byte and bit 7 takes the carry-less
+// sum of the two top bits and the bias
+__device__ __forceinline__ uint32_t add_biased_bytes(uint32_t x, uint32_t y) {
+  const uint32_t s = (x & 0x7F7F7F7Fu) + (y & 0x7F7F7F7Fu);
+  return s ^ (~(x ^ y) & 0x80808080u);
+}
+
 // Sum over the W consecutive lanes of a row group (W a power of two dividing
 // 32); every lane of the warp takes part.
 __device__ __forceinline__ float seg_sum(float x, int W) {

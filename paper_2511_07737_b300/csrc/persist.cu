@@ -9,9 +9,11 @@
 // the multi-kernel path every step pays three kernel boundaries, which is what
 // bounds a step of an instance with a few thousand clauses; here a launch pays
 // one.  State layout, per-instance records and every result follow the
-// multi-kernel path: G is summed per sample in occurrence order exactly as the
-// clause-length 4..7 update kernel does, and an instance freezes at the step
-// whose forward finds a sample with no unsatisfied clause.
+// multi-kernel path: G is formed from exact integer counts (per sample, the
+// signed counts of the products of R's bit planes, folded with the Moebius
+// coefficients of the dL/dR table), so only FP32 rounding order differs from
+// it, and an instance freezes at the step whose forward finds a sample with no
+// unsatisfied clause.
 #include "internal.h"
 #include "kernels.cuh"
 
@@ -45,17 +47,22 @@ __device__ __forceinline__ uint32_t *ps_bits(const StateDev &sd, int64_t t) {
 // whole launch (layout [row][word][33]: the samples of one lane start on
 // their own bank) and are written back once at the end; otherwise they are
 // read and written in global memory at every step.
-// SPT: samples per thread in the update.  With SPT = 8 (N <= 256) four
-// threads share a 32-sample word and a block has 1024 threads: four times the
-// threads of SPT = 32 (N >= 512, 256 threads), each with a quarter of the
-// per-sample work, so a small instance's step has more warps in flight.
+// SPT: samples per thread in the update's sample phase; Q = 32 / SPT threads
+// share a 32-sample word, and a block has 1024 (SPT 8), 512 (16) or 256 (32)
+// threads.  With clause length <= 3 the Q threads of a word also
+// share its occurrences in the counting phase.
+template <int SPT>
+constexpr int ps_block() { return SPT == 8 ? 1024 : (SPT == 16 ? 512 : 256); }
+
 template <int BIN, int NORM, bool RES, int SPT>
-__global__ void __launch_bounds__(SPT == 8 ? 1024 : 256, SPT == 8 ? 1 : 2)
+__global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
     k_persist(ProbDev pd, StateDev sd, Hyper hy, LrSched ls, int32_t K, int32_t vmax) {
-  constexpr int BS = SPT == 8 ? 1024 : 256, NW = BS / 32, Q = 32 / SPT;
+  constexpr int BS = ps_block<SPT>(), NW = BS / 32, Q = 32 / SPT;
   extern __shared__ __align__(16) float smP[];
   __shared__ int64_t sh_t0;
-  __shared__ int sh_skip, sh_found;
+  __shared__ int sh_skip, sh_found, sh_mu0, sh_mi0, sh_fs;
+  __shared__ float sh_L;
+  __shared__ int64_t sh_ft;
   __shared__ float sh_ls[NW], etab[8];
   __shared__ int sh_mu[NW], sh_mi[NW];
   __shared__ StepParams sh_sps[kPsSched];   // step scalars of the next kPsSched steps
@@ -78,7 +85,13 @@ __global__ void __launch_bounds__(SPT == 8 ? 1024 : 256, SPT == 8 ? 1 : 2)
   float *tab = smP + 8 * N;                             // [N][8] with 8 floats of padding per word (ps_tab)
   // the instance's bits, both step parities, rows numbered from the instance's
   // first variable: every gather of the forward and the backward reads them here
-  uint32_t *sbits = reinterpret_cast<uint32_t *>(tab + 264 * W);   // [2][vmax][W]
+  // S and the unsatisfied count of every sample, and the instance's status
+  // fields, are kept in shared memory and written to the state once at the end
+  // of the launch: only the last step's values are visible outside, and a block
+  // barrier after global stores waits for them (about 1.5K cycles a step)
+  float *sS = tab + 264 * W;                                     // [N]
+  int32_t *sU = reinterpret_cast<int32_t *>(sS + N);             // [N]
+  uint32_t *sbits = reinterpret_cast<uint32_t *>(sU + N);        // [2][vmax][W]
   const size_t vw = (size_t)vmax * W;
   for (int64_t i = tid; i < (int64_t)I.n_vars * W; i += BS)
     sbits[(t0 & 1) * vw + i] = ps_bits(sd, t0)[(size_t)I.v_off * W + i];
@@ -152,8 +165,8 @@ __global__ void __launch_bounds__(SPT == 8 ? 1024 : 256, SPT == 8 ? 1 : 2)
       const int h0 = hist[i];
       lsum += S;
       if (h0 < mu || (h0 == mu && i < mi)) { mu = h0; mi = i; }
-      sd.S[(size_t)inst * N + i] = S;
-      sd.unsat[(size_t)inst * N + i] = h0;
+      sS[i] = S;
+      sU[i] = h0;
     }
     for (int o = 16; o > 0; o >>= 1) {
       lsum += __shfl_xor_sync(0xFFFFFFFFu, lsum, o);
@@ -162,21 +175,26 @@ __global__ void __launch_bounds__(SPT == 8 ? 1024 : 256, SPT == 8 ? 1 : 2)
     }
     if (lane == 0) { sh_ls[warp] = lsum; sh_mu[warp] = mu; sh_mi[warp] = mi; }
     __syncthreads();
-    if (tid == 0) {
-      float L = 0.f;
-      for (int q = 0; q < NW; ++q) {
-        L += sh_ls[q];
-        if (sh_mu[q] < mu || (sh_mu[q] == mu && sh_mi[q] < mi)) { mu = sh_mu[q]; mi = sh_mi[q]; }
+    if (warp == 0) {
+      // the warps' partials, one per lane, reduced across warp 0 (a serial loop
+      // over them in one thread cost about 2.8K cycles per step)
+      float L = lane < NW ? sh_ls[lane] : 0.f;
+      mu = lane < NW ? sh_mu[lane] : 0x7FFFFFFF;
+      mi = lane < NW ? sh_mi[lane] : 0x7FFFFFFF;
+      for (int o = 16; o > 0; o >>= 1) {
+        L += __shfl_xor_sync(0xFFFFFFFFu, L, o);
+        const int u2 = __shfl_xor_sync(0xFFFFFFFFu, mu, o), i2 = __shfl_xor_sync(0xFFFFFFFFu, mi, o);
+        if (u2 < mu || (u2 == mu && i2 < mi)) { mu = u2; mi = i2; }
       }
-      InstState *is = sd.inst + inst;
-      is->loss = -L;
-      is->min_unsat = mu;
-      is->best_sample = mi;
-      if (mu == 0) {
-        is->found = 1;
-        is->found_sample = mi;
-        is->found_step = t;
-        sh_found = 1;
+      if (lane == 0) {
+        sh_L = -L;
+        sh_mu0 = mu;
+        sh_mi0 = mi;
+        if (mu == 0) {
+          sh_found = 1;
+          sh_fs = mi;
+          sh_ft = t;
+        }
       }
     }
     __syncthreads();
@@ -203,11 +221,83 @@ __global__ void __launch_bounds__(SPT == 8 ? 1024 : 256, SPT == 8 ? 1 : 2)
       float acc[SPT];
 #pragma unroll
       for (int j = 0; j < SPT; ++j) acc[j] = 0.f;
-      if (act) {
+      const bool two = pd.rec_stride == 4;   // clause length <= 3: R <= 3, masks b0, b1, b0 b1
+      if (two) {
+        // Clause length <= 3: the word's occurrences are dealt round-robin to
+        // its Q threads, each counting all 32 samples of the word in strided
+        // byte counters (byte b of sc[m][j] counts sample 8b + j); the Q
+        // partial counts are summed byte-wise across the threads and thread q
+        // folds its own samples SPT q + j.  An occurrence is decoded and
+        // gathered once per word instead of once per thread.  The chunk rounds
+        // are warp-uniform (shuffles).
+        const int q = rl % Q;
+        uint32_t own = 0;
+        int32_t o0 = 0, deg = 0;
+        if (act) {
+          own = bsrc[(size_t)vl * W + w];
+          o0 = __ldg(pd.vptr + v);
+          deg = __ldg(pd.vptr + v + 1) - o0;
+        }
+        int maxdeg = deg;
+        for (int o = 16; o > 0; o >>= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xFFFFFFFFu, maxdeg, o));
+        const int tb = ps_tab(32 * w + sb);
+        const int4 *xr4 = reinterpret_cast<const int4 *>(pd.xrec) + o0;   // {hdr, lit, lit, 0} per occurrence
+        int nsign = 0;
+        for (int32_t c0 = 0; c0 < maxdeg; c0 += kPsChunk) {
+          const int32_t ce = min(deg, c0 + kPsChunk);
+          uint32_t sc[3][8];
+#pragma unroll
+          for (int mk = 0; mk < 3; ++mk)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sc[mk][j] = 0x80808080u;
+#pragma unroll 2
+          for (int32_t o = c0 + q; o < ce; o += Q) {
+            const int4 ra = __ldg(xr4 + o);
+            const int h = ra.x, len = h >> 1;
+            const uint32_t a = own ^ (0u - (uint32_t)(h & 1));
+            const uint32_t bb =
+                len > 1 ? (bsrc[(size_t)((ra.y >> 1) - I.v_off) * W + w] ^ (0u - (uint32_t)(ra.y & 1))) : 0u;
+            const uint32_t cc =
+                len > 2 ? (bsrc[(size_t)((ra.z >> 1) - I.v_off) * W + w] ^ (0u - (uint32_t)(ra.z & 1))) : 0u;
+            const uint32_t p0 = a ^ bb ^ cc, p1 = (a & bb) | (cc & (a ^ bb));   // R = p0 + 2 p1
+            const uint32_t sg = (h & 1) ? 0xFFFFFFFFu : 1u;
+            nsign += (int)sg;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const uint32_t t0 = (p0 >> j) & 0x01010101u, t1 = (p1 >> j) & 0x01010101u;
+              sc[0][j] += t0 * sg;
+              sc[1][j] += t1 * sg;
+              sc[2][j] += (t0 & t1) * sg;
+            }
+          }
+#pragma unroll
+          for (int o = 1; o < Q; o <<= 1)
+#pragma unroll
+            for (int mk = 0; mk < 3; ++mk)
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                sc[mk][j] = add_biased_bytes(sc[mk][j], __shfl_xor_sync(0xFFFFFFFFu, sc[mk][j], o));
+#pragma unroll
+          for (int j = 0; j < SPT; ++j) {   // sample SPT q + j: byte (SPT q + j) / 8 of counter (j mod 8)
+            const float *cf = tab + tb + 8 * j;
+            const uint32_t bq = (uint32_t)((SPT / 8) * q + (j >> 3));
+            float g = acc[j];
+            g = fmaf(biased_byte(sc[0][j & 7], bq), cf[1], g);
+            g = fmaf(biased_byte(sc[1][j & 7], bq), cf[2], g);
+            g = fmaf(biased_byte(sc[2][j & 7], bq), cf[3], g);
+            acc[j] = g;
+          }
+        }
+#pragma unroll
+        for (int o = 1; o < Q; o <<= 1) nsign += __shfl_xor_sync(0xFFFFFFFFu, nsign, o);
+        if (act) {
+#pragma unroll
+          for (int j = 0; j < SPT; ++j) acc[j] = fmaf((float)nsign, tab[tb + 8 * j], acc[j]);
+        }
+      } else if (act) {
         const uint32_t own = bsrc[(size_t)vl * W + w];
         const int32_t o0 = __ldg(pd.vptr + v), o1 = __ldg(pd.vptr + v + 1);
         const int tb = ps_tab(32 * w + sb);
-        const bool two = pd.rec_stride == 4;   // clause length <= 3: R <= 3, masks b0, b1, b0 b1
         int nsign = 0;
         for (int32_t c0 = o0; c0 < o1; c0 += kPsChunk) {
           const int32_t c1 = min(o1, c0 + kPsChunk);
@@ -339,11 +429,29 @@ __global__ void __launch_bounds__(SPT == 8 ? 1024 : 256, SPT == 8 ? 1 : 2)
     }
     __syncthreads();   // the bits, z and normaliser of step t + 1 are written before its forward
   }
+  __syncthreads();
+  // the last forward's S, unsatisfied counts and status (and the model's sample and step)
+  if (ran && K > 0) {
+    for (int i = tid; i < N; i += BS) {
+      sd.S[(size_t)inst * N + i] = sS[i];
+      sd.unsat[(size_t)inst * N + i] = sU[i];
+    }
+    if (tid == 0) {
+      InstState *is = sd.inst + inst;
+      is->loss = sh_L;
+      is->min_unsat = sh_mu0;
+      is->best_sample = sh_mi0;
+      if (found) {
+        is->found = 1;
+        is->found_sample = sh_fs;
+        is->found_step = sh_ft;
+      }
+    }
+  }
   // an instance found in this launch keeps its model in both bit buffers (the
   // multi-kernel path copies a frozen instance's bits at every step)
-  __syncthreads();
   if (found && ran) {
-    const int64_t tf = sd.inst[inst].found_step;
+    const int64_t tf = sh_ft;
     for (int64_t i = tid; i < (int64_t)I.n_vars * W; i += BS) {
       if (RES) sbits[((tf + 1) & 1) * vw + i] = sbits[(tf & 1) * vw + i];
       else ps_bits(sd, tf + 1)[(size_t)I.v_off * W + i] = ps_bits(sd, tf)[(size_t)I.v_off * W + i];
@@ -393,12 +501,12 @@ __global__ void __launch_bounds__(SPT == 8 ? 1024 : 256, SPT == 8 ? 1 : 2)
   }
 }
 
-// histogram [8][N] int32, then the table: 264 floats per 32-sample word
-// histogram [8][N] int32, the table (264 floats per 32-sample word), the bits
-// [2][vmax][N/32]; resident: z, m, v [vmax][N/32][33] and the normaliser [vmax]
+// histogram [8][N] int32, the table (264 floats per 32-sample word), S and the
+// unsatisfied counts [N] each, the bits [2][vmax][N/32]; resident: z, m, v
+// [vmax][N/32][33] and the normaliser [vmax]
 int64_t persist_smem_bytes(int N, int32_t vmax, bool resident) {
   const int64_t vw = (int64_t)vmax * (N / 32);
-  return 4 * (8LL * N + 264LL * (N / 32) + 2 * vw + (resident ? 3 * 33 * vw + vmax : 0));
+  return 4 * (8LL * N + 264LL * (N / 32) + 2LL * N + 2 * vw + (resident ? 3 * 33 * vw + vmax : 0));
 }
 
 cudaError_t launch_persist(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls, int32_t K,
@@ -411,10 +519,13 @@ cudaError_t launch_persist(const ProbDev &pd, const StateDev &sd, const Hyper &h
     return cudaGetLastError();
   };
   const bool ph = hy.binarize == TSAT_BIN_PHILOX;
-  const bool small = sd.N <= 256;   // 8 samples per thread, 1024-thread blocks
-#define PS_GO(B, M)                                                                          \
-  (small ? (resident ? go(k_persist<B, M, true, 8>, 1024) : go(k_persist<B, M, false, 8>, 1024)) \
-         : (resident ? go(k_persist<B, M, true, 32>, 256) : go(k_persist<B, M, false, 32>, 256)))
+  // samples per thread: resident instances run at 512 threads (16), the
+  // others hide their global z, m, v latency with 1024 (8); measured at
+  // N = 32..256, n = 100..1000 (16 is 16-31 % faster when resident, 8 is
+  // 8-20 % faster when not)
+  const int spt = sd.N > 256 ? 32 : (resident ? 16 : 8);
+#define PS_GO1(B, M, S) (resident ? go(k_persist<B, M, true, S>, ps_block<S>()) : go(k_persist<B, M, false, S>, ps_block<S>()))
+#define PS_GO(B, M) (spt == 8 ? PS_GO1(B, M, 8) : (spt == 16 ? PS_GO1(B, M, 16) : PS_GO1(B, M, 32)))
   switch (hy.norm) {
     case TSAT_NORM_SIGNED_MEAN:
       return ph ? PS_GO(TSAT_BIN_PHILOX, TSAT_NORM_SIGNED_MEAN) : PS_GO(TSAT_BIN_DET, TSAT_NORM_SIGNED_MEAN);
@@ -424,6 +535,7 @@ cudaError_t launch_persist(const ProbDev &pd, const StateDev &sd, const Hyper &h
       return ph ? PS_GO(TSAT_BIN_PHILOX, TSAT_NORM_NONE) : PS_GO(TSAT_BIN_DET, TSAT_NORM_NONE);
   }
 #undef PS_GO
+#undef PS_GO1
 }
 
 }  // namespace tsat
