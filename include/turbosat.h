@@ -186,7 +186,7 @@ int tsat_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t st
  * FP32 state.  Each block keeps its instance's bits (both step parities) in
  * shared memory.  Requirements: the STE layer, hp->mix_restart = 0, clauses
  * of at most 7 literals, clauses x longest clause x samples <= 2^26 per
- * instance, and 4 (18.25 N + 2 n_vars N / 32) bytes of shared memory <= 200
+ * instance, and 4 (18.5 N + 2 n_vars N / 32) bytes of shared memory <= 200
  * KiB for the largest instance (about 25,000 variables at N = 32, 12,500 at
  * N = 64, 500 at N = 1024); else TSAT_EINVAL / TSAT_ERANGE.  Async on
  * `stream`. */

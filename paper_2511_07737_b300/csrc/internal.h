@@ -87,10 +87,13 @@ struct tsat_state {
   float *fwd_scratch = nullptr;     // tsat_forward outputs staging
   // schedules
   int32_t upd_blocks_per_sm = 0;   // 0: resident blocks per SM from the occupancy API
+  mutable int32_t occ_bps = -1;     // that occupancy figure, queried once per state
   int32_t upd_rows_per_item = 1;
   int32_t sm_count = 148;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  void *h_stat = nullptr;           // pinned host copy of the header and status records (tsat_status)
+  size_t h_stat_bytes = 0;
   std::map<GraphKey, cudaGraphExec_t> graphs;
   int32_t launches_per_step = 3;
 };

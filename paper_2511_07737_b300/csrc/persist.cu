@@ -14,6 +14,8 @@
 // coefficients of the dL/dR table), so only FP32 rounding order differs from
 // it, and an instance freezes at the step whose forward finds a sample with no
 // unsatisfied clause.
+#include <unordered_map>
+
 #include "internal.h"
 #include "kernels.cuh"
 
@@ -21,10 +23,13 @@ namespace tsat {
 
 constexpr int kPsSched = 256;   // steps whose scalars are formed at once (one per thread)
 
-// dL/dR table of one sample: 8 floats (r = 0..7); each word's 32 samples are
-// followed by 8 floats of padding (264 floats per word), so that the lanes of
-// one lookup (same bit, rows at different words) start on different banks
-__device__ __forceinline__ int ps_tab(int s) { return 8 * s + 8 * (s >> 5); }
+// dL/dR table of one sample: 8 floats (r = 0..7); every 16 samples are
+// followed by 8 floats of padding (272 floats per 32-sample word), so that the
+// lanes of one lookup (same bit, threads at different words or at the two
+// halves of a word) start on different banks
+__device__ __forceinline__ int ps_tab(int s) { return 8 * s + 8 * (s >> 4); }
+// offset of sample s0 + j from ps_tab(s0), s0 a multiple of 16 or j + s0 % 16 < 16
+__device__ __forceinline__ int ps_tab_rel(int j) { return 8 * j + 8 * (j >> 4); }
 
 // In place: c[m] = sum over m' subset of m of (-1)^{|m| - |m'|} g[m'] (R's three
 // bit planes b0, b1, b2 as the bits of m), so that g[R] = sum over the
@@ -82,15 +87,14 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
   const InstInfo I = pd.inst[inst];
   const int lmax = I.lmax;
   int32_t *hist = reinterpret_cast<int32_t *>(smP);   // [lmax + 1][N]
-  float *tab = smP + 8 * N;                             // [N][8] with 8 floats of padding per word (ps_tab)
-  // the instance's bits, both step parities, rows numbered from the instance's
-  // first variable: every gather of the forward and the backward reads them here
+  float *tab = smP + 8 * N;                             // [N][8] with 8 floats of padding per 16 samples (ps_tab)
   // S and the unsatisfied count of every sample, and the instance's status
   // fields, are kept in shared memory and written to the state once at the end
-  // of the launch: only the last step's values are visible outside, and a block
-  // barrier after global stores waits for them (about 1.5K cycles a step)
-  float *sS = tab + 264 * W;                                     // [N]
+  // of the launch: only the last step's values are visible outside
+  float *sS = tab + 272 * W;                                     // [N]
   int32_t *sU = reinterpret_cast<int32_t *>(sS + N);             // [N]
+  // the instance's bits, both step parities, rows numbered from the instance's
+  // first variable: every gather of the forward and the backward reads them here
   uint32_t *sbits = reinterpret_cast<uint32_t *>(sU + N);        // [2][vmax][W]
   const size_t vw = (size_t)vmax * W;
   for (int64_t i = tid; i < (int64_t)I.n_vars * W; i += BS)
@@ -128,16 +132,31 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
       uint32_t pl[3] = {0u, 0u, 0u};
       if (active) {
         const int c = I.c_off + 32 * g + lane;
-        const int32_t b = __ldg(pd.cptr + c), e = __ldg(pd.cptr + c + 1);
-        for (int32_t j = b; j < e; ++j) {
-          const int32_t lit = __ldg(pd.clit + j);
-          bitslice_add<3>(pl, bsrc[(size_t)((lit >> 1) - I.v_off) * W + w] ^ (0u - (uint32_t)(lit & 1)));
+        if (pd.crec) {
+          // clause length <= 3: one record {v0, v1, v2, negation bytes | length << 24}
+          // instead of the clause pointers and literals (a missing literal repeats v0)
+          const int4 cr = __ldg(pd.crec + c);
+          const uint32_t len = (uint32_t)cr.w >> 24;
+          const uint32_t a = bsrc[(size_t)(cr.x - I.v_off) * W + w] ^ __byte_perm((uint32_t)cr.w, 0u, 0x0000u);
+          const uint32_t b =
+              len > 1 ? (bsrc[(size_t)(cr.y - I.v_off) * W + w] ^ __byte_perm((uint32_t)cr.w, 0u, 0x1111u)) : 0u;
+          const uint32_t d =
+              len > 2 ? (bsrc[(size_t)(cr.z - I.v_off) * W + w] ^ __byte_perm((uint32_t)cr.w, 0u, 0x2222u)) : 0u;
+          pl[0] = a ^ b ^ d;
+          pl[1] = (a & b) | (d & (a ^ b));
+        } else {
+          const int32_t b = __ldg(pd.cptr + c), e = __ldg(pd.cptr + c + 1);
+          for (int32_t j = b; j < e; ++j) {
+            const int32_t lit = __ldg(pd.clit + j);
+            bitslice_add<3>(pl, bsrc[(size_t)((lit >> 1) - I.v_off) * W + w] ^ (0u - (uint32_t)(lit & 1)));
+          }
         }
       }
       const uint32_t valid = __ballot_sync(0xFFFFFFFFu, active);
       uint32_t tp[3];
-#pragma unroll
-      for (int p = 0; p < 3; ++p) tp[p] = warp_transpose32(pl[p], lane);
+      tp[0] = warp_transpose32(pl[0], lane);
+      tp[1] = warp_transpose32(pl[1], lane);
+      tp[2] = pd.crec ? 0u : warp_transpose32(pl[2], lane);   // R <= 3 with clause records
       for (int r = 0; r <= lmax; ++r) {
         const int cnt = __popc(valid & bitslice_eq<3>(tp, r));
         if (cnt) atomicAdd(hist + r * N + 32 * w + lane, cnt);
@@ -279,7 +298,7 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
                 sc[mk][j] = add_biased_bytes(sc[mk][j], __shfl_xor_sync(0xFFFFFFFFu, sc[mk][j], o));
 #pragma unroll
           for (int j = 0; j < SPT; ++j) {   // sample SPT q + j: byte (SPT q + j) / 8 of counter (j mod 8)
-            const float *cf = tab + tb + 8 * j;
+            const float *cf = tab + tb + ps_tab_rel(j);
             const uint32_t bq = (uint32_t)((SPT / 8) * q + (j >> 3));
             float g = acc[j];
             g = fmaf(biased_byte(sc[0][j & 7], bq), cf[1], g);
@@ -292,7 +311,7 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
         for (int o = 1; o < Q; o <<= 1) nsign += __shfl_xor_sync(0xFFFFFFFFu, nsign, o);
         if (act) {
 #pragma unroll
-          for (int j = 0; j < SPT; ++j) acc[j] = fmaf((float)nsign, tab[tb + 8 * j], acc[j]);
+          for (int j = 0; j < SPT; ++j) acc[j] = fmaf((float)nsign, tab[tb + ps_tab_rel(j)], acc[j]);
         }
       } else if (act) {
         const uint32_t own = bsrc[(size_t)vl * W + w];
@@ -344,7 +363,7 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
           for (int u = 0; u < NWD; ++u)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              const float *cf = tab + tb + 8 * (4 * u + e);
+              const float *cf = tab + tb + ps_tab_rel(4 * u + e);
               float g = acc[4 * u + e];
               g = fmaf(biased_byte(sc[0][u], e), cf[1], g);
               g = fmaf(biased_byte(sc[1][u], e), cf[2], g);
@@ -357,7 +376,7 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
             }
         }
 #pragma unroll
-        for (int j = 0; j < SPT; ++j) acc[j] = fmaf((float)nsign, tab[tb + 8 * j], acc[j]);
+        for (int j = 0; j < SPT; ++j) acc[j] = fmaf((float)nsign, tab[tb + ps_tab_rel(j)], acc[j]);
       }
       const size_t off = RES ? ((size_t)vl * W + w) * 33 + sb : (size_t)v * N + 32 * w + sb;
       float *zp = RES ? smz : sd.z, *mp = RES ? smm : sd.m, *vp = RES ? smv : sd.v;
@@ -501,20 +520,27 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
   }
 }
 
-// histogram [8][N] int32, the table (264 floats per 32-sample word), S and the
+// histogram [8][N] int32, the table (272 floats per 32-sample word), S and the
 // unsatisfied counts [N] each, the bits [2][vmax][N/32]; resident: z, m, v
 // [vmax][N/32][33] and the normaliser [vmax]
 int64_t persist_smem_bytes(int N, int32_t vmax, bool resident) {
   const int64_t vw = (int64_t)vmax * (N / 32);
-  return 4 * (8LL * N + 264LL * (N / 32) + 2LL * N + 2 * vw + (resident ? 3 * 33 * vw + vmax : 0));
+  return 4 * (8LL * N + 272LL * (N / 32) + 2LL * N + 2 * vw + (resident ? 3 * 33 * vw + vmax : 0));
 }
 
 cudaError_t launch_persist(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls, int32_t K,
                            int32_t vmax, bool resident, cudaStream_t st) {
   const int smem = (int)persist_smem_bytes(sd.N, vmax, resident);
   auto go = [&](auto kern, int block) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
+    // the largest dynamic shared memory set so far for each kernel instance:
+    // one attribute call per instance and size, not one per launch
+    static std::unordered_map<const void *, int> smem_set;
+    int &have = smem_set[reinterpret_cast<const void *>(kern)];
+    if (smem > have) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      have = smem;
+    }
     kern<<<pd.n_inst, block, smem, st>>>(pd, sd, hy, ls, K, vmax);
     return cudaGetLastError();
   };
