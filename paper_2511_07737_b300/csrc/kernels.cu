@@ -381,6 +381,10 @@ __device__ __forceinline__ void fwd_unit(const ProbDev &pd, const uint32_t *bw, 
   }
 }
 
+// W: words per row as a compile-time constant (16 or 32, i.e. N = 512 or 1024,
+// the sizes this kernel runs at); the row-group arithmetic then folds into
+// immediates (0.433 -> 0.331 ms at n = 1e6, N = 1024).
+template <int WC>
 __global__ void __launch_bounds__(kBlock, 4) k_fwd_w3(ProbDev pd, StateDev sd, int32_t *hist, int skip_frozen) {
   extern __shared__ int32_t shh[];   // [nr][N] block histogram; sample 32 w + i at 32 w + ((i + w) & 31)
   const StateHdr *hdr = sd.hdr;
@@ -388,7 +392,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_fwd_w3(ProbDev pd, StateDev sd, i
   const int4 it = pd.items[blockIdx.x];
   const int inst = it.x;
   if (skip_frozen && sd.inst[inst].found) return;
-  const int W = sd.W, N = sd.N, RW = 32 / W, lm1 = sd.lm1;
+  constexpr int W = WC, RW = 32 / W, N = 32 * W;
+  const int lm1 = sd.lm1;
   const int nr = min(pd.inst[inst].lmax, 3) + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rsub = lane / W, w = lane % W;
@@ -1414,9 +1419,10 @@ cudaError_t launch_relaxed_lits(const ProbDev &pd, const StateDev &sd, const Hyp
 cudaError_t launch_fwd_hist(const ProbDev &pd, const StateDev &sd, int32_t *hist, int skip_frozen, cudaStream_t st) {
   const int P = planes_for(pd.lmax);
   const int W = sd.W;
-  if (pd.crec && pd.lmax <= 3 && W >= 16) {   // word per lane (clause records, vertical counters)
+  if (pd.crec && pd.lmax <= 3 && W >= 16) {   // word per lane (clause records, vertical counters); N is 512 or 1024
     const int smem = (int)sizeof(int32_t) * 4 * sd.N;
-    k_fwd_w3<<<pd.n_items, kBlock, smem, st>>>(pd, sd, hist, skip_frozen);
+    if (W == 32) k_fwd_w3<32><<<pd.n_items, kBlock, smem, st>>>(pd, sd, hist, skip_frozen);
+    else k_fwd_w3<16><<<pd.n_items, kBlock, smem, st>>>(pd, sd, hist, skip_frozen);
     return cudaGetLastError();
   }
   const int WB = (P >= 4) ? 1 : (W >= 4 ? 4 : W);
