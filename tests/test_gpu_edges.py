@@ -144,3 +144,19 @@ def test_hundreds_of_tiny_instances(persistent):
     fn = (lambda st: ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=False)) if persistent else None
     status, _, _, _ = run_lockstep(insts, 32, hp, 2, fn)
     assert len(status["inst"]) == 300
+
+
+@pytest.mark.parametrize("n,m,N,persistent", [(40, 2400, 64, False), (40, 2400, 64, True), (60, 3600, 256, True),
+                                              (40, 2400, 1024, True), (40, 2400, 1024, False)])
+def test_variables_with_more_than_127_occurrences(n, m, N, persistent):
+    """Clause length 3 with about 180 occurrences per variable: the fused
+    updates count occurrences in signed byte counters of at most 127 per
+    chunk, so every row takes several chunks (persistent solver: resident at
+    N = 64 with 16 samples per thread, not resident at N = 256 with 8, 32 at
+    N = 1024)."""
+    inst = cnfgen.planted_ksat(n, m, 3, 75)
+    deg = np.bincount(np.abs(inst.lits) - 1, minlength=n)
+    assert deg.min() > 127
+    hp = ts.hparams(seed=10, norm=ts.NORM_ABSMEAN, binarize=ts.BIN_PHILOX, tau=1.5)
+    fn = (lambda st: ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=False)) if persistent else None
+    run_lockstep([inst], N, hp, 3, fn)
