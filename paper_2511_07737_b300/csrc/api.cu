@@ -248,7 +248,7 @@ int tsat_state_create(tsat_problem *p, void *d_state, size_t state_bytes, int32_
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev);
-  auto fail = [&](cudaError_t e, const char *w) { delete s; return cuda_fail(e, w); };
+  auto fail = [&](cudaError_t e, const char *w) { tsat_state_free(s); return cuda_fail(e, w); };   // releases what was created
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
   if ((e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
