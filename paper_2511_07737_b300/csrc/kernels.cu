@@ -858,13 +858,11 @@ __global__ void __launch_bounds__(kUpd3Block, kUpd3MinB) k_update3(ProbDev pd, S
     const bool act = valid && !frozen;
     const float4 *gd4 = reinterpret_cast<const float4 *>(sd.gdelta + (size_t)inst * 4 * N);   // [4][N/4]
     if (MODE == 0 && act) {
-      // the row's z, m, v stream into L2 while the occurrences are counted:
-      // each lane asks for the 128-byte lines of its own word (per-line
-      // prefetches are 0.5 % faster here than one bulk prefetch per array)
-      const size_t ro = (size_t)v * N + 32 * w;
-      prefetch_l2_line(zsrc + ro);
-      prefetch_l2_line(sd.m + ro);
-      prefetch_l2_line(sd.v + ro);
+      // the row's z streams into L2 while the occurrences are counted: each
+      // lane asks for the 128-byte line of its own word (per-line prefetches
+      // are 0.5 % faster here than one bulk prefetch per array); m and v are
+      // asked for only before pass 1 (below)
+      prefetch_l2_line(zsrc + (size_t)v * N + 32 * w);
     }
 
     // the row group's next row: its vptr entries now, its first record round
@@ -960,6 +958,16 @@ __global__ void __launch_bounds__(kUpd3Block, kUpd3MinB) k_update3(ProbDev pd, S
     if (w < dn) nrec = __ldg(xrec4 + o0n + w);
     crec = nrec;
     have_crec = true;
+    // m and v are first read in pass 2.  Prefetched here rather than at the
+    // row's start, they spend a third as long in L2, where the prefetched
+    // rows of all resident warps (about 50 MB with all three arrays) would
+    // otherwise crowd out the bits array the gathers read (update at n = 1e6:
+    // 5.48 -> 5.03 ms; before pass 2 instead: 5.07; no z prefetch: 5.36)
+    if (MODE == 0 && act) {
+      const size_t ro = (size_t)v * N + 32 * w;
+      prefetch_l2_line(sd.m + ro);
+      prefetch_l2_line(sd.v + ro);
+    }
     // ---- sample phase, pass 1: G of samples s = 4Wk + 4w + e, Eq. 5 dot product
     const float nu = act ? sd.nu[v] : 1.0f;
     const float rnu = __frcp_rn(nu);
