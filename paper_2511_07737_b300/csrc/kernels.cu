@@ -857,17 +857,10 @@ __global__ void __launch_bounds__(kUpd3Block, kUpd3MinB) k_update3(ProbDev pd, S
     }
     const bool act = valid && !frozen;
     const float4 *gd4 = reinterpret_cast<const float4 *>(sd.gdelta + (size_t)inst * 4 * N);   // [4][N/4]
-    if (MODE == 0 && act) {
-      // the row's z streams into L2 while the occurrences are counted: each
-      // lane asks for the 128-byte line of its own word (per-line prefetches
-      // are 0.5 % faster here than one bulk prefetch per array); m and v are
-      // asked for only before pass 1 (below)
-      prefetch_l2_line(zsrc + (size_t)v * N + 32 * w);
-    }
 
     // the row group's next row: its vptr entries now, its first record round
     // before pass 1, and an L2 prefetch of the bits rows its occurrences will
-    // gather after pass 2 (the bits array is larger than L2 at scale)
+    // gather at this row's end (the bits array is larger than L2 at scale)
     const int64_t vn = v + nwarps * RW;
     int32_t o0n = 0, dn = 0;
     if (vn < pd.V) {
@@ -882,6 +875,14 @@ __global__ void __launch_bounds__(kUpd3Block, kUpd3MinB) k_update3(ProbDev pd, S
       o0 = __ldg(pd.vptr + v);
       o1 = __ldg(pd.vptr + v + 1);
     }
+    // The row's z is prefetched into L2 three quarters of the way through its
+    // occurrences, m and v just before pass 1: each lane asks for the 128-byte
+    // line of its own word.  Lines prefetched earlier sit longer in L2 and push
+    // out the bits rows the gathers read (update at n = 1e6: all three at the
+    // row's start 5.48 ms, z at the start and m, v before pass 1 5.03, z at a
+    // quarter / half / three quarters of the occurrences 5.04 / 5.00 / 4.99,
+    // no z prefetch 5.36)
+    const uint32_t zpf_at = (MODE == 0 && act) ? (uint32_t)(o1 - o0) * 3u >> 2 : 0xFFFFFFFFu;
     const uint32_t own = act ? __ldg(bsrc + v * W + w) : 0u;
     bool first = true;   // no earlier chunk folded into gbuf
     // every lane of the warp runs the same number of record rounds (shuffles)
@@ -909,6 +910,7 @@ __global__ void __launch_bounds__(kUpd3Block, kUpd3MinB) k_update3(ProbDev pd, S
           rc.x = __shfl_sync(0xFFFFFFFFu, myrec.x, rbase + i);
           rc.y = __shfl_sync(0xFFFFFFFFu, myrec.y, rbase + i);
           rc.z = __shfl_sync(0xFFFFFFFFu, myrec.z, rbase + i);
+          if ((uint32_t)(c0 + r0 + i) == zpf_at) prefetch_l2_line(zsrc + (size_t)v * N + 32 * w);
           if (RW > 1 && r0 + i >= cn) continue;       // this row has no occurrence here
           const uint32_t len = (uint32_t)rc.x >> 1;
           const uint32_t a = own ^ (0u - (uint32_t)(rc.x & 1));
@@ -958,11 +960,10 @@ __global__ void __launch_bounds__(kUpd3Block, kUpd3MinB) k_update3(ProbDev pd, S
     if (w < dn) nrec = __ldg(xrec4 + o0n + w);
     crec = nrec;
     have_crec = true;
-    // m and v are first read in pass 2.  Prefetched here rather than at the
-    // row's start, they spend a third as long in L2, where the prefetched
-    // rows of all resident warps (about 50 MB with all three arrays) would
-    // otherwise crowd out the bits array the gathers read (update at n = 1e6:
-    // 5.48 -> 5.03 ms; before pass 2 instead: 5.07; no z prefetch: 5.36)
+    // m and v are first read in pass 2; prefetched here (see above) rather
+    // than at the row's start, they spend a third as long in L2, where the
+    // prefetched rows of all resident warps would otherwise crowd out the bits
+    // array the gathers read (before pass 2 instead: 5.07 ms)
     if (MODE == 0 && act) {
       const size_t ro = (size_t)v * N + 32 * w;
       prefetch_l2_line(sd.m + ro);
@@ -1034,11 +1035,13 @@ __global__ void __launch_bounds__(kUpd3Block, kUpd3MinB) k_update3(ProbDev pd, S
         st_cs(sd.v + off, make_float4(vq[0], vq[1], vq[2], vq[3]));
       }
     }
-    if (w < dn) {
-      prefetch_l2_line(bsrc + (size_t)(nrec.y >> 1) * W);
-      if ((nrec.x >> 1) > 2) prefetch_l2_line(bsrc + (size_t)(nrec.z >> 1) * W);
+    if constexpr (MODE == 1) {
+      if (w < dn) {
+        prefetch_l2_line(bsrc + (size_t)(nrec.y >> 1) * W);
+        if ((nrec.x >> 1) > 2) prefetch_l2_line(bsrc + (size_t)(nrec.z >> 1) * W);
+      }
+      continue;
     }
-    if constexpr (MODE == 1) continue;
     const float tot = seg_sum(psum, W);
     __syncwarp();   // every lane's count words are consumed: their space takes the nibbles
     // ---- Eq. 2 / Philox bits of step t+1: the lane's samples of pass k form
@@ -1094,6 +1097,12 @@ __global__ void __launch_bounds__(kUpd3Block, kUpd3MinB) k_update3(ProbDev pd, S
       for (int c = 0; c < 8; ++c) word |= nbuf[cswz(ist + c)] << (4 * c);
       bdst[v * W + w] = word;
       if (w == 0) sd.nu[v] = nun;
+    }
+    // the bits rows the next row's first record round will gather, into L2
+    // (at the row's end: 0.4 % faster than after pass 2; without it 5.69 ms)
+    if (w < dn) {
+      prefetch_l2_line(bsrc + (size_t)(nrec.y >> 1) * W);
+      if ((nrec.x >> 1) > 2) prefetch_l2_line(bsrc + (size_t)(nrec.z >> 1) * W);
     }
   }
 }
