@@ -111,6 +111,9 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
     }
     for (int i = tid; i < I.n_vars; i += BS) snu[i] = sd.nu[I.v_off + i];
   }
+  // the histogram starts at zero; each step's update phase clears it again
+  // for the next step's forward (the barrier ending the step orders the two)
+  for (int i = tid; i < (lmax + 1) * N; i += BS) hist[i] = 0;
   __syncthreads();
   int found = sh_found;
   const bool ran = !found;   // the instance is live at the start of the launch
@@ -122,8 +125,6 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
     }
     // ---- forward (Eq. 1): lane = clause, 32 samples of word w; bit-sliced R,
     // warp transpose, popcounts of the R = r masks into the block histogram
-    for (int i = tid; i < (lmax + 1) * N; i += BS) hist[i] = 0;
-    __syncthreads();
     const uint32_t *bsrc = sbits + (t & 1) * vw;
     const int ngroups = (I.n_clauses + 31) >> 5;
     for (int task = warp; task < ngroups * W; task += NW) {
@@ -194,9 +195,12 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
     }
     if (lane == 0) { sh_ls[warp] = lsum; sh_mu[warp] = mu; sh_mi[warp] = mi; }
     __syncthreads();
-    if (warp == 0) {
-      // the warps' partials, one per lane, reduced across warp 0 (a serial loop
-      // over them in one thread cost about 2.8K cycles per step)
+    {
+      // every warp reduces the warps' partials (one per lane) itself: the
+      // inputs and the butterfly order are the same, so all warps reach the same
+      // loss and fewest-unsatisfied sample and know without another barrier
+      // whether the instance is found (the partials are rewritten only after
+      // the barrier that ends the step)
       float L = lane < NW ? sh_ls[lane] : 0.f;
       mu = lane < NW ? sh_mu[lane] : 0x7FFFFFFF;
       mi = lane < NW ? sh_mi[lane] : 0x7FFFFFFF;
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
         const int u2 = __shfl_xor_sync(0xFFFFFFFFu, mu, o), i2 = __shfl_xor_sync(0xFFFFFFFFu, mi, o);
         if (u2 < mu || (u2 == mu && i2 < mi)) { mu = u2; mi = i2; }
       }
-      if (lane == 0) {
+      if (tid == 0) {
         sh_L = -L;
         sh_mu0 = mu;
         sh_mi0 = mi;
@@ -215,10 +219,10 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
           sh_ft = t;
         }
       }
+      found = mu == 0;
     }
-    __syncthreads();
-    found = sh_found;
     if (found) break;   // the bits of step t are the model; z, m, v stay
+    for (int i = tid; i < (lmax + 1) * N; i += BS) hist[i] = 0;   // read for the last time above
     // ---- fused update: thread = (row, word w); G of its 32 samples summed over
     // the row's occurrences in record order, then Eq. 5, AdamW, the new
     // normaliser and the bits of step t + 1
