@@ -772,17 +772,21 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
 //     signed occurrences whose R has plane-0 bit, plane-1 bit, both bits set;
 //     gamma[R] = g0 + b0 d1 + b1 d2 + b0 b1 d3 turns the STE sum into
 //     G = (n+ - n-) g0 + C0 d1 + C1 d2 + C01 d3 (exact rewrite).
-// Sample phase: each counter register holds 4 consecutive samples, so the
-// counts go to shared memory as words indexed by sample/4 and each lane reads
-// back the words of its own 4 consecutive samples per pass (8 passes), with
-// coalesced 16-byte accesses to z, m, v (z is read in both passes; the second
-// read hits L2).  Row reductions (Eq. 5 dot product, new normaliser) are
-// shuffles across the row's lanes; each lane binarises its 4 samples into a
-// nibble and lane w assembles bits word w from the eight nibbles of its
-// samples.  The counting loop and the two sample passes are unrolled by 2
-// (two passes' z, m, v loads in flight: 6.24 -> 6.01 ms at n = 1e6); full
-// unrolling loses: with 24 warps per SM in different phases,
-// instruction-cache misses cost more than the loop overhead.
+// The counters are strided (byte b of counter j counts sample 8b + j, so a
+// bit plane is added with one shift and one mask per register); a 4x4 byte
+// transpose per row turns them into words of 4 consecutive samples, stored in
+// shared memory by sample/4.  Sample phase: each lane reads back the words of
+// its own 4 consecutive samples per pass (8 passes), with coalesced 16-byte
+// accesses to z, m, v (z is read in both passes; the second read hits L2).
+// Row reductions (Eq. 5 dot product, new normaliser) are shuffles across the
+// row's lanes; each lane binarises its 4 samples into a nibble and lane w
+// assembles bits word w from the eight nibbles of its samples.  The row's z,
+// m, v and the next row's gathered bits rows are prefetched into L2 as late
+// as still pays (see the prefetches below), to keep the bits array resident.
+// The counting loop and the two sample passes are unrolled by 2 (two passes'
+// z, m, v loads in flight: 6.24 -> 6.01 ms at n = 1e6); full unrolling loses:
+// with 28 warps per SM in different phases, instruction-cache misses cost
+// more than the loop overhead.
 constexpr int kCntChunk = 127;   // occurrences per byte-counter chunk (|count| <= 127)
 // Blocks of 4 warps at <= 73 registers: 7 blocks (28 warps) per SM.  Measured
 // at n = 1e6, N = 1024: 5.97 ms, against 6.02 ms for 8-warp blocks at 80
