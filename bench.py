@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--experiment", default="throughput",
-                    choices=["throughput", "time_to_sat", "batch", "relaxed", "proposer", "mixing"],
+                    choices=["throughput", "time_to_sat", "batch", "relaxed", "proposer", "mixing", "literal_rows"],
                     help="throughput (default, the driver's line) or one of the other workloads")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the experiment workloads (quick runs)")
     ap.add_argument("--solve-steps", type=int, default=1000, help="step cap of the batch experiment's solve phase")
@@ -489,6 +489,63 @@ def exp_time_to_sat(args):
     _emit(out)
 
 
+def exp_literal_rows(args):
+    """The 2V independent-literal-row reading (one trainable row per literal,
+    no tie x' = not x) against the default one row per variable, on the
+    time-to-SAT workload: 32 planted 3-SAT instances n=100 m=426, N=64,
+    absmean Eq. 5, tau 2, lr0 0.5, cap 500 steps, graph path.  The 2V model
+    runs the library on the transformed formula (literal_rows.split_literals),
+    which the library freezes once a sample satisfies it; each decoded
+    assignment (x_v = row v+) is then judged on the original formula."""
+    import torch
+    from paper_2511_07737_b300 import cnfgen, literal_rows
+    from paper_2511_07737_b300 import turbosat as ts
+    n_inst = max(4, int(32 * args.scale))
+    insts = [cnfgen.planted_ksat(100, 426, 3, j) for j in range(n_inst)]
+    kw = dict(norm=1, tau=2.0, lr0=0.5)
+
+    def run(inst, j, split):
+        src = literal_rows.split_literals(inst) if split else inst
+        prob = ts.Problem([(src.n_vars, src.clause_ptr, src.lits)])
+        st = ts.State(prob, 64)
+        hp = ts.hparams(seed=j + 1, **kw)
+        ts.tsat_init(st.h, hp)
+        for _ in range(50):
+            ts.tsat_step(st.h, hp, 10, stop_on_sat=True)
+            if ts.tsat_status(st.h, 1)["inst"][0]["found"]:
+                break
+        return prob, st, hp, ts.tsat_status(st.h, 1)["inst"][0]
+
+    froze, froze_steps, decoded_sat, decoded_min, incons = 0, [], 0, [], []
+    dflt_solved, dflt_steps = 0, []
+    for j, inst in enumerate(insts):
+        _, st, hp, x = run(inst, j, True)
+        if x["found"]:
+            froze += 1
+            froze_steps.append(x["found_step"])
+        orig = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
+        u = literal_rows.decoded_unsat(orig, st, hp.tau)
+        decoded_min.append(int(u.min()))
+        decoded_sat += int(u.min() == 0)
+        incons.append(literal_rows.inconsistent_fraction(st, inst.n_vars))
+        del st, orig
+        _, st, _, x = run(inst, j, False)
+        if x["found"]:
+            dflt_solved += 1
+            dflt_steps.append(x["found_step"])
+        del st
+        torch.cuda.empty_cache()
+    _emit({"experiment": "literal_rows", "instances": n_inst,
+           "workload": "planted 3-SAT n=100 m=426, N=64, absmean, tau 2, lr0 0.5, cap 500 steps, graph path",
+           "two_v_rows": {"frozen_on_transformed_formula": froze,
+                          "median_freeze_step": float(np.median(froze_steps)) if froze_steps else None,
+                          "decoded_models_of_original": decoded_sat,
+                          "median_min_unsat_of_decoded": float(np.median(decoded_min)),
+                          "mean_inconsistent_literal_pairs": float(np.mean(incons))},
+           "one_row_per_variable": {"solved": dflt_solved,
+                                    "median_steps_to_sat": float(np.median(dflt_steps)) if dflt_steps else None}})
+
+
 def exp_batch(args):
     """512 planted k-SAT instances (k uniform 3..7, n log-uniform 200-50,000,
     ratio 0.9 x threshold), 64 restarts each, one launch per kernel per step
@@ -665,7 +722,7 @@ def main():
     if args.experiment != "throughput":
         if rank == 0:
             {"time_to_sat": exp_time_to_sat, "batch": exp_batch, "relaxed": exp_relaxed,
-             "proposer": exp_proposer, "mixing": exp_mixing}[args.experiment](args)
+             "proposer": exp_proposer, "mixing": exp_mixing, "literal_rows": exp_literal_rows}[args.experiment](args)
         return
     ours(args, w, rank, world, local)
 

@@ -160,3 +160,24 @@ def test_variables_with_more_than_127_occurrences(n, m, N, persistent):
     hp = ts.hparams(seed=10, norm=ts.NORM_ABSMEAN, binarize=ts.BIN_PHILOX, tau=1.5)
     fn = (lambda st: ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=False)) if persistent else None
     run_lockstep([inst], N, hp, 3, fn)
+
+
+def test_literal_rows_model_matches_the_oracle_and_decodes():
+    """The 2V literal-row model (one independent row per literal, built as a
+    CNF transform) runs the unchanged kernels: lock-step parity against the
+    oracle on the transformed formula, and the unsatisfied counts of the
+    decoded assignment (x_v = row v+) on the original formula equal the
+    oracle's exact check."""
+    from paper_2511_07737_b300 import literal_rows
+    inst = cnfgen.planted_ksat(100, 426, 3, 3)
+    t = literal_rows.split_literals(inst)
+    hp = ts.hparams(seed=4, norm=ts.NORM_ABSMEAN, tau=2.0, lr0=0.5)
+    _, _, st, _ = run_lockstep([t], 64, hp, 3)
+    orig = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
+    u = literal_rows.decoded_unsat(orig, st, hp.tau)
+    X = snapshot(st)["X"][:inst.n_vars]
+    ref, _ = oracle.check(oracle.CNF(inst.n_vars, inst.clause_ptr, inst.lits), X)
+    np.testing.assert_array_equal(u, ref)
+    frac = literal_rows.inconsistent_fraction(st, inst.n_vars)
+    both = (X == snapshot(st)["X"][inst.n_vars:]).mean()
+    assert abs(frac - both) < 1e-12
