@@ -126,11 +126,16 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
     // ---- forward (Eq. 1): lane = clause, 32 samples of word w; bit-sliced R,
     // warp transpose, popcounts of the R = r masks into the block histogram
     const uint32_t *bsrc = sbits + (t & 1) * vw;
+    // A task is a group of 32 clauses (lane = clause) and WT words of the
+    // samples (WT = 2 when N >= 64): the clause is decoded once for both words
+    // and a small instance needs half the task rounds (n = 100, N = 64: 14
+    // tasks for 16 warps instead of 28)
     const int ngroups = (I.n_clauses + 31) >> 5;
-    for (int task = warp; task < ngroups * W; task += NW) {
-      const int g = task / W, w = task - g * W;
+    const int WT = W >= 2 ? 2 : 1, wtasks = W / WT;
+    for (int task = warp; task < ngroups * wtasks; task += NW) {
+      const int g = task / wtasks, w0 = (task - g * wtasks) * WT;
       const bool active = 32 * g + lane < I.n_clauses;
-      uint32_t pl[3] = {0u, 0u, 0u};
+      uint32_t pl[2][3] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
       if (active) {
         const int c = I.c_off + 32 * g + lane;
         if (pd.crec) {
@@ -138,29 +143,44 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
           // instead of the clause pointers and literals (a missing literal repeats v0)
           const int4 cr = __ldg(pd.crec + c);
           const uint32_t len = (uint32_t)cr.w >> 24;
-          const uint32_t a = bsrc[(size_t)(cr.x - I.v_off) * W + w] ^ __byte_perm((uint32_t)cr.w, 0u, 0x0000u);
-          const uint32_t b =
-              len > 1 ? (bsrc[(size_t)(cr.y - I.v_off) * W + w] ^ __byte_perm((uint32_t)cr.w, 0u, 0x1111u)) : 0u;
-          const uint32_t d =
-              len > 2 ? (bsrc[(size_t)(cr.z - I.v_off) * W + w] ^ __byte_perm((uint32_t)cr.w, 0u, 0x2222u)) : 0u;
-          pl[0] = a ^ b ^ d;
-          pl[1] = (a & b) | (d & (a ^ b));
+          const uint32_t na = __byte_perm((uint32_t)cr.w, 0u, 0x0000u), nb = __byte_perm((uint32_t)cr.w, 0u, 0x1111u),
+                         nd = __byte_perm((uint32_t)cr.w, 0u, 0x2222u);
+          const uint32_t *ra = bsrc + (size_t)(cr.x - I.v_off) * W + w0, *rb = bsrc + (size_t)(cr.y - I.v_off) * W + w0,
+                         *rd = bsrc + (size_t)(cr.z - I.v_off) * W + w0;
+#pragma unroll
+          for (int ww = 0; ww < 2; ++ww) {
+            if (ww < WT) {
+              const uint32_t a = ra[ww] ^ na;
+              const uint32_t b = len > 1 ? (rb[ww] ^ nb) : 0u;
+              const uint32_t d = len > 2 ? (rd[ww] ^ nd) : 0u;
+              pl[ww][0] = a ^ b ^ d;
+              pl[ww][1] = (a & b) | (d & (a ^ b));
+            }
+          }
         } else {
           const int32_t b = __ldg(pd.cptr + c), e = __ldg(pd.cptr + c + 1);
           for (int32_t j = b; j < e; ++j) {
             const int32_t lit = __ldg(pd.clit + j);
-            bitslice_add<3>(pl, bsrc[(size_t)((lit >> 1) - I.v_off) * W + w] ^ (0u - (uint32_t)(lit & 1)));
+            const uint32_t *row = bsrc + (size_t)((lit >> 1) - I.v_off) * W + w0, neg = 0u - (uint32_t)(lit & 1);
+#pragma unroll
+            for (int ww = 0; ww < 2; ++ww)
+              if (ww < WT) bitslice_add<3>(pl[ww], row[ww] ^ neg);
           }
         }
       }
       const uint32_t valid = __ballot_sync(0xFFFFFFFFu, active);
-      uint32_t tp[3];
-      tp[0] = warp_transpose32(pl[0], lane);
-      tp[1] = warp_transpose32(pl[1], lane);
-      tp[2] = pd.crec ? 0u : warp_transpose32(pl[2], lane);   // R <= 3 with clause records
-      for (int r = 0; r <= lmax; ++r) {
-        const int cnt = __popc(valid & bitslice_eq<3>(tp, r));
-        if (cnt) atomicAdd(hist + r * N + 32 * w + lane, cnt);
+#pragma unroll
+      for (int ww = 0; ww < 2; ++ww) {
+        if (ww < WT) {
+          uint32_t tp[3];
+          tp[0] = warp_transpose32(pl[ww][0], lane);
+          tp[1] = warp_transpose32(pl[ww][1], lane);
+          tp[2] = pd.crec ? 0u : warp_transpose32(pl[ww][2], lane);   // R <= 3 with clause records
+          for (int r = 0; r <= lmax; ++r) {
+            const int cnt = __popc(valid & bitslice_eq<3>(tp, r));
+            if (cnt) atomicAdd(hist + r * N + 32 * (w0 + ww) + lane, cnt);
+          }
+        }
       }
     }
     __syncthreads();
