@@ -285,9 +285,9 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
         for (int o = 16; o > 0; o >>= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xFFFFFFFFu, maxdeg, o));
         const int tb = ps_tab(32 * w + sb);
         const int4 *xr4 = reinterpret_cast<const int4 *>(pd.xrec) + o0;   // {hdr, lit, lit, 0} per occurrence
-        int nsign = 0;
         for (int32_t c0 = 0; c0 < maxdeg; c0 += kPsChunk) {
           const int32_t ce = min(deg, c0 + kPsChunk);
+          int nsign = 0;   // signed occurrences of the chunk
           uint32_t sc[3][8];
 #pragma unroll
           for (int mk = 0; mk < 3; ++mk)
@@ -321,21 +321,19 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
               for (int j = 0; j < 8; ++j)
                 sc[mk][j] = add_biased_bytes(sc[mk][j], __shfl_xor_sync(0xFFFFFFFFu, sc[mk][j], o));
 #pragma unroll
-          for (int j = 0; j < SPT; ++j) {   // sample SPT q + j: byte (SPT q + j) / 8 of counter (j mod 8)
-            const float *cf = tab + tb + ps_tab_rel(j);
+          for (int o = 1; o < Q; o <<= 1) nsign += __shfl_xor_sync(0xFFFFFFFFu, nsign, o);
+          // sample SPT q + j: byte (SPT q + j) / 8 of counter (j mod 8); its
+          // coefficients c0..c3 are one aligned 16-byte load
+#pragma unroll
+          for (int j = 0; j < SPT; ++j) {
+            const float4 cf = *reinterpret_cast<const float4 *>(tab + tb + ps_tab_rel(j));
             const uint32_t bq = (uint32_t)((SPT / 8) * q + (j >> 3));
-            float g = acc[j];
-            g = fmaf(biased_byte(sc[0][j & 7], bq), cf[1], g);
-            g = fmaf(biased_byte(sc[1][j & 7], bq), cf[2], g);
-            g = fmaf(biased_byte(sc[2][j & 7], bq), cf[3], g);
+            float g = fmaf((float)nsign, cf.x, acc[j]);
+            g = fmaf(biased_byte(sc[0][j & 7], bq), cf.y, g);
+            g = fmaf(biased_byte(sc[1][j & 7], bq), cf.z, g);
+            g = fmaf(biased_byte(sc[2][j & 7], bq), cf.w, g);
             acc[j] = g;
           }
-        }
-#pragma unroll
-        for (int o = 1; o < Q; o <<= 1) nsign += __shfl_xor_sync(0xFFFFFFFFu, nsign, o);
-        if (act) {
-#pragma unroll
-          for (int j = 0; j < SPT; ++j) acc[j] = fmaf((float)nsign, tab[tb + ps_tab_rel(j)], acc[j]);
         }
       } else if (act) {
         const uint32_t own = bsrc[(size_t)vl * W + w];
