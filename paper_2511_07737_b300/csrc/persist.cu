@@ -129,13 +129,16 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
     // A task is a group of 32 clauses (lane = clause) and WT words of the
     // samples (WT = 2 when N >= 64): the clause is decoded once for both words
     // and a small instance needs half the task rounds (n = 100, N = 64: 14
-    // tasks for 16 warps instead of 28)
+    // tasks for 16 warps instead of 28).  The 1024-thread kernel (SPT 8, 64
+    // registers) keeps one word per task, which spills less under its register
+    // cap (264 against 292 bytes) at the same speed.
+    constexpr int WTM = SPT == 8 ? 1 : 2;
     const int ngroups = (I.n_clauses + 31) >> 5;
-    const int WT = W >= 2 ? 2 : 1, wtasks = W / WT;
+    const int WT = W >= WTM ? WTM : 1, wtasks = W / WT;
     for (int task = warp; task < ngroups * wtasks; task += NW) {
       const int g = task / wtasks, w0 = (task - g * wtasks) * WT;
       const bool active = 32 * g + lane < I.n_clauses;
-      uint32_t pl[2][3] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
+      uint32_t pl[WTM][3] = {};
       if (active) {
         const int c = I.c_off + 32 * g + lane;
         if (pd.crec) {
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
           const uint32_t *ra = bsrc + (size_t)(cr.x - I.v_off) * W + w0, *rb = bsrc + (size_t)(cr.y - I.v_off) * W + w0,
                          *rd = bsrc + (size_t)(cr.z - I.v_off) * W + w0;
 #pragma unroll
-          for (int ww = 0; ww < 2; ++ww) {
+          for (int ww = 0; ww < WTM; ++ww) {
             if (ww < WT) {
               const uint32_t a = ra[ww] ^ na;
               const uint32_t b = len > 1 ? (rb[ww] ^ nb) : 0u;
@@ -163,14 +166,14 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
             const int32_t lit = __ldg(pd.clit + j);
             const uint32_t *row = bsrc + (size_t)((lit >> 1) - I.v_off) * W + w0, neg = 0u - (uint32_t)(lit & 1);
 #pragma unroll
-            for (int ww = 0; ww < 2; ++ww)
+            for (int ww = 0; ww < WTM; ++ww)
               if (ww < WT) bitslice_add<3>(pl[ww], row[ww] ^ neg);
           }
         }
       }
       const uint32_t valid = __ballot_sync(0xFFFFFFFFu, active);
 #pragma unroll
-      for (int ww = 0; ww < 2; ++ww) {
+      for (int ww = 0; ww < WTM; ++ww) {
         if (ww < WT) {
           uint32_t tp[3];
           tp[0] = warp_transpose32(pl[ww][0], lane);
