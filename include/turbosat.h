@@ -154,7 +154,11 @@ int tsat_problem_csr(const tsat_problem *p, int32_t *h_cptr, int32_t *h_clit);
  *   z, m, v   float [V][N]     trainable A_real (one row per variable) and AdamW moments
  *   bits      uint32 [2][V][N/32]  binarised A, bit (i mod 32) of word i/32 = x_vi
  *   nu        float [V]        normaliser of the current z (Eq. 5)
- * plus per-instance histograms, gamma tables, S and status records. */
+ * plus per-instance histograms, gamma tables, S and status records.
+ * d_state stays caller-owned.  tsat_state_create also makes the state's own
+ * stream, two events and a pinned host buffer for tsat_status (the header plus
+ * 32 bytes per instance); tsat_state_free releases them, and so does a failed
+ * tsat_state_create. */
 int tsat_state_bytes(const tsat_problem *p, int32_t n_samples, int32_t layer,
                      int32_t relaxed_dtype, size_t *state_bytes);
 int tsat_state_create(tsat_problem *p, void *d_state, size_t state_bytes, int32_t n_samples,
