@@ -28,6 +28,11 @@ CASES = [
     ("k7-N128", lambda: [cnfgen.planted_ksat(300, 9000, 7, 8)], 128, dict(norm=0, binarize=0)),
     ("short-dup-N256", lambda: [cnfgen.tiny_random(200, 1500, 9, kmin=1, kmax=5)], 256, dict(norm=1, binarize=1)),
     ("batch-k3..7-N64", lambda: cnfgen.batch_ksat(9, 10, n_lo=40, n_hi=600), 64, dict(norm=1, binarize=1)),
+    # clause pointers and literals (clauses longer than 3) with two sample words
+    # per forward task: resident at N = 64 (16 samples per thread) and at N = 1024
+    ("k5-N64-resident", lambda: [cnfgen.planted_ksat(60, 400, 5, 12)], 64, dict(norm=1, binarize=1)),
+    ("short-dup-N64-resident", lambda: [cnfgen.tiny_random(50, 300, 14, kmin=1, kmax=5)], 64, dict(norm=0, binarize=0)),
+    ("k5-N1024", lambda: [cnfgen.planted_ksat(60, 1200, 5, 13)], 1024, dict(norm=2, binarize=1)),
 ]
 
 
@@ -59,7 +64,8 @@ def test_persistent_lockstep(name, gen, N, kw):
             assert status["inst"][j]["best_sample"] == oracle.best_sample(r["unsat"])
             assert abs(status["inst"][j]["loss"] - r["L"]) <= TOL_F32 * abs(r["L"])
         live = ~frozen
-        assert_adamw_z(s1["z"][live], z[live], s1["m"][live], m[live], s1["v"][live], v[live], t, hp)
+        if live.any():
+            assert_adamw_z(s1["z"][live], z[live], s1["m"][live], m[live], s1["v"][live], v[live], t, hp)
         X = oracle.binarize_f32(s1["z"], s1["nu"], hp.binarize, c=0.25 / hp.bin_temp, seed=hp.seed, t=t + 1)
         np.testing.assert_array_equal(s1["X"][live], X[live])
         np.testing.assert_array_equal(s1["X"][frozen], s0["X"][frozen])
