@@ -15,6 +15,9 @@ Parity status per function (the pins live in ``tests/test_oracle_*.py``):
   smoothmin                     : closed forms, tau -> inf limit, FD
   objective (STE and relaxed)   : FD on the smooth surrogate / direct FD
   normalize(+_backward)         : FD through the surrogate
+  nu_f32                        : exact means of dyadic FP32 rows (closed
+                                  form), the +-1e-12 guard cases, FP64 (not
+                                  FP32) accumulation, permutation / scaling
   lr / adamw                    : torch.optim.AdamW + LambdaLR in FP64,
                                   the schedule values stated in Sec. IV-A
   philox4x32_10                 : published answer vectors (SC'11 / Random123)
@@ -22,6 +25,10 @@ Parity status per function (the pins live in ``tests/test_oracle_*.py``):
   binarize_f32                  : deterministic mode vs sign rule, T -> 0
                                   reduction to it, Philox mode frequency
   best_sample / topk            : brute force on small arrays
+  mpnn.forward                  : closed form of a selector network on a
+                                  hand-sized graph (feature vector, block
+                                  order [h; a; h_neg], output head), a dense
+                                  incidence restatement, FD of the backward
 """
 from __future__ import annotations
 

@@ -1,14 +1,22 @@
-"""Build of the C-ABI CUDA library ``libturbosat.so`` for sm_103a (nvcc)."""
+"""Build of the C-ABI CUDA library ``libturbosat.so`` for sm_103a (nvcc).
+
+Each ``csrc/*.cu`` compiles to its own object in ``_build/`` (in parallel, and
+only when the source or a header changed); the objects are then linked into
+the shared library.
+"""
 from __future__ import annotations
 
 import glob
 import os
 import subprocess
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libturbosat.so")
+OBJ_DIR = os.path.join(ROOT, "_build", "turbosat")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC"]
 
 
 def sources():
@@ -18,6 +26,14 @@ def sources():
 def headers():
     return sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh")) + glob.glob(os.path.join(HERE, "csrc", "*.h"))
                   + glob.glob(os.path.join(ROOT, "include", "*.h")))
+
+
+def _nvcc() -> str:
+    return os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+
+
+def _obj(src: str) -> str:
+    return os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
 
 
 def stale() -> bool:
@@ -30,12 +46,24 @@ def stale() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not stale():
         return LIB
-    nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
-           "-Xcompiler", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"),
-           "-o", LIB + ".tmp", *sources(), "-lcudart"]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
+    os.makedirs(OBJ_DIR, exist_ok=True)
+    newest_header = max((os.path.getmtime(h) for h in headers()), default=0.0)
+
+    def compile_one(src: str) -> None:
+        obj = _obj(src)
+        if (not force and os.path.exists(obj) and os.path.getmtime(obj) >= os.path.getmtime(src)
+                and os.path.getmtime(obj) >= newest_header):
+            return
+        cmd = [_nvcc(), *ARCH, *FLAGS, "-I", os.path.join(ROOT, "include"), "-c", "-o", obj + ".tmp", src]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        subprocess.run(cmd, check=True)
+        os.replace(obj + ".tmp", obj)
+
+    srcs = sources()
+    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+        list(ex.map(compile_one, srcs))
+    cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *[_obj(s) for s in srcs], "-lcudart"]
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB

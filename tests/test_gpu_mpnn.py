@@ -70,3 +70,20 @@ def test_training_lowers_loss_and_learned_init_beats_random():
     if res.get("matched_k", 0) >= 10:
         m = res["matched_median_steps"]
         assert m["learned"] <= m["random"], res
+
+
+def test_mpnn_forward_closed_form_on_the_hand_sized_graph():
+    """The selector weights (exact in BF16) of the oracle's composition pin:
+    the kernels' logits equal the closed form computed from the clause lists."""
+    from tests.test_oracle_mpnn import _selector_logits_by_hand, _selector_params
+    clauses = [[(0, 0), (1, 1)], [(0, 0), (1, 0), (2, 0)], [(0, 0), (2, 1), (3, 0)], [(0, 1), (3, 0)]]
+    ptr = np.array([0, 2, 5, 8, 10], np.int64)
+    lits = np.array([1, -2, 1, 2, 3, 1, -3, 4, -1, 4], np.int32)
+    prob = ts.Problem([(4, ptr, lits)])
+    params = torch.tensor(_selector_params(), dtype=torch.float32, device="cuda")
+    ws = torch.empty((ts.tsat_mpnn_workspace_bytes(prob.h) + 7) // 8, dtype=torch.int64, device="cuda")
+    logits = torch.empty(4, device="cuda")
+    ts.tsat_mpnn_forward(prob.h, params, ws, logits)
+    torch.cuda.synchronize()
+    want = _selector_logits_by_hand(4, clauses)
+    assert rel_err(logits.cpu().numpy(), want) < 1e-5

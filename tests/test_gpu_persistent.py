@@ -128,3 +128,43 @@ def test_persistent_rejects_what_it_does_not_run():
     ts.tsat_init(rel.h, hr)
     with pytest.raises(ts.TsatError):
         ts.tsat_step_persistent(rel.h, hr, 1)
+
+
+KSTEP_CASES = [
+    # resident: z, m, v and nu stay in shared memory for the whole launch
+    ("resident-3sat-n100-N64", lambda: [cnfgen.planted_ksat(100, 426, 3, 0)], 64,
+     dict(norm=1, binarize=0, tau=2.0, lr0=0.5)),
+    ("resident-batch-k3..5-N64-philox", lambda: cnfgen.batch_ksat(6, 40, n_lo=40, n_hi=150, ks=[3, 4, 5]), 64,
+     dict(norm=0, binarize=1, bin_temp=0.5)),
+    # not resident: z, m, v and nu read and written in global memory every step
+    ("global-3sat-n1000-N64", lambda: [cnfgen.planted_ksat(1000, 4000, 3, 2)], 64,
+     dict(norm=1, binarize=0, tau=2.0, lr0=0.5)),
+    ("global-k5-n60-N1024-philox", lambda: [cnfgen.planted_ksat(60, 1200, 5, 13)], 1024,
+     dict(norm=2, binarize=1)),
+]
+
+
+@pytest.mark.parametrize("k", [7, 300])
+@pytest.mark.parametrize("name,gen,N,kw", KSTEP_CASES, ids=[c[0] for c in KSTEP_CASES])
+def test_persistent_k_steps_equal_k_single_step_launches(name, gen, N, kw, k):
+    """One launch of k steps leaves the state bit for bit as k launches of one
+    step: the carried shared-memory state and its write-back, the step scalars
+    formed 256 steps at a time (k = 300 crosses that batch), the bits ping-pong
+    inside a launch, and the freezing of solved instances (found step, sample)."""
+    insts = gen()
+    hp = ts.hparams(seed=21, **kw)
+    prob, st_a, _ = make(insts, N)
+    st_b = ts.State(prob, N)
+    for st in (st_a, st_b):
+        ts.tsat_init(st.h, hp)
+    ts.tsat_step_persistent(st_a.h, hp, k, stop_on_sat=False)
+    for _ in range(k):
+        ts.tsat_step_persistent(st_b.h, hp, 1, stop_on_sat=False)
+    a, b = snapshot(st_a), snapshot(st_b)
+    for key in ("z", "m", "v", "nu", "bits"):
+        np.testing.assert_array_equal(a[key].view(np.uint32), b[key].view(np.uint32), err_msg=key)
+    sa, sb = ts.tsat_status(st_a.h, len(insts)), ts.tsat_status(st_b.h, len(insts))
+    assert sa["step"] == sb["step"] == k
+    assert sa["inst"] == sb["inst"]
+    if name.startswith("resident-3sat") and k == 300:
+        assert sa["inst"][0]["found"]        # the freezing path ran inside the long launch

@@ -266,3 +266,52 @@ def test_first_step_after_a_mixing_restart_is_a_fresh_adam_step():
     lr = oracle.lr_at(R + 1, hp.lr0, hp.lr_factor, hp.decay_period, hp.restart_period, hp.lr_floor)
     ref = z1 * (1 - lr * hp.weight_decay) - lr * g / (np.abs(g) + hp.eps)
     np.testing.assert_allclose(z, ref, rtol=1e-12, atol=1e-15)
+
+
+def test_nu_f32_exact_means_guard_and_fp64_accumulation():
+    """The FP32-input normaliser of Eq. 5 (the statistic the GPU's nu is held
+    to).  Rows are built from dyadic values, so every mean below is exact in
+    FP64 and known in closed form; the guard replaces magnitudes below 1e-12
+    by +-1e-12 (0 -> +1e-12); the sums run in FP64, not FP32."""
+    N = 64
+    half = N // 2
+    dev = (np.arange(half) % 5 + 1) / 8.0                    # 1/8 .. 5/8, dyadic
+    rows, mean0, mean1 = [], [], []
+    for c in (0.75, -1.5, 3.0):                               # c + d, c - d pairs: mean c exactly
+        rows.append(np.concatenate([c + dev, c - dev]))
+        mean0.append(c)
+        mean1.append(abs(c))                                  # |c| > 5/8: no value changes sign
+    a, b, k = 1.25, 0.5, 40                                   # k values a, N - k values -b
+    rows.append(np.array([a] * k + [-b] * (N - k)))
+    mean0.append((k * a - (N - k) * b) / N)
+    mean1.append((k * a + (N - k) * b) / N)
+    big = 2.0 ** 24                                           # FP32 would lose the ones next to 2^24
+    rows.append(np.array([big] + [1.0] * (N - 2) + [-big]))
+    mean0.append((N - 2) / N)
+    mean1.append((2 * big + N - 2) / N)
+    z = np.array(rows, np.float32)
+    assert np.array_equal(z.astype(np.float64), np.array(rows))   # every value is exact in FP32
+    np.testing.assert_array_equal(oracle.nu_f32(z, 0), mean0)
+    np.testing.assert_array_equal(oracle.nu_f32(z, 1), mean1)
+    np.testing.assert_array_equal(oracle.nu_f32(z, 2), 1.0)
+    # permutation invariance and exact scaling by a power of two
+    perm = np.random.default_rng(0).permutation(N)
+    np.testing.assert_array_equal(oracle.nu_f32(z[:, perm], 0), mean0)
+    np.testing.assert_array_equal(oracle.nu_f32(z * np.float32(0.25), 1), np.array(mean1) * 0.25)
+    # the guard: exact zero, mean -1e-13, mean +5e-13, and a mean just outside it
+    tiny_neg = np.float32(-1e-13 * N)
+    tiny_pos = np.float32(5e-13 * N)
+    outside = np.float32(-2e-12 * N)
+    g = np.zeros((5, N), np.float32)
+    g[1, 0] = tiny_neg
+    g[2, 0] = tiny_pos
+    g[3, 0] = outside
+    g[4, :half], g[4, half:] = 1.5, -1.5                      # signed mean 0, mean |z| 1.5
+    nu0 = oracle.nu_f32(g, 0)
+    assert nu0[0] == 1e-12 and nu0[1] == -1e-12 and nu0[2] == 1e-12 and nu0[4] == 1e-12
+    assert nu0[3] == float(outside) / N and nu0[3] < -1e-12
+    nu1 = oracle.nu_f32(g, 1)
+    assert nu1[0] == 1e-12 and nu1[1] == 1e-12 and nu1[2] == 1e-12   # mean |z| is never negative
+    assert nu1[3] == -float(outside) / N and nu1[4] == 1.5
+    # the FP64 normaliser of the same values agrees (same definition, FP64 inputs)
+    np.testing.assert_array_equal(oracle.normalize(z.astype(np.float64), 0)[0], mean0)
