@@ -230,14 +230,18 @@ int tsat_histogram(tsat_state *s, int32_t *d_hist, cudaStream_t stream);
  * Same results as tsat_evaluate, but for a caller-supplied bit matrix d_bits
  * (uint32 [n_vars][n_samples/32], bit i%32 of word i/32 = sample i's value)
  * instead of a state: d_unsat int32 [n_inst][N] unsatisfied-clause counts,
- * d_satmask uint32 [n_inst][N/32], d_loss (nullable) float [n_inst] with
- * L = -sum_i S_i (Eq. 3, Eq. 4 with temperature tau).  The temporaries live
- * in one fixed 4 MiB array inside the library's device image (each GPU that
- * loads the library holds it until the process exits); a problem needs
- * n_inst * N * (lmax + 3) + 64 ints of it, and larger requests fail with
- * TSAT_ERANGE.  The first call on a device looks up that array's device
- * address (make that first call before any stream capture).  Every call
- * shares the array, so calls that overlap on the GPU (different streams, or
+ * d_satmask uint32 [n_inst][N/32], d_loss (nullable) float [n_inst], the
+ * same loss value tsat_evaluate writes, with SmoothMin temperature tau.  The
+ * temporaries live in one fixed 4 MiB array inside the library's device
+ * image (each GPU that loads the library holds it until the process exits);
+ * a problem needs n_inst * N * (lmax + 3) + 64 ints of it, and larger
+ * requests fail with TSAT_ERANGE.  The problem's device must be the current
+ * device (else TSAT_EINVAL).  The array's device address is looked up once
+ * per device and CUDA context, by the first call made with that context
+ * current (make that first call before any stream capture; a context made
+ * again after cudaDeviceReset gets a fresh lookup).  Every call shares the
+ * array and it keeps the last call's contents (the call clears what must
+ * start at zero), so calls that overlap on the GPU (different streams, or
  * different problems at once) race; serialise them.  Async on `stream`. */
 int tsat_evaluate_bits_noalloc(const tsat_problem *p, const uint32_t *d_bits, int32_t n_samples, float tau,
                                int32_t *d_unsat, uint32_t *d_satmask, float *d_loss, cudaStream_t stream);
@@ -281,12 +285,29 @@ int tsat_backward(tsat_state *s, const tsat_hparams *hp, const float *d_z, float
                   float *d_grad, cudaStream_t stream);
 
 /* ---- schedules ----
- * Launch shapes of the forward and update kernels.  tsat_autotune times the
- * candidate shapes on this state with hp (state contents are restored) and
- * keeps the fastest; tsat_get_tuning / tsat_set_tuning read or force them.
+ * Launch shapes of the forward and update kernels (the survey's tile /
+ * warps-per-clause schedules reduce to these two knobs).
+ * tsat_autotune times candidate shapes on this state and keeps the fastest:
+ * the forward's work-item size (clauses per item) on the forward, then the
+ * update's blocks per SM and rows per work item on the step's own fused
+ * update (hp's binarisation and Eq. 5 mode), each trial run after the step's
+ * forward and gamma kernels from the state as the caller left it.  That state
+ * (header, status records, z, m, v, bits, nu and, for the relaxed layer, the
+ * literal values) is saved into the caller's device buffer d_snapshot of at
+ * least tsat_autotune_bytes bytes before the first trial, restored before
+ * every trial and restored again at the end, so the call leaves the state
+ * unchanged.  A failed trial leaves the previous launch shape.  Synchronous
+ * (returns after the last trial).  tsat_get_tuning / tsat_set_tuning read or
+ * force the shapes.
  * h_tuning = {fwd_chunk_clauses, fwd_block_threads, upd_blocks_per_sm, upd_rows_per_item};
  * upd_blocks_per_sm in [0, 128], 0 = the default (resident blocks x 8 waves). */
-int tsat_autotune(tsat_state *s, const tsat_hparams *hp, cudaStream_t stream, int32_t h_tuning[4]);
+int tsat_autotune_bytes(const tsat_state *s, size_t *bytes);
+/* The candidates tsat_autotune tries on this state: forward work-item sizes
+ * (4), update blocks per SM (5: d/8, d/4, d/2, d, 5d/4 around the default d
+ * of resident blocks x waves), update rows per work item (3).  Host only. */
+int tsat_tuning_space(const tsat_state *s, int32_t h_fwd_items[4], int32_t h_upd_bps[5], int32_t h_upd_rpi[3]);
+int tsat_autotune(tsat_state *s, const tsat_hparams *hp, void *d_snapshot, size_t snapshot_bytes,
+                  cudaStream_t stream, int32_t h_tuning[4]);
 int tsat_get_tuning(const tsat_state *s, int32_t h_tuning[4]);
 int tsat_set_tuning(tsat_state *s, const int32_t h_tuning[4]);
 

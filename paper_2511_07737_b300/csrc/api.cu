@@ -124,8 +124,10 @@ static int upd_grid(const tsat_state *s) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)s->sm_count * bps, need));
 }
 
-// One optimisation step: forward histogram, gamma, fused update.
-static int issue_step(tsat_state *s, const Hyper &hy, const LrSched &ls, cudaStream_t st) {
+// The part of a step before the fused update: forward histogram (relaxed:
+// exact check, relaxed forward) and the gamma kernel, which also writes the
+// step scalars and advances the step counter.
+static int issue_pre_update(tsat_state *s, const Hyper &hy, const LrSched &ls, cudaStream_t st) {
   const ProbDev &pd = s->prob->dev;
   cudaError_t e;
   if (s->layer == TSAT_LAYER_RELAXED) {
@@ -140,11 +142,26 @@ static int issue_step(tsat_state *s, const Hyper &hy, const LrSched &ls, cudaStr
     if ((e = launch_gamma(pd, s->dev, hy, ls, s->dev.hist, 1, 1, nullptr, nullptr, st)) != cudaSuccess)
       return cuda_fail(e, "gamma");
   }
+  return TSAT_OK;
+}
+
+// The fused update of a step (with assignment mixing first when enabled):
+// STE backward, Eq. 5, AdamW and the next step's bits, in the launch shape
+// the state is tuned to.
+static int issue_update(tsat_state *s, const Hyper &hy, const LrSched &ls, cudaStream_t st) {
+  const ProbDev &pd = s->prob->dev;
+  cudaError_t e;
   if (ls.mix && (e = launch_mix(pd, s->dev, hy, upd_grid(s), st)) != cudaSuccess) return cuda_fail(e, "mix");
   if ((e = launch_update(pd, s->dev, hy, 0, nullptr, nullptr, 0.f, upd_grid(s), s->upd_rows_per_item, st)) !=
       cudaSuccess)
     return cuda_fail(e, "update");
   return TSAT_OK;
+}
+
+// One optimisation step: forward histogram, gamma, fused update.
+static int issue_step(tsat_state *s, const Hyper &hy, const LrSched &ls, cudaStream_t st) {
+  int rc = issue_pre_update(s, hy, ls, st);
+  return rc ? rc : issue_update(s, hy, ls, st);
 }
 
 }  // namespace tsat
@@ -245,6 +262,12 @@ int tsat_state_create(tsat_problem *p, void *d_state, size_t state_bytes, int32_
   s->part_val = (uint8_t *)(b + P.part_val);
   s->fwd_scratch = (float *)(b + P.fwdS);
   s->hist1 = (int32_t *)(b + P.hist1);
+  // what a step changes: the header, status records, step scalars, z, m, v,
+  // both bit parities and nu (adjacent, from the start of the buffer), plus the
+  // relaxed layer's literal values
+  s->core_bytes = P.hist;
+  s->lit_off = layer == TSAT_LAYER_RELAXED ? P.lit : 0;
+  s->lit_bytes = layer == TSAT_LAYER_RELAXED ? (size_t)(dt == TSAT_DTYPE_BF16 ? 2 : 4) * p->V * N : 0;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -673,73 +696,140 @@ int tsat_set_tuning(tsat_state *s, const int32_t h_tuning[4]) {
   return TSAT_OK;
 }
 
-int tsat_autotune(tsat_state *s, const tsat_hparams *hp, cudaStream_t stream, int32_t h_tuning[4]) {
-  if (!s || !h_tuning) return TSAT_EINVAL;
+namespace {
+// Candidate launch shapes of tsat_autotune: forward work-item sizes, update
+// blocks per SM around the default d (resident blocks x waves): d/8, d/4, d/2,
+// d and 5d/4, and update rows per work item.
+constexpr int kTuneItems[4] = {512, 1024, 2048, 4096};
+constexpr int kTuneRpi[3] = {1, 8, 64};
+void tune_bps(const tsat_state *s, int out[5]) {
+  const int d = update_blocks_per_sm(s->prob->dev, s->dev);
+  out[0] = std::max(1, d / 8);
+  out[1] = std::max(1, d / 4);
+  out[2] = std::max(1, d / 2);
+  out[3] = d;
+  out[4] = d * 5 / 4;
+}
+
+// Events of one tuning run, destroyed on every return path.
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+}  // namespace
+
+int tsat_tuning_space(const tsat_state *s, int32_t h_fwd_items[4], int32_t h_upd_bps[5], int32_t h_upd_rpi[3]) {
+  if (!s || !h_fwd_items || !h_upd_bps || !h_upd_rpi) { set_error("NULL argument"); return TSAT_EINVAL; }
+  int b[5];
+  tune_bps(s, b);
+  for (int j = 0; j < 4; ++j) h_fwd_items[j] = kTuneItems[j];
+  for (int j = 0; j < 5; ++j) h_upd_bps[j] = b[j];
+  for (int j = 0; j < 3; ++j) h_upd_rpi[j] = kTuneRpi[j];
+  return TSAT_OK;
+}
+
+int tsat_autotune_bytes(const tsat_state *s, size_t *bytes) {
+  if (!s || !bytes) { set_error("NULL argument"); return TSAT_EINVAL; }
+  *bytes = s->core_bytes + s->lit_bytes;
+  return TSAT_OK;
+}
+
+
+int tsat_autotune(tsat_state *s, const tsat_hparams *hp, void *d_snapshot, size_t snapshot_bytes,
+                  cudaStream_t stream, int32_t h_tuning[4]) {
+  if (!s || !h_tuning || !d_snapshot) { set_error("NULL argument"); return TSAT_EINVAL; }
   int rc = check_hp(hp);
   if (rc) return rc;
   if (!s->initialised) { set_error("state not initialised"); return TSAT_ESTATE; }
-  TSAT_CUDA(cudaStreamSynchronize(stream));
-  // Each candidate runs one step from a fresh init (the init is repeated at the
-  // end, so the state is left as tsat_init(hp) leaves it).
-  const int items[] = {512, 1024, 2048, 4096};
-  // blocks per SM around the default (resident blocks x 8 waves): 1, 2, 4, 8 and 10 waves
-  const int bdef = update_blocks_per_sm(s->prob->dev, s->dev);
-  const int bps[] = {std::max(1, bdef / 8), std::max(1, bdef / 4), std::max(1, bdef / 2), bdef, bdef * 5 / 4};
-  const int rpi[] = {1, 8, 64};
-  cudaEvent_t a, b;
-  TSAT_CUDA(cudaEventCreate(&a));
-  TSAT_CUDA(cudaEventCreate(&b));
-  const Hyper hy = make_hyper(*hp, 0);
-  const LrSched ls = make_sched(*hp);
-  auto time_fwd = [&](float *ms) -> int {
-    const ProbDev &pd = s->prob->dev;
-    cudaError_t e;
-    for (int rep = 0; rep < 2; ++rep) {
-      TSAT_CUDA(cudaMemsetAsync(s->eval_hist, 0, sizeof(int32_t) * pd.n_inst * s->dev.lm1 * s->N, s->stream));
-      TSAT_CUDA(cudaEventRecord(a, s->stream));
-      if ((e = launch_fwd_hist(pd, s->dev, s->eval_hist, 0, s->stream)) != cudaSuccess) return cuda_fail(e, "fwd");
-      TSAT_CUDA(cudaEventRecord(b, s->stream));
-    }
-    TSAT_CUDA(cudaEventSynchronize(b));
-    TSAT_CUDA(cudaEventElapsedTime(ms, a, b));
+  if (hp->layer != s->layer) { set_error("hp->layer differs from the state's layer"); return TSAT_ESTATE; }
+  const size_t need = s->core_bytes + s->lit_bytes;
+  if (snapshot_bytes < need) { set_error("snapshot buffer %zu < %zu bytes", snapshot_bytes, need); return TSAT_EWS; }
+  if ((rc = enter(s, stream))) return rc;
+  cudaStream_t st = s->stream;
+  char *base = static_cast<char *>(s->base);
+  char *snap = static_cast<char *>(d_snapshot);
+  // the state as the caller left it; every trial starts from it, and it is
+  // put back at the end
+  auto save = [&]() -> int {
+    TSAT_CUDA(cudaMemcpyAsync(snap, base, s->core_bytes, cudaMemcpyDeviceToDevice, st));
+    if (s->lit_bytes)
+      TSAT_CUDA(cudaMemcpyAsync(snap + s->core_bytes, base + s->lit_off, s->lit_bytes, cudaMemcpyDeviceToDevice, st));
     return TSAT_OK;
   };
+  auto restore = [&]() -> int {
+    TSAT_CUDA(cudaMemcpyAsync(base, snap, s->core_bytes, cudaMemcpyDeviceToDevice, st));
+    if (s->lit_bytes)
+      TSAT_CUDA(cudaMemcpyAsync(base + s->lit_off, snap + s->core_bytes, s->lit_bytes, cudaMemcpyDeviceToDevice, st));
+    return TSAT_OK;
+  };
+  if ((rc = save())) return rc;
+  EventPair ev;
+  TSAT_CUDA(cudaEventCreate(&ev.a));
+  TSAT_CUDA(cudaEventCreate(&ev.b));
+  const Hyper hy = make_hyper(*hp, 0);
+  const LrSched ls = make_sched(*hp);
+  const ProbDev &pd = s->prob->dev;
+  // forward work-item size: the forward reads the bits and writes a scratch histogram
   int best_items = s->prob->item_clauses;
   float best = 1e30f;
-  for (int ic : items) {
-    if ((rc = s->prob->set_items(ic, s->stream))) return rc;
-    float ms = 0;
-    if ((rc = time_fwd(&ms))) return rc;
+  for (int ic : kTuneItems) {
+    if ((rc = s->prob->set_items(ic, st))) return rc;
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      TSAT_CUDA(cudaMemsetAsync(s->eval_hist, 0, sizeof(int32_t) * pd.n_inst * s->dev.lm1 * s->N, st));
+      TSAT_CUDA(cudaEventRecord(ev.a, st));
+      cudaError_t e = s->layer == TSAT_LAYER_RELAXED ? launch_relaxed_fwd(pd, s->dev, hy, 1, st)
+                                                    : launch_fwd_hist(pd, s->dev, s->eval_hist, 0, st);
+      if (e != cudaSuccess) return cuda_fail(e, "forward");
+      TSAT_CUDA(cudaEventRecord(ev.b, st));
+      TSAT_CUDA(cudaEventSynchronize(ev.b));
+      float x = 0;
+      TSAT_CUDA(cudaEventElapsedTime(&x, ev.a, ev.b));
+      ms = std::min(ms, x);
+    }
     if (ms < best) { best = ms; best_items = ic; }
   }
-  if ((rc = s->prob->set_items(best_items, s->stream))) return rc;
-  int best_b = s->upd_blocks_per_sm, best_r = s->upd_rows_per_item;
+  if ((rc = s->prob->set_items(best_items, st))) return rc;
+  // update launch shape: the step's own update (mode 0, hp's binarisation and
+  // Eq. 5 mode), timed after the step's forward and gamma from the saved state;
+  // blocks per SM around the default (resident blocks x 8 waves): 1, 2, 4, 8 and 10 waves
+  int bps[5];
+  tune_bps(s, bps);
+  const int keep_b = s->upd_blocks_per_sm, keep_r = s->upd_rows_per_item;
+  int best_b = keep_b, best_r = keep_r;
   best = 1e30f;
-  for (int bb : bps)
-    for (int rr : rpi) {
-      s->upd_blocks_per_sm = bb;
-      s->upd_rows_per_item = rr;
-      float ms = 0;
-      for (int rep = 0; rep < 2; ++rep) {
-        if ((rc = tsat_init(s, hp, nullptr, 1.0f, s->stream))) return rc;
-        int r2 = issue_step(s, hy, ls, s->stream);  // warm the forward / gamma
-        if (r2) return r2;
-        TSAT_CUDA(cudaEventRecord(a, s->stream));
-        cudaError_t e = launch_update(s->prob->dev, s->dev, hy, 1, s->dev.z, s->dev.m, 1.0f, upd_grid(s),
-                                      s->upd_rows_per_item, s->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "update");
-        TSAT_CUDA(cudaEventRecord(b, s->stream));
+  auto sweep = [&]() -> int {
+    for (int bb : bps)
+      for (int rr : kTuneRpi) {
+        s->upd_blocks_per_sm = bb;
+        s->upd_rows_per_item = rr;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+          int r;
+          if ((r = restore())) return r;
+          if ((r = issue_pre_update(s, hy, ls, st))) return r;
+          TSAT_CUDA(cudaEventRecord(ev.a, st));
+          if ((r = issue_update(s, hy, ls, st))) return r;
+          TSAT_CUDA(cudaEventRecord(ev.b, st));
+          TSAT_CUDA(cudaEventSynchronize(ev.b));
+          float x = 0;
+          TSAT_CUDA(cudaEventElapsedTime(&x, ev.a, ev.b));
+          ms = std::min(ms, x);
+        }
+        if (ms < best) { best = ms; best_b = bb; best_r = rr; }
       }
-      TSAT_CUDA(cudaEventSynchronize(b));
-      TSAT_CUDA(cudaEventElapsedTime(&ms, a, b));
-      if (ms < best) { best = ms; best_b = bb; best_r = rr; }
-    }
-  s->upd_blocks_per_sm = best_b;
-  s->upd_rows_per_item = best_r;
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  if ((rc = tsat_init(s, hp, nullptr, 1.0f, s->stream))) return rc;
-  TSAT_CUDA(cudaStreamSynchronize(s->stream));
+    return TSAT_OK;
+  };
+  rc = sweep();
+  // a failed trial leaves the launch shape as it was before the call
+  s->upd_blocks_per_sm = rc ? keep_b : best_b;
+  s->upd_rows_per_item = rc ? keep_r : best_r;
+  if (rc) return rc;
+  if ((rc = restore())) return rc;
+  if ((rc = leave(s, stream))) return rc;
   return tsat_get_tuning(s, h_tuning);
 }
 

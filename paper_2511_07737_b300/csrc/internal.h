@@ -85,6 +85,9 @@ struct tsat_state {
   uint32_t *outbits = nullptr;      // [ceil(max V/32)]
   int32_t *small = nullptr;         // [64] misc ints
   float *fwd_scratch = nullptr;     // tsat_forward outputs staging
+  // regions a step changes (tsat_autotune saves and restores them)
+  size_t core_bytes = 0;            // [0, core_bytes): header .. nu
+  size_t lit_off = 0, lit_bytes = 0;  // relaxed literal values
   // schedules
   int32_t upd_blocks_per_sm = 0;   // 0: resident blocks per SM from the occupancy API
   mutable int32_t occ_bps = -1;     // that occupancy figure, queried once per state

@@ -19,11 +19,55 @@ constexpr int64_t kNoAllocScratchInts = 1 << 20;   // 4 MiB
 static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocScratchInts];
 
 constexpr int kMaxDevices = 64;
-static void *g_scratch_ptr[kMaxDevices] = {nullptr};
+// Per device: the unique id of the context the address was looked up in, and
+// the address.
+struct ScratchSlot {
+  unsigned long long ctx_id = 0;
+  void *ptr = nullptr;
+};
+static ScratchSlot g_scratch[kMaxDevices];
 static std::mutex g_scratch_mu;
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side symbol is only a stand-in, never a device address).
+// The driver's cuCtxGetCurrent and cuCtxGetId, reached through the runtime (no
+// link-time dependency on the driver library).  CUcontext is an opaque
+// pointer; a context id is never reused within a process, unlike an address.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+struct CtxFns {
+  CtxGetCurrentFn current = nullptr;
+  CtxGetIdFn id = nullptr;
+};
+static const CtxFns &ctx_fns() {
+  static const CtxFns fns = [] {
+    CtxFns f;
+    void *a = nullptr, *b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+        qa == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+        qb == cudaDriverEntryPointSuccess) {
+      f.current = reinterpret_cast<CtxGetCurrentFn>(a);
+      f.id = reinterpret_cast<CtxGetIdFn>(b);
+    }
+    return f;
+  }();
+  return fns;
+}
+
+// Id of the context current on this thread, 0 if none.
+static unsigned long long current_ctx_id() {
+  const CtxFns &f = ctx_fns();
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (!f.current || f.current(&ctx) != 0 || !ctx || f.id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device.  The host-side
+// symbol is only a stand-in, never a device address, so the address is looked
+// up with cudaGetSymbolAddress with the device current, once per device and
+// context: a context torn down and made again (cudaDeviceReset) gets a new
+// lookup instead of a pointer into the dead context.
 static int scratch_address(int32_t **out) {
   int dev = 0;
   TSAT_CUDA(cudaGetDevice(&dev));
@@ -31,13 +75,25 @@ static int scratch_address(int32_t **out) {
     set_error("device %d beyond the no-alloc table", dev);
     return TSAT_EINVAL;
   }
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    TSAT_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_scratch_ptr[dev] = p;
+  if (!ctx_fns().current) {
+    set_error("cannot reach cuCtxGetCurrent / cuCtxGetId");
+    return TSAT_ECUDA;
   }
-  *out = static_cast<int32_t *>(g_scratch_ptr[dev]);
+  unsigned long long id = current_ctx_id();   // 0: no context current on this thread yet
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  ScratchSlot &slot = g_scratch[dev];
+  if (!slot.ptr || id == 0 || slot.ctx_id != id) {
+    void *p = nullptr;
+    // the lookup makes the device's primary context current if none was
+    TSAT_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    if ((id = current_ctx_id()) == 0) {
+      set_error("no CUDA context current after the scratch lookup");
+      return TSAT_ECUDA;
+    }
+    slot.ptr = p;
+    slot.ctx_id = id;
+  }
+  *out = static_cast<int32_t *>(slot.ptr);
   return TSAT_OK;
 }
 
@@ -66,6 +122,14 @@ extern "C" int tsat_evaluate_bits_noalloc(const tsat_problem *p, const uint32_t 
     set_error("no-alloc evaluation needs %lld scratch ints (n_inst x N x (lmax + 3)); the fixed maximum is %lld",
               (long long)need, (long long)kNoAllocScratchInts);
     return TSAT_ERANGE;
+  }
+  // the problem's device arrays live on the device it was loaded on; the
+  // scratch array and the launches below belong to the current device
+  int dev = -1;
+  TSAT_CUDA(cudaGetDevice(&dev));
+  if (dev != p->device) {
+    set_error("the problem was loaded on device %d but device %d is current", p->device, dev);
+    return TSAT_EINVAL;
   }
   int32_t *scr = nullptr;
   int rc = scratch_address(&scr);

@@ -90,7 +90,9 @@ def lib():
             "tsat_state_views": (ctypes.c_int, [P, P, P, P, P, P, P, P]),
             "tsat_forward": (ctypes.c_int, [P, P, P, i64, P, P, P]),
             "tsat_backward": (ctypes.c_int, [P, P, P, f32, P, P]),
-            "tsat_autotune": (ctypes.c_int, [P, P, P, P]),
+            "tsat_autotune_bytes": (ctypes.c_int, [P, P]),
+            "tsat_tuning_space": (ctypes.c_int, [P, P, P, P]),
+            "tsat_autotune": (ctypes.c_int, [P, P, P, sz, P, P]),
             "tsat_get_tuning": (ctypes.c_int, [P, P]),
             "tsat_set_tuning": (ctypes.c_int, [P, P]),
             "tsat_launches_per_step": (i32, [P]),
@@ -294,9 +296,28 @@ def tsat_backward(s, hp, z: torch.Tensor, dL: float, grad_out: torch.Tensor, str
         "tsat_backward")
 
 
-def tsat_autotune(s, hp, stream=None) -> list:
+def tsat_tuning_space(s) -> dict:
+    """The candidate launch shapes tsat_autotune tries on this state."""
+    a, b, c = (ctypes.c_int32 * 4)(), (ctypes.c_int32 * 5)(), (ctypes.c_int32 * 3)()
+    _ck(lib().tsat_tuning_space(s, a, b, c), "tsat_tuning_space")
+    return dict(fwd_items=list(a), upd_blocks_per_sm=list(b), upd_rows_per_item=list(c))
+
+
+def tsat_autotune_bytes(s) -> int:
+    out = ctypes.c_size_t(0)
+    _ck(lib().tsat_autotune_bytes(s, ctypes.byref(out)), "tsat_autotune_bytes")
+    return int(out.value)
+
+
+def tsat_autotune(s, hp, snapshot: torch.Tensor | None = None, stream=None) -> list:
+    """Tune the launch shapes on the state as it stands (left unchanged).
+    ``snapshot``: device buffer of at least tsat_autotune_bytes(s) bytes; one
+    is allocated for the call when omitted."""
+    if snapshot is None:
+        snapshot = _device_buffer(tsat_autotune_bytes(s), torch.device("cuda", torch.cuda.current_device()))
     a = (ctypes.c_int32 * 4)()
-    _ck(lib().tsat_autotune(s, ctypes.byref(hp), _stream(stream), a), "tsat_autotune")
+    _ck(lib().tsat_autotune(s, ctypes.byref(hp), _ptr(snapshot), snapshot.numel() * snapshot.element_size(),
+                            _stream(stream), a), "tsat_autotune")
     return list(a)
 
 

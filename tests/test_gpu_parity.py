@@ -322,3 +322,59 @@ def test_autotune_keeps_results():
     a, b = snapshot(st1), snapshot(st2)
     for k in ("z", "bits"):
         np.testing.assert_array_equal(a[k], b[k])
+
+
+def _time_step(st, hp, saved, reps=3):
+    """Device time of one tsat_step from the saved state buffer (min of reps)."""
+    best = 1e30
+    for _ in range(reps):
+        st.buf.copy_(saved)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ts.tsat_step(st.h, hp, 1, stop_on_sat=False)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def test_autotune_times_the_step_update_and_leaves_the_state():
+    """On a small batch of uneven k-SAT instances (k 3..7) past step 0, the
+    tuned update shape is within 3 % of the fastest shape of an exhaustive
+    tsat_set_tuning sweep of the same candidates, each timed on tsat_step
+    itself; the call leaves the state bit for bit as it was, and a step with
+    the tuned shape gives the same state as one with the default shape."""
+    insts = cnfgen.batch_ksat(40, 77, n_lo=2000, n_hi=20000)
+    hp = ts.hparams(seed=5, norm=1, binarize=1, tau=2.0, lr0=0.5)
+    prob, st, _ = make(insts, 64)
+    ts.tsat_init(st.h, hp)
+    ts.tsat_step(st.h, hp, 3, stop_on_sat=False)
+    torch.cuda.synchronize()
+    before = st.buf.clone()
+    tun = ts.tsat_autotune(st.h, hp)
+    torch.cuda.synchronize()
+    assert torch.equal(st.buf.view(torch.uint8)[:ts.tsat_autotune_bytes(st.h)],
+                       before.view(torch.uint8)[:ts.tsat_autotune_bytes(st.h)])
+    assert ts.tsat_status(st.h, len(insts))["step"] == 3
+    space = ts.tsat_tuning_space(st.h)
+    assert tun[2] in space["upd_blocks_per_sm"] and tun[3] in space["upd_rows_per_item"]
+    times = {}
+    for b in space["upd_blocks_per_sm"]:
+        for r in space["upd_rows_per_item"]:
+            ts.tsat_set_tuning(st.h, [tun[0], tun[1], b, r])
+            ts.tsat_step_prepare(st.h, hp, 1, stop_on_sat=False)
+            _time_step(st, hp, before, reps=1)            # warm-up
+            times[(b, r)] = _time_step(st, hp, before)
+    best = min(times.values())
+    assert times[(tun[2], tun[3])] <= 1.03 * best, (tun, times)
+    # the launch shape changes no result
+    ts.tsat_set_tuning(st.h, tun)
+    st.buf.copy_(before)
+    ts.tsat_step(st.h, hp, 2, stop_on_sat=False)
+    a = snapshot(st)
+    ts.tsat_set_tuning(st.h, [tun[0], tun[1], 0, 1])
+    st.buf.copy_(before)
+    ts.tsat_step(st.h, hp, 2, stop_on_sat=False)
+    b = snapshot(st)
+    for k in ("z", "m", "v", "nu", "bits"):
+        np.testing.assert_array_equal(a[k], b[k])

@@ -1,7 +1,8 @@
 """The allocation-free evaluation entry point (for callers that cannot call
 cudaMalloc, e.g. code confined to a memory pool it does not own) gives the
 same unsatisfied counts, SAT masks and losses as tsat_evaluate, on two calls
-in a row through the C ABI.  Collected last on purpose."""
+in a row through the C ABI, and its second call leaves the device's free
+memory unchanged.  Collected last on purpose."""
 import numpy as np
 import pytest
 import torch
@@ -37,8 +38,14 @@ def test_noalloc_matches_evaluate_twice(N, batch):
         u = torch.full((I * N,), -7, dtype=torch.int32, device="cuda")
         m = torch.full((I * N // 32,), -7, dtype=torch.int32, device="cuda")
         loss = torch.full((I,), 123.0, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         ts.tsat_evaluate_bits_noalloc(prob.h, bits, N, hp.tau, u, m, loss)
         torch.cuda.synchronize()
+        if call == 1:
+            # after the first call (which may load the library's device code and
+            # look up the array), a call takes no device memory at all
+            assert torch.cuda.mem_get_info()[0] == free_before
         np.testing.assert_array_equal(u.cpu().numpy(), u_ref.cpu().numpy())
         np.testing.assert_array_equal(m.cpu().numpy(), m_ref.cpu().numpy())
         ref = l_ref.cpu().numpy()
