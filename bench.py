@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tts", action="store_true", help="skip the time-to-SAT sub-object of the default line")
     ap.add_argument("--experiment", default="throughput",
                     choices=["throughput", "time_to_sat", "batch", "relaxed", "proposer", "mixing", "literal_rows"],
                     help="throughput (default, the driver's line) or one of the other workloads")
@@ -173,6 +174,26 @@ def traffic_for(kernel, workload):
     return e.get("bytes_per_launch")
 
 
+def host_description() -> dict:
+    """CPU model, logical cores and RAM of this host (for the CPU baseline)."""
+    model, mem_gb = None, None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemTotal"):
+                mem_gb = round(int(line.split()[1]) / 1024 ** 2, 1)
+                break
+    except OSError:
+        pass
+    return {"cpu_model": model, "logical_cpus": os.cpu_count(), "ram_gb": mem_gb}
+
+
 # ---------------------------------------------------------------- oracle (CPU baseline / reference arm)
 def oracle_run(inst, cols, steps, budget_s=None, seed=1):
     import oracle
@@ -214,9 +235,93 @@ def reference_arm(args, w, rank, world):
             "ms_per_step": 1e3 * r["seconds"] / r["steps"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "oracle_columns": cols},
-            "cpu_baseline": {"value": val, "unit": unit, "cores": r["cores"], "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": unit, "cores": r["cores"], "kind": "oracle", "sample": sample,
+                             "host": host_description()},
             "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- time to SAT (metric 2) for the default line
+TTS_READINGS = {
+    "paper: signed-mean Eq. 5, tau 1, lr0 0.1": dict(norm=0, tau=1.0, lr0=0.1),
+    "paper schedule, sign-keeping Eq. 5 (mean |z|), tau 2, lr0 0.1": dict(norm=1, tau=2.0, lr0=0.1),
+    "tuned: mean |z| Eq. 5, tau 2, lr0 0.5": dict(norm=1, tau=2.0, lr0=0.5),
+}
+
+
+def time_to_sat_summary(ts, torch, n_inst=32, cap=500):
+    """Time to the first satisfying assignment on planted 3-SAT n=100 m=426
+    (ratio 4.26), N=64, deterministic Eq. 2, cap 500 steps, seeds 0..31: wall
+    time from tsat_init to the host seeing the found flag, each instance alone
+    in one persistent launch that stops at the first model ("plain"), and all
+    instances as one batch in one persistent launch ("batched")."""
+    from paper_2511_07737_b300 import cnfgen
+    insts = [cnfgen.planted_ksat(100, 426, 3, j) for j in range(n_inst)]
+    out = {"workload": f"{n_inst} x planted 3-SAT n=100 m=426 (ratio 4.26), N=64, deterministic Eq. 2, "
+                       f"cap {cap} steps, persistent solver",
+           "unit": "ms", "readings": {}}
+    for name, kw in TTS_READINGS.items():
+        walls, steps = [], []
+        for j, inst in enumerate(insts):
+            prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
+            st = ts.State(prob, 64)
+            hp = ts.hparams(seed=j + 1, **kw)
+            ts.tsat_init(st.h, hp)
+            ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)     # first launch: kernel attributes
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ts.tsat_init(st.h, hp)
+            ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
+            x = ts.tsat_status(st.h, 1)["inst"][0]
+            el = time.perf_counter() - t0
+            if x["found"]:
+                walls.append(el)
+                steps.append(x["found_step"])
+        prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in insts])
+        st = ts.State(prob, 64)
+        hp = ts.hparams(seed=1, **kw)
+        ts.tsat_init(st.h, hp)
+        ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ts.tsat_init(st.h, hp)
+        ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
+        sb = ts.tsat_status(st.h, n_inst)
+        batch_ms = 1e3 * (time.perf_counter() - t0)
+        out["readings"][name] = {
+            "plain": {"solved": len(walls), "of": n_inst,
+                      "median_ms_to_sat": 1e3 * float(np.median(walls)) if walls else None,
+                      "median_steps_to_sat": float(np.median(steps)) if steps else None},
+            "batched": {"solved": int(sum(x["found"] for x in sb["inst"])), "of": n_inst,
+                        "ms_whole_batch": batch_ms, "steps_run": sb["step"]}}
+    return out
+
+
+def progress_reading(ts, torch, prob, N, K, seed):
+    """The throughput workload under the sign-keeping reading that makes
+    progress (mean |z| Eq. 5, tau 2, lr0 0.5, deterministic Eq. 2): K steps
+    from a fresh init, device time, and the fewest unsatisfied clauses over
+    the samples before and after."""
+    hp = ts.hparams(seed=seed, norm=ts.NORM_ABSMEAN, binarize=ts.BIN_DET, tau=2.0, lr0=0.5)
+    st = ts.State(prob, N)
+    ts.tsat_init(st.h, hp)
+    ts.tsat_step_prepare(st.h, hp, K, stop_on_sat=False)
+    ts.tsat_step(st.h, hp, 1, stop_on_sat=False)                  # step 0: status of the initial bits
+    before = ts.tsat_status(st.h, 1)["inst"][0]["min_unsat"]
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    ts.tsat_step(st.h, hp, K, stop_on_sat=False)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    after = ts.tsat_status(st.h, 1)["inst"][0]["min_unsat"]
+    del st
+    return {"reading": "mean |z| Eq. 5, tau 2, lr0 0.5, deterministic Eq. 2", "steps": K,
+            "value": prob.info["nnz"] * N * K / (ms / 1e3), "unit": "literal-clause evals/s",
+            "ms_per_step": ms / K, "min_unsat_at_step0": before, "min_unsat_after": after,
+            "n_clauses": prob.info["n_clauses"]}
 
 
 # ---------------------------------------------------------------- our arm
@@ -283,8 +388,10 @@ def ours(args, w, rank, world, local):
                         "evals_per_s": evals_step / (t_fwd / 1e3)},
             "gamma_ms": t_gamma}
     del st
+    progress = progress_reading(ts, torch, prob, N, K, w["seed"] + rank) if rank == 0 else None
     del prob
     torch.cuda.empty_cache()
+    tts = time_to_sat_summary(ts, torch) if rank == 0 and not args.no_tts else None
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -332,7 +439,7 @@ def ours(args, w, rank, world, local):
         cols = min(ORACLE_COLS, N)
         r = oracle_run(inst, cols, 10_000, budget_s=15.0)
         cpu = {"value": r["evals"] / r["seconds"], "unit": "literal-clause evals/s", "cores": r["cores"],
-               "kind": "oracle",
+               "kind": "oracle", "host": host_description(),
                "sample": f"{r['steps']} oracle steps on {cols} of {N} sample columns of the same instance "
                          f"({r['seconds']:.1f} s)"}
     if rank == 0:
@@ -345,6 +452,7 @@ def ours(args, w, rank, world, local):
                            "binarize": "Philox-sampled", "l2": "state 12.6 GB > L2 126 MB, no flush needed",
                            "parallelism": f"replicas x{world}", "min_unsat_after": status["inst"][0]["min_unsat"]},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "progress_reading": progress, "time_to_sat": tts,
                 "gpu_launches": K * launches_per_step,
                 "impl": "ours"}
         print(json.dumps(line), flush=True)
