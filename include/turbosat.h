@@ -145,6 +145,16 @@ void tsat_problem_free(tsat_problem *p);
 /* Sizes after de-duplication: h_info = {n_inst, n_vars, n_clauses, nnz, lmax, n_items,
  * occurrence-record words, workspace bytes in use}. */
 int tsat_problem_info(const tsat_problem *p, int64_t h_info[8]);
+/* Random streams per instance.  Every random draw of an instance (the init of
+ * Sec. IV-A and the Philox-sampled binarisation) uses a Philox4x32-10 key
+ * whose low word is seed_low + the instance's id, and counters that carry the
+ * instance-local variable index, so an instance gets the same draws whichever
+ * batch it is loaded in.  Ids default to the position in the loaded batch
+ * (0 .. n_inst-1; a single instance: id 0, i.e. the plain seed); a caller
+ * that splits a batch over several processes sets each instance's position in
+ * the whole batch here, before tsat_init.  h_ids: int32 [n_inst], >= 0.
+ * Synchronous (waits for `stream`). */
+int tsat_problem_set_instance_ids(tsat_problem *p, const int32_t *h_ids, cudaStream_t stream);
 /* Device CSR views for inspection (clause-major, lit = (global var << 1) | negated):
  * copies cptr (n_clauses+1 int32) and clit (nnz int32) to host buffers. */
 int tsat_problem_csr(const tsat_problem *p, int32_t *h_cptr, int32_t *h_clit);
@@ -200,6 +210,49 @@ int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps,
 /* Capture and instantiate the graph tsat_step(hp, n_steps, stop_on_sat) would
  * replay, without running it (keeps graph building out of timed regions). */
 int tsat_step_prepare(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat);
+
+/* ---- sample sharding (one problem's samples over several processes) ----
+ * The paper ran on up to two GPUs (Sec. V) without saying how.  Every part of
+ * a step except Eq. 5 reads one sample column only (Eq. 1 forward, Eqs. 3-4,
+ * the straight-through backward of Sec. III-B), so the N samples split into
+ * shards of equal power-of-two size, one state (n_samples = the shard's size)
+ * per process.  Eq. 5 couples a row's samples through two sums over all N:
+ * sum_i G_vi z_vi (its chain rule) and sum_i z_vi or sum_i |z_vi| (the new
+ * normaliser).  A sharded step is therefore
+ *     tsat_shard_grad -> all-reduce d_rowdot -> tsat_shard_update ->
+ *     all-reduce d_rowsum -> tsat_shard_finish
+ * and the init is tsat_shard_init -> all-reduce d_rowsum -> tsat_shard_finish;
+ * the caller makes the all-reduces (sums of float [V], NCCL between GPUs).
+ * Random draws use the samples' global indices, so the shards draw what one
+ * state of all N samples would; FP32 sums differ from it in order only.
+ * tsat_state_set_shard: this state holds samples [sample_base, sample_base +
+ *   n_samples) of n_total (sample_base a multiple of n_samples); call before
+ *   tsat_shard_init.  A shard refuses tsat_init, tsat_step(_persistent),
+ *   tsat_forward / tsat_backward, tsat_autotune and tsat_profile_step
+ *   (TSAT_ESTATE).
+ * tsat_shard_init: Irwin-Hall init of z (Sec. IV-A), m = v = 0, step 0;
+ *   d_rowsum float [V] receives this shard's row sums of z (|z| for mean |z|).
+ * tsat_shard_grad: the step's forward and gamma (status records of this
+ *   shard's samples, freezing of an instance when one of them satisfies it,
+ *   step scalars; the step counter advances), d_G float [V][n_samples] = the
+ *   straight-through gradient of L with respect to the normalised assignment
+ *   of this shard's samples, d_rowdot float [V] = sum over them of G z (0 for
+ *   frozen instances and without normalisation).
+ * tsat_shard_update: with d_rowdot_total (the all-reduced d_rowdot), the Eq. 5
+ *   chain rule, AdamW and the new z, m, v of live rows; d_rowsum float [V] =
+ *   this shard's row sums of the new z (|z|).
+ * tsat_shard_finish: with d_rowsum_total, nu_v = total / n_total (guarded as
+ *   in Eq. 5's reading; 1 without normalisation) and the bits of the current
+ *   step (Eq. 2 or the Philox rule); frozen instances keep theirs.
+ * Requirements: the STE layer, hp->mix_restart = 0, and the same hp on every
+ * shard.  found_sample in tsat_status is an index within the shard.  All
+ * async on `stream`. */
+int tsat_state_set_shard(tsat_state *s, int32_t sample_base, int32_t n_total);
+int tsat_shard_init(tsat_state *s, const tsat_hparams *hp, float *d_rowsum, cudaStream_t stream);
+int tsat_shard_grad(tsat_state *s, const tsat_hparams *hp, float *d_G, float *d_rowdot, cudaStream_t stream);
+int tsat_shard_update(tsat_state *s, const tsat_hparams *hp, const float *d_G, const float *d_rowdot_total,
+                      float *d_rowsum, cudaStream_t stream);
+int tsat_shard_finish(tsat_state *s, const tsat_hparams *hp, const float *d_rowsum_total, cudaStream_t stream);
 
 /* Runs n_steps steps as individual launches on the state's stream with CUDA
  * events around each kernel and returns the average device time per launch

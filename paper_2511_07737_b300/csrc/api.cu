@@ -60,7 +60,7 @@ static StatePlan plan_state(const tsat_problem *p, int32_t N, int32_t layer, int
   return S;
 }
 
-static Hyper make_hyper(const tsat_hparams &hp, int stop) {
+Hyper make_hyper(const tsat_hparams &hp, int stop) {
   Hyper h{};
   h.tau = hp.tau;
   h.beta1 = (float)hp.beta1;
@@ -77,7 +77,7 @@ static Hyper make_hyper(const tsat_hparams &hp, int stop) {
   return h;
 }
 
-static LrSched make_sched(const tsat_hparams &hp) {
+LrSched make_sched(const tsat_hparams &hp) {
   LrSched l{};
   l.lr0 = hp.lr0;
   l.factor = hp.lr_factor;
@@ -103,19 +103,21 @@ static int check_hp(const tsat_hparams *hp) {
 }
 
 // caller stream -> internal stream ordering
-static int enter(tsat_state *s, cudaStream_t user) {
+int state_enter(tsat_state *s, cudaStream_t user) {
   TSAT_CUDA(cudaEventRecord(s->ev_in, user));
   TSAT_CUDA(cudaStreamWaitEvent(s->stream, s->ev_in, 0));
   return TSAT_OK;
 }
-static int leave(tsat_state *s, cudaStream_t user) {
+int state_leave(tsat_state *s, cudaStream_t user) {
   TSAT_CUDA(cudaEventRecord(s->ev_out, s->stream));
   TSAT_CUDA(cudaStreamWaitEvent(user, s->ev_out, 0));
   return TSAT_OK;
 }
+static int enter(tsat_state *s, cudaStream_t user) { return state_enter(s, user); }
+static int leave(tsat_state *s, cudaStream_t user) { return state_leave(s, user); }
 
 // Update grid: resident blocks per SM (occupancy API) unless tuned explicitly.
-static int upd_grid(const tsat_state *s) {
+int update_grid(const tsat_state *s) {
   if (s->upd_blocks_per_sm <= 0 && s->occ_bps < 0) s->occ_bps = update_blocks_per_sm(s->prob->dev, s->dev);
   const int bps = s->upd_blocks_per_sm > 0 ? s->upd_blocks_per_sm : s->occ_bps;
   // no more blocks than needed to give every warp a row group (32/W rows)
@@ -151,8 +153,8 @@ static int issue_pre_update(tsat_state *s, const Hyper &hy, const LrSched &ls, c
 static int issue_update(tsat_state *s, const Hyper &hy, const LrSched &ls, cudaStream_t st) {
   const ProbDev &pd = s->prob->dev;
   cudaError_t e;
-  if (ls.mix && (e = launch_mix(pd, s->dev, hy, upd_grid(s), st)) != cudaSuccess) return cuda_fail(e, "mix");
-  if ((e = launch_update(pd, s->dev, hy, 0, nullptr, nullptr, 0.f, upd_grid(s), s->upd_rows_per_item, st)) !=
+  if (ls.mix && (e = launch_mix(pd, s->dev, hy, update_grid(s), st)) != cudaSuccess) return cuda_fail(e, "mix");
+  if ((e = launch_update(pd, s->dev, hy, 0, nullptr, nullptr, 0.f, update_grid(s), s->upd_rows_per_item, st)) !=
       cudaSuccess)
     return cuda_fail(e, "update");
   return TSAT_OK;
@@ -162,6 +164,46 @@ static int issue_update(tsat_state *s, const Hyper &hy, const LrSched &ls, cudaS
 static int issue_step(tsat_state *s, const Hyper &hy, const LrSched &ls, cudaStream_t st) {
   int rc = issue_pre_update(s, hy, ls, st);
   return rc ? rc : issue_update(s, hy, ls, st);
+}
+
+__global__ void k_reset(StateDev sd, int n_inst) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j == 0) {
+    sd.hdr->t = 0;
+    sd.hdr->all_done = 0;
+    sd.hdr->err = 0;
+    sd.hdr->n_active = n_inst;
+    sd.hdr->blocks_done = 0;
+  }
+  if (j < n_inst) {
+    InstState is{};
+    is.found = 0;
+    is.found_sample = -1;
+    is.found_step = -1;
+    is.min_unsat = -1;
+    is.best_sample = -1;
+    is.loss = 0.f;
+    sd.inst[j] = is;
+  }
+}
+
+int reset_state(tsat_state *s, cudaStream_t st) {
+  const int n = s->prob->dev.n_inst;
+  k_reset<<<(n + 255) / 256, 256, 0, st>>>(s->dev, n);
+  TSAT_LAUNCH_CHECK("reset");
+  return TSAT_OK;
+}
+
+// A sample shard (tsat_state_set_shard) holds part of each row's samples: the
+// calls that form Eq. 5's means over the state's own samples would take them
+// over the shard only, so they refuse it.
+static int check_not_shard(const tsat_state *s) {
+  if (s->dev.n_total != s->N) {
+    set_error("the state holds samples [%d, %d) of %d: run it with the tsat_shard_* calls", s->dev.sample_base,
+              s->dev.sample_base + s->N, s->dev.n_total);
+    return TSAT_ESTATE;
+  }
+  return TSAT_OK;
 }
 
 }  // namespace tsat
@@ -226,6 +268,8 @@ int tsat_state_create(tsat_problem *p, void *d_state, size_t state_bytes, int32_
   StateDev &D = s->dev;
   D.N = N;
   D.W = N / 32;
+  D.sample_base = 0;
+  D.n_total = N;
   D.lm1 = p->lmax + 1;
   D.layer = layer;
   D.hdr = (StateHdr *)(b + P.hdr);
@@ -301,31 +345,12 @@ void tsat_state_free(tsat_state *s) {
   delete s;
 }
 
-__global__ void k_reset(StateDev sd, int n_inst) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j == 0) {
-    sd.hdr->t = 0;
-    sd.hdr->all_done = 0;
-    sd.hdr->err = 0;
-    sd.hdr->n_active = n_inst;
-    sd.hdr->blocks_done = 0;
-  }
-  if (j < n_inst) {
-    InstState is{};
-    is.found = 0;
-    is.found_sample = -1;
-    is.found_step = -1;
-    is.min_unsat = -1;
-    is.best_sample = -1;
-    is.loss = 0.f;
-    sd.inst[j] = is;
-  }
-}
 
 int tsat_init(tsat_state *s, const tsat_hparams *hp, const float *d_logits, float scale, cudaStream_t stream) {
   if (!s) return TSAT_EINVAL;
   int rc = check_hp(hp);
   if (rc) return rc;
+  if ((rc = check_not_shard(s))) return rc;
   if (hp->layer != s->layer) { set_error("hp->layer differs from the state's layer"); return TSAT_ESTATE; }
   if ((rc = enter(s, stream))) return rc;
   const Hyper hy = make_hyper(*hp, 0);
@@ -334,10 +359,10 @@ int tsat_init(tsat_state *s, const tsat_hparams *hp, const float *d_logits, floa
   TSAT_CUDA(cudaMemsetAsync(s->dev.hist, 0, histb, s->stream));
   k_reset<<<(pd.n_inst + 255) / 256, 256, 0, s->stream>>>(s->dev, pd.n_inst);
   TSAT_LAUNCH_CHECK("reset");
-  cudaError_t e = launch_init(pd, s->dev, hy, d_logits, scale, upd_grid(s), s->stream);
+  cudaError_t e = launch_init(pd, s->dev, hy, d_logits, scale, update_grid(s), s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "init");
   if (s->layer == TSAT_LAYER_RELAXED) {
-    e = launch_relaxed_lits(pd, s->dev, hy, nullptr, upd_grid(s), s->stream);
+    e = launch_relaxed_lits(pd, s->dev, hy, nullptr, update_grid(s), s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "relaxed literals");
   }
   s->initialised = true;
@@ -387,6 +412,7 @@ static int check_step_args(tsat_state *s, const tsat_hparams *hp, int32_t n_step
   if (!s) return TSAT_EINVAL;
   int rc = check_hp(hp);
   if (rc) return rc;
+  if ((rc = check_not_shard(s))) return rc;
   if (!s->initialised) { set_error("state not initialised"); return TSAT_ESTATE; }
   if (hp->layer != s->layer) { set_error("hp->layer differs from the state's layer"); return TSAT_ESTATE; }
   if (n_steps <= 0) { set_error("n_steps must be positive"); return TSAT_EINVAL; }
@@ -474,9 +500,9 @@ int tsat_profile_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, fl
       if (e == cudaSuccess) e = launch_gamma(pd, s->dev, hy, ls, s->dev.hist, 1, 1, nullptr, nullptr, st);
     }
     TSAT_CUDA(cudaEventRecord(ev[2], st));
-    if (e == cudaSuccess && ls.mix) e = launch_mix(pd, s->dev, hy, upd_grid(s), st);
+    if (e == cudaSuccess && ls.mix) e = launch_mix(pd, s->dev, hy, update_grid(s), st);
     if (e == cudaSuccess)
-      e = launch_update(pd, s->dev, hy, 0, nullptr, nullptr, 0.f, upd_grid(s), s->upd_rows_per_item, st);
+      e = launch_update(pd, s->dev, hy, 0, nullptr, nullptr, 0.f, update_grid(s), s->upd_rows_per_item, st);
     TSAT_CUDA(cudaEventRecord(ev[3], st));
     TSAT_CUDA(cudaEventSynchronize(ev[3]));
     float a = 0, b = 0, c = 0, d = 0;
@@ -632,6 +658,7 @@ int tsat_forward(tsat_state *s, const tsat_hparams *hp, const float *d_z, int64_
   if (!s || !d_z || !d_S || !d_loss) { set_error("NULL argument"); return TSAT_EINVAL; }
   int rc = check_hp(hp);
   if (rc) return rc;
+  if ((rc = check_not_shard(s))) return rc;
   if (hp->layer != s->layer) { set_error("hp->layer differs from the state's layer"); return TSAT_ESTATE; }
   if ((rc = enter(s, stream))) return rc;
   const ProbDev &pd = s->prob->dev;
@@ -643,14 +670,14 @@ int tsat_forward(tsat_state *s, const tsat_hparams *hp, const float *d_z, int64_
   }
   cudaError_t e;
   if (s->layer == TSAT_LAYER_RELAXED) {
-    if ((e = launch_relaxed_lits(pd, s->dev, hy, d_z, upd_grid(s), s->stream)) != cudaSuccess)
+    if ((e = launch_relaxed_lits(pd, s->dev, hy, d_z, update_grid(s), s->stream)) != cudaSuccess)
       return cuda_fail(e, "relaxed literals");
     if ((e = launch_relaxed_fwd(pd, s->dev, hy, 0, s->stream)) != cudaSuccess) return cuda_fail(e, "relaxed forward");
     if ((e = launch_relaxed_gamma(pd, s->dev, hy, ls, 0, d_loss, d_S, s->stream)) != cudaSuccess)
       return cuda_fail(e, "relaxed gamma");
   } else {
     const size_t n = (size_t)pd.n_inst * s->N;
-    if ((e = launch_binarize(pd, s->dev, hy, d_z, t_bin, upd_grid(s), s->stream)) != cudaSuccess)
+    if ((e = launch_binarize(pd, s->dev, hy, d_z, t_bin, update_grid(s), s->stream)) != cudaSuccess)
       return cuda_fail(e, "binarize");
     TSAT_CUDA(cudaMemsetAsync(s->eval_hist, 0, sizeof(int32_t) * n * s->dev.lm1, s->stream));
     if ((e = launch_fwd_hist(pd, s->dev, s->eval_hist, 0, s->stream)) != cudaSuccess) return cuda_fail(e, "forward");
@@ -665,9 +692,10 @@ int tsat_backward(tsat_state *s, const tsat_hparams *hp, const float *d_z, float
   if (!s || !d_z || !d_grad) { set_error("NULL argument"); return TSAT_EINVAL; }
   int rc = check_hp(hp);
   if (rc) return rc;
+  if ((rc = check_not_shard(s))) return rc;
   if ((rc = enter(s, stream))) return rc;
   const Hyper hy = make_hyper(*hp, 0);
-  cudaError_t e = launch_update(s->prob->dev, s->dev, hy, 1, d_z, d_grad, dL, upd_grid(s), s->upd_rows_per_item,
+  cudaError_t e = launch_update(s->prob->dev, s->dev, hy, 1, d_z, d_grad, dL, update_grid(s), s->upd_rows_per_item,
                                 s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "backward");
   return leave(s, stream);
@@ -743,6 +771,7 @@ int tsat_autotune(tsat_state *s, const tsat_hparams *hp, void *d_snapshot, size_
   if (!s || !h_tuning || !d_snapshot) { set_error("NULL argument"); return TSAT_EINVAL; }
   int rc = check_hp(hp);
   if (rc) return rc;
+  if ((rc = check_not_shard(s))) return rc;
   if (!s->initialised) { set_error("state not initialised"); return TSAT_ESTATE; }
   if (hp->layer != s->layer) { set_error("hp->layer differs from the state's layer"); return TSAT_ESTATE; }
   const size_t need = s->core_bytes + s->lit_bytes;

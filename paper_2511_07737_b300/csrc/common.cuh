@@ -19,7 +19,8 @@ __device__ __forceinline__ uint32_t half16(uint32_t w0, uint32_t w1, int h) {
 
 struct InstInfo {
   int32_t v_off, n_vars, c_off, n_clauses;
-  int32_t lmax, item_off, n_items, pad;
+  int32_t lmax, item_off, n_items;
+  int32_t gid;   // the instance's id for its random streams (default: its index in the loaded batch)
 };
 
 // Problem view passed by value to kernels.
@@ -71,6 +72,8 @@ struct StepParams {
 
 struct StateDev {
   int32_t N, W, lm1, layer;    // samples, words per row, histogram width, layer
+  int32_t sample_base;         // global index of this state's first sample (sample-sharded states; else 0)
+  int32_t n_total;             // samples of the whole problem over all shards (= N when not sharded)
   StateHdr *hdr;
   InstState *inst;
   StepParams *sp;
@@ -115,6 +118,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
   }
   return c;
+}
+
+// Philox stream of one variable row: the counter's row word is the
+// instance-local variable index and the key's low word is offset by the
+// instance's id, so an instance's random draws (init and sampled
+// binarisation) are the same whichever batch it is loaded in and wherever its
+// rows sit.  A single instance (id 0, first row 0) keeps the plain layout:
+// row word = variable index, key = the seed.
+struct RowStream {
+  uint32_t row, k0;
+};
+__device__ __forceinline__ RowStream row_stream(const ProbDev &pd, uint32_t key0, int inst, int64_t v) {
+  const int32_t voff = __ldg(&pd.inst[inst].v_off), gid = __ldg(&pd.inst[inst].gid);
+  return RowStream{(uint32_t)(v - voff), key0 + (uint32_t)gid};
 }
 
 // ---------------------------------------------------------------- bit tricks

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "kernels.cuh"
 #include "turbosat.h"
 
 namespace tsat {
@@ -64,6 +65,16 @@ struct GraphKey {
     return hp < o.hp;
   }
 };
+
+namespace tsat {
+// Host helpers shared by the entry points (api.cu).
+Hyper make_hyper(const tsat_hparams &hp, int stop);
+LrSched make_sched(const tsat_hparams &hp);
+int state_enter(tsat_state *s, cudaStream_t user);   // the state's stream waits for the caller's
+int state_leave(tsat_state *s, cudaStream_t user);   // the caller's stream waits for the state's
+int update_grid(const tsat_state *s);                // blocks of the fused update
+int reset_state(tsat_state *s, cudaStream_t st);     // step counter and status records to their start
+}  // namespace tsat
 
 struct tsat_state {
   tsat_problem *prob = nullptr;

@@ -76,9 +76,10 @@ __device__ __forceinline__ void store_lits(const StateDev &sd, size_t off, const
 
 // New normaliser (Eq. 5), Eq. 2 / Philox bits for step t, and (relaxed layer)
 // the literal values sigmoid(z / nu).
-__device__ __forceinline__ void row_binarize_store(const StateDev &sd, const Hyper &hy, const Group &g,
-                                                   float *red, int64_t v, const float zq[4], int64_t t,
-                                                   uint32_t *dst_bits, bool want_lits = false) {
+__device__ __forceinline__ void row_binarize_store(const ProbDev &pd, const StateDev &sd, const Hyper &hy,
+                                                   const Group &g, float *red, int inst, int64_t v,
+                                                   const float zq[4], int64_t t, uint32_t *dst_bits,
+                                                   bool want_lits = false) {
   const int N = sd.N;
   float nu = 1.0f;
   if (hy.norm != TSAT_NORM_NONE) {
@@ -90,8 +91,10 @@ __device__ __forceinline__ void row_binarize_store(const StateDev &sd, const Hyp
   const int s0 = g.gl * 4;
   // samples s0 .. s0+3 are halves 0..3 or 4..7 of the block s0 / 8
   uint4 rnd = make_uint4(0, 0, 0, 0);
-  if (hy.binarize == TSAT_BIN_PHILOX)
-    rnd = philox4x32_10(make_uint4((uint32_t)(g.gl >> 1), (uint32_t)v, (uint32_t)t, kTagBin), hy.key0, hy.key1);
+  if (hy.binarize == TSAT_BIN_PHILOX) {
+    const RowStream rs = row_stream(pd, hy.key0, inst, v);
+    rnd = philox4x32_10(make_uint4((uint32_t)(g.gl >> 1), rs.row, (uint32_t)t, kTagBin), rs.k0, hy.key1);
+  }
   const uint32_t w0 = (g.gl & 1) ? rnd.z : rnd.x, w1 = (g.gl & 1) ? rnd.w : rnd.y;
   uint32_t nib = 0;
   float a[4];
@@ -122,12 +125,16 @@ __global__ void __launch_bounds__(kBlock) k_init(ProbDev pd, StateDev sd, Hyper 
   for (int64_t v = (int64_t)blockIdx.x * RPB + g.grp; v < rows_round; v += NG) {
     if (v >= pd.V) continue;  // whole group skips together (group-uniform v)
     const int s0 = g.gl * 4;
+    const int inst = __ldg(pd.var_inst + v);
+    const RowStream rs = row_stream(pd, hy.key0, inst, v);
     float zq[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       int32_t acc = 0;
       for (uint32_t j = 0; j < 3; ++j) {
-        uint4 o = philox4x32_10(make_uint4((uint32_t)(s0 + s), (uint32_t)v, j, kTagInit), hy.key0, hy.key1);
+        // counter: the sample's global index (sample-sharded states start at sample_base)
+        uint4 o = philox4x32_10(make_uint4((uint32_t)(sd.sample_base + s0 + s), rs.row, j, kTagInit), rs.k0,
+                                hy.key1);
         acc += (int32_t)(o.x >> 8) + (int32_t)(o.y >> 8) + (int32_t)(o.z >> 8) + (int32_t)(o.w >> 8);
       }
       float noise = __int2float_rn(acc - 6 * (1 << 24)) * (1.0f / 16777216.0f);
@@ -137,7 +144,7 @@ __global__ void __launch_bounds__(kBlock) k_init(ProbDev pd, StateDev sd, Hyper 
     st_cs(sd.z + off, make_float4(zq[0], zq[1], zq[2], zq[3]));
     st_cs(sd.m + off, make_float4(0.f, 0.f, 0.f, 0.f));
     st_cs(sd.v + off, make_float4(0.f, 0.f, 0.f, 0.f));
-    row_binarize_store(sd, hy, g, red + (GT > 32 ? g.grp * 8 : 0), v, zq, 0, sd.bits);
+    row_binarize_store(pd, sd, hy, g, red + (GT > 32 ? g.grp * 8 : 0), inst, v, zq, 0, sd.bits);
   }
 }
 
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(kBlock) k_mix(ProbDev pd, StateDev sd, Hyper h
     *reinterpret_cast<float4 *>(sd.z + off) = make_float4(zq[0], zq[1], zq[2], zq[3]);
     *reinterpret_cast<float4 *>(sd.m + off) = make_float4(0.f, 0.f, 0.f, 0.f);
     *reinterpret_cast<float4 *>(sd.v + off) = make_float4(0.f, 0.f, 0.f, 0.f);
-    row_binarize_store(sd, hy, g, red + (GT > 32 ? g.grp * 8 : 0), v, zq, sp.t + 1, bdst,
+    row_binarize_store(pd, sd, hy, g, red + (GT > 32 ? g.grp * 8 : 0), inst, v, zq, sp.t + 1, bdst,
                        sd.layer == TSAT_LAYER_RELAXED);
   }
 }
@@ -197,7 +204,8 @@ __global__ void __launch_bounds__(kBlock) k_binarize(ProbDev pd, StateDev sd, Hy
     const float *zsrc = zin ? zin : sd.z;
     float4 z4 = *reinterpret_cast<const float4 *>(zsrc + (size_t)v * sd.N + s0);
     float zq[4] = {z4.x, z4.y, z4.z, z4.w};
-    row_binarize_store(sd, hy, g, red + (GT > 32 ? g.grp * 8 : 0), v, zq, t_bin, dst, want_lits != 0);
+    row_binarize_store(pd, sd, hy, g, red + (GT > 32 ? g.grp * 8 : 0), __ldg(pd.var_inst + v), v, zq, t_bin, dst,
+                       want_lits != 0);
   }
 }
 
@@ -754,7 +762,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
       st_cs(sd.m + off, make_float4(mq[0], mq[1], mq[2], mq[3]));
       st_cs(sd.v + off, make_float4(vq[0], vq[1], vq[2], vq[3]));
       // ---- new normaliser and Eq. 2 for step t+1
-      row_binarize_store(sd, hy, g, red, v, zn, tcur + 1, bdst, RELAX);
+      row_binarize_store(pd, sd, hy, g, red, inst, v, zn, tcur + 1, bdst, RELAX);
     }
   }
 }
@@ -1052,6 +1060,12 @@ __global__ void __launch_bounds__(kUpd3Block, kUpd3MinB) k_update3(ProbDev pd, S
     // nibble (Wk + w) of the row, stored at word isam + W k; lane w then joins
     // nibbles 8w .. 8w + 7 (its counting-layout words) into bits word w
     if (valid && frozen) bdst[v * W + w] = bsrc[v * W + w];
+    uint32_t prow = 0, pk0 = hy.key0;   // the row's Philox stream (instance-local row, instance key)
+    if (BIN == TSAT_BIN_PHILOX && valid) {
+      const RowStream rs = row_stream(pd, hy.key0, inst, v);
+      prow = rs.row;
+      pk0 = rs.k0;
+    }
     const float nun = (NORM == TSAT_NORM_NONE) ? 1.0f : guard_nu(tot / (float)N);
     const float rnn = __frcp_rn(nun);
     // Philox: samples 4(Wk + w) .. +3 are halves 0..3 (w even) or 4..7 (w odd)
@@ -1064,7 +1078,7 @@ __global__ void __launch_bounds__(kUpd3Block, kUpd3MinB) k_update3(ProbDev pd, S
       uint32_t own0 = 0, own1 = 0, oth0 = 0, oth1 = 0;
       if constexpr (BIN == TSAT_BIN_PHILOX) {
         const uint32_t blk = (uint32_t)((W * (2 * kk + (w & 1)) + (w & ~1)) >> 1);
-        const uint4 r = philox4x32_10(make_uint4(blk, (uint32_t)v, (uint32_t)(tcur + 1), kTagBin), hy.key0, hy.key1);
+        const uint4 r = philox4x32_10(make_uint4(blk, prow, (uint32_t)(tcur + 1), kTagBin), pk0, hy.key1);
         const uint32_t s0 = (w & 1) ? r.x : r.z, s1 = (w & 1) ? r.y : r.w;   // the partner's words
         const uint32_t g0 = __shfl_xor_sync(0xFFFFFFFFu, s0, 1), g1 = __shfl_xor_sync(0xFFFFFFFFu, s1, 1);
         if (W == 1) {                   // pass 2kk: words 0, 1; pass 2kk + 1: words 2, 3
@@ -1292,10 +1306,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_updateL(ProbDev pd, StateDev sd, 
         const float rnn = __frcp_rn(nun);
         uint32_t word = 0;
         if constexpr (BIN == TSAT_BIN_PHILOX) {
+          const RowStream rs = row_stream(pd, hy.key0, cur, v);
 #pragma unroll 1
           for (int h = 0; h < 4; ++h) {   // samples 32 w + 8 h + e: block 4 w + h, half e
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)(4 * w + h), (uint32_t)v, (uint32_t)(tcur + 1), kTagBin),
-                                          hy.key0, hy.key1);
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)(4 * w + h), rs.row, (uint32_t)(tcur + 1), kTagBin),
+                                          rs.k0, hy.key1);
 #pragma unroll
             for (int e = 0; e < 8; ++e)
               word |= binarize_one(__fmul_rn(gbuf[(8 * h + e) * kGS + lane], rnn), TSAT_BIN_PHILOX, hy.bin_c,

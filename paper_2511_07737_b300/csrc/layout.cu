@@ -462,6 +462,7 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
     I.c_off = (int32_t)coff;
     I.n_clauses = descs[j].n_clauses;
     I.lmax = 0;
+    I.gid = j;
     for (int32_t c = 0; c < descs[j].n_clauses; ++c) raw_cptr[coff + c] = loff + descs[j].h_clause_ptr[c];
     voff += descs[j].n_vars;
     coff += descs[j].n_clauses;
@@ -586,6 +587,18 @@ int tsat_problem_info(const tsat_problem *p, int64_t h_info[8]) {
   h_info[3] = p->nnz;
   h_info[4] = p->lmax;
   h_info[5] = p->dev.n_items;
+  return TSAT_OK;
+}
+
+int tsat_problem_set_instance_ids(tsat_problem *p, const int32_t *h_ids, cudaStream_t stream) {
+  if (!p || !h_ids) { set_error("NULL argument"); return TSAT_EINVAL; }
+  for (int32_t j = 0; j < p->n_inst; ++j) {
+    if (h_ids[j] < 0) { set_error("instance id %d of instance %d is negative", h_ids[j], j); return TSAT_EINVAL; }
+    p->inst[j].gid = h_ids[j];
+  }
+  TSAT_CUDA(cudaMemcpyAsync(const_cast<InstInfo *>(p->dev.inst), p->inst.data(), sizeof(InstInfo) * p->n_inst,
+                            cudaMemcpyHostToDevice, stream));
+  TSAT_CUDA(cudaStreamSynchronize(stream));
   return TSAT_OK;
 }
 

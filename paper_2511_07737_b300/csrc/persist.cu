@@ -445,8 +445,10 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
         if constexpr (BIN == TSAT_BIN_PHILOX) {
 #pragma unroll
           for (int hb = 0; hb < SPT / 8; ++hb) {   // samples 32 w + sb + 8 hb + e: block 4 w + sb / 8 + hb, half e
+            // the row's Philox stream: instance-local row, key offset by the instance's id
             const uint4 r = philox4x32_10(
-                make_uint4((uint32_t)(4 * w + (sb >> 3) + hb), (uint32_t)v, (uint32_t)(t + 1), kTagBin), hy.key0, hy.key1);
+                make_uint4((uint32_t)(4 * w + (sb >> 3) + hb), (uint32_t)vl, (uint32_t)(t + 1), kTagBin),
+                hy.key0 + (uint32_t)I.gid, hy.key1);
 #pragma unroll
             for (int e = 0; e < 8; ++e)
               part_bits |= binarize_one(__fmul_rn(acc[8 * hb + e], rnn), TSAT_BIN_PHILOX, hy.bin_c,

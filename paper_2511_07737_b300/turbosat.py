@@ -90,6 +90,12 @@ def lib():
             "tsat_state_views": (ctypes.c_int, [P, P, P, P, P, P, P, P]),
             "tsat_forward": (ctypes.c_int, [P, P, P, i64, P, P, P]),
             "tsat_backward": (ctypes.c_int, [P, P, P, f32, P, P]),
+            "tsat_problem_set_instance_ids": (ctypes.c_int, [P, P, P]),
+            "tsat_state_set_shard": (ctypes.c_int, [P, i32, i32]),
+            "tsat_shard_init": (ctypes.c_int, [P, P, P, P]),
+            "tsat_shard_grad": (ctypes.c_int, [P, P, P, P, P]),
+            "tsat_shard_update": (ctypes.c_int, [P, P, P, P, P, P]),
+            "tsat_shard_finish": (ctypes.c_int, [P, P, P, P]),
             "tsat_autotune_bytes": (ctypes.c_int, [P, P]),
             "tsat_tuning_space": (ctypes.c_int, [P, P, P, P]),
             "tsat_autotune": (ctypes.c_int, [P, P, P, sz, P, P]),
@@ -192,6 +198,33 @@ def tsat_problem_csr(h):
     clit = np.zeros(max(1, info["nnz"]), np.int32)
     _ck(lib().tsat_problem_csr(h, _ptr(cptr), _ptr(clit)), "tsat_problem_csr")
     return cptr, clit[: info["nnz"]]
+
+
+def tsat_problem_set_instance_ids(h, ids, stream=None):
+    """Per-instance random-stream ids (default: position in the loaded batch)."""
+    a = np.ascontiguousarray(ids, dtype=np.int32)
+    _ck(lib().tsat_problem_set_instance_ids(h, _ptr(a), _stream(stream)), "tsat_problem_set_instance_ids")
+
+
+def tsat_state_set_shard(s, sample_base: int, n_total: int):
+    _ck(lib().tsat_state_set_shard(s, int(sample_base), int(n_total)), "tsat_state_set_shard")
+
+
+def tsat_shard_init(s, hp, rowsum: torch.Tensor, stream=None):
+    _ck(lib().tsat_shard_init(s, ctypes.byref(hp), _ptr(rowsum), _stream(stream)), "tsat_shard_init")
+
+
+def tsat_shard_grad(s, hp, G: torch.Tensor, rowdot: torch.Tensor, stream=None):
+    _ck(lib().tsat_shard_grad(s, ctypes.byref(hp), _ptr(G), _ptr(rowdot), _stream(stream)), "tsat_shard_grad")
+
+
+def tsat_shard_update(s, hp, G: torch.Tensor, rowdot_total: torch.Tensor, rowsum: torch.Tensor, stream=None):
+    _ck(lib().tsat_shard_update(s, ctypes.byref(hp), _ptr(G), _ptr(rowdot_total), _ptr(rowsum), _stream(stream)),
+        "tsat_shard_update")
+
+
+def tsat_shard_finish(s, hp, rowsum_total: torch.Tensor, stream=None):
+    _ck(lib().tsat_shard_finish(s, ctypes.byref(hp), _ptr(rowsum_total), _stream(stream)), "tsat_shard_finish")
 
 
 def tsat_state_bytes(h, n_samples: int, layer: int = LAYER_STE, dtype: int = DTYPE_F32) -> int:

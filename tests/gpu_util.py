@@ -18,6 +18,23 @@ def unpack_bits(words: np.ndarray, N: int) -> np.ndarray:
     return np.unpackbits(w.view(np.uint8), axis=1, bitorder="little")[:, :N]
 
 
+def stream_seed(seed: int, gid: int) -> int:
+    """Philox key of instance `gid`: the library offsets the key's low word by
+    the instance's id (its position in the loaded batch by default)."""
+    return (seed & ~0xFFFFFFFF) | ((seed + gid) & 0xFFFFFFFF)
+
+
+def binarize_like_gpu(z, nu, hp, t, offsets):
+    """The oracle's Eq. 2 / Philox bits of a loaded batch: each instance's rows
+    with its own key and instance-local row indices (its random stream)."""
+    X = np.zeros(z.shape, np.uint8)
+    for j in range(len(offsets) - 1):
+        a, b = int(offsets[j]), int(offsets[j + 1])
+        X[a:b] = oracle.binarize_f32(z[a:b], nu[a:b], hp.binarize, c=0.25 / hp.bin_temp,
+                                     seed=stream_seed(hp.seed, j), t=t)
+    return X
+
+
 def snapshot(st: ts.State) -> dict:
     torch.cuda.synchronize()
     out = {k: st.view(k).cpu().numpy().copy() for k in ("z", "m", "v", "nu")}
@@ -118,7 +135,7 @@ def run_lockstep(insts, N, hp, steps, step_fn=None):
         live = ~frozen
         if live.any():
             assert_adamw_z(s1["z"][live], z[live], s1["m"][live], m[live], s1["v"][live], v[live], t, hp)
-        X = oracle.binarize_f32(s1["z"], s1["nu"], hp.binarize, c=0.25 / hp.bin_temp, seed=hp.seed, t=t + 1)
+        X = binarize_like_gpu(s1["z"], s1["nu"], hp, t + 1, offs)
         np.testing.assert_array_equal(s1["X"][live], X[live])
         np.testing.assert_array_equal(s1["X"][frozen], s0["X"][frozen])
         nu_ref = oracle.nu_f32(s1["z"], hp.norm)

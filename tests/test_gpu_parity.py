@@ -11,7 +11,8 @@ import oracle
 from paper_2511_07737_b300 import cnfgen
 from paper_2511_07737_b300 import turbosat as ts
 from tests.conftest import rel_err
-from tests.gpu_util import TOL_BF16, TOL_F32, assert_adamw_z, lockstep, make, snapshot, unpack_bits
+from tests.gpu_util import (TOL_BF16, TOL_F32, assert_adamw_z, binarize_like_gpu, lockstep, make, snapshot,
+                            unpack_bits)
 
 pytestmark = pytest.mark.gpu
 
@@ -115,7 +116,7 @@ def test_lockstep_ste(name, gen, N, kw, steps):
         live = ~frozen
         assert_adamw_z(s1["z"][live], z[live], s1["m"][live], m[live], s1["v"][live], v[live], t, hp)
         # bits of step t+1: Eq. 2 / Philox rule on the GPU's own FP32 z and nu
-        X = oracle.binarize_f32(s1["z"], s1["nu"], hp.binarize, c=0.25 / hp.bin_temp, seed=hp.seed, t=t + 1)
+        X = binarize_like_gpu(s1["z"], s1["nu"], hp, t + 1, offs)
         np.testing.assert_array_equal(s1["X"][live], X[live])
         np.testing.assert_array_equal(s1["X"][frozen], s0["X"][frozen])
         nu_ref = oracle.nu_f32(s1["z"], hp.norm)
@@ -148,7 +149,7 @@ def test_lockstep_assignment_mixing_at_restarts():
         else:
             cnt = t % 3 if t >= 3 else t + 1
             assert_adamw_z(s1["z"], z, s1["m"], m, s1["v"], v, t, hp, cnt=cnt)
-        X = oracle.binarize_f32(s1["z"], s1["nu"], hp.binarize, c=0.25 / hp.bin_temp, seed=hp.seed, t=t + 1)
+        X = binarize_like_gpu(s1["z"], s1["nu"], hp, t + 1, offs)
         np.testing.assert_array_equal(s1["X"], X)
         nu_ref = oracle.nu_f32(s1["z"], hp.norm)
         assert np.all(np.abs(s1["nu"] - nu_ref) <= 2e-6 * np.abs(s1["z"]).mean(axis=1) + 2e-6 * np.abs(nu_ref))

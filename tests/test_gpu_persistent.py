@@ -8,7 +8,7 @@ import torch
 import oracle
 from paper_2511_07737_b300 import cnfgen
 from paper_2511_07737_b300 import turbosat as ts
-from tests.gpu_util import TOL_F32, assert_adamw_z, lockstep, make, snapshot, unpack_bits
+from tests.gpu_util import TOL_F32, assert_adamw_z, binarize_like_gpu, lockstep, make, snapshot, unpack_bits
 
 pytestmark = pytest.mark.gpu
 
@@ -66,7 +66,7 @@ def test_persistent_lockstep(name, gen, N, kw):
         live = ~frozen
         if live.any():
             assert_adamw_z(s1["z"][live], z[live], s1["m"][live], m[live], s1["v"][live], v[live], t, hp)
-        X = oracle.binarize_f32(s1["z"], s1["nu"], hp.binarize, c=0.25 / hp.bin_temp, seed=hp.seed, t=t + 1)
+        X = binarize_like_gpu(s1["z"], s1["nu"], hp, t + 1, offs)
         np.testing.assert_array_equal(s1["X"][live], X[live])
         np.testing.assert_array_equal(s1["X"][frozen], s0["X"][frozen])
         nu_ref = oracle.nu_f32(s1["z"], hp.norm)
