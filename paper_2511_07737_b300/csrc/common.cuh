@@ -212,6 +212,15 @@ __device__ __forceinline__ float guard_nu(float mu) {
   return mu;
 }
 
+// Streaming (evict-first) 16-byte load and store of the state arrays.
+__device__ __forceinline__ float4 ld_cs(const float *p) { return __ldcs(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ void st_cs(float *p, float4 v) { __stcs(reinterpret_cast<float4 *>(p), v); }
+
+// Bits of step t: the ping-pong half t & 1.
+__device__ __forceinline__ const uint32_t *cur_bits(const StateDev &sd, int64_t t) {
+  return sd.bits + (size_t)(t & 1) * (size_t)sd.V * sd.W;
+}
+
 // Eq. 2 / Philox rule on one value, decided in FP32 without contraction.
 // half: the sample's 16-bit Philox output (counter (i / 8, v, t, kTagBin),
 // half i mod 8 of the four output words, low half first); u = half 2^-16.

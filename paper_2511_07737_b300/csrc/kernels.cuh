@@ -66,6 +66,11 @@ cudaError_t best_select(const ProbDev &pd, const StateDev &sd, int inst, int n_v
                         int32_t *small, int32_t *part_var, uint8_t *part_val, uint32_t *outbits,
                         cudaStream_t st);
 void prepare_update_attrs(int lmax);
+// fused update for clause length 4..7 (update_long.cu)
+cudaError_t launch_updateL(const ProbDev &pd, const StateDev &sd, const Hyper &hy, int mode, const float *zin,
+                           float *grad, float dL, int grid, cudaStream_t st);
+void prepare_updateL_attrs(int bytes);
+int updateL_resident_blocks(int N);
 int update_blocks_per_sm(const ProbDev &pd, const StateDev &sd);
 int update_warps_per_block(const ProbDev &pd, const StateDev &sd);
 
