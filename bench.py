@@ -683,6 +683,17 @@ def exp_batch(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     kms = ts.tsat_profile_step(st.h, hp, 2)
+    # the same steps as one cluster-persistent launch (instances dealt to
+    # thread-block clusters), from the same state
+    cl_ms = None
+    if info["lmax"] >= 4:
+        ts.tsat_step_clustered(st.h, hp, 1, stop_on_sat=False)      # bins and kernel attributes
+        torch.cuda.synchronize()
+        e0.record()
+        ts.tsat_step_clustered(st.h, hp, K, stop_on_sat=False)
+        e1.record()
+        torch.cuda.synchronize()
+        cl_ms = e0.elapsed_time(e1) / K
     # solve phase: fresh init, up to 1000 steps with solved instances frozen
     ts.tsat_init(st.h, hp)
     torch.cuda.synchronize()
@@ -711,6 +722,9 @@ def exp_batch(args):
            "samples_per_instance": 64, "n_vars": info["n_vars"], "n_clauses": info["n_clauses"], "nnz": info["nnz"],
            "lmax": info["lmax"], "steps": K, "ms_per_step": ms / K, "evals_per_s": info["nnz"] * 64 * K / (ms / 1e3),
            "kernel_ms": {"forward": kms[0], "gamma": kms[1], "update": kms[2]}, "tuning": tun,
+           "cluster_persistent": None if cl_ms is None else {
+               "ms_per_step": cl_ms, "evals_per_s": info["nnz"] * 64 / (cl_ms / 1e3),
+               "launch": f"one launch of {K} steps, thread-block clusters of 4 blocks"},
            "solve": {"steps_cap": args.solve_steps, "steps_run": done, "seconds": solve_s,
                      "solved": sum(d["solved"] for d in by_k.values()), "by_k": by_k},
            "generation_s": gen_s})

@@ -207,6 +207,24 @@ int tsat_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t st
 int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
                          cudaStream_t stream);
 
+/* The same n_steps steps for a batch whose instances are too large for one
+ * block, in one launch of thread-block clusters (4 blocks of 768 threads, one
+ * per SM, as many clusters as fit on the device).  The host deals the
+ * instances to the clusters so that each holds about the same number of
+ * literal occurrences (largest first, once per state); a cluster runs its
+ * instances one after another, every warp of its blocks on the same
+ * instance: the forward (Eq. 1) into per-block histograms, a cluster barrier,
+ * every block sums the histograms over distributed shared memory and forms
+ * Eq. 4 and the dL/dR table, the fused update of the instance's rows
+ * (straight-through backward, Eq. 5, AdamW, re-binarisation), a cluster
+ * barrier.  Results follow tsat_step (freezing, status records, step counter,
+ * stop_on_sat); FP32 sums may differ from it in rounding order.
+ * tsat_step_persistent takes this path by itself when an instance does not
+ * fit one block.  Requirements: the STE layer, hp->mix_restart = 0, a longest
+ * clause of 4..7 literals, N <= 128; else TSAT_EINVAL.  Async on `stream`. */
+int tsat_step_clustered(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
+                        cudaStream_t stream);
+
 /* Capture and instantiate the graph tsat_step(hp, n_steps, stop_on_sat) would
  * replay, without running it (keeps graph building out of timed regions). */
 int tsat_step_prepare(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat);

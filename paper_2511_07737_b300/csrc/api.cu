@@ -14,6 +14,7 @@ struct StatePlan {
   size_t hdr, inst, sp, z, m, v, bits, nu, hist, gamma, gdelta, S, unsat;
   size_t ehist, eunsat, gcol, sel, digits, selstate, outbits, small, part_var, part_val, fwdS, hist1;
   size_t lit, rbuf, dr16, zy, zs;
+  size_t cbins;
   size_t total;
 };
 
@@ -49,6 +50,7 @@ static StatePlan plan_state(const tsat_problem *p, int32_t N, int32_t layer, int
   S.part_val = take(TSAT_MAX_PARTIAL_K);
   S.fwdS = take(sizeof(float) * I * N);
   S.hist1 = take(sizeof(int32_t) * 32);
+  S.cbins = take(sizeof(int32_t) * (I + kMaxClusters + 1));
   if (layer == TSAT_LAYER_RELAXED) {
     S.lit = take((dt == TSAT_DTYPE_BF16 ? 2 : 4) * V * N);
     S.rbuf = take(sizeof(float) * (size_t)p->C * N);
@@ -306,6 +308,7 @@ int tsat_state_create(tsat_problem *p, void *d_state, size_t state_bytes, int32_
   s->part_val = (uint8_t *)(b + P.part_val);
   s->fwd_scratch = (float *)(b + P.fwdS);
   s->hist1 = (int32_t *)(b + P.hist1);
+  s->cl_bins = (int32_t *)(b + P.cbins);
   // what a step changes: the header, status records, step scalars, z, m, v,
   // both bit parities and nu (adjacent, from the start of the buffer), plus the
   // relaxed layer's literal values
@@ -450,8 +453,16 @@ int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps,
     return TSAT_EINVAL;
   }
   int32_t vmax = 0;
+  bool too_big = false;
   for (const InstInfo &I : p->inst) {
     vmax = std::max(vmax, I.n_vars);
+    too_big = too_big || (int64_t)I.n_clauses * I.lmax * s->N > kPersistMaxWork;
+  }
+  too_big = too_big || persist_smem_bytes(s->N, vmax, false) > kPersistMaxSmem;
+  // instances too large for one block: clusters of blocks, when the batch suits them
+  if (too_big && p->dev.rec_stride == 8 && s->N <= 128)
+    return tsat_step_clustered(s, hp, n_steps, stop_on_sat, stream);
+  for (const InstInfo &I : p->inst) {
     if ((int64_t)I.n_clauses * I.lmax * s->N > kPersistMaxWork) {
       set_error("instance too large for one block: %d clauses x %d literals x %d samples > %lld", I.n_clauses,
                 I.lmax, s->N, (long long)kPersistMaxWork);
@@ -469,6 +480,42 @@ int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps,
   const LrSched ls = make_sched(*hp);
   cudaError_t e = launch_persist(p->dev, s->dev, hy, ls, n_steps, vmax, resident, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "persistent solver");
+  return leave(s, stream);
+}
+
+int tsat_step_clustered(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
+                        cudaStream_t stream) {
+  int rc = check_step_args(s, hp, n_steps);
+  if (rc) return rc;
+  const tsat_problem *p = s->prob;
+  if (s->layer != TSAT_LAYER_STE || hp->mix_restart) {
+    set_error("the cluster solver runs the STE layer without assignment mixing");
+    return TSAT_EINVAL;
+  }
+  if (p->dev.rec_stride != 8 || s->N > 128) {
+    set_error("the cluster solver needs a longest clause of 4..7 literals and at most 128 samples (longest %d, N %d)",
+              p->lmax, s->N);
+    return TSAT_EINVAL;
+  }
+  if (s->cl_ncl == 0) {   // the launch's clusters and the instance bins, once per state
+    int ncl = std::min(cluster_grid_clusters(s->N), kMaxClusters);
+    if (ncl <= 0) {
+      set_error("no cluster of the solver fits on this device");
+      return TSAT_ECUDA;
+    }
+    std::vector<int32_t> ptr, list;
+    cluster_bins(p, ncl, ptr, list);
+    TSAT_CUDA(cudaMemcpy(s->cl_bins, ptr.data(), sizeof(int32_t) * ptr.size(), cudaMemcpyHostToDevice));
+    TSAT_CUDA(cudaMemcpy(s->cl_bins + ptr.size(), list.data(), sizeof(int32_t) * list.size(),
+                         cudaMemcpyHostToDevice));
+    s->cl_ncl = ncl;
+  }
+  if ((rc = enter(s, stream))) return rc;
+  const Hyper hy = make_hyper(*hp, stop_on_sat ? 1 : 0);
+  const LrSched ls = make_sched(*hp);
+  cudaError_t e = launch_cluster(p->dev, s->dev, hy, ls, n_steps, s->cl_ncl, s->cl_bins,
+                                 s->cl_bins + s->cl_ncl + 1, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cluster solver");
   return leave(s, stream);
 }
 

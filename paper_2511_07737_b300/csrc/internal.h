@@ -53,6 +53,7 @@ struct tsat_problem {
   tsat::Layout lay{};
   tsat::ProbDev dev{};
   std::vector<tsat::InstInfo> inst;  // host copy (lmax filled after the build)
+  std::vector<int64_t> inst_nnz;     // literal occurrences of each instance as loaded (before de-duplication)
   int set_items(int32_t item_clauses, cudaStream_t stream);
 };
 
@@ -74,6 +75,13 @@ int state_enter(tsat_state *s, cudaStream_t user);   // the state's stream waits
 int state_leave(tsat_state *s, cudaStream_t user);   // the caller's stream waits for the state's
 int update_grid(const tsat_state *s);                // blocks of the fused update
 int reset_state(tsat_state *s, cudaStream_t st);     // step counter and status records to their start
+// cluster-persistent solver (cluster.cu)
+constexpr int kMaxClusters = 256;
+int cluster_grid_clusters(int N);
+int cluster_smem_bytes(int N);
+void cluster_bins(const tsat_problem *p, int ncl, std::vector<int32_t> &ptr, std::vector<int32_t> &list);
+cudaError_t launch_cluster(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls, int32_t K,
+                           int ncl, const int32_t *bin_ptr, const int32_t *bin_inst, cudaStream_t st);
 }  // namespace tsat
 
 struct tsat_state {
@@ -109,5 +117,9 @@ struct tsat_state {
   void *h_stat = nullptr;           // pinned host copy of the header and status records (tsat_status)
   size_t h_stat_bytes = 0;
   std::map<GraphKey, cudaGraphExec_t> graphs;
+  // cluster-persistent solver: clusters of the launch and the instance bins
+  // (device arrays in the state buffer: bin offsets [ncl + 1], instances [n_inst])
+  int32_t cl_ncl = 0;
+  int32_t *cl_bins = nullptr;
   int32_t launches_per_step = 3;
 };

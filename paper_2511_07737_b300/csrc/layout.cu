@@ -453,6 +453,7 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
   char *w = (char *)d_ws;
   // host: instance table and global raw clause offsets
   p->inst.resize(n_inst);
+  p->inst_nnz.resize(n_inst);
   std::vector<int64_t> raw_cptr((size_t)s.C + 1);
   int64_t voff = 0, coff = 0, loff = 0;
   for (int32_t j = 0; j < n_inst; ++j) {
@@ -463,6 +464,7 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
     I.n_clauses = descs[j].n_clauses;
     I.lmax = 0;
     I.gid = j;
+    p->inst_nnz[j] = descs[j].h_clause_ptr[descs[j].n_clauses];
     for (int32_t c = 0; c < descs[j].n_clauses; ++c) raw_cptr[coff + c] = loff + descs[j].h_clause_ptr[c];
     voff += descs[j].n_vars;
     coff += descs[j].n_clauses;

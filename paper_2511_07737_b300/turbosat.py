@@ -84,6 +84,7 @@ def lib():
             "tsat_evaluate": (ctypes.c_int, [P, P, P, P, P, P]),
             "tsat_histogram": (ctypes.c_int, [P, P, P]),
             "tsat_step_persistent": (ctypes.c_int, [P, P, i32, i32, P]),
+            "tsat_step_clustered": (ctypes.c_int, [P, P, i32, i32, P]),
             "tsat_best": (ctypes.c_int, [P, P, i32, i32, P, P, P, P, P, P, P]),
             "tsat_partial_k": (i32, [i32]),
             "tsat_status": (ctypes.c_int, [P, P, P, P, P]),
@@ -252,6 +253,12 @@ def tsat_step_persistent(s, hp: tsat_hparams, n_steps: int, stop_on_sat: bool = 
     """n_steps steps of a batch of small instances in one launch (one block per instance)."""
     _ck(lib().tsat_step_persistent(s, ctypes.byref(hp), int(n_steps), int(bool(stop_on_sat)), _stream(stream)),
         "tsat_step_persistent")
+
+
+def tsat_step_clustered(s, hp: tsat_hparams, n_steps: int, stop_on_sat: bool = True, stream=None):
+    """n_steps steps of a batch of larger instances in one launch of thread-block clusters."""
+    _ck(lib().tsat_step_clustered(s, ctypes.byref(hp), int(n_steps), int(bool(stop_on_sat)), _stream(stream)),
+        "tsat_step_clustered")
 
 
 def tsat_step_prepare(s, hp: tsat_hparams, n_steps: int, stop_on_sat: bool = True):
