@@ -13,7 +13,9 @@
 //     h_l  = relu(Wl_t [h_l ; a_l ; h_{l^1}] + bl_t)
 //   logit_v = wo [h_{2v} ; h_{2v+1}] + bo
 // Every gradient of a gather is the opposite gather (no atomics); weight
-// gradients reduce per-block partials in a fixed order.
+// gradients reduce per-block partials in a fixed order.  The dense layers,
+// their input gradients and their weight gradients run on the tensor cores
+// (tcgen05.mma, mpnn_tc.cu).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -50,6 +52,7 @@ struct MpWs {  // activations kept for the backward pass
   __nv_bfloat16 *wb;               // BF16 copy of the parameters
   float *ldeg;                     // [2V] literal degrees
   float *dlog, *lossv;             // [V] dL/dlogit and per-variable loss terms
+  int *err;                        // set by a tensor-core layer whose completion wait timed out
 };
 constexpr int kPartBlocks = 256;
 
@@ -71,6 +74,7 @@ static size_t mp_ws_bytes(int64_t V, int64_t C) {
   add(sizeof(float) * L);
   add(sizeof(float) * V);
   add(sizeof(float) * V);
+  add(sizeof(int) * 4);
   return b;
 }
 
@@ -96,6 +100,7 @@ static MpWs mp_ws_plan(void *base, int64_t V, int64_t C) {
   w.ldeg = (float *)take(sizeof(float) * L);
   w.dlog = (float *)take(sizeof(float) * V);
   w.lossv = (float *)take(sizeof(float) * V);
+  w.err = (int *)take(sizeof(int) * 4);
   return w;
 }
 
@@ -118,43 +123,20 @@ __global__ void k_mp_feat(ProbDev pd, float *ldeg, float *feat) {
   }
 }
 
-// Y[r][0:64] = act( sum_j X_j[r ^ xj][0:Kj] . W[:, offs_j]^T + b ),  W bf16 [64][Ktot]
 struct DIn {
   const float *x;
   int K, xr;
 };
-template <int NIN>
-__global__ void __launch_bounds__(256) k_mp_dense(DIn i0, DIn i1, DIn i2, int64_t M, const __nv_bfloat16 *W,
-                                                  const __nv_bfloat16 *bias, int relu, float *Y) {
-  extern __shared__ float ws[];   // [Ktot][64] (transposed weights)
-  const int Kt = i0.K + (NIN > 1 ? i1.K : 0) + (NIN > 2 ? i2.K : 0);
-  for (int k = threadIdx.x; k < Kt * kH; k += blockDim.x) {
-    const int o = k / Kt, kk = k % Kt;
-    ws[kk * kH + o] = __bfloat162float(W[o * Kt + kk]);
-  }
-  __syncthreads();
-  const int o = threadIdx.x & 63, rsub = threadIdx.x >> 6;   // 4 rows per pass
-  const float bo = __bfloat162float(bias[o]);
-  for (int64_t r = (int64_t)blockIdx.x * 4 + rsub; r < M; r += (int64_t)gridDim.x * 4) {
-    float acc = bo;
-    int koff = 0;
-    {
-      const float *x = i0.x + (r ^ i0.xr) * i0.K;
-      for (int k = 0; k < i0.K; ++k) acc = fmaf(x[k], ws[(koff + k) * kH + o], acc);
-      koff += i0.K;
-    }
-    if (NIN > 1) {
-      const float *x = i1.x + (r ^ i1.xr) * i1.K;
-      for (int k = 0; k < i1.K; ++k) acc = fmaf(x[k], ws[(koff + k) * kH + o], acc);
-      koff += i1.K;
-    }
-    if (NIN > 2) {
-      const float *x = i2.x + (r ^ i2.xr) * i2.K;
-      for (int k = 0; k < i2.K; ++k) acc = fmaf(x[k], ws[(koff + k) * kH + o], acc);
-    }
-    Y[r * kH + o] = relu ? fmaxf(acc, 0.f) : acc;
-  }
-}
+
+// tensor-core dense layers (mpnn_tc.cu)
+cudaError_t mp_dense_tc(int nin, const float *x0, int k0, int xr0, const float *x1, int k1, int xr1, const float *x2,
+                        int k2, int xr2, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias, int relu,
+                        float *Y, int *err, cudaStream_t st);
+cudaError_t mp_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, int Ktot, int koff, float *dX, int accumulate,
+                     int xr, int *err, cudaStream_t st);
+int mp_wgrad_tc(const float *dZ, int64_t M, int nin, const float *x0, int k0, int xr0, const float *x1, int k1,
+                int xr1, const float *x2, int k2, int xr2, float *part, int max_blocks, int *err, cudaStream_t st,
+                cudaError_t *e);
 
 // m_c = mean_{l in c} h_l
 __global__ void k_mp_clause_mean(ProbDev pd, const float *h, float *m) {
@@ -226,48 +208,6 @@ __global__ void k_mp_out_bwd(ProbDev pd, const float *dlog, const __nv_bfloat16 
 __global__ void k_mp_relu_bwd(const float *Y, float *dY, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     if (!(Y[i] > 0.f)) dY[i] = 0.f;
-}
-
-// dX[r][0:K] = dZ[r][0:64] . W[0:64][koff : koff+K]   (one input slice)
-__global__ void __launch_bounds__(256) k_mp_dx(const float *dZ, int64_t M, const __nv_bfloat16 *W, int Ktot, int koff,
-                                               int K, float *dX, int accumulate, int xr) {
-  extern __shared__ float ws2[];   // [64][K]
-  for (int k = threadIdx.x; k < kH * K; k += blockDim.x) {
-    const int o = k / K, kk = k % K;
-    ws2[o * K + kk] = __bfloat162float(W[o * Ktot + koff + kk]);
-  }
-  __syncthreads();
-  const int per = blockDim.x / K;   // rows per pass
-  const int kk = threadIdx.x % K, rsub = threadIdx.x / K;
-  if (rsub >= per) return;
-  for (int64_t r = (int64_t)blockIdx.x * per + rsub; r < M; r += (int64_t)gridDim.x * per) {
-    const float *dz = dZ + r * kH;
-    float acc = 0.f;
-    for (int o = 0; o < kH; ++o) acc = fmaf(dz[o], ws2[o * K + kk], acc);
-    float *dst = dX + (r ^ xr) * K + kk;
-    *dst = accumulate ? *dst + acc : acc;
-  }
-}
-
-// partial weight gradients: part[b][o][k] = sum_{rows of block b} dZ[r][o] X[r^xr][k]; db in column K
-__global__ void __launch_bounds__(256) k_mp_wgrad(const float *dZ, int64_t M, DIn i0, DIn i1, DIn i2, int nin,
-                                                  float *part) {
-  const int Kt = i0.K + (nin > 1 ? i1.K : 0) + (nin > 2 ? i2.K : 0);
-  const int ncol = Kt + 1;                 // + bias column
-  float *out = part + (size_t)blockIdx.x * kH * ncol;
-  const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
-  for (int idx = threadIdx.x; idx < kH * ncol; idx += blockDim.x) {
-    const int o = idx / ncol, k = idx % ncol;
-    const float *xp;
-    int K, xr, kk;
-    if (k == Kt) { xp = nullptr; K = 0; xr = 0; kk = 0; }
-    else if (k < i0.K) { xp = i0.x; K = i0.K; xr = i0.xr; kk = k; }
-    else if (k < i0.K + i1.K) { xp = i1.x; K = i1.K; xr = i1.xr; kk = k - i0.K; }
-    else { xp = i2.x; K = i2.K; xr = i2.xr; kk = k - i0.K - i1.K; }
-    float acc = 0.f;
-    for (int64_t r = r0; r < r1; ++r) acc = fmaf(dZ[r * kH + o], xp ? xp[(r ^ xr) * K + kk] : 1.0f, acc);
-    out[idx] = acc;
-  }
 }
 
 // grad[W(o,k)] (+)= sum_b part[b][o][k], bias into gbias[o]
@@ -386,33 +326,28 @@ static int grid_for(int64_t work, int per_block) {
 }
 
 static cudaError_t dense(int nin, DIn a, DIn b, DIn c, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias,
-                         int relu, float *Y, cudaStream_t st) {
-  const int Kt = a.K + (nin > 1 ? b.K : 0) + (nin > 2 ? c.K : 0);
-  const size_t smem = sizeof(float) * Kt * kH;
-  const int g = grid_for(M, 4 * 16);
-  if (nin == 1) k_mp_dense<1><<<g, 256, smem, st>>>(a, b, c, M, W, bias, relu, Y);
-  else if (nin == 2) k_mp_dense<2><<<g, 256, smem, st>>>(a, b, c, M, W, bias, relu, Y);
-  else k_mp_dense<3><<<g, 256, smem, st>>>(a, b, c, M, W, bias, relu, Y);
-  return cudaGetLastError();
+                         int relu, float *Y, int *err, cudaStream_t st) {
+  return mp_dense_tc(nin, a.x, a.K, a.xr, b.x, b.K, b.xr, c.x, c.K, c.xr, M, W, bias, relu, Y, err, st);
 }
 
 static int mp_forward(const tsat_problem *p, const float *params, MpWs &w, float *logits, cudaStream_t st) {
   const ProbDev &pd = p->dev;
   const int64_t L = 2 * (int64_t)p->V, C = p->C;
+  TSAT_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   k_mp_to_bf16<<<64, 256, 0, st>>>(params, w.wb, kNParams);
   k_mp_feat<<<grid_for(p->V, 256), 256, 0, st>>>(pd, w.ldeg, w.feat);
   TSAT_LAUNCH_CHECK("mpnn features");
   DIn none{nullptr, 0, 0};
-  cudaError_t e = dense(1, DIn{w.feat, kFeat, 0}, none, none, L, w.wb + kOffW0, w.wb + kOffB0, 1, w.h[0], st);
+  cudaError_t e = dense(1, DIn{w.feat, kFeat, 0}, none, none, L, w.wb + kOffW0, w.wb + kOffB0, 1, w.h[0], w.err, st);
   if (e != cudaSuccess) return cuda_fail(e, "mpnn input layer");
   for (int t = 0; t < kLayers; ++t) {
     k_mp_clause_mean<<<grid_for(C * 32, 256), 256, 0, st>>>(pd, w.h[t], w.m[t]);
-    if ((e = dense(1, DIn{w.m[t], kH, 0}, none, none, C, w.wb + off_wc(t), w.wb + off_bc(t), 1, w.e[t], st)) !=
+    if ((e = dense(1, DIn{w.m[t], kH, 0}, none, none, C, w.wb + off_wc(t), w.wb + off_bc(t), 1, w.e[t], w.err, st)) !=
         cudaSuccess)
       return cuda_fail(e, "mpnn clause layer");
     k_mp_lit_mean<<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.e[t], w.ldeg, w.a[t]);
     if ((e = dense(3, DIn{w.h[t], kH, 0}, DIn{w.a[t], kH, 0}, DIn{w.h[t], kH, 1}, L, w.wb + off_wl(t),
-                   w.wb + off_bl(t), 1, w.h[t + 1], st)) != cudaSuccess)
+                   w.wb + off_bl(t), 1, w.h[t + 1], w.err, st)) != cudaSuccess)
       return cuda_fail(e, "mpnn literal layer");
   }
   if (logits) k_mp_out<<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.h[kLayers], w.wb, logits);
@@ -421,20 +356,21 @@ static int mp_forward(const tsat_problem *p, const float *params, MpWs &w, float
 }
 
 static int wgrad(int nin, DIn a, DIn b, DIn c, const float *dZ, int64_t M, float *part, float *gW, float *gb,
-                 cudaStream_t st) {
+                 int *err, cudaStream_t st) {
   const int Kt = a.K + (nin > 1 ? b.K : 0) + (nin > 2 ? c.K : 0);
-  const int nb = (int)std::min<int64_t>(kPartBlocks, std::max<int64_t>(1, M / 64));
-  k_mp_wgrad<<<nb, 256, 0, st>>>(dZ, M, a, b, c, nin, part);
+  cudaError_t e = cudaSuccess;
+  const int nb = mp_wgrad_tc(dZ, M, nin, a.x, a.K, a.xr, b.x, b.K, b.xr, c.x, c.K, c.xr, part, kPartBlocks, err, st, &e);
+  if (e != cudaSuccess) return cuda_fail(e, "mpnn weight gradient");
   k_mp_wgrad_reduce<<<(kH * (Kt + 1) + 255) / 256, 256, 0, st>>>(part, nb, Kt, gW, gb);
   TSAT_LAUNCH_CHECK("mpnn weight gradient");
   return TSAT_OK;
 }
 
 static int dx(const float *dZ, int64_t M, const __nv_bfloat16 *W, int Ktot, int koff, int K, float *dX, int acc,
-              int xr, cudaStream_t st) {
-  const int per = 256 / K;
-  k_mp_dx<<<grid_for(M, per * 8), 256, sizeof(float) * kH * K, st>>>(dZ, M, W, Ktot, koff, K, dX, acc, xr);
-  TSAT_LAUNCH_CHECK("mpnn input gradient");
+              int xr, int *err, cudaStream_t st) {
+  if (K != kH) { set_error("mpnn input gradient of a %d-wide slice", K); return TSAT_EINVAL; }
+  cudaError_t e = mp_dx_tc(dZ, M, W, Ktot, koff, dX, acc, xr, err, st);
+  if (e != cudaSuccess) return cuda_fail(e, "mpnn input gradient");
   return TSAT_OK;
 }
 
@@ -455,19 +391,20 @@ static int mp_backward(const tsat_problem *p, MpWs &w, const float *dlog, float 
     // literal layer: h[t+1] = relu(Wl [h[t]; a[t]; h[t]^1] + bl)
     k_mp_relu_bwd<<<grid_for(L * kH, 256), 256, 0, st>>>(w.h[t + 1], w.dh, L * kH);
     if ((rc = wgrad(3, DIn{w.h[t], kH, 0}, DIn{w.a[t], kH, 0}, DIn{w.h[t], kH, 1}, w.dh, L, w.part,
-                    grad + off_wl(t), grad + off_bl(t), st)))
+                    grad + off_wl(t), grad + off_bl(t), w.err, st)))
       return rc;
     const __nv_bfloat16 *Wl = w.wb + off_wl(t);
-    if ((rc = dx(w.dh, L, Wl, 3 * kH, 0, kH, w.dh2, 0, 0, st))) return rc;         // from h_l
-    if ((rc = dx(w.dh, L, Wl, 3 * kH, 2 * kH, kH, w.dh2, 1, 1, st))) return rc;    // from h_{l^1}
-    if ((rc = dx(w.dh, L, Wl, 3 * kH, kH, kH, w.da, 0, 0, st))) return rc;         // from a_l
+    if ((rc = dx(w.dh, L, Wl, 3 * kH, 0, kH, w.dh2, 0, 0, w.err, st))) return rc;         // from h_l
+    if ((rc = dx(w.dh, L, Wl, 3 * kH, 2 * kH, kH, w.dh2, 1, 1, w.err, st))) return rc;    // from h_{l^1}
+    if ((rc = dx(w.dh, L, Wl, 3 * kH, kH, kH, w.da, 0, 0, w.err, st))) return rc;         // from a_l
     // a = mean over owning clauses of e  ->  de
     k_mp_clause_from_lit<<<grid_for(C * 32, 256), 256, 0, st>>>(pd, w.da, w.ldeg, w.de);
     // clause layer: e = relu(Wc m + bc)
     k_mp_relu_bwd<<<grid_for(C * kH, 256), 256, 0, st>>>(w.e[t], w.de, C * kH);
-    if ((rc = wgrad(1, DIn{w.m[t], kH, 0}, none, none, w.de, C, w.part, grad + off_wc(t), grad + off_bc(t), st)))
+    if ((rc = wgrad(1, DIn{w.m[t], kH, 0}, none, none, w.de, C, w.part, grad + off_wc(t), grad + off_bc(t), w.err,
+                    st)))
       return rc;
-    if ((rc = dx(w.de, C, w.wb + off_wc(t), kH, 0, kH, w.dm, 0, 0, st))) return rc;
+    if ((rc = dx(w.de, C, w.wb + off_wc(t), kH, 0, kH, w.dm, 0, 0, w.err, st))) return rc;
     // m = mean of h over the clause's literals -> dh2 += ...
     k_mp_lit_from_clause<<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.dm, w.dh2);
     TSAT_LAUNCH_CHECK("mpnn layer backward");
@@ -475,7 +412,8 @@ static int mp_backward(const tsat_problem *p, MpWs &w, const float *dlog, float 
   }
   // input layer
   k_mp_relu_bwd<<<grid_for(L * kH, 256), 256, 0, st>>>(w.h[0], w.dh, L * kH);
-  if ((rc = wgrad(1, DIn{w.feat, kFeat, 0}, none, none, w.dh, L, w.part, grad + kOffW0, grad + kOffB0, st))) return rc;
+  if ((rc = wgrad(1, DIn{w.feat, kFeat, 0}, none, none, w.dh, L, w.part, grad + kOffW0, grad + kOffB0, w.err, st)))
+    return rc;
   return TSAT_OK;
 }
 
