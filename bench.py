@@ -739,11 +739,19 @@ def exp_relaxed(args):
     from paper_2511_07737_b300 import turbosat as ts
     n = int(2_000_000 * args.scale)
     inst = cnfgen.structured_mixed(n, 4 * n, 5)
-    prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
-    info = prob.info
-    res = {"experiment": "relaxed", "n_vars": info["n_vars"], "n_clauses": info["n_clauses"], "nnz": info["nnz"],
-           "lmax": info["lmax"], "samples": 256, "results": {}}
-    for name, dt in (("fp32", ts.DTYPE_F32), ("bf16", ts.DTYPE_BF16)):
+    res = {"experiment": "relaxed", "samples": 256, "results": {}}
+    loads = {}
+    for loc in (True, False):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loads[loc] = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)], locality=loc)
+        torch.cuda.synchronize()
+        res["load_seconds_" + ("locality" if loc else "given_order")] = time.perf_counter() - t0
+    info = loads[True].info
+    res.update({"n_vars": info["n_vars"], "n_clauses": info["n_clauses"], "nnz": info["nnz"], "lmax": info["lmax"]})
+    for name, dt, loc in (("fp32", ts.DTYPE_F32, True), ("bf16", ts.DTYPE_BF16, True),
+                          ("fp32_given_clause_order", ts.DTYPE_F32, False)):
+        prob = loads[loc]
         st = ts.State(prob, 256, ts.LAYER_RELAXED, dt)
         hp = ts.hparams(seed=3, norm=1, layer=ts.LAYER_RELAXED)
         ts.tsat_init(st.h, hp)

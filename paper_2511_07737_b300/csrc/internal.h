@@ -54,6 +54,7 @@ struct tsat_problem {
   tsat::ProbDev dev{};
   std::vector<tsat::InstInfo> inst;  // host copy (lmax filled after the build)
   std::vector<int64_t> inst_nnz;     // literal occurrences of each instance as loaded (before de-duplication)
+  std::vector<int32_t> cperm;        // clause order of a locality load: loaded clause -> caller's index (else empty)
   int set_items(int32_t item_clauses, cudaStream_t stream);
 };
 

@@ -429,7 +429,14 @@ int tsat_problem_bytes(int32_t n_inst, const tsat_cnf_desc *descs, size_t *ws_by
 
 int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size_t ws_bytes,
                     cudaStream_t stream, tsat_problem **out) {
+  return tsat_load_batch_ex(n_inst, descs, 0u, d_ws, ws_bytes, stream, out);
+}
+
+int tsat_load_batch_ex(int32_t n_inst, const tsat_cnf_desc *descs, uint32_t flags, void *d_ws, size_t ws_bytes,
+                       cudaStream_t stream, tsat_problem **out) {
   if (!out || !d_ws) { set_error("NULL output or workspace"); return TSAT_EINVAL; }
+  if (flags & ~(uint32_t)TSAT_LOAD_CLAUSE_LOCALITY) { set_error("unknown load flags %#x", flags); return TSAT_EINVAL; }
+  const bool locality = (flags & TSAT_LOAD_CLAUSE_LOCALITY) != 0;
   *out = nullptr;
   Sizes s;
   int rc = measure(n_inst, descs, &s);
@@ -455,6 +462,11 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
   p->inst.resize(n_inst);
   p->inst_nnz.resize(n_inst);
   std::vector<int64_t> raw_cptr((size_t)s.C + 1);
+  // clause order: as given, or (locality) each instance's clauses ordered by
+  // their smallest variable, ties in the given order (a counting sort);
+  // cperm maps a loaded clause to its index in the caller's batch
+  std::vector<std::vector<int32_t>> plits(locality ? n_inst : 0);
+  if (locality) p->cperm.resize((size_t)s.C);
   int64_t voff = 0, coff = 0, loff = 0;
   for (int32_t j = 0; j < n_inst; ++j) {
     InstInfo &I = p->inst[j];
@@ -464,11 +476,38 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
     I.n_clauses = descs[j].n_clauses;
     I.lmax = 0;
     I.gid = j;
-    p->inst_nnz[j] = descs[j].h_clause_ptr[descs[j].n_clauses];
-    for (int32_t c = 0; c < descs[j].n_clauses; ++c) raw_cptr[coff + c] = loff + descs[j].h_clause_ptr[c];
+    const int64_t *cp = descs[j].h_clause_ptr;
+    p->inst_nnz[j] = cp[descs[j].n_clauses];
+    if (!locality) {
+      for (int32_t c = 0; c < descs[j].n_clauses; ++c) raw_cptr[coff + c] = loff + cp[c];
+    } else {
+      const int32_t nc = descs[j].n_clauses, nv = descs[j].n_vars;
+      const int32_t *lits = descs[j].h_lits;
+      std::vector<int32_t> key((size_t)nc), start((size_t)nv + 2, 0);
+      for (int32_t c = 0; c < nc; ++c) {
+        int32_t mn = nv;   // empty or invalid clauses last (the build reports them)
+        for (int64_t k = cp[c]; k < cp[c + 1]; ++k) {
+          const int32_t a = lits[k] < 0 ? -lits[k] : lits[k];
+          if (a >= 1 && a <= nv) mn = std::min(mn, a - 1);
+        }
+        key[c] = mn;
+        ++start[mn + 1];
+      }
+      for (int32_t v = 0; v <= nv; ++v) start[v + 1] += start[v];
+      std::vector<int32_t> order((size_t)nc);
+      for (int32_t c = 0; c < nc; ++c) order[start[key[c]]++] = c;
+      std::vector<int32_t> &pl = plits[j];
+      pl.reserve((size_t)cp[nc]);
+      for (int32_t q = 0; q < nc; ++q) {
+        const int32_t c = order[q];
+        raw_cptr[coff + q] = loff + (int64_t)pl.size();
+        pl.insert(pl.end(), lits + cp[c], lits + cp[c + 1]);
+        p->cperm[coff + q] = (int32_t)(coff + c);
+      }
+    }
     voff += descs[j].n_vars;
     coff += descs[j].n_clauses;
-    loff += descs[j].h_clause_ptr[descs[j].n_clauses];
+    loff += cp[descs[j].n_clauses];
   }
   raw_cptr[s.C] = loff;
   auto fail = [&](int code) { delete p; return code; };
@@ -478,7 +517,7 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
   int64_t lo = 0;
   for (int32_t j = 0; j < n_inst; ++j) {
     int64_t n = descs[j].h_clause_ptr[descs[j].n_clauses];
-    if (n) CK(cudaMemcpyAsync(w + L.raw_lits + sizeof(int32_t) * lo, descs[j].h_lits,
+    if (n) CK(cudaMemcpyAsync(w + L.raw_lits + sizeof(int32_t) * lo, locality ? plits[j].data() : descs[j].h_lits,
                               sizeof(int32_t) * n, cudaMemcpyHostToDevice, stream));
     lo += n;
   }
@@ -506,6 +545,7 @@ int tsat_load_batch(int32_t n_inst, const tsat_cnf_desc *descs, void *d_ws, size
   if (herr != ~0ull) {
     int code = (int)(herr & 0xFF);
     long long c = (long long)(herr >> 8);
+    if (!p->cperm.empty() && c >= 0 && c < (long long)p->cperm.size()) c = p->cperm[(size_t)c];
     set_error("clause %lld (global index) is invalid", c);
     return fail(code == 1 ? TSAT_EVAR : code == 2 ? TSAT_EEMPTY : TSAT_ELEN);
   }
@@ -608,6 +648,14 @@ int tsat_problem_csr(const tsat_problem *p, int32_t *h_cptr, int32_t *h_clit) {
   if (!p || !h_cptr || !h_clit) return TSAT_EINVAL;
   TSAT_CUDA(cudaMemcpy(h_cptr, p->dev.cptr, sizeof(int32_t) * (p->C + 1), cudaMemcpyDeviceToHost));
   TSAT_CUDA(cudaMemcpy(h_clit, p->dev.clit, sizeof(int32_t) * p->nnz, cudaMemcpyDeviceToHost));
+  if (!p->cperm.empty()) {   // back to the caller's clause order
+    std::vector<int32_t> cp(h_cptr, h_cptr + p->C + 1), cl(h_clit, h_clit + p->nnz), len((size_t)p->C);
+    for (int32_t q = 0; q < p->C; ++q) len[(size_t)p->cperm[q]] = cp[q + 1] - cp[q];
+    h_cptr[0] = 0;
+    for (int32_t c = 0; c < p->C; ++c) h_cptr[c + 1] = h_cptr[c] + len[c];
+    for (int32_t q = 0; q < p->C; ++q)
+      std::copy(cl.begin() + cp[q], cl.begin() + cp[q + 1], h_clit + h_cptr[p->cperm[q]]);
+  }
   return TSAT_OK;
 }
 

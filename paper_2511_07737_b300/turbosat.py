@@ -71,6 +71,7 @@ def lib():
             "tsat_problem_bytes": (ctypes.c_int, [i32, P, P]),
             "tsat_load_batch": (ctypes.c_int, [i32, P, P, sz, P, P]),
             "tsat_load": (ctypes.c_int, [i32, i32, P, P, P, sz, P, P]),
+            "tsat_load_batch_ex": (ctypes.c_int, [i32, P, ctypes.c_uint32, P, sz, P, P]),
             "tsat_problem_free": (None, [P]),
             "tsat_problem_info": (ctypes.c_int, [P, P]),
             "tsat_problem_csr": (ctypes.c_int, [P, P, P]),
@@ -178,11 +179,14 @@ def tsat_problem_bytes(instances) -> int:
     return int(out.value)
 
 
-def tsat_load_batch(instances, ws: torch.Tensor, stream=None) -> ctypes.c_void_p:
+LOAD_CLAUSE_LOCALITY = 1
+
+
+def tsat_load_batch(instances, ws: torch.Tensor, stream=None, flags: int = 0) -> ctypes.c_void_p:
     arr, keep = _descs(instances)
     h = ctypes.c_void_p()
-    _ck(lib().tsat_load_batch(len(instances), arr, _ptr(ws), ws.numel() * ws.element_size(), _stream(stream),
-                              ctypes.byref(h)), "tsat_load_batch")
+    _ck(lib().tsat_load_batch_ex(len(instances), arr, int(flags), _ptr(ws), ws.numel() * ws.element_size(),
+                                 _stream(stream), ctypes.byref(h)), "tsat_load_batch")
     return h
 
 
@@ -414,10 +418,12 @@ def _device_buffer(nbytes: int, device) -> torch.Tensor:
 class Problem:
     """A loaded batch of CNFs: the library handle plus its workspace tensor."""
 
-    def __init__(self, instances, device="cuda", stream=None):
+    def __init__(self, instances, device="cuda", stream=None, locality: bool = False):
+        """locality: store each instance's clauses ordered by their smallest
+        variable (TSAT_LOAD_CLAUSE_LOCALITY; for the relaxed layer)."""
         self.instances = [(int(n), np.asarray(p), np.asarray(l)) for (n, p, l) in instances]
         self.ws = _device_buffer(tsat_problem_bytes(self.instances), device)
-        self.h = tsat_load_batch(self.instances, self.ws, stream)
+        self.h = tsat_load_batch(self.instances, self.ws, stream, LOAD_CLAUSE_LOCALITY if locality else 0)
         self.info = tsat_problem_info(self.h)
         self.var_offsets = np.concatenate([[0], np.cumsum([n for (n, _, _) in self.instances])]).astype(np.int64)
 

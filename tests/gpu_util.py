@@ -68,8 +68,8 @@ def lockstep(cnfs, offsets, hp, t, snap):
     return z, m, v, res
 
 
-def make(instances, N, layer=ts.LAYER_STE, dtype=ts.DTYPE_F32):
-    prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in instances])
+def make(instances, N, layer=ts.LAYER_STE, dtype=ts.DTYPE_F32, locality=False):
+    prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in instances], locality=locality)
     st = ts.State(prob, N, layer, dtype)
     cnfs = [oracle.CNF(i.n_vars, i.clause_ptr, i.lits) for i in instances]
     return prob, st, cnfs

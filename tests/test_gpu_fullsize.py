@@ -118,7 +118,8 @@ def _bit_columns(words: np.ndarray, cols: np.ndarray) -> np.ndarray:
 @pytest.fixture(scope="module")
 def structured():
     inst = cnfgen.structured_mixed(2_000_000, 8_000_000, 5)
-    prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
+    # loaded as the relaxed experiment loads it: clauses ordered by smallest variable
+    prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)], locality=True)
     return inst, prob, oracle.CNF(inst.n_vars, inst.clause_ptr, inst.lits)
 
 

@@ -24,9 +24,13 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def test_layout_matches_oracle_parse():
+@pytest.mark.parametrize("locality", [False, True])
+def test_layout_matches_oracle_parse(locality):
+    """The device CSR equals the oracle's parse; with the locality load the
+    clauses are stored ordered by their smallest variable and exported in the
+    caller's order."""
     inst = cnfgen.tiny_random(40, 300, 3, kmin=1, kmax=9)     # duplicates and tautologies
-    prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
+    prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)], locality=locality)
     cptr, clit = ts.tsat_problem_csr(prob.h)
     cnf = oracle.CNF(inst.n_vars, inst.clause_ptr, inst.lits)
     np.testing.assert_array_equal(cptr.astype(np.int64), cnf.cptr)
@@ -35,6 +39,38 @@ def test_layout_matches_oracle_parse():
         ref = sorted(((cnf.var[j] << 1) | cnf.neg[j]) for j in range(cnf.cptr[c], cnf.cptr[c + 1]))
         assert gpu == ref
     assert prob.info["lmax"] == cnf.lmax
+
+
+def test_locality_load_keeps_results_and_numbering():
+    """A batch loaded with its clauses ordered by smallest variable gives the
+    same integer results and the same (up to FP32 summation order) state as the
+    caller's order: unsatisfied counts exactly, the relaxed layer's m / v within
+    1e-5 and z within its AdamW bound after a step; errors name the caller's
+    clause index."""
+    insts = [cnfgen.structured_mixed(3000, 12000, 21, communities=8), cnfgen.planted_ksat(500, 2100, 3, 4)]
+    hp = ts.hparams(seed=5, norm=1, layer=ts.LAYER_RELAXED, tau=1.1)
+    outs = []
+    for loc in (False, True):
+        prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in insts], locality=loc)
+        st = ts.State(prob, 64, ts.LAYER_RELAXED)
+        ts.tsat_init(st.h, hp)
+        ts.tsat_step(st.h, hp, 1, stop_on_sat=False)
+        u = torch.zeros(2 * 64, dtype=torch.int32, device="cuda")
+        sm = torch.zeros(4, dtype=torch.int32, device="cuda")
+        ts.tsat_evaluate(st.h, hp, u, sm)
+        outs.append((snapshot(st), u.cpu().numpy()))
+    (a, ua), (b, ub) = outs
+    np.testing.assert_array_equal(ua, ub)
+    # one step from the same init: m, v to 1e-5; z to the first-order AdamW
+    # bound of its m / v differences (where |g| is near eps the update is
+    # ill-conditioned, as in the oracle lock-step)
+    assert_adamw_z(b["z"], a["z"].astype(np.float64), b["m"], a["m"].astype(np.float64), b["v"],
+                   a["v"].astype(np.float64), 0, hp)
+    bad_ptr = np.array([0, 2, 4, 4, 6], np.int64)
+    bad_lits = np.array([3, -2, 1, 2, 2, 1], np.int32)       # clause 2 (caller's order) is empty
+    with pytest.raises(ts.TsatError) as e:
+        ts.Problem([(3, bad_ptr, bad_lits)], locality=True)
+    assert e.value.status == -3 and "clause 2 " in str(e.value)
 
 
 @pytest.mark.parametrize("bad,status", [
@@ -181,10 +217,11 @@ def test_autograd_hooks_match_oracle_gradient(norm, k, N):
     assert rel_err(grad.cpu().numpy(), g) < TOL_F32
 
 
-@pytest.mark.parametrize("dtype,tol", [(ts.DTYPE_F32, TOL_F32), (ts.DTYPE_BF16, TOL_BF16)])
-def test_lockstep_relaxed(dtype, tol):
+@pytest.mark.parametrize("dtype,tol,locality", [(ts.DTYPE_F32, TOL_F32, False), (ts.DTYPE_BF16, TOL_BF16, False),
+                                                (ts.DTYPE_F32, TOL_F32, True), (ts.DTYPE_BF16, TOL_BF16, True)])
+def test_lockstep_relaxed(dtype, tol, locality):
     inst = cnfgen.structured_mixed(1024, 4000, 5, communities=8)
-    prob, st, cnfs = make([inst], 64, layer=ts.LAYER_RELAXED, dtype=dtype)
+    prob, st, cnfs = make([inst], 64, layer=ts.LAYER_RELAXED, dtype=dtype, locality=locality)
     hp = ts.hparams(seed=5, norm=1, layer=ts.LAYER_RELAXED, tau=1.1)
     ts.tsat_init(st.h, hp)
     for t in range(3):
