@@ -161,17 +161,20 @@ def kernel_sha():
 
 
 def traffic_for(kernel, workload):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source."""
+    """(DRAM bytes per launch, how they were obtained) from a committed ncu
+    summary, if it was taken on the current kernel source; (None, reason)
+    otherwise."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
     except (OSError, ValueError):
-        return None
+        return None, "no ncu summary"
     e = d.get(f"{kernel}:{workload}")
-    if not e or e.get("kernel_sha") != kernel_sha():
-        return None
-    return e.get("bytes_per_launch")
+    if not e:
+        return None, "no ncu summary for this workload"
+    if e.get("kernel_sha") != kernel_sha():
+        return None, "kernel source changed since the ncu capture"
+    return e.get("bytes_per_launch"), e.get("source")
 
 
 def host_description() -> dict:
@@ -378,10 +381,11 @@ def ours(args, w, rank, world, local):
     ub = update_bytes(info, N)
     ach = ub / (t_upd / 1e3) / 1e9
     fb = forward_bytes(info, N)
+    traffic, traffic_note = traffic_for("k_update", args.workload)
     roof = {"bound": "hbm", "kernel": "k_update (fused STE backward + Eq. 5 + AdamW + Philox binarise)",
             "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": peak_note,
             "algorithmic_bytes_per_launch": ub, "launch_ms": t_upd,
-            "traffic": traffic_for("k_update", args.workload),
+            "traffic": traffic, "traffic_note": traffic_note,
             "share_of_step": t_upd / (t_fwd + t_gamma + t_upd),
             "forward": {"launch_ms": t_fwd, "algorithmic_bytes_per_launch": fb,
                         "achieved_gbs": fb / (t_fwd / 1e3) / 1e9,
