@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-SAT sub-object of the default line")
     ap.add_argument("--experiment", default="throughput",
-                    choices=["throughput", "time_to_sat", "batch", "relaxed", "proposer", "mixing", "literal_rows"],
+                    choices=["throughput", "time_to_sat", "batch", "relaxed", "proposer", "proposer_step", "mixing",
+                             "literal_rows"],
                     help="throughput (default, the driver's line) or one of the other workloads")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the experiment workloads (quick runs)")
     ap.add_argument("--solve-steps", type=int, default=1000, help="step cap of the batch experiment's solve phase")
@@ -810,6 +811,46 @@ def exp_proposer(args):
            "eval_4sat_ratio_9.0": r_hard, "eval_4sat_0.6x_threshold": r_easy})
 
 
+def exp_proposer_step(args):
+    """Proposer kernels alone: one training step (forward, loss, backward) and
+    one forward of the message-passing network on a graph of 64 planted
+    instances (3- and 5-SAT, n 2,000-5,000, 0.9 x threshold), CUDA events on
+    the library stream, 3 warm-up calls, then 10 timed calls of each."""
+    import torch
+    from paper_2511_07737_b300 import cnfgen
+    from paper_2511_07737_b300 import turbosat as ts
+    n_inst = max(4, int(64 * args.scale))
+    insts = cnfgen.batch_ksat(n_inst, 101, n_lo=2000, n_hi=5000, ks=[3, 5], ratio_scale=0.9)
+    prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in insts])
+    n_par = ts.tsat_mpnn_param_count()
+    params = torch.empty(n_par, device="cuda")
+    ts.tsat_mpnn_init(params, 7)
+    ws = torch.empty((ts.tsat_mpnn_workspace_bytes(prob.h) + 7) // 8, dtype=torch.int64, device="cuda")
+    V = prob.info["n_vars"]
+    y = torch.tensor(np.concatenate([i.planted for i in insts]).astype(np.uint8), device="cuda")
+    logits = torch.empty(V, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros(n_par, device="cuda")
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_step = timed(lambda: ts.tsat_mpnn_loss_grad(prob.h, params, ws, y, logits, loss, grad))
+    t_fwd = timed(lambda: ts.tsat_mpnn_forward(prob.h, params, ws, logits))
+    _emit({"experiment": "proposer_step", "instances": n_inst, "n_vars": V, "n_clauses": prob.info["n_clauses"],
+           "nnz": prob.info["nnz"], "train_step_ms": t_step, "forward_ms": t_fwd, "loss": float(loss.item())})
+
+
 def exp_mixing(args):
     """Assignment mixing at lr restarts on or off, same schedule (restart 360,
     decay 30): 32 planted 3-SAT instances n=1000 m=4000 (ratio 4.0) solved as
@@ -856,7 +897,8 @@ def main():
     if args.experiment != "throughput":
         if rank == 0:
             {"time_to_sat": exp_time_to_sat, "batch": exp_batch, "relaxed": exp_relaxed,
-             "proposer": exp_proposer, "mixing": exp_mixing, "literal_rows": exp_literal_rows}[args.experiment](args)
+             "proposer": exp_proposer, "proposer_step": exp_proposer_step, "mixing": exp_mixing,
+             "literal_rows": exp_literal_rows}[args.experiment](args)
         return
     ours(args, w, rank, world, local)
 

@@ -54,7 +54,7 @@ struct MpWs {  // activations kept for the backward pass
   float *dlog, *lossv;             // [V] dL/dlogit and per-variable loss terms
   int *err;                        // set by a tensor-core layer whose completion wait timed out
 };
-constexpr int kPartBlocks = 256;
+constexpr int kPartBlocks = 148 * 3;   // weight-gradient blocks: three per SM
 
 static size_t mp_ws_bytes(int64_t V, int64_t C) {
   const int64_t L = 2 * V;
@@ -129,14 +129,15 @@ struct DIn {
 };
 
 // tensor-core dense layers (mpnn_tc.cu)
-cudaError_t mp_dense_tc(int nin, const float *x0, int k0, int xr0, const float *x1, int k1, int xr1, const float *x2,
-                        int k2, int xr2, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias, int relu,
-                        float *Y, int *err, cudaStream_t st);
-cudaError_t mp_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, int Ktot, int koff, float *dX, int accumulate,
-                     int xr, int *err, cudaStream_t st);
-int mp_wgrad_tc(const float *dZ, int64_t M, int nin, const float *x0, int k0, int xr0, const float *x1, int k1,
-                int xr1, const float *x2, int k2, int xr2, float *part, int max_blocks, int *err, cudaStream_t st,
-                cudaError_t *e);
+cudaError_t mp_dense_tc(const float *x, int K, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias, float *Y,
+                        int *err, cudaStream_t st);
+cudaError_t mp_literal_tc(const float *h, const float *a, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias,
+                          float *Y, int *err, cudaStream_t st);
+cudaError_t mp_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, float *dX, int *err, cudaStream_t st);
+cudaError_t mp_literal_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, float *dh, float *da, int *err,
+                             cudaStream_t st);
+int mp_wgrad_tc(const float *dZ, int64_t M, int nin, int K, const float *const *x, const int *xr, float *part,
+                int max_blocks, int *err, cudaStream_t st, cudaError_t *e);
 
 // m_c = mean_{l in c} h_l
 __global__ void k_mp_clause_mean(ProbDev pd, const float *h, float *m) {
@@ -325,11 +326,6 @@ static int grid_for(int64_t work, int per_block) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(148 * 16, (work + per_block - 1) / per_block));
 }
 
-static cudaError_t dense(int nin, DIn a, DIn b, DIn c, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias,
-                         int relu, float *Y, int *err, cudaStream_t st) {
-  return mp_dense_tc(nin, a.x, a.K, a.xr, b.x, b.K, b.xr, c.x, c.K, c.xr, M, W, bias, relu, Y, err, st);
-}
-
 static int mp_forward(const tsat_problem *p, const float *params, MpWs &w, float *logits, cudaStream_t st) {
   const ProbDev &pd = p->dev;
   const int64_t L = 2 * (int64_t)p->V, C = p->C;
@@ -337,17 +333,15 @@ static int mp_forward(const tsat_problem *p, const float *params, MpWs &w, float
   k_mp_to_bf16<<<64, 256, 0, st>>>(params, w.wb, kNParams);
   k_mp_feat<<<grid_for(p->V, 256), 256, 0, st>>>(pd, w.ldeg, w.feat);
   TSAT_LAUNCH_CHECK("mpnn features");
-  DIn none{nullptr, 0, 0};
-  cudaError_t e = dense(1, DIn{w.feat, kFeat, 0}, none, none, L, w.wb + kOffW0, w.wb + kOffB0, 1, w.h[0], w.err, st);
+  cudaError_t e = mp_dense_tc(w.feat, kFeat, L, w.wb + kOffW0, w.wb + kOffB0, w.h[0], w.err, st);
   if (e != cudaSuccess) return cuda_fail(e, "mpnn input layer");
   for (int t = 0; t < kLayers; ++t) {
     k_mp_clause_mean<<<grid_for(C * 32, 256), 256, 0, st>>>(pd, w.h[t], w.m[t]);
-    if ((e = dense(1, DIn{w.m[t], kH, 0}, none, none, C, w.wb + off_wc(t), w.wb + off_bc(t), 1, w.e[t], w.err, st)) !=
-        cudaSuccess)
+    if ((e = mp_dense_tc(w.m[t], kH, C, w.wb + off_wc(t), w.wb + off_bc(t), w.e[t], w.err, st)) != cudaSuccess)
       return cuda_fail(e, "mpnn clause layer");
     k_mp_lit_mean<<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.e[t], w.ldeg, w.a[t]);
-    if ((e = dense(3, DIn{w.h[t], kH, 0}, DIn{w.a[t], kH, 0}, DIn{w.h[t], kH, 1}, L, w.wb + off_wl(t),
-                   w.wb + off_bl(t), 1, w.h[t + 1], w.err, st)) != cudaSuccess)
+    if ((e = mp_literal_tc(w.h[t], w.a[t], L, w.wb + off_wl(t), w.wb + off_bl(t), w.h[t + 1], w.err, st)) !=
+        cudaSuccess)
       return cuda_fail(e, "mpnn literal layer");
   }
   if (logits) k_mp_out<<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.h[kLayers], w.wb, logits);
@@ -358,19 +352,13 @@ static int mp_forward(const tsat_problem *p, const float *params, MpWs &w, float
 static int wgrad(int nin, DIn a, DIn b, DIn c, const float *dZ, int64_t M, float *part, float *gW, float *gb,
                  int *err, cudaStream_t st) {
   const int Kt = a.K + (nin > 1 ? b.K : 0) + (nin > 2 ? c.K : 0);
+  const float *x[3] = {a.x, b.x, c.x};
+  const int xr[3] = {a.xr, b.xr, c.xr};
   cudaError_t e = cudaSuccess;
-  const int nb = mp_wgrad_tc(dZ, M, nin, a.x, a.K, a.xr, b.x, b.K, b.xr, c.x, c.K, c.xr, part, kPartBlocks, err, st, &e);
+  const int nb = mp_wgrad_tc(dZ, M, nin, a.K, x, xr, part, kPartBlocks, err, st, &e);
   if (e != cudaSuccess) return cuda_fail(e, "mpnn weight gradient");
   k_mp_wgrad_reduce<<<(kH * (Kt + 1) + 255) / 256, 256, 0, st>>>(part, nb, Kt, gW, gb);
   TSAT_LAUNCH_CHECK("mpnn weight gradient");
-  return TSAT_OK;
-}
-
-static int dx(const float *dZ, int64_t M, const __nv_bfloat16 *W, int Ktot, int koff, int K, float *dX, int acc,
-              int xr, int *err, cudaStream_t st) {
-  if (K != kH) { set_error("mpnn input gradient of a %d-wide slice", K); return TSAT_EINVAL; }
-  cudaError_t e = mp_dx_tc(dZ, M, W, Ktot, koff, dX, acc, xr, err, st);
-  if (e != cudaSuccess) return cuda_fail(e, "mpnn input gradient");
   return TSAT_OK;
 }
 
@@ -393,10 +381,9 @@ static int mp_backward(const tsat_problem *p, MpWs &w, const float *dlog, float 
     if ((rc = wgrad(3, DIn{w.h[t], kH, 0}, DIn{w.a[t], kH, 0}, DIn{w.h[t], kH, 1}, w.dh, L, w.part,
                     grad + off_wl(t), grad + off_bl(t), w.err, st)))
       return rc;
-    const __nv_bfloat16 *Wl = w.wb + off_wl(t);
-    if ((rc = dx(w.dh, L, Wl, 3 * kH, 0, kH, w.dh2, 0, 0, w.err, st))) return rc;         // from h_l
-    if ((rc = dx(w.dh, L, Wl, 3 * kH, 2 * kH, kH, w.dh2, 1, 1, w.err, st))) return rc;    // from h_{l^1}
-    if ((rc = dx(w.dh, L, Wl, 3 * kH, kH, kH, w.da, 0, 0, w.err, st))) return rc;         // from a_l
+    // dh2 from h_l and h_{l^1}, da from a_l
+    cudaError_t e = mp_literal_dx_tc(w.dh, L, w.wb + off_wl(t), w.dh2, w.da, w.err, st);
+    if (e != cudaSuccess) return cuda_fail(e, "mpnn literal-layer input gradient");
     // a = mean over owning clauses of e  ->  de
     k_mp_clause_from_lit<<<grid_for(C * 32, 256), 256, 0, st>>>(pd, w.da, w.ldeg, w.de);
     // clause layer: e = relu(Wc m + bc)
@@ -404,7 +391,8 @@ static int mp_backward(const tsat_problem *p, MpWs &w, const float *dlog, float 
     if ((rc = wgrad(1, DIn{w.m[t], kH, 0}, none, none, w.de, C, w.part, grad + off_wc(t), grad + off_bc(t), w.err,
                     st)))
       return rc;
-    if ((rc = dx(w.de, C, w.wb + off_wc(t), kH, 0, kH, w.dm, 0, 0, w.err, st))) return rc;
+    if ((e = mp_dx_tc(w.de, C, w.wb + off_wc(t), w.dm, w.err, st)) != cudaSuccess)
+      return cuda_fail(e, "mpnn clause-layer input gradient");
     // m = mean of h over the clause's literals -> dh2 += ...
     k_mp_lit_from_clause<<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.dm, w.dh2);
     TSAT_LAUNCH_CHECK("mpnn layer backward");
@@ -442,6 +430,7 @@ int tsat_mpnn_forward(const tsat_problem *p, const float *d_params, void *d_ws, 
                       cudaStream_t stream) {
   if (!p || !d_params || !d_ws || !d_logits) return TSAT_EINVAL;
   if (ws_bytes < mp_ws_bytes(p->V, p->C)) { set_error("mpnn workspace too small"); return TSAT_EWS; }
+  if ((uintptr_t)d_ws & 255u) { set_error("mpnn workspace not 256-byte aligned"); return TSAT_EINVAL; }
   MpWs w = mp_ws_plan(d_ws, p->V, p->C);
   return mp_forward(p, d_params, w, d_logits, stream);
 }
@@ -450,6 +439,7 @@ int tsat_mpnn_loss_grad(const tsat_problem *p, const float *d_params, void *d_ws
                         const uint8_t *d_targets, float *d_logits, float *d_loss, float *d_grad, cudaStream_t stream) {
   if (!p || !d_params || !d_ws || !d_targets || !d_logits || !d_loss || !d_grad) return TSAT_EINVAL;
   if (ws_bytes < mp_ws_bytes(p->V, p->C)) { set_error("mpnn workspace too small"); return TSAT_EWS; }
+  if ((uintptr_t)d_ws & 255u) { set_error("mpnn workspace not 256-byte aligned"); return TSAT_EINVAL; }
   MpWs w = mp_ws_plan(d_ws, p->V, p->C);
   int rc = mp_forward(p, d_params, w, d_logits, stream);
   if (rc) return rc;

@@ -1,10 +1,18 @@
 // mpnn_tc.cu -- the proposer's dense layers on the 5th-generation tensor cores
 // (tcgen05.mma, BF16 operands, FP32 accumulation in tensor memory).
 //
-// Y[r][0:64] = act( sum_j X_j[r ^ xr_j][0:K_j] . B_j^T + bias )
-//   forward layers: B_j = the weight slice W[:, koff_j : koff_j + K_j] (64 x K_j)
-//   input gradient: one slice, B = W[:, koff : koff + 64]^T (the 64 outputs are
-//                   the slice's inputs, the reduction runs over W's 64 rows)
+// Layer forms (64 outputs; W is BF16, row-major [64][Ktot]):
+//   dense       Y[r]  = relu(W x[r] + b)                          x: K = 3 or 64
+//   literal     Y[r]  = relu(W0 h[r] + W1 a[r] + W2 h[r^1] + b)   W = [W0 W1 W2], 64 x 192
+//   dx          dX[r] = W^T dZ[r]                                 W: 64 x 64
+//   literal dx  dh[r] = W0^T dZ[r] + W2^T dZ[r^1],  da[r] = W1^T dZ[r]
+//   weight grad part[b][o][k] = sum over block b's rows r of dZ[r][o] X[r][k],
+//               with a column of ones after the last k for the bias gradient.
+// Rows r and r^1 are the two literals of a variable.  Tiles start at
+// multiples of 128 rows, so both sit in one tile, in adjacent tensor-memory
+// lanes of the same warp: the r^1 terms are computed into a second
+// accumulator and exchanged between lane pairs (shfl_xor 1) in the epilogue,
+// and h and dZ are staged once.
 //
 // The weights are BF16 (the network's declared precision), so B is exact in
 // BF16.  The activations are FP32: each is split into three BF16 parts,
@@ -13,17 +21,16 @@
 // accumulated into the same FP32 tile -- the layer keeps FP32 accuracy with
 // BF16 tensor-core inputs.
 //
-// A block of 128 threads owns a tile of 128 rows.  Per input slice it stages
-// the three BF16 parts of its rows and (once per block) the BF16 weight slices
-// into shared memory in the no-swizzle K-major core-matrix layout (8 x 16-byte
-// core matrices; K-adjacent ones 128 bytes apart, 8-row groups K/8 x 128 bytes
-// apart), makes the writes visible to the tensor core's async proxy, and one
-// thread issues 3 x (K/16) MMAs of shape 128 x 64 x 16 into a 64-column tensor
-// memory tile; tcgen05.commit signals an mbarrier when they are done.  Every
-// wait on the mbarrier is bounded: on time-out the block records an error in
-// the caller's flag and leaves after freeing its tensor memory.  The epilogue
-// reads the accumulator with tcgen05.ld (warp q: rows 32q .. 32q + 31, one row
-// per thread), adds the bias and applies the ReLU.
+// Shared-memory operands use the no-swizzle K-major core-matrix layout (8 x
+// 16-byte core matrices; K-adjacent ones 128 bytes apart, 8-row groups K/8 x
+// 128 bytes apart).  Forward / dx blocks stage the weights once, then loop
+// over 128-row tiles: every thread issues all of its tile loads (16-byte
+// vectors) before the first conversion, each warp's stores cover contiguous
+// shared memory, one thread issues the MMAs (M 128, N 64, K 16), and
+// tcgen05.commit signals an mbarrier.  Every wait on the mbarrier is bounded:
+// on time-out the block records an error in the caller's flag and leaves after
+// freeing its tensor memory.  The epilogue reads the accumulators with
+// tcgen05.ld (warp q: rows 32q .. 32q + 31, one row per thread).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -35,14 +42,18 @@ namespace tsat {
 
 constexpr int kTcRows = 128;      // rows per tile (MMA M)
 constexpr int kTcN = 64;          // outputs (MMA N)
-constexpr int kTcMaxK = 192;      // widest input (three 64-wide slices)
 constexpr int kTcParts = 3;       // BF16 parts of an FP32 activation
 constexpr uint32_t kTcSpinLimit = 1u << 24;
 
-// shared memory: B [64 x kTcMaxK] bf16, A [3 parts][128 x 64] bf16, mbarrier, tmem address
-constexpr int kTcBBytes = kTcN * kTcMaxK * 2;
-constexpr int kTcABytes = kTcParts * kTcRows * 64 * 2;
-constexpr int kTcSmem = kTcBBytes + kTcABytes + 64;
+// forward / dx shared memory: B [3 blocks][64 x 64] bf16, A [3 parts][128 x 64] bf16, mbarrier, tmem address
+constexpr int kTcBBlock = kTcN * 64 * 2;
+constexpr int kTcAPart = kTcRows * 64 * 2;
+constexpr int kTcSmem = 3 * kTcBBlock + kTcParts * kTcAPart + 64;
+// the literal input gradient holds 256 tensor-memory columns, so at most two
+// of its blocks may share an SM: its shared memory is padded past a third
+constexpr int kTcSmemTwoPerSm = 80 * 1024;
+
+enum TcForm { kDense = 0, kLiteral = 1, kDx = 2, kLiteralDx = 3 };
 
 // Byte offset of element (row, k) in the K-major no-swizzle layout with
 // kw = K (row width in elements, a multiple of 8).
@@ -72,6 +83,10 @@ __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t 
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
       "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar) : "memory");
 }
 
 // Bounded wait for mbarrier phase `parity`; false on time-out.
@@ -104,49 +119,171 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-struct TcIn {
-  const float *x;   // [rows][K]
-  int K, xr;        // row r reads x[r ^ xr]
-  int koff;         // first column of the slice in W (forward) / of the inputs (input gradient)
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 &hi, __nv_bfloat16 &mid, __nv_bfloat16 &lo) {
+  hi = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(hi);
+  mid = __float2bfloat16_rn(r1);
+  lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// The three parts of two values as packed pairs (first value in the low half).
+__device__ __forceinline__ void split3x2(float x, float y, uint32_t &hi, uint32_t &mid, uint32_t &lo) {
+  __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+  split3(x, h0, m0, l0);
+  split3(y, h1, m1, l1);
+  hi = pack2(h0, h1);
+  mid = pack2(m0, m1);
+  lo = pack2(l0, l1);
+}
+
+// Rows [r0, r0 + 128) of a 64-wide FP32 matrix (rows at or past M are zero)
+// as three BF16 parts, part p at sA + p * kTcAPart.  Warp q covers k in
+// [16q, 16q + 16): in load i, lanes 4a .. 4a + 3 read 64 bytes of row 8i + a,
+// so every load instruction reads eight 64-byte segments; all 16 loads are
+// issued before the first conversion; each warp's 8-byte stores fill 256
+// contiguous bytes (two K-adjacent core matrices).
+__device__ __forceinline__ void stage_a64(unsigned char *sA, const float *__restrict__ x, int64_t r0, int64_t M,
+                                          int tid) {
+  const int warp = tid >> 5, lane = tid & 31;
+  const int k = 16 * warp + 4 * (lane & 3);
+  float4 v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {   // rows past M load row M - 1 and are zeroed, so no load is conditional
+    const int64_t r = r0 + 8 * i + (lane >> 2);
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(x + (size_t)min(r, M - 1) * 64 + k));
+    v[i] = r < M ? t : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const uint32_t o = tc_off(8 * i + (lane >> 2), k, 64);
+    uint2 h, m, l;
+    split3x2(v[i].x, v[i].y, h.x, m.x, l.x);
+    split3x2(v[i].z, v[i].w, h.y, m.y, l.y);
+    *reinterpret_cast<uint2 *>(sA + o) = h;
+    *reinterpret_cast<uint2 *>(sA + kTcAPart + o) = m;
+    *reinterpret_cast<uint2 *>(sA + 2 * kTcAPart + o) = l;
+  }
+}
+
+// The 3-wide input features: one row per thread, columns 3..15 zero (K 16).
+__device__ __forceinline__ void stage_a3(unsigned char *sA, const float *__restrict__ x, int64_t r0, int64_t M,
+                                         int tid) {
+  const int64_t r = r0 + tid, rc = min(r, M - 1);
+  const bool in = r < M;
+  const float f0 = in ? __ldg(x + 3 * rc) : 0.f, f1 = in ? __ldg(x + 3 * rc + 1) : 0.f,
+              f2 = in ? __ldg(x + 3 * rc + 2) : 0.f;
+  uint32_t h01, m01, l01, h2, m2, l2;
+  split3x2(f0, f1, h01, m01, l01);
+  split3x2(f2, 0.f, h2, m2, l2);
+  const uint32_t o = tc_off(tid, 0, 16);
+  const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+  *reinterpret_cast<uint4 *>(sA + o) = make_uint4(h01, h2, 0u, 0u);
+  *reinterpret_cast<uint4 *>(sA + o + 128) = z;
+  *reinterpret_cast<uint4 *>(sA + kTcAPart + o) = make_uint4(m01, m2, 0u, 0u);
+  *reinterpret_cast<uint4 *>(sA + kTcAPart + o + 128) = z;
+  *reinterpret_cast<uint4 *>(sA + 2 * kTcAPart + o) = make_uint4(l01, l2, 0u, 0u);
+  *reinterpret_cast<uint4 *>(sA + 2 * kTcAPart + o + 128) = z;
+}
+
+// Weight block j as the MMA's B operand [64 n][64 k] at sB + j * kTcBBlock:
+//   TRANS = false: B[n][k] = W[n][64 j + k]   (forward)
+//   TRANS = true : B[n][k] = W[k][64 j + n]   (input gradient)
+// Forward: 16-byte chunk e holds k 8c .. 8c + 7 of row n with n = 8(e >> 6) +
+// (e & 7), c = (e >> 3) & 7, which is byte offset 16 e of the layout.
+template <bool TRANS>
+__device__ __forceinline__ void stage_b64(unsigned char *sB, const __nv_bfloat16 *__restrict__ W, int Ktot, int j,
+                                          int tid) {
+  unsigned char *dst = sB + j * kTcBBlock;
+  uint4 t[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int e = i * kTcRows + tid;
+    if (!TRANS) {
+      const int n = ((e >> 6) << 3) | (e & 7), c = (e >> 3) & 7;
+      t[i] = __ldg(reinterpret_cast<const uint4 *>(W + (size_t)n * Ktot + 64 * j + 8 * c));
+    } else {
+      const int k = e & 63, c = e >> 6;
+      t[i] = __ldg(reinterpret_cast<const uint4 *>(W + (size_t)k * Ktot + 64 * j + 8 * c));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int e = i * kTcRows + tid;
+    if (!TRANS) {
+      *reinterpret_cast<uint4 *>(dst + 16 * e) = t[i];
+    } else {   // the eight n of the chunk go to eight rows of the layout
+      const int k = e & 63, c = e >> 6;
+      unsigned char *d = dst + tc_off(8 * c, k, 64);
+      *reinterpret_cast<unsigned short *>(d + 0 * 16) = (unsigned short)(t[i].x & 0xFFFFu);
+      *reinterpret_cast<unsigned short *>(d + 1 * 16) = (unsigned short)(t[i].x >> 16);
+      *reinterpret_cast<unsigned short *>(d + 2 * 16) = (unsigned short)(t[i].y & 0xFFFFu);
+      *reinterpret_cast<unsigned short *>(d + 3 * 16) = (unsigned short)(t[i].y >> 16);
+      *reinterpret_cast<unsigned short *>(d + 4 * 16) = (unsigned short)(t[i].z & 0xFFFFu);
+      *reinterpret_cast<unsigned short *>(d + 5 * 16) = (unsigned short)(t[i].z >> 16);
+      *reinterpret_cast<unsigned short *>(d + 6 * 16) = (unsigned short)(t[i].w & 0xFFFFu);
+      *reinterpret_cast<unsigned short *>(d + 7 * 16) = (unsigned short)(t[i].w >> 16);
+    }
+  }
+}
+
+// The 3-wide input layer's weights: B[n][k] = W[n][k] for k < 3, zero to k 16.
+__device__ __forceinline__ void stage_b3(unsigned char *sB, const __nv_bfloat16 *__restrict__ W, int tid) {
+  if (tid < kTcN) {
+    const __nv_bfloat16 zb = __float2bfloat16_rn(0.f);
+    const uint32_t o = tc_off(tid, 0, 16);
+    *reinterpret_cast<uint4 *>(sB + o) =
+        make_uint4(pack2(W[3 * tid], W[3 * tid + 1]), pack2(W[3 * tid + 2], zb), 0u, 0u);
+    *reinterpret_cast<uint4 *>(sB + o + 128) = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+struct TcArgs {
+  const float *x0, *x1;          // A sources: dense / dx: x0; literal: h = x0, a = x1; literal dx: dZ = x0
+  int K;                         // dense: width of x0 (3 or 64)
+  int64_t M;                     // rows
+  const __nv_bfloat16 *W, *bias;
+  float *y0, *y1;                // outputs: y0 (Y, dX, dh), y1 (literal dx: da)
+  int *err;
 };
 
-// TRANSB = false: forward, B_j = W[:, koff_j : koff_j + K_j], Y = act(sum + bias)
-// TRANSB = true : input gradient, one slice, B = W[:, koff : koff + 64]^T,
-//                 Y[r ^ yxr] = (accumulate ? Y : 0) + sum
-template <int NIN, bool TRANSB>
-__global__ void __launch_bounds__(kTcRows) k_mp_tc(TcIn i0, TcIn i1, TcIn i2, int64_t M, const __nv_bfloat16 *W,
-                                                   int Ktot, const __nv_bfloat16 *bias, int relu, float *Y, int yxr,
-                                                   int accumulate, int *err) {
+// MMAs of one staged A tile (3 parts, kA wide) against weight block j into
+// the accumulator at tensor-memory column `col`.
+__device__ __forceinline__ void tc_mma_tile(uint32_t tmem, uint32_t col, uint32_t sa, uint32_t sb, int j, int kA,
+                                            bool first) {
+  for (int part = 0; part < kTcParts; ++part)
+    for (int ks = 0; ks < kA / 16; ++ks) {
+      const uint64_t ad = tc_desc(sa + part * kTcAPart + ks * 256, 128, (uint32_t)(kA / 8) * 128);
+      const uint64_t bd = tc_desc(sb + j * kTcBBlock + ks * 256, 128, (uint32_t)(kA / 8) * 128);
+      tc_mma(tmem + col, ad, bd, (first && part == 0 && ks == 0) ? 0u : 1u);
+    }
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(kTcRows) k_mp_tc(TcArgs g) {
+  constexpr int NB = (FORM == kLiteral || FORM == kLiteralDx) ? 3 : 1;   // weight blocks
+  constexpr uint32_t NCOL = FORM == kLiteralDx ? 256 : (FORM == kLiteral ? 128 : 64);   // tensor-memory columns
   extern __shared__ __align__(1024) unsigned char smt[];
-  unsigned char *sB = smt;                          // [64][Kb] K-major
-  unsigned char *sA = smt + kTcBBytes;               // [3][128][64] K-major
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(smt + kTcBBytes + kTcABytes);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(smt + kTcBBytes + kTcABytes + 16);
+  unsigned char *sB = smt;
+  unsigned char *sA = smt + 3 * kTcBBlock;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sA + kTcParts * kTcAPart);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(sA + kTcParts * kTcAPart + 16);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const TcIn in[3] = {i0, i1, i2};
-  // B in shared memory: width Kb (the padded widths of the slices)
-  int Kp[3], kb0[3], Kb = 0;
+  const bool k3 = FORM == kDense && g.K == 3;
+  const int kA = k3 ? 16 : 64;
+  if (k3) {
+    stage_b3(sB, g.W, tid);
+  } else {
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    Kp[j] = j < NIN ? (in[j].K + 15) / 16 * 16 : 0;
-    kb0[j] = Kb;
-    Kb += Kp[j];
+    for (int j = 0; j < NB; ++j) stage_b64<FORM == kDx || FORM == kLiteralDx>(sB, g.W, NB * 64, j, tid);
   }
-  for (int e = tid; e < kTcN * Kb; e += kTcRows) {
-    const int n = e / Kb, kk = e - n * Kb;
-    int j = 0;
-    while (j + 1 < NIN && kk >= kb0[j + 1]) ++j;
-    const int k = kk - kb0[j];
-    __nv_bfloat16 val = __float2bfloat16_rn(0.f);
-    if (k < in[j].K) val = TRANSB ? W[(size_t)k * Ktot + in[j].koff + n] : W[(size_t)n * Ktot + in[j].koff + k];
-    *reinterpret_cast<__nv_bfloat16 *>(sB + tc_off(n, kk, Kb)) = val;
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
-  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
-                 "r"(kTcN)
+                 "r"(NCOL)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
@@ -158,129 +295,166 @@ __global__ void __launch_bounds__(kTcRows) k_mp_tc(TcIn i0, TcIn i1, TcIn i2, in
   const uint32_t mb = smem_u32(mbar), sa = smem_u32(sA), sb = smem_u32(sB);
   uint32_t phase = 0;
   bool ok = true;
-  const int64_t ntiles = (M + kTcRows - 1) / kTcRows;
+  const int64_t M = g.M, ntiles = (M + kTcRows - 1) / kTcRows;
   for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const int64_t r0 = tile * kTcRows;
-#pragma unroll
-    for (int j = 0; j < NIN; ++j) {
-      // the three BF16 parts of the slice's activations (rows past M are zero)
-      const int K = in[j].K, K16 = Kp[j];
-      for (int e = tid; e < kTcRows * K16; e += kTcRows) {
-        const int row = e / K16, k = e - row * K16;
-        const int64_t r = r0 + row;
-        float x = 0.f;
-        if (r < M && k < K) x = in[j].x[(size_t)(r ^ in[j].xr) * K + k];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        const float r1 = x - __bfloat162float(hi);
-        const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
-        const uint32_t o = tc_off(row, k, K16);
-        *reinterpret_cast<__nv_bfloat16 *>(sA + o) = hi;
-        *reinterpret_cast<__nv_bfloat16 *>(sA + kTcRows * 64 * 2 + o) = mid;
-        *reinterpret_cast<__nv_bfloat16 *>(sA + 2 * kTcRows * 64 * 2 + o) = lo;
+    // stage 0: x (dense), dZ (dx, literal dx) or h (literal)
+    if (k3)
+      stage_a3(sA, g.x0, r0, M, tid);
+    else
+      stage_a64(sA, g.x0, r0, M, tid);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      if (FORM == kLiteral) {
+        tc_mma_tile(tmem, 0, sa, sb, 0, 64, true);     // W0 h[r]
+        tc_mma_tile(tmem, 64, sa, sb, 2, 64, true);    // W2 h[r]  (moved to row r^1 in the epilogue)
+      } else if (FORM == kLiteralDx) {
+        tc_mma_tile(tmem, 0, sa, sb, 0, 64, true);     // W0^T dZ[r]
+        tc_mma_tile(tmem, 64, sa, sb, 1, 64, true);    // W1^T dZ[r]
+        tc_mma_tile(tmem, 128, sa, sb, 2, 64, true);   // W2^T dZ[r]  (moved to row r^1)
+      } else {
+        tc_mma_tile(tmem, 0, sa, sb, 0, kA, true);
       }
+      tc_commit(mb);
+    }
+    ok = tc_wait(mb, phase);   // the MMAs are done: the A tile may be overwritten
+    phase ^= 1u;
+    if (!ok) break;
+    if (FORM == kLiteral) {   // stage 1: a
+      stage_a64(sA, g.x1, r0, M, tid);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       __syncthreads();
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        for (int part = 0; part < kTcParts; ++part)
-          for (int ks = 0; ks < K16 / 16; ++ks) {
-            const uint64_t ad = tc_desc(sa + part * kTcRows * 64 * 2 + ks * 256, 128, (uint32_t)(K16 / 8) * 128);
-            const uint64_t bd = tc_desc(sb + (uint32_t)(kb0[j] / 8) * 128 + ks * 256, 128, (uint32_t)(Kb / 8) * 128);
-            tc_mma(tmem, ad, bd, (j > 0 || part > 0 || ks > 0) ? 1u : 0u);
-          }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
-                     : "memory");
+        tc_mma_tile(tmem, 0, sa, sb, 1, 64, false);   // + W1 a[r]
+        tc_commit(mb);
       }
-      ok = tc_wait(mb, phase);   // the slice's MMAs are done: its A tile may be overwritten
+      ok = tc_wait(mb, phase);
       phase ^= 1u;
       if (!ok) break;
     }
-    if (!ok) break;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    // epilogue: warp q reads rows 32 q .. 32 q + 31 (tensor memory lanes), 64 columns
-    const int row = 32 * warp + (tid & 31);
-    const int64_t r = r0 + row;
+    // epilogue: warp q reads rows 32 q .. 32 q + 31 (tensor memory lanes)
+    const int64_t r = r0 + 32 * warp + (tid & 31);
+    const uint32_t lrow = (uint32_t)(32 * warp) << 16;
 #pragma unroll
     for (int c = 0; c < kTcN; c += 16) {
-      float v[16];
-      tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+      float v[16], u[16];
+      tc_ld16(tmem + lrow + (uint32_t)c, v);
+      if (FORM == kLiteral || FORM == kLiteralDx) {
+        float s[16];
+        tc_ld16(tmem + lrow + (uint32_t)(FORM == kLiteral ? 64 : 128) + (uint32_t)c, s);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, s[q], 1);
+      }
+      if (FORM == kLiteralDx) tc_ld16(tmem + lrow + 64u + (uint32_t)c, u);
       if (r < M) {
-        float *dst = TRANSB ? Y + (size_t)(r ^ yxr) * kTcN + c : Y + (size_t)r * kTcN + c;
+        float *dst = g.y0 + (size_t)r * kTcN + c;
 #pragma unroll
         for (int q = 0; q < 16; q += 4) {
           float4 o = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-          if (!TRANSB) {
-            o.x += __bfloat162float(bias[c + q]);
-            o.y += __bfloat162float(bias[c + q + 1]);
-            o.z += __bfloat162float(bias[c + q + 2]);
-            o.w += __bfloat162float(bias[c + q + 3]);
-            if (relu) {
-              o.x = fmaxf(o.x, 0.f);
-              o.y = fmaxf(o.y, 0.f);
-              o.z = fmaxf(o.z, 0.f);
-              o.w = fmaxf(o.w, 0.f);
-            }
-          } else if (accumulate) {
-            const float4 p = *reinterpret_cast<const float4 *>(dst + q);
-            o.x += p.x;
-            o.y += p.y;
-            o.z += p.z;
-            o.w += p.w;
+          if (FORM == kDense || FORM == kLiteral) {
+            o.x = fmaxf(o.x + __bfloat162float(g.bias[c + q]), 0.f);
+            o.y = fmaxf(o.y + __bfloat162float(g.bias[c + q + 1]), 0.f);
+            o.z = fmaxf(o.z + __bfloat162float(g.bias[c + q + 2]), 0.f);
+            o.w = fmaxf(o.w + __bfloat162float(g.bias[c + q + 3]), 0.f);
           }
           *reinterpret_cast<float4 *>(dst + q) = o;
+          if (FORM == kLiteralDx)
+            *reinterpret_cast<float4 *>(g.y1 + (size_t)r * kTcN + c + q) =
+                make_float4(u[q], u[q + 1], u[q + 2], u[q + 3]);
         }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();   // every warp has read the accumulator before the next tile's MMAs
+    __syncthreads();   // every warp has read the accumulators before the next tile's MMAs
   }
-  if (!ok && err && (tid & 31) == 0) atomicExch(err, 1);
+  if (!ok && g.err && (tid & 31) == 0) atomicExch(g.err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcN) : "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NCOL) : "memory");
 }
 
 // ---------------------------------------------------------------- weight gradient
-// part[b][o][k] = sum over block b's rows r of dZ[r][o] X[r ^ xr][k], k < Kt,
+// part[b][o][k] = sum over block b's rows r of dZ[r][o] X[r][k], k < Kt,
 // and part[b][o][Kt] = sum of dZ[r][o] (the bias gradient: a column of ones).
 // As MMAs: D[k][o] = sum_r X[r][k] dZ[r][o], the rows as the reduction
-// dimension (64 per tile, 4 MMAs of K = 16), k in M-tiles of 128 (at most two:
+// dimension (32 per tile, 2 MMAs of K = 16), k in M-tiles of 128 (at most two:
 // Kt + 1 <= 193), o as N = 64.  Both operands are FP32 and split into three
 // BF16 parts; the six products hi.hi, hi.mid, mid.hi, hi.lo, lo.hi, mid.mid
-// keep the sum at about FP32 accuracy.  The tiles are staged transposed
-// (rows contiguous, K-major for the MMA).
-constexpr int kWgRows = 64;                                       // rows per tile (MMA reduction)
-constexpr int kWgAPart = kTcRows * kWgRows * 2;                   // one part of one k M-tile
-constexpr int kWgBPart = kTcN * kWgRows * 2;                      // one part of the dZ tile
+// keep the sum at about FP32 accuracy.
+// Both tiles are stored transposed (rows contiguous, K-major for the MMA).  A
+// warp reads an 8-row x 32-column block as four 8 x 8 pieces in the register
+// layout of an 8 x 8 matrix fragment (lane t: row t / 4, columns 2 (t % 4)
+// and 2 (t % 4) + 1, one 8-byte load per piece) and writes each piece
+// transposed with one stmatrix .trans: row j of piece i (16 bytes: the eight
+// rows' values of column 8 i + j) is one row of a core matrix.
+constexpr int kWgRows = 32;                                   // rows per tile (MMA reduction)
+constexpr int kWgAPart = kTcRows * kWgRows * 2;               // one part of one k M-tile
+constexpr int kWgBPart = kTcN * kWgRows * 2;                  // one part of the dZ tile
 constexpr int kWgSmem = 2 * kTcParts * kWgAPart + kTcParts * kWgBPart + 64;
 
-__device__ __forceinline__ void split3(float x, __nv_bfloat16 &hi, __nv_bfloat16 &mid, __nv_bfloat16 &lo) {
-  hi = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(hi);
-  mid = __float2bfloat16_rn(r1);
-  lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+__device__ __forceinline__ void stmatrix_t4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "r"(a), "r"(b),
+               "r"(c), "r"(d)
+               : "memory");
 }
 
-__global__ void __launch_bounds__(kTcRows) k_mp_tc_wgrad(const float *dZ, int64_t M, TcIn i0, TcIn i1, TcIn i2,
-                                                         int nin, float *part, int *err) {
+// One 8-row x 32-column block of a 64-wide FP32 matrix: rows rt + 8 rg .. +7
+// (row r read from row r ^ xr, rows at or past r1 zero), columns cb .. cb + 31.
+__device__ __forceinline__ void wg_load(const float *__restrict__ x, int xr, int64_t rt, int64_t r1, int rg, int cb,
+                                        int lane, float2 (&v)[4]) {
+  // rows past r1 load row r1 - 1 (a row of the block, rt < r1) and are zeroed: no load is conditional
+  const int64_t r = rt + 8 * rg + (lane >> 2);
+  const float *p = x + (size_t)(min(r, r1 - 1) ^ xr) * 64 + cb + 2 * (lane & 3);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 t = __ldg(reinterpret_cast<const float2 *>(p + 8 * i));
+    v[i] = r < r1 ? t : make_float2(0.f, 0.f);
+  }
+}
+
+// Store the block transposed: column c of the block becomes row m0 + c of a
+// K-major operand with 32-wide rows (part p at base + p * pstride).
+__device__ __forceinline__ void wg_store(uint32_t base, uint32_t pstride, int m0, int rg, int lane,
+                                         const float2 (&v)[4]) {
+  uint32_t h[4], m[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) split3x2(v[i].x, v[i].y, h[i], m[i], l[i]);
+  const uint32_t a = base + tc_off(m0 + 8 * (lane >> 3) + (lane & 7), 8 * rg, kWgRows);
+  stmatrix_t4(a, h[0], h[1], h[2], h[3]);
+  stmatrix_t4(a + pstride, m[0], m[1], m[2], m[3]);
+  stmatrix_t4(a + 2 * pstride, l[0], l[1], l[2], l[3]);
+}
+
+// NIN 64-wide inputs (KIN = 64) or the 3-wide input features (NIN = 1, KIN = 3).
+template <int NIN, int KIN>
+__global__ void __launch_bounds__(kTcRows) k_mp_tc_wgrad(const float *dZ, int64_t M, const float *x0, int xr0,
+                                                         const float *x1, int xr1, const float *x2, int xr2,
+                                                         float *part, int *err) {
+  constexpr int Kt = NIN * KIN, ncol = Kt + 1, nmt = (ncol + kTcRows - 1) / kTcRows;
+  constexpr uint32_t NCOL = nmt * kTcN;
+  // X blocks of 8 rows x 32 columns per warp per tile: warp w takes row group
+  // w and every 32-column group of the concatenated input
+  constexpr int XT = KIN == 64 ? 2 * NIN : 0;
   extern __shared__ __align__(1024) unsigned char smw[];
-  unsigned char *sA = smw;                                   // [2 m-tiles][3 parts][128 k][64 rows]
-  unsigned char *sB = smw + 2 * kTcParts * kWgAPart;         // [3 parts][64 o][64 rows]
+  unsigned char *sA = smw;                                   // [nmt][3 parts][128 k][32 rows]
+  unsigned char *sB = smw + 2 * kTcParts * kWgAPart;         // [3 parts][64 o][32 rows]
   uint64_t *mbar = reinterpret_cast<uint64_t *>(sB + kTcParts * kWgBPart);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(sB + kTcParts * kWgBPart + 16);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const TcIn in[3] = {i0, i1, i2};
-  const int Kt = i0.K + (nin > 1 ? i1.K : 0) + (nin > 2 ? i2.K : 0);
-  const int ncol = Kt + 1, nmt = (ncol + kTcRows - 1) / kTcRows;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the X^T operand's rows past the ones column stay zero
+  for (int e = tid; e < nmt * kTcParts * kWgAPart / 16; e += kTcRows)
+    reinterpret_cast<uint4 *>(sA)[e] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
-                 "r"(2 * kTcN)
+                 "r"(NCOL)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -290,66 +464,67 @@ __global__ void __launch_bounds__(kTcRows) k_mp_tc_wgrad(const float *dZ, int64_
   uint32_t phase = 0;
   bool ok = true, first = true;
   for (int64_t rt = r0; rt < r1 && ok; rt += kWgRows) {
-    // X^T tile parts: A[mt][p][k][row]; k = Kt is the ones column, rows past r1 are zero
-    for (int e = tid; e < nmt * kTcRows * kWgRows; e += kTcRows) {
-      const int kk = e / kWgRows, row = e - kk * kWgRows;
+    // loads first (X blocks, then the two dZ blocks of this warp), then conversions and stores
+    float2 xv[XT > 0 ? XT : 1][4], zv[2][4];
+#pragma unroll
+    for (int i = 0; i < XT; ++i) {   // column group i: input i / 2, columns 32 (i % 2) ..
+      const float *xi = i < 2 ? x0 : (i < 4 ? x1 : x2);
+      const int xri = i < 2 ? xr0 : (i < 4 ? xr1 : xr2);
+      wg_load(xi, xri, rt, r1, warp, 32 * (i & 1), lane, xv[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) wg_load(dZ, 0, rt, r1, warp, 32 * i, lane, zv[i]);
+    if (KIN == 3 && tid < 3 * kWgRows) {   // the 3-wide features, one value per thread
+      const int row = tid & (kWgRows - 1), f = tid >> 5;
       const int64_t r = rt + row;
-      float x = 0.f;
-      if (r < r1) {
-        if (kk == Kt) {
-          x = 1.f;
-        } else if (kk < Kt) {
-          const int j = kk < in[0].K ? 0 : (kk < in[0].K + in[1].K ? 1 : 2);
-          const int k = kk - (j == 0 ? 0 : (j == 1 ? in[0].K : in[0].K + in[1].K));
-          x = in[j].x[(size_t)(r ^ in[j].xr) * in[j].K + k];
-        }
-      }
       __nv_bfloat16 h, m, l;
-      split3(x, h, m, l);
-      const int mt = kk / kTcRows;
-      const uint32_t o = (uint32_t)(mt * kTcParts * kWgAPart) + tc_off(kk - mt * kTcRows, row, kWgRows);
+      split3(r < r1 ? __ldg(x0 + 3 * (r ^ xr0) + f) : 0.f, h, m, l);
+      const uint32_t o = tc_off(f, row, kWgRows);
       *reinterpret_cast<__nv_bfloat16 *>(sA + o) = h;
       *reinterpret_cast<__nv_bfloat16 *>(sA + kWgAPart + o) = m;
       *reinterpret_cast<__nv_bfloat16 *>(sA + 2 * kWgAPart + o) = l;
     }
-    // dZ^T tile parts: B[p][o][row]
-    for (int e = tid; e < kTcN * kWgRows; e += kTcRows) {
-      const int row = e / kTcN, oo = e - row * kTcN;
-      const int64_t r = rt + row;
-      const float z = r < r1 ? dZ[(size_t)r * kTcN + oo] : 0.f;
-      __nv_bfloat16 h, m, l;
-      split3(z, h, m, l);
-      const uint32_t o = tc_off(oo, row, kWgRows);
-      *reinterpret_cast<__nv_bfloat16 *>(sB + o) = h;
-      *reinterpret_cast<__nv_bfloat16 *>(sB + kWgBPart + o) = m;
-      *reinterpret_cast<__nv_bfloat16 *>(sB + 2 * kWgBPart + o) = l;
+    if (tid < kWgRows) {   // the ones column (zero past r1); its mid and lo parts stay zero
+      constexpr int mt = Kt / kTcRows;
+      const uint32_t o = (uint32_t)(mt * kTcParts * kWgAPart) + tc_off(Kt - mt * kTcRows, tid, kWgRows);
+      *reinterpret_cast<__nv_bfloat16 *>(sA + o) = __float2bfloat16_rn(rt + tid < r1 ? 1.f : 0.f);
     }
+#pragma unroll
+    for (int i = 0; i < XT; ++i) {
+      const int k = 32 * i, mt = k / kTcRows;
+      wg_store(sa + (uint32_t)(mt * kTcParts * kWgAPart), kWgAPart, k - mt * kTcRows, warp, lane, xv[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) wg_store(sb, kWgBPart, 32 * i, warp, lane, zv[i]);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       // (A part, B part) products kept: hi.hi, hi.mid, mid.hi, hi.lo, lo.hi, mid.mid
       const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
+#pragma unroll
       for (int mt = 0; mt < nmt; ++mt)
+#pragma unroll
         for (int q = 0; q < 6; ++q)
+#pragma unroll
           for (int ks = 0; ks < kWgRows / 16; ++ks) {
             const uint64_t ad = tc_desc(sa + mt * kTcParts * kWgAPart + pa[q] * kWgAPart + ks * 256, 128,
                                         (uint32_t)(kWgRows / 8) * 128);
             const uint64_t bd = tc_desc(sb + pb[q] * kWgBPart + ks * 256, 128, (uint32_t)(kWgRows / 8) * 128);
             tc_mma(tmem + (uint32_t)(mt * kTcN), ad, bd, (first && q == 0 && ks == 0) ? 0u : 1u);
           }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
-                   : "memory");
+      tc_commit(mb);
     }
     first = false;
-    ok = tc_wait(mb, phase);
+    ok = tc_wait(mb, phase);   // the MMAs are done: the tiles may be overwritten
     phase ^= 1u;
   }
   if (ok) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     float *out = part + (size_t)blockIdx.x * kTcN * ncol;
+#pragma unroll
     for (int mt = 0; mt < nmt; ++mt) {
-      const int k = mt * kTcRows + 32 * warp + (tid & 31);
+      const int k = mt * kTcRows + 32 * warp + lane;
 #pragma unroll
       for (int c = 0; c < kTcN; c += 16) {
         float v[16];
@@ -359,67 +534,95 @@ __global__ void __launch_bounds__(kTcRows) k_mp_tc_wgrad(const float *dZ, int64_
           for (int q = 0; q < 16; ++q) out[(size_t)(c + q) * ncol + k] = first ? 0.f : v[q];
       }
     }
-  } else if (err && (tid & 31) == 0) {
+  } else if (err && lane == 0) {
     atomicExch(err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * kTcN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NCOL) : "memory");
 }
 
-// Partial weight gradients of one layer into part[nb][64][Kt + 1]; returns nb.
-int mp_wgrad_tc(const float *dZ, int64_t M, int nin, const float *x0, int k0, int xr0, const float *x1, int k1,
-                int xr1, const float *x2, int k2, int xr2, float *part, int max_blocks, int *err, cudaStream_t st,
-                cudaError_t *e) {
+// ---------------------------------------------------------------- host side
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <typename Kern>
+static cudaError_t set_smem(Kern kern, int bytes, bool &done) {
+  if (done) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <int FORM>
+static cudaError_t tc_go(const TcArgs &g, cudaStream_t st) {
   static bool attr = false;
-  if (!attr) {
-    *e = cudaFuncSetAttribute(k_mp_tc_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
-    if (*e != cudaSuccess) return 0;
-    attr = true;
-  }
-  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(max_blocks, (M + 4 * kWgRows - 1) / (4 * kWgRows)));
-  const TcIn a{x0, k0, xr0, 0}, b{x1, k1, xr1, 0}, c{x2, k2, xr2, 0};
-  k_mp_tc_wgrad<<<nb, kTcRows, kWgSmem, st>>>(dZ, M, a, b, c, nin, part, err);
-  *e = cudaGetLastError();
-  return nb;
-}
-
-static int tc_grid(int64_t M) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>(148 * 3, (M + kTcRows - 1) / kTcRows));
-}
-
-template <int NIN, bool TRANSB>
-static cudaError_t tc_go(TcIn a, TcIn b, TcIn c, int64_t M, const __nv_bfloat16 *W, int Ktot,
-                         const __nv_bfloat16 *bias, int relu, float *Y, int yxr, int accumulate, int *err,
-                         cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_mp_tc<NIN, TRANSB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  k_mp_tc<NIN, TRANSB><<<tc_grid(M), kTcRows, kTcSmem, st>>>(a, b, c, M, W, Ktot, bias, relu, Y, yxr, accumulate,
-                                                              err);
+  const int smem = FORM == kLiteralDx ? kTcSmemTwoPerSm : kTcSmem;
+  cudaError_t e = set_smem(k_mp_tc<FORM>, smem, attr);
+  if (e != cudaSuccess) return e;
+  const int per_sm = FORM == kLiteralDx ? 2 : 3;   // as many as shared and tensor memory allow
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(148 * per_sm, (g.M + kTcRows - 1) / kTcRows));
+  k_mp_tc<FORM><<<grid, kTcRows, smem, st>>>(g);
   return cudaGetLastError();
 }
 
-// Y[r] = act(sum_j x_j[r ^ xr_j] . W[:, koff_j : koff_j + K_j]^T + bias), W bf16 [64][Ktot]
-cudaError_t mp_dense_tc(int nin, const float *x0, int k0, int xr0, const float *x1, int k1, int xr1, const float *x2,
-                        int k2, int xr2, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias, int relu,
-                        float *Y, int *err, cudaStream_t st) {
-  const int Ktot = k0 + (nin > 1 ? k1 : 0) + (nin > 2 ? k2 : 0);
-  const TcIn a{x0, k0, xr0, 0}, b{x1, k1, xr1, k0}, c{x2, k2, xr2, k0 + k1};
-  if (nin == 1) return tc_go<1, false>(a, b, c, M, W, Ktot, bias, relu, Y, 0, 0, err, st);
-  if (nin == 2) return tc_go<2, false>(a, b, c, M, W, Ktot, bias, relu, Y, 0, 0, err, st);
-  return tc_go<3, false>(a, b, c, M, W, Ktot, bias, relu, Y, 0, 0, err, st);
+// Y[r] = relu(W x[r] + b), x FP32 [M][K] with K = 3 or 64, W bf16 [64][K]
+cudaError_t mp_dense_tc(const float *x, int K, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias, float *Y,
+                        int *err, cudaStream_t st) {
+  if ((K != 3 && K != 64) || !aligned16(x) || !aligned16(W) || !aligned16(Y)) return cudaErrorInvalidValue;
+  return tc_go<kDense>(TcArgs{x, nullptr, K, M, W, bias, Y, nullptr, err}, st);
 }
 
-// dX[r ^ xr] (+)= dZ[r] . W[:, koff : koff + 64]   (dZ [M][64], W bf16 [64][Ktot])
-cudaError_t mp_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, int Ktot, int koff, float *dX, int accumulate,
-                     int xr, int *err, cudaStream_t st) {
-  const TcIn a{dZ, kTcN, 0, koff}, none{nullptr, 0, 0, 0};
-  return tc_go<1, true>(a, none, none, M, W, Ktot, nullptr, 0, dX, xr, accumulate, err, st);
+// Y[r] = relu(W0 h[r] + W1 a[r] + W2 h[r^1] + b), W bf16 [64][192], M even
+cudaError_t mp_literal_tc(const float *h, const float *a, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias,
+                          float *Y, int *err, cudaStream_t st) {
+  if ((M & 1) || !aligned16(h) || !aligned16(a) || !aligned16(W) || !aligned16(Y)) return cudaErrorInvalidValue;
+  return tc_go<kLiteral>(TcArgs{h, a, 64, M, W, bias, Y, nullptr, err}, st);
+}
+
+// dX[r] = W^T dZ[r], W bf16 [64][64]
+cudaError_t mp_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, float *dX, int *err, cudaStream_t st) {
+  if (!aligned16(dZ) || !aligned16(W) || !aligned16(dX)) return cudaErrorInvalidValue;
+  return tc_go<kDx>(TcArgs{dZ, nullptr, 64, M, W, nullptr, dX, nullptr, err}, st);
+}
+
+// dh[r] = W0^T dZ[r] + W2^T dZ[r^1], da[r] = W1^T dZ[r], W bf16 [64][192], M even
+cudaError_t mp_literal_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, float *dh, float *da, int *err,
+                             cudaStream_t st) {
+  if ((M & 1) || !aligned16(dZ) || !aligned16(W) || !aligned16(dh) || !aligned16(da)) return cudaErrorInvalidValue;
+  return tc_go<kLiteralDx>(TcArgs{dZ, nullptr, 64, M, W, nullptr, dh, da, err}, st);
+}
+
+template <int NIN, int KIN>
+static cudaError_t wg_go(const float *dZ, int64_t M, const float *const *x, const int *xr, float *part, int nb,
+                         int *err, cudaStream_t st) {
+  static bool attr = false;
+  cudaError_t e = set_smem(k_mp_tc_wgrad<NIN, KIN>, kWgSmem, attr);
+  if (e != cudaSuccess) return e;
+  k_mp_tc_wgrad<NIN, KIN><<<nb, kTcRows, kWgSmem, st>>>(dZ, M, x[0], xr[0], x[1], xr[1], x[2], xr[2], part, err);
+  return cudaGetLastError();
+}
+
+// Partial weight gradients of one layer into part[nb][64][K nin + 1] (nin
+// 64-wide inputs, or nin = 1 with the 3-wide features); returns nb.
+int mp_wgrad_tc(const float *dZ, int64_t M, int nin, int K, const float *const *x, const int *xr, float *part,
+                int max_blocks, int *err, cudaStream_t st, cudaError_t *e) {
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(max_blocks, (M + 16 * kWgRows - 1) / (16 * kWgRows)));
+  bool al = aligned16(dZ);
+  for (int i = 0; i < nin; ++i) al = al && aligned16(x[i]);
+  const float *xx[3] = {x[0], nin > 1 ? x[1] : nullptr, nin > 2 ? x[2] : nullptr};
+  const int rr[3] = {xr[0], nin > 1 ? xr[1] : 0, nin > 2 ? xr[2] : 0};
+  if (!al)
+    *e = cudaErrorInvalidValue;
+  else if (nin == 1 && K == 3)
+    *e = wg_go<1, 3>(dZ, M, xx, rr, part, nb, err, st);
+  else if (nin == 1 && K == 64)
+    *e = wg_go<1, 64>(dZ, M, xx, rr, part, nb, err, st);
+  else if (nin == 3 && K == 64)
+    *e = wg_go<3, 64>(dZ, M, xx, rr, part, nb, err, st);
+  else
+    *e = cudaErrorInvalidValue;
+  return nb;
 }
 
 }  // namespace tsat

@@ -41,6 +41,28 @@ def test_mpnn_forward_and_gradient_match_oracle():
     assert rel_err(grad.cpu().numpy(), g_ref) < 1e-4
 
 
+def test_mpnn_matches_oracle_when_blocks_loop_over_tiles():
+    # 66,000 literal rows and 156,000 clause rows: more 128-row tiles than the
+    # dense layers launch blocks (148 x 3), so every block loops over tiles,
+    # and the weight-gradient blocks each reduce dozens of 32-row tiles
+    insts = [cnfgen.planted_ksat(30000, 126000, 3, 5), cnfgen.planted_ksat(3000, 30000, 5, 6)]
+    prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in insts])
+    pr = Proposer(seed=11)
+    y = np.concatenate([i.planted for i in insts]).astype(np.uint8)
+    ws = pr._ws(prob)
+    logits = torch.empty(prob.info["n_vars"], device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros_like(pr.params)
+    ts.tsat_mpnn_loss_grad(prob.h, pr.params, ws, torch.tensor(y, device="cuda"), logits, loss, grad)
+    torch.cuda.synchronize()
+    params = mpnn.bf16_round(pr.params.cpu().numpy())
+    g = mpnn.Graph([oracle.CNF(i.n_vars, i.clause_ptr, i.lits) for i in insts])
+    l_ref, g_ref, lg_ref = mpnn.loss_and_grad(g, params, y)
+    assert rel_err(logits.cpu().numpy(), lg_ref) < 1e-5
+    assert abs(loss.item() - l_ref) < 1e-5 * abs(l_ref)
+    assert rel_err(grad.cpu().numpy(), g_ref) < 1e-4
+
+
 def test_training_lowers_loss_and_learned_init_beats_random():
     # solver settings and ratios where the gradient solver finds models within
     # the step cap (3-SAT at 0.9x, 5-SAT at 0.5x, 4-SAT at 0.6x of threshold)
