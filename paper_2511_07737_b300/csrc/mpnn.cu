@@ -50,7 +50,8 @@ struct MpWs {  // activations kept for the backward pass
   float *dh, *dh2, *da, *de, *dm;  // gradient buffers
   float *part;                     // weight-gradient partials [kPartBlocks][64][193]
   __nv_bfloat16 *wb;               // BF16 copy of the parameters
-  float *ldeg;                     // [2V] literal degrees
+  float *linv;                     // [2V] 1 / max(literal degree, 1)
+  float *cinv;                     // [C] 1 / clause length
   float *dlog, *lossv;             // [V] dL/dlogit and per-variable loss terms
   int *err;                        // set by a tensor-core layer whose completion wait timed out
 };
@@ -72,6 +73,7 @@ static size_t mp_ws_bytes(int64_t V, int64_t C) {
   add(sizeof(float) * kPartBlocks * kH * (3 * kH + 1));
   add(sizeof(__nv_bfloat16) * kNParams);
   add(sizeof(float) * L);
+  add(sizeof(float) * C);
   add(sizeof(float) * V);
   add(sizeof(float) * V);
   add(sizeof(int) * 4);
@@ -97,7 +99,8 @@ static MpWs mp_ws_plan(void *base, int64_t V, int64_t C) {
   w.dm = (float *)take(sizeof(float) * C * kH);
   w.part = (float *)take(sizeof(float) * kPartBlocks * kH * (3 * kH + 1));
   w.wb = (__nv_bfloat16 *)take(sizeof(__nv_bfloat16) * kNParams);
-  w.ldeg = (float *)take(sizeof(float) * L);
+  w.linv = (float *)take(sizeof(float) * L);
+  w.cinv = (float *)take(sizeof(float) * C);
   w.dlog = (float *)take(sizeof(float) * V);
   w.lossv = (float *)take(sizeof(float) * V);
   w.err = (int *)take(sizeof(int) * 4);
@@ -109,18 +112,25 @@ __global__ void k_mp_to_bf16(const float *p, __nv_bfloat16 *b, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = __float2bfloat16_rn(p[i]);
 }
 
-// literal degrees and input features
-__global__ void k_mp_feat(ProbDev pd, float *ldeg, float *feat) {
+// input features and the inverse literal degrees (1 / max(deg, 1), the
+// variable-major mean's scale)
+__global__ void k_mp_feat(ProbDev pd, float *linv, float *feat) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < pd.V; v += (int64_t)gridDim.x * blockDim.x) {
     int dp = 0, dn = 0;
     for (int32_t o = pd.vptr[v]; o < pd.vptr[v + 1]; ++o) (pd.vocc[o] & 1) ? ++dn : ++dp;
-    ldeg[2 * v] = (float)dp;
-    ldeg[2 * v + 1] = (float)dn;
+    linv[2 * v] = 1.0f / fmaxf((float)dp, 1.f);
+    linv[2 * v + 1] = 1.0f / fmaxf((float)dn, 1.f);
     const float lp = logf(1.0f + (float)dp), ln = logf(1.0f + (float)dn);
     float *f0 = feat + (2 * v) * kFeat, *f1 = feat + (2 * v + 1) * kFeat;
     f0[0] = 1.f; f0[1] = lp; f0[2] = ln;
     f1[0] = 1.f; f1[1] = ln; f1[2] = lp;
   }
+}
+
+// 1 / clause length (the clause-major mean's scale)
+__global__ void k_mp_cinv(ProbDev pd, float *cinv) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < pd.C; c += (int64_t)gridDim.x * blockDim.x)
+    cinv[c] = 1.0f / (float)(pd.cptr[c + 1] - pd.cptr[c]);
 }
 
 struct DIn {
@@ -133,43 +143,148 @@ cudaError_t mp_dense_tc(const float *x, int K, int64_t M, const __nv_bfloat16 *W
                         int *err, cudaStream_t st);
 cudaError_t mp_literal_tc(const float *h, const float *a, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias,
                           float *Y, int *err, cudaStream_t st);
-cudaError_t mp_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, float *dX, int *err, cudaStream_t st);
-cudaError_t mp_literal_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, float *dh, float *da, int *err,
-                             cudaStream_t st);
+cudaError_t mp_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, const float *rscale, float *dX, int *err,
+                     cudaStream_t st);
+cudaError_t mp_literal_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, const float *rscale, float *dh,
+                             float *da, int *err, cudaStream_t st);
 int mp_wgrad_tc(const float *dZ, int64_t M, int nin, int K, const float *const *x, const int *xr, float *part,
                 int max_blocks, int *err, cudaStream_t st, cudaError_t *e);
 
-// m_c = mean_{l in c} h_l
-__global__ void k_mp_clause_mean(ProbDev pd, const float *h, float *m) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < pd.C;
-       c += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const int32_t b = pd.cptr[c], e = pd.cptr[c + 1];
-    float2 acc = make_float2(0.f, 0.f);
-    for (int32_t j = b; j < e; ++j) {
-      const float2 x = reinterpret_cast<const float2 *>(h + (int64_t)pd.clit[j] * kH)[lane];
-      acc.x += x.x;
-      acc.y += x.y;
+__device__ __forceinline__ int warp_max(int x) {
+  for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xFFFFFFFFu, x, o));
+  return x;
+}
+
+__device__ __forceinline__ void add4(float4 &a, const float4 &b) {
+  a.x += b.x;
+  a.y += b.y;
+  a.z += b.z;
+  a.w += b.w;
+}
+
+__device__ __forceinline__ float4 scale4(const float4 &a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
+
+// y = x where m > 0, else 0 (the ReLU's backward, mask from its output)
+__device__ __forceinline__ float4 relu_mask4(const float4 &x, const float4 &m) {
+  return make_float4(m.x > 0.f ? x.x : 0.f, m.y > 0.f ? x.y : 0.f, m.z > 0.f ? x.z : 0.f, m.w > 0.f ? x.w : 0.f);
+}
+
+// Clause-major gather: out[c] = sum over the literals l of clause c of
+// src[l] (64 floats), for 4 clauses per warp (8 lanes per clause, 8 floats
+// per lane as two float4).  The literal ids of a clause are loaded 8 at a time
+// by its lanes and broadcast by shuffles; the row loads of all four clauses
+// are issued together, four rows per round (the round count follows the
+// warp's longest clause; a shorter clause's loads past its end are predicated
+// off).
+//   MODE 0 (forward, clause mean): out[c] = sum * cinv[c]
+//   MODE 1 (backward of the variable-major mean, src pre-scaled by 1 / deg):
+//          out[c] = sum where e[c] > 0 (the clause layer's ReLU), else 0
+template <int MODE>
+__global__ void __launch_bounds__(256) k_mp_clause_gather(ProbDev pd, const float *__restrict__ src,
+                                                          const float *__restrict__ cinv, const float *__restrict__ e,
+                                                          float *__restrict__ out) {
+  const int lane = threadIdx.x & 31, gl = lane & 7, gbase = lane & ~7;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; c0 < pd.C; c0 += nw * 4) {
+    const int64_t c = c0 + (lane >> 3);
+    int32_t b = 0, n = 0;
+    if (c < pd.C) {
+      b = __ldg(pd.cptr + c);
+      n = __ldg(pd.cptr + c + 1) - b;
     }
-    const float s = 1.0f / (float)(e - b);
-    reinterpret_cast<float2 *>(m + c * kH)[lane] = make_float2(acc.x * s, acc.y * s);
+    const int nmax = warp_max(n);
+    float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+    for (int o = 0; o < nmax; o += 8) {
+      const int cnt = min(max(n - o, 0), 8);
+      const int32_t myl = gl < cnt ? __ldg(pd.clit + b + o + gl) : 0;
+      const int rounds = min(nmax - o, 8);
+      for (int j = 0; j < rounds; j += 4) {
+        float4 x[4][2];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {   // predicated loads: a clause past its end loads nothing
+          const int32_t l = __shfl_sync(0xFFFFFFFFu, myl, gbase + ((j + q) & 7));
+          const float4 *p = reinterpret_cast<const float4 *>(src + (int64_t)l * kH) + 2 * gl;
+          const bool in = j + q < cnt;
+          x[q][0] = in ? __ldg(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+          x[q][1] = in ? __ldg(p + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          add4(s0, x[q][0]);
+          add4(s1, x[q][1]);
+        }
+      }
+    }
+    if (c < pd.C) {
+      float4 *dst = reinterpret_cast<float4 *>(out + c * kH) + 2 * gl;
+      if (MODE == 0) {
+        const float s = __ldg(cinv + c);
+        dst[0] = scale4(s0, s);
+        dst[1] = scale4(s1, s);
+      } else {
+        const float4 *ep = reinterpret_cast<const float4 *>(e + c * kH) + 2 * gl;
+        dst[0] = relu_mask4(s0, __ldg(ep));
+        dst[1] = relu_mask4(s1, __ldg(ep + 1));
+      }
+    }
   }
 }
 
-// a_l = mean_{c owns l} e_c   (warp per variable: both literals)
-__global__ void k_mp_lit_mean(ProbDev pd, const float *e, const float *ldeg, float *a) {
+// Variable-major gather: for both literals of variable v, the sum over the
+// clauses c owning the literal of src[c] (64 floats), warp per variable (two
+// floats per lane).  The occurrence records are loaded 32 at a time by the
+// lanes and broadcast; 8 row loads are issued per round (predicated off past
+// the last occurrence).
+//   MODE 0 (forward, literal mean): out[l] = sum * linv[l]
+//   MODE 1 (backward of the clause-major mean, src pre-scaled by 1 / |c|):
+//          out[l] = (out[l] + sum) where h[l] > 0, else 0 (the ReLU of the
+//          layer that produced h, whose backward comes next)
+template <int MODE>
+__global__ void __launch_bounds__(256) k_mp_var_gather(ProbDev pd, const float *__restrict__ src,
+                                                       const float *__restrict__ linv, const float *__restrict__ h,
+                                                       float *__restrict__ out) {
   const int lane = threadIdx.x & 31;
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < pd.V;
-       v += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < pd.V; v += nw) {
+    const int32_t ob = __ldg(pd.vptr + v), oe = __ldg(pd.vptr + v + 1);
     float2 ap = make_float2(0.f, 0.f), an = ap;
-    for (int32_t o = pd.vptr[v]; o < pd.vptr[v + 1]; ++o) {
-      const int32_t oc = pd.vocc[o];
-      const float2 x = reinterpret_cast<const float2 *>(e + (int64_t)(oc >> 1) * kH)[lane];
-      if (oc & 1) { an.x += x.x; an.y += x.y; } else { ap.x += x.x; ap.y += x.y; }
+    for (int32_t base = ob; base < oe; base += 32) {
+      const int cnt = min(32, oe - base);
+      const int32_t myoc = lane < cnt ? __ldg(pd.vocc + base + lane) : 0;
+      for (int j = 0; j < cnt; j += 8) {
+        float2 x[8];
+        int32_t oc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {   // predicated loads past the last occurrence
+          oc[q] = __shfl_sync(0xFFFFFFFFu, myoc, (j + q) & 31);
+          x[q] = j + q < cnt ? __ldg(reinterpret_cast<const float2 *>(src + (int64_t)(oc[q] >> 1) * kH) + lane)
+                             : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (oc[q] & 1) {
+            an.x += x[q].x;
+            an.y += x[q].y;
+          } else {
+            ap.x += x[q].x;
+            ap.y += x[q].y;
+          }
+        }
+      }
     }
-    const float sp = 1.0f / fmaxf(ldeg[2 * v], 1.f), sn = 1.0f / fmaxf(ldeg[2 * v + 1], 1.f);
-    reinterpret_cast<float2 *>(a + (2 * v) * kH)[lane] = make_float2(ap.x * sp, ap.y * sp);
-    reinterpret_cast<float2 *>(a + (2 * v + 1) * kH)[lane] = make_float2(an.x * sn, an.y * sn);
+    float2 *p0 = reinterpret_cast<float2 *>(out + (2 * v) * kH) + lane;
+    float2 *p1 = reinterpret_cast<float2 *>(out + (2 * v + 1) * kH) + lane;
+    if (MODE == 0) {
+      const float sp = __ldg(linv + 2 * v), sn = __ldg(linv + 2 * v + 1);
+      *p0 = make_float2(ap.x * sp, ap.y * sp);
+      *p1 = make_float2(an.x * sn, an.y * sn);
+    } else {
+      const float2 m0 = __ldg(reinterpret_cast<const float2 *>(h + (2 * v) * kH) + lane);
+      const float2 m1 = __ldg(reinterpret_cast<const float2 *>(h + (2 * v + 1) * kH) + lane);
+      const float2 d0 = *p0, d1 = *p1;
+      *p0 = make_float2(m0.x > 0.f ? d0.x + ap.x : 0.f, m0.y > 0.f ? d0.y + ap.y : 0.f);
+      *p1 = make_float2(m1.x > 0.f ? d1.x + an.x : 0.f, m1.y > 0.f ? d1.y + an.y : 0.f);
+    }
   }
 }
 
@@ -196,19 +311,14 @@ __global__ void k_mp_bce(ProbDev pd, const float *logits, const uint8_t *y, floa
 }
 
 // output layer backward: dh3[2v .. 2v+1] = dlogit_v * wo
-__global__ void k_mp_out_bwd(ProbDev pd, const float *dlog, const __nv_bfloat16 *wb, float *dh) {
+// dh[l] = dlogit[v] wo[k] where h[l] > 0 (the last literal layer's ReLU), else 0
+__global__ void k_mp_out_bwd(ProbDev pd, const float *dlog, const __nv_bfloat16 *wb, const float *h, float *dh) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)pd.V * 2 * kH;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = i / (2 * kH);
     const int k = (int)(i % (2 * kH));
-    dh[2 * v * kH + k] = dlog[v] * __bfloat162float(wb[kOffOut + k]);
+    dh[i] = h[i] > 0.f ? dlog[v] * __bfloat162float(wb[kOffOut + k]) : 0.f;
   }
-}
-
-// in place: dZ = dY * [Y > 0]
-__global__ void k_mp_relu_bwd(const float *Y, float *dY, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (!(Y[i] > 0.f)) dY[i] = 0.f;
 }
 
 // grad[W(o,k)] (+)= sum_b part[b][o][k], bias into gbias[o]
@@ -219,42 +329,6 @@ __global__ void k_mp_wgrad_reduce(const float *part, int nb, int Kt, float *gW, 
     for (int b = 0; b < nb; ++b) s += part[(size_t)b * kH * ncol + idx];
     const int o = idx / ncol, k = idx % ncol;
     if (k == Kt) gb[o] = s; else gW[o * Kt + k] = s;
-  }
-}
-
-// de_c += sum_{l in c} da_l / deg_l ;  (transpose of the variable-major mean)
-__global__ void k_mp_clause_from_lit(ProbDev pd, const float *da, const float *ldeg, float *de) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < pd.C;
-       c += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int32_t j = pd.cptr[c]; j < pd.cptr[c + 1]; ++j) {
-      const int32_t l = pd.clit[j];
-      const float s = 1.0f / fmaxf(ldeg[l], 1.f);
-      const float2 x = reinterpret_cast<const float2 *>(da + (int64_t)l * kH)[lane];
-      acc.x += x.x * s;
-      acc.y += x.y * s;
-    }
-    reinterpret_cast<float2 *>(de + c * kH)[lane] = acc;
-  }
-}
-
-// dh_l += sum_{c owns l} dm_c / |c| ;  (transpose of the clause-major mean)
-__global__ void k_mp_lit_from_clause(ProbDev pd, const float *dm, float *dh) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < pd.V;
-       v += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    float2 ap = make_float2(0.f, 0.f), an = ap;
-    for (int32_t o = pd.vptr[v]; o < pd.vptr[v + 1]; ++o) {
-      const int32_t oc = pd.vocc[o], c = oc >> 1;
-      const float s = 1.0f / (float)(pd.cptr[c + 1] - pd.cptr[c]);
-      const float2 x = reinterpret_cast<const float2 *>(dm + (int64_t)c * kH)[lane];
-      if (oc & 1) { an.x += x.x * s; an.y += x.y * s; } else { ap.x += x.x * s; ap.y += x.y * s; }
-    }
-    float2 *p0 = reinterpret_cast<float2 *>(dh + (2 * v) * kH) + lane;
-    float2 *p1 = reinterpret_cast<float2 *>(dh + (2 * v + 1) * kH) + lane;
-    p0->x += ap.x; p0->y += ap.y;
-    p1->x += an.x; p1->y += an.y;
   }
 }
 
@@ -331,15 +405,16 @@ static int mp_forward(const tsat_problem *p, const float *params, MpWs &w, float
   const int64_t L = 2 * (int64_t)p->V, C = p->C;
   TSAT_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   k_mp_to_bf16<<<64, 256, 0, st>>>(params, w.wb, kNParams);
-  k_mp_feat<<<grid_for(p->V, 256), 256, 0, st>>>(pd, w.ldeg, w.feat);
+  k_mp_feat<<<grid_for(p->V, 256), 256, 0, st>>>(pd, w.linv, w.feat);
+  k_mp_cinv<<<grid_for(C, 256), 256, 0, st>>>(pd, w.cinv);
   TSAT_LAUNCH_CHECK("mpnn features");
   cudaError_t e = mp_dense_tc(w.feat, kFeat, L, w.wb + kOffW0, w.wb + kOffB0, w.h[0], w.err, st);
   if (e != cudaSuccess) return cuda_fail(e, "mpnn input layer");
   for (int t = 0; t < kLayers; ++t) {
-    k_mp_clause_mean<<<grid_for(C * 32, 256), 256, 0, st>>>(pd, w.h[t], w.m[t]);
+    k_mp_clause_gather<0><<<grid_for(C * 8, 256), 256, 0, st>>>(pd, w.h[t], w.cinv, nullptr, w.m[t]);
     if ((e = mp_dense_tc(w.m[t], kH, C, w.wb + off_wc(t), w.wb + off_bc(t), w.e[t], w.err, st)) != cudaSuccess)
       return cuda_fail(e, "mpnn clause layer");
-    k_mp_lit_mean<<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.e[t], w.ldeg, w.a[t]);
+    k_mp_var_gather<0><<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.e[t], w.linv, nullptr, w.a[t]);
     if ((e = mp_literal_tc(w.h[t], w.a[t], L, w.wb + off_wl(t), w.wb + off_bl(t), w.h[t + 1], w.err, st)) !=
         cudaSuccess)
       return cuda_fail(e, "mpnn literal layer");
@@ -367,39 +442,36 @@ static int mp_backward(const tsat_problem *p, MpWs &w, const float *dlog, float 
   const int64_t L = 2 * (int64_t)p->V, C = p->C;
   DIn none{nullptr, 0, 0};
   int rc;
-  // output layer
+  // output layer; dh leaves masked by the last literal layer's ReLU
   {
     const int nb = (int)std::min<int64_t>(kPartBlocks, std::max<int64_t>(1, p->V / 64));
     k_mp_out_wgrad<<<nb, 256, 0, st>>>(pd, w.h[kLayers], dlog, w.part);
     k_mp_out_reduce<<<1, 256, 0, st>>>(w.part, nb, grad);
-    k_mp_out_bwd<<<grid_for(p->V * 2 * kH, 256), 256, 0, st>>>(pd, dlog, w.wb, w.dh);
+    k_mp_out_bwd<<<grid_for(p->V * 2 * kH, 256), 256, 0, st>>>(pd, dlog, w.wb, w.h[kLayers], w.dh);
     TSAT_LAUNCH_CHECK("mpnn output backward");
   }
   for (int t = kLayers - 1; t >= 0; --t) {
-    // literal layer: h[t+1] = relu(Wl [h[t]; a[t]; h[t]^1] + bl)
-    k_mp_relu_bwd<<<grid_for(L * kH, 256), 256, 0, st>>>(w.h[t + 1], w.dh, L * kH);
+    // literal layer: h[t+1] = relu(Wl [h[t]; a[t]; h[t]^1] + bl), dh = dL/d(pre-activation)
     if ((rc = wgrad(3, DIn{w.h[t], kH, 0}, DIn{w.a[t], kH, 0}, DIn{w.h[t], kH, 1}, w.dh, L, w.part,
                     grad + off_wl(t), grad + off_bl(t), w.err, st)))
       return rc;
-    // dh2 from h_l and h_{l^1}, da from a_l
-    cudaError_t e = mp_literal_dx_tc(w.dh, L, w.wb + off_wl(t), w.dh2, w.da, w.err, st);
+    // dh2 from h_l and h_{l^1}; da from a_l, scaled by 1 / deg_l (the transpose of the variable-major mean)
+    cudaError_t e = mp_literal_dx_tc(w.dh, L, w.wb + off_wl(t), w.linv, w.dh2, w.da, w.err, st);
     if (e != cudaSuccess) return cuda_fail(e, "mpnn literal-layer input gradient");
-    // a = mean over owning clauses of e  ->  de
-    k_mp_clause_from_lit<<<grid_for(C * 32, 256), 256, 0, st>>>(pd, w.da, w.ldeg, w.de);
-    // clause layer: e = relu(Wc m + bc)
-    k_mp_relu_bwd<<<grid_for(C * kH, 256), 256, 0, st>>>(w.e[t], w.de, C * kH);
+    // a = mean over owning clauses of e  ->  de, masked by the clause layer's ReLU (e = relu(Wc m + bc))
+    k_mp_clause_gather<1><<<grid_for(C * 8, 256), 256, 0, st>>>(pd, w.da, nullptr, w.e[t], w.de);
     if ((rc = wgrad(1, DIn{w.m[t], kH, 0}, none, none, w.de, C, w.part, grad + off_wc(t), grad + off_bc(t), w.err,
                     st)))
       return rc;
-    if ((e = mp_dx_tc(w.de, C, w.wb + off_wc(t), w.dm, w.err, st)) != cudaSuccess)
+    // dm scaled by 1 / |c| (the transpose of the clause-major mean)
+    if ((e = mp_dx_tc(w.de, C, w.wb + off_wc(t), w.cinv, w.dm, w.err, st)) != cudaSuccess)
       return cuda_fail(e, "mpnn clause-layer input gradient");
-    // m = mean of h over the clause's literals -> dh2 += ...
-    k_mp_lit_from_clause<<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.dm, w.dh2);
+    // m = mean of h over the clause's literals -> dh2 += ..., then masked by the ReLU that produced h[t]
+    k_mp_var_gather<1><<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.dm, nullptr, w.h[t], w.dh2);
     TSAT_LAUNCH_CHECK("mpnn layer backward");
     std::swap(w.dh, w.dh2);
   }
-  // input layer
-  k_mp_relu_bwd<<<grid_for(L * kH, 256), 256, 0, st>>>(w.h[0], w.dh, L * kH);
+  // input layer (dh is masked by its ReLU already)
   if ((rc = wgrad(1, DIn{w.feat, kFeat, 0}, none, none, w.dh, L, w.part, grad + kOffW0, grad + kOffB0, w.err, st)))
     return rc;
   return TSAT_OK;

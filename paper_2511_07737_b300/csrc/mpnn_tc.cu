@@ -4,8 +4,10 @@
 // Layer forms (64 outputs; W is BF16, row-major [64][Ktot]):
 //   dense       Y[r]  = relu(W x[r] + b)                          x: K = 3 or 64
 //   literal     Y[r]  = relu(W0 h[r] + W1 a[r] + W2 h[r^1] + b)   W = [W0 W1 W2], 64 x 192
-//   dx          dX[r] = W^T dZ[r]                                 W: 64 x 64
-//   literal dx  dh[r] = W0^T dZ[r] + W2^T dZ[r^1],  da[r] = W1^T dZ[r]
+//   dx          dX[r] = s[r] W^T dZ[r]                            W: 64 x 64
+//   literal dx  dh[r] = W0^T dZ[r] + W2^T dZ[r^1],  da[r] = s[r] W1^T dZ[r]
+// (s: a per-row scale, the 1 / count of the mean that the next backward
+// gather transposes)
 //   weight grad part[b][o][k] = sum over block b's rows r of dZ[r][o] X[r][k],
 //               with a column of ones after the last k for the bias gradient.
 // Rows r and r^1 are the two literals of a variable.  Tiles start at
@@ -246,6 +248,7 @@ struct TcArgs {
   int K;                         // dense: width of x0 (3 or 64)
   int64_t M;                     // rows
   const __nv_bfloat16 *W, *bias;
+  const float *rscale;           // dx: per-row scale of dX; literal dx: per-row scale of da
   float *y0, *y1;                // outputs: y0 (Y, dX, dh), y1 (literal dx: da)
   int *err;
 };
@@ -351,6 +354,14 @@ __global__ void __launch_bounds__(kTcRows) k_mp_tc(TcArgs g) {
       }
       if (FORM == kLiteralDx) tc_ld16(tmem + lrow + 64u + (uint32_t)c, u);
       if (r < M) {
+        if (FORM == kDx || FORM == kLiteralDx) {   // the gather that follows reads scaled rows
+          const float sc = __ldg(g.rscale + r);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            if (FORM == kDx) v[q] *= sc;
+            else u[q] *= sc;
+          }
+        }
         float *dst = g.y0 + (size_t)r * kTcN + c;
 #pragma unroll
         for (int q = 0; q < 16; q += 4) {
@@ -570,27 +581,29 @@ static cudaError_t tc_go(const TcArgs &g, cudaStream_t st) {
 cudaError_t mp_dense_tc(const float *x, int K, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias, float *Y,
                         int *err, cudaStream_t st) {
   if ((K != 3 && K != 64) || !aligned16(x) || !aligned16(W) || !aligned16(Y)) return cudaErrorInvalidValue;
-  return tc_go<kDense>(TcArgs{x, nullptr, K, M, W, bias, Y, nullptr, err}, st);
+  return tc_go<kDense>(TcArgs{x, nullptr, K, M, W, bias, nullptr, Y, nullptr, err}, st);
 }
 
 // Y[r] = relu(W0 h[r] + W1 a[r] + W2 h[r^1] + b), W bf16 [64][192], M even
 cudaError_t mp_literal_tc(const float *h, const float *a, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias,
                           float *Y, int *err, cudaStream_t st) {
   if ((M & 1) || !aligned16(h) || !aligned16(a) || !aligned16(W) || !aligned16(Y)) return cudaErrorInvalidValue;
-  return tc_go<kLiteral>(TcArgs{h, a, 64, M, W, bias, Y, nullptr, err}, st);
+  return tc_go<kLiteral>(TcArgs{h, a, 64, M, W, bias, nullptr, Y, nullptr, err}, st);
 }
 
-// dX[r] = W^T dZ[r], W bf16 [64][64]
-cudaError_t mp_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, float *dX, int *err, cudaStream_t st) {
-  if (!aligned16(dZ) || !aligned16(W) || !aligned16(dX)) return cudaErrorInvalidValue;
-  return tc_go<kDx>(TcArgs{dZ, nullptr, 64, M, W, nullptr, dX, nullptr, err}, st);
+// dX[r] = rscale[r] W^T dZ[r], W bf16 [64][64]
+cudaError_t mp_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, const float *rscale, float *dX, int *err,
+                     cudaStream_t st) {
+  if (!rscale || !aligned16(dZ) || !aligned16(W) || !aligned16(dX)) return cudaErrorInvalidValue;
+  return tc_go<kDx>(TcArgs{dZ, nullptr, 64, M, W, nullptr, rscale, dX, nullptr, err}, st);
 }
 
-// dh[r] = W0^T dZ[r] + W2^T dZ[r^1], da[r] = W1^T dZ[r], W bf16 [64][192], M even
-cudaError_t mp_literal_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, float *dh, float *da, int *err,
-                             cudaStream_t st) {
-  if ((M & 1) || !aligned16(dZ) || !aligned16(W) || !aligned16(dh) || !aligned16(da)) return cudaErrorInvalidValue;
-  return tc_go<kLiteralDx>(TcArgs{dZ, nullptr, 64, M, W, nullptr, dh, da, err}, st);
+// dh[r] = W0^T dZ[r] + W2^T dZ[r^1], da[r] = rscale[r] W1^T dZ[r], W bf16 [64][192], M even
+cudaError_t mp_literal_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, const float *rscale, float *dh,
+                             float *da, int *err, cudaStream_t st) {
+  if ((M & 1) || !rscale || !aligned16(dZ) || !aligned16(W) || !aligned16(dh) || !aligned16(da))
+    return cudaErrorInvalidValue;
+  return tc_go<kLiteralDx>(TcArgs{dZ, nullptr, 64, M, W, nullptr, rscale, dh, da, err}, st);
 }
 
 template <int NIN, int KIN>
