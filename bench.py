@@ -847,6 +847,7 @@ def exp_proposer_step(args):
 
     t_step = timed(lambda: ts.tsat_mpnn_loss_grad(prob.h, params, ws, y, logits, loss, grad))
     t_fwd = timed(lambda: ts.tsat_mpnn_forward(prob.h, params, ws, logits))
+    ts.tsat_mpnn_status(prob.h, ws)
     _emit({"experiment": "proposer_step", "instances": n_inst, "n_vars": V, "n_clauses": prob.info["n_clauses"],
            "nnz": prob.info["nnz"], "train_step_ms": t_step, "forward_ms": t_fwd, "loss": float(loss.item())})
 

@@ -46,7 +46,7 @@ extern "C" {
 #define TSAT_EEMPTY -3    /* an empty clause: the formula is unsatisfiable by definition */
 #define TSAT_EWS -4       /* workspace / state buffer smaller than the queried size */
 #define TSAT_ECUDA -5     /* a CUDA runtime call failed; see tsat_last_error() */
-#define TSAT_ETIMEOUT -6  /* a device-side wait gave up (reserved; no kernel waits today) */
+#define TSAT_ETIMEOUT -6  /* a device-side wait gave up (the proposer's tensor-core layers: tsat_mpnn_status) */
 #define TSAT_ENOMEM -7    /* host allocation failed */
 #define TSAT_ELEN -8      /* a clause is longer than TSAT_MAX_CLAUSE_LEN after de-duplication */
 #define TSAT_ESTATE -9    /* handle used with a state it was not built for, or not initialised */
@@ -419,6 +419,12 @@ int tsat_mpnn_loss_grad(const tsat_problem *p, const float *d_params, void *d_ws
                         const uint8_t *d_targets, float *d_logits, float *d_loss, float *d_grad, cudaStream_t stream);
 int tsat_mpnn_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int64_t step, float lr,
                    cudaStream_t stream);
+/* Whether the last tsat_mpnn_forward / tsat_mpnn_loss_grad on this workspace
+ * completed every tensor-core layer.  Each layer's wait for its MMAs is
+ * bounded; one that gives up sets a flag in the workspace (the forward clears
+ * it when it starts) and leaves its outputs invalid.  Synchronises `stream`,
+ * reads the flag: TSAT_OK, or TSAT_ETIMEOUT when a wait gave up. */
+int tsat_mpnn_status(const tsat_problem *p, const void *d_ws, size_t ws_bytes, cudaStream_t stream);
 
 /* Number of kernel launches one step issues (for launch accounting). */
 int32_t tsat_launches_per_step(const tsat_state *s);

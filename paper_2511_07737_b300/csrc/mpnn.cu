@@ -521,6 +521,20 @@ int tsat_mpnn_loss_grad(const tsat_problem *p, const float *d_params, void *d_ws
   return mp_backward(p, w, w.dlog, d_grad, stream);
 }
 
+int tsat_mpnn_status(const tsat_problem *p, const void *d_ws, size_t ws_bytes, cudaStream_t stream) {
+  if (!p || !d_ws) return TSAT_EINVAL;
+  if (ws_bytes < mp_ws_bytes(p->V, p->C)) { set_error("mpnn workspace too small"); return TSAT_EWS; }
+  if ((uintptr_t)d_ws & 255u) { set_error("mpnn workspace not 256-byte aligned"); return TSAT_EINVAL; }
+  const MpWs w = mp_ws_plan(const_cast<void *>(d_ws), p->V, p->C);
+  int flag = 0;
+  TSAT_CUDA(cudaMemcpyAsync(&flag, w.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  TSAT_CUDA(cudaStreamSynchronize(stream));
+  if (flag) {
+    set_error("a tensor-core layer of the proposer gave up waiting for its MMAs; its outputs are not valid");
+    return TSAT_ETIMEOUT;
+  }
+  return TSAT_OK;
+}
 int tsat_mpnn_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int64_t step, float lr,
                    cudaStream_t stream) {
   if (!d_params || !d_grad || !d_m || !d_v || step < 1) return TSAT_EINVAL;

@@ -93,6 +93,7 @@ class Proposer:
         out = torch.empty(prob.info["n_vars"], dtype=torch.float32, device=self.device)
         ws = self._ws(prob)
         ts.tsat_mpnn_forward(prob.h, self.params, ws, out)
+        ts.tsat_mpnn_status(prob.h, ws)
         return out
 
     def train_step(self, prob: ts.Problem, targets: torch.Tensor, lr: float = 1e-3) -> float:
@@ -100,6 +101,7 @@ class Proposer:
         logits = torch.empty(prob.info["n_vars"], dtype=torch.float32, device=self.device)
         loss = torch.zeros(1, dtype=torch.float32, device=self.device)
         ts.tsat_mpnn_loss_grad(prob.h, self.params, ws, targets, logits, loss, self.grad)
+        ts.tsat_mpnn_status(prob.h, ws)
         self.step += 1
         ts.tsat_mpnn_adam(self.params, self.grad, self.m, self.v, self.step, lr)
         return float(loss.item()) / prob.info["n_inst"]

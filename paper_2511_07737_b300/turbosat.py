@@ -111,6 +111,7 @@ def lib():
             "tsat_mpnn_forward": (ctypes.c_int, [P, P, P, sz, P, P]),
             "tsat_mpnn_loss_grad": (ctypes.c_int, [P, P, P, sz, P, P, P, P, P]),
             "tsat_mpnn_adam": (ctypes.c_int, [P, P, P, P, i64, f32, P]),
+            "tsat_mpnn_status": (ctypes.c_int, [P, P, sz, P]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -407,6 +408,12 @@ def tsat_mpnn_loss_grad(h, params, ws, targets, logits, loss, grad, stream=None)
 def tsat_mpnn_adam(params, grad, m, v, step: int, lr: float, stream=None):
     _ck(lib().tsat_mpnn_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr), _stream(stream)),
         "tsat_mpnn_adam")
+
+
+def tsat_mpnn_status(h, ws: torch.Tensor, stream=None):
+    """Raise if a tensor-core layer of the last proposer call on `ws` gave up
+    waiting for its MMAs (TSAT_ETIMEOUT); synchronises the stream."""
+    _ck(lib().tsat_mpnn_status(h, _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "tsat_mpnn_status")
 
 
 # ---------------------------------------------------------------- lifetime holders

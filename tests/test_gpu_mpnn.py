@@ -32,7 +32,7 @@ def test_mpnn_forward_and_gradient_match_oracle():
     loss = torch.zeros(1, device="cuda")
     grad = torch.zeros_like(pr.params)
     ts.tsat_mpnn_loss_grad(prob.h, pr.params, ws, torch.tensor(y, device="cuda"), logits, loss, grad)
-    torch.cuda.synchronize()
+    ts.tsat_mpnn_status(prob.h, ws)                          # every tensor-core layer's wait completed
     params = mpnn.bf16_round(pr.params.cpu().numpy())       # the kernels compute with BF16 weights
     g = mpnn.Graph([oracle.CNF(i.n_vars, i.clause_ptr, i.lits) for i in insts])
     l_ref, g_ref, lg_ref = mpnn.loss_and_grad(g, params, y)
