@@ -26,13 +26,15 @@
 // Shared-memory operands use the no-swizzle K-major core-matrix layout (8 x
 // 16-byte core matrices; K-adjacent ones 128 bytes apart, 8-row groups K/8 x
 // 128 bytes apart).  Forward / dx blocks stage the weights once, then loop
-// over 128-row tiles: every thread issues all of its tile loads (16-byte
-// vectors) before the first conversion, each warp's stores cover contiguous
-// shared memory, one thread issues the MMAs (M 128, N 64, K 16), and
-// tcgen05.commit signals an mbarrier.  Every wait on the mbarrier is bounded:
-// on time-out the block records an error in the caller's flag and leaves after
-// freeing its tensor memory.  The epilogue reads the accumulators with
-// tcgen05.ld (warp q: rows 32q .. 32q + 31, one row per thread).
+// over 128-row tiles: the tile's FP32 rows arrive by one bulk copy per tile
+// (64-wide dense, dx) or by 16-byte vector loads all issued before the first
+// conversion, each warp's stores of the BF16 parts cover contiguous shared
+// memory, one thread issues the MMAs (M 128, N 64, K 16), and tcgen05.commit
+// signals an mbarrier.  Every wait on an mbarrier is bounded, and the outcome
+// is decided for the whole block: on time-out the block records an error in the
+// caller's flag and leaves after freeing its tensor memory.  The epilogue reads
+// the accumulators with tcgen05.ld (warp q: rows 32q .. 32q + 31, one row per
+// thread) into an output tile in shared memory, written out whole rows at a time.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -253,6 +255,21 @@ struct TcArgs {
   int *err;
 };
 
+// Output tiles pass through shared memory, rows kOtStride floats apart (the
+// row-per-thread writes then spread over the banks): tile_out writes the
+// tile's rows below M with 16 lanes per 256-byte row, two rows per warp store.
+constexpr int kOtStride = 68;
+
+__device__ __forceinline__ void tile_out(const float *otile, float *y, int64_t r0, int64_t M, int tid) {
+#pragma unroll 4
+  for (int i = 0; i < kTcRows / 8; ++i) {
+    const int rr = 8 * i + (tid >> 4), c4 = 4 * (tid & 15);
+    if (r0 + rr < M)
+      *reinterpret_cast<float4 *>(y + (size_t)(r0 + rr) * kTcN + c4) =
+          *reinterpret_cast<const float4 *>(otile + rr * kOtStride + c4);
+  }
+}
+
 // MMAs of one staged A tile (3 parts, kA wide) against weight block j into
 // the accumulator at tensor-memory column `col`.
 __device__ __forceinline__ void tc_mma_tile(uint32_t tmem, uint32_t col, uint32_t sa, uint32_t sb, int j, int kA,
@@ -265,6 +282,9 @@ __device__ __forceinline__ void tc_mma_tile(uint32_t tmem, uint32_t col, uint32_
     }
 }
 
+// The dense layer on the 3-wide input features, the literal layer and the
+// literal input gradient: tiles staged by per-thread vector loads (the
+// 64-wide dense layer and dx use the bulk-staged k_mp_tcb below).
 template <int FORM>
 __global__ void __launch_bounds__(kTcRows) k_mp_tc(TcArgs g) {
   constexpr int NB = (FORM == kLiteral || FORM == kLiteralDx) ? 3 : 1;   // weight blocks
@@ -322,7 +342,9 @@ __global__ void __launch_bounds__(kTcRows) k_mp_tc(TcArgs g) {
       }
       tc_commit(mb);
     }
-    ok = tc_wait(mb, phase);   // the MMAs are done: the A tile may be overwritten
+    // the MMAs are done (the A tile may be overwritten); the decision is the
+    // whole block's, so no thread leaves the loop while others wait at a barrier
+    ok = __syncthreads_and(tc_wait(mb, phase)) != 0;
     phase ^= 1u;
     if (!ok) break;
     if (FORM == kLiteral) {   // stage 1: a
@@ -334,17 +356,21 @@ __global__ void __launch_bounds__(kTcRows) k_mp_tc(TcArgs g) {
         tc_mma_tile(tmem, 0, sa, sb, 1, 64, false);   // + W1 a[r]
         tc_commit(mb);
       }
-      ok = tc_wait(mb, phase);
+      ok = __syncthreads_and(tc_wait(mb, phase)) != 0;
       phase ^= 1u;
       if (!ok) break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    // epilogue: warp q reads rows 32 q .. 32 q + 31 (tensor memory lanes)
-    const int64_t r = r0 + 32 * warp + (tid & 31);
+    // epilogue: warp q reads rows 32 q .. 32 q + 31 (tensor memory lanes) into
+    // the output tile in shared memory (the A parts are free once the MMAs
+    // are done), then the tile goes out two whole rows per warp store; the
+    // literal input gradient writes its two outputs one after the other
+    float *otile = reinterpret_cast<float *>(sA);
+    const int row = 32 * warp + (tid & 31);
     const uint32_t lrow = (uint32_t)(32 * warp) << 16;
 #pragma unroll
     for (int c = 0; c < kTcN; c += 16) {
-      float v[16], u[16];
+      float v[16];
       tc_ld16(tmem + lrow + (uint32_t)c, v);
       if (FORM == kLiteral || FORM == kLiteralDx) {
         float s[16];
@@ -352,40 +378,187 @@ __global__ void __launch_bounds__(kTcRows) k_mp_tc(TcArgs g) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, s[q], 1);
       }
-      if (FORM == kLiteralDx) tc_ld16(tmem + lrow + 64u + (uint32_t)c, u);
-      if (r < M) {
-        if (FORM == kDx || FORM == kLiteralDx) {   // the gather that follows reads scaled rows
-          const float sc = __ldg(g.rscale + r);
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            if (FORM == kDx) v[q] *= sc;
-            else u[q] *= sc;
-          }
+      for (int q = 0; q < 16; q += 4) {
+        float4 o = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        if (FORM == kDense || FORM == kLiteral) {
+          o.x = fmaxf(o.x + __bfloat162float(g.bias[c + q]), 0.f);
+          o.y = fmaxf(o.y + __bfloat162float(g.bias[c + q + 1]), 0.f);
+          o.z = fmaxf(o.z + __bfloat162float(g.bias[c + q + 2]), 0.f);
+          o.w = fmaxf(o.w + __bfloat162float(g.bias[c + q + 3]), 0.f);
         }
-        float *dst = g.y0 + (size_t)r * kTcN + c;
-#pragma unroll
-        for (int q = 0; q < 16; q += 4) {
-          float4 o = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-          if (FORM == kDense || FORM == kLiteral) {
-            o.x = fmaxf(o.x + __bfloat162float(g.bias[c + q]), 0.f);
-            o.y = fmaxf(o.y + __bfloat162float(g.bias[c + q + 1]), 0.f);
-            o.z = fmaxf(o.z + __bfloat162float(g.bias[c + q + 2]), 0.f);
-            o.w = fmaxf(o.w + __bfloat162float(g.bias[c + q + 3]), 0.f);
-          }
-          *reinterpret_cast<float4 *>(dst + q) = o;
-          if (FORM == kLiteralDx)
-            *reinterpret_cast<float4 *>(g.y1 + (size_t)r * kTcN + c + q) =
-                make_float4(u[q], u[q + 1], u[q + 2], u[q + 3]);
-        }
+        *reinterpret_cast<float4 *>(otile + row * kOtStride + c + q) = o;
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();   // every warp has read the accumulators before the next tile's MMAs
+    __syncthreads();
+    tile_out(otile, g.y0, r0, M, tid);
+    if (FORM == kLiteralDx) {   // da = s W1^T dZ, scaled for the gather that follows
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const float sc = __ldg(g.rscale + min(r0 + row, M - 1));
+#pragma unroll
+      for (int c = 0; c < kTcN; c += 16) {
+        float u[16];
+        tc_ld16(tmem + lrow + 64u + (uint32_t)c, u);
+#pragma unroll
+        for (int q = 0; q < 16; q += 4)
+          *reinterpret_cast<float4 *>(otile + row * kOtStride + c + q) =
+              make_float4(u[q] * sc, u[q + 1] * sc, u[q + 2] * sc, u[q + 3] * sc);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncthreads();
+      tile_out(otile, g.y1, r0, M, tid);
+    }
+    __syncthreads();   // the output tile is read before the next tile's parts overwrite it
   }
   if (!ok && g.err && (tid & 31) == 0) atomicExch(g.err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NCOL) : "memory");
+}
+
+// ---------------------------------------------------------------- bulk-staged forms
+// The dense layer with 64-wide input (the clause layer) and the dx form read
+// one contiguous FP32 tile per 128 rows (32 KB).  One thread fetches it with a
+// 1-D bulk copy (cp.async.bulk, global -> shared, completing on an mbarrier)
+// into a staging buffer; as soon as the block has turned the staged rows into
+// the three BF16 parts, that thread issues the copy of the block's next tile,
+// which then runs under this tile's MMAs and epilogue.  Shared memory: B
+// [64 x 64] bf16 | A [3 parts][128 x 64] bf16 | FP32 tile [128][64] | two
+// mbarriers (tile copy, MMAs) | tensor-memory address: 88 KB, two blocks per SM.
+constexpr int kTbStage = kTcRows * 64 * 4;
+constexpr int kTbSmem = kTcBBlock + kTcParts * kTcAPart + kTbStage + 64;
+
+// Copy `bytes` (a multiple of 16) from global `src` to shared `dst`, completing
+// on the mbarrier `bar` (one arrival with the byte count).
+__device__ __forceinline__ void tb_fetch(uint32_t dst, const float *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// The staged rows (row-major [128][64] FP32) as three BF16 parts, with the
+// thread mapping of stage_a64 (each warp's stores fill contiguous shared memory).
+__device__ __forceinline__ void convert_a64(unsigned char *sA, const float *stg, int tid) {
+  const int warp = tid >> 5, lane = tid & 31;
+  const int k = 16 * warp + 4 * (lane & 3);
+  float4 v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = *reinterpret_cast<const float4 *>(stg + (8 * i + (lane >> 2)) * 64 + k);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const uint32_t o = tc_off(8 * i + (lane >> 2), k, 64);
+    uint2 h, m, l;
+    split3x2(v[i].x, v[i].y, h.x, m.x, l.x);
+    split3x2(v[i].z, v[i].w, h.y, m.y, l.y);
+    *reinterpret_cast<uint2 *>(sA + o) = h;
+    *reinterpret_cast<uint2 *>(sA + kTcAPart + o) = m;
+    *reinterpret_cast<uint2 *>(sA + 2 * kTcAPart + o) = l;
+  }
+}
+
+// FORM: kDense (64-wide input) or kDx.
+template <int FORM>
+__global__ void __launch_bounds__(kTcRows) k_mp_tcb(TcArgs g) {
+  extern __shared__ __align__(1024) unsigned char smb[];
+  unsigned char *sB = smb;
+  unsigned char *sA = smb + kTcBBlock;
+  float *stg = reinterpret_cast<float *>(sA + kTcParts * kTcAPart);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(stg) + kTbStage);   // copy, MMAs
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(stg) + kTbStage + 16);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  stage_b64<FORM == kDx>(sB, g.W, 64, 0, tid);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bars)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bars + 1)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "r"(kTcN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t lb = smem_u32(bars), mb = smem_u32(bars + 1), sa = smem_u32(sA), sb = smem_u32(sB),
+                 ss = smem_u32(stg);
+  const int64_t M = g.M, ntiles = (M + kTcRows - 1) / kTcRows;
+  auto tile_bytes = [&](int64_t t) { return (uint32_t)(min((int64_t)kTcRows, M - t * kTcRows) * 64 * 4); };
+  uint32_t lph = 0, mph = 0;
+  bool ok = true, pending = false;   // pending: a copy issued and not yet waited for (thread 0)
+  int64_t tile = blockIdx.x;
+  if (tid == 0 && tile < ntiles) {
+    tb_fetch(ss, g.x0 + (size_t)tile * kTcRows * 64, tile_bytes(tile), lb);
+    pending = true;
+  }
+  for (; tile < ntiles && ok; tile += gridDim.x) {
+    const int64_t r0 = tile * kTcRows;
+    const bool got = tc_wait(lb, lph);
+    ok = __syncthreads_and(got) != 0;   // the tile's rows are in shared memory
+    if (got) {                          // else the copy may still be in flight: waited for below
+      lph ^= 1u;
+      pending = false;
+    }
+    if (!ok) break;
+    convert_a64(sA, stg, tid);   // rows past M hold stale values; their outputs are not stored
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();             // the parts are written and the staged rows consumed
+    if (tid == 0) {
+      const int64_t nt = tile + gridDim.x;
+      if (nt < ntiles) {         // the next tile's copy runs under this tile's MMAs and epilogue
+        tb_fetch(ss, g.x0 + (size_t)nt * kTcRows * 64, tile_bytes(nt), lb);
+        pending = true;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      tc_mma_tile(tmem, 0, sa, sb, 0, 64, true);
+      tc_commit(mb);
+    }
+    ok = __syncthreads_and(tc_wait(mb, mph)) != 0;
+    mph ^= 1u;
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    // epilogue: the accumulator rows (thread = row) into the output tile in
+    // shared memory (the A parts are free once the MMAs are done), then out
+    // with each warp writing two whole rows per store
+    float *otile = reinterpret_cast<float *>(sA);
+    const int row = 32 * warp + (tid & 31);
+    const float sc = FORM == kDx ? __ldg(g.rscale + min(r0 + row, M - 1)) : 1.0f;
+#pragma unroll
+    for (int c = 0; c < kTcN; c += 16) {
+      float v[16];
+      tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+#pragma unroll
+      for (int q = 0; q < 16; q += 4) {
+        float4 o;
+        if (FORM == kDense)
+          o = make_float4(fmaxf(v[q] + __bfloat162float(g.bias[c + q]), 0.f),
+                          fmaxf(v[q + 1] + __bfloat162float(g.bias[c + q + 1]), 0.f),
+                          fmaxf(v[q + 2] + __bfloat162float(g.bias[c + q + 2]), 0.f),
+                          fmaxf(v[q + 3] + __bfloat162float(g.bias[c + q + 3]), 0.f));
+        else
+          o = make_float4(v[q] * sc, v[q + 1] * sc, v[q + 2] * sc, v[q + 3] * sc);
+        *reinterpret_cast<float4 *>(otile + row * kOtStride + c + q) = o;
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();   // the tile is in shared memory; every warp has read the accumulator
+    tile_out(otile, g.y0, r0, M, tid);
+    __syncthreads();   // the output tile is read before the next tile's parts overwrite it
+  }
+  if (!ok) {
+    if (g.err && (tid & 31) == 0) atomicExch(g.err, 1);
+    if (tid == 0 && pending) tc_wait(lb, lph);   // a copy still in flight lands before the block leaves
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcN) : "memory");
 }
 
 // ---------------------------------------------------------------- weight gradient
@@ -527,7 +700,7 @@ __global__ void __launch_bounds__(kTcRows) k_mp_tc_wgrad(const float *dZ, int64_
       tc_commit(mb);
     }
     first = false;
-    ok = tc_wait(mb, phase);   // the MMAs are done: the tiles may be overwritten
+    ok = __syncthreads_and(tc_wait(mb, phase)) != 0;   // the MMAs are done (block-wide decision)
     phase ^= 1u;
   }
   if (ok) {
@@ -577,11 +750,22 @@ static cudaError_t tc_go(const TcArgs &g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int FORM>
+static cudaError_t tb_go(const TcArgs &g, cudaStream_t st) {
+  static bool attr = false;
+  cudaError_t e = set_smem(k_mp_tcb<FORM>, kTbSmem, attr);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(148 * 2, (g.M + kTcRows - 1) / kTcRows));
+  k_mp_tcb<FORM><<<grid, kTcRows, kTbSmem, st>>>(g);
+  return cudaGetLastError();
+}
+
 // Y[r] = relu(W x[r] + b), x FP32 [M][K] with K = 3 or 64, W bf16 [64][K]
 cudaError_t mp_dense_tc(const float *x, int K, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias, float *Y,
                         int *err, cudaStream_t st) {
   if ((K != 3 && K != 64) || !aligned16(x) || !aligned16(W) || !aligned16(Y)) return cudaErrorInvalidValue;
-  return tc_go<kDense>(TcArgs{x, nullptr, K, M, W, bias, nullptr, Y, nullptr, err}, st);
+  const TcArgs g{x, nullptr, K, M, W, bias, nullptr, Y, nullptr, err};
+  return K == 64 ? tb_go<kDense>(g, st) : tc_go<kDense>(g, st);
 }
 
 // Y[r] = relu(W0 h[r] + W1 a[r] + W2 h[r^1] + b), W bf16 [64][192], M even
@@ -595,7 +779,7 @@ cudaError_t mp_literal_tc(const float *h, const float *a, int64_t M, const __nv_
 cudaError_t mp_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W, const float *rscale, float *dX, int *err,
                      cudaStream_t st) {
   if (!rscale || !aligned16(dZ) || !aligned16(W) || !aligned16(dX)) return cudaErrorInvalidValue;
-  return tc_go<kDx>(TcArgs{dZ, nullptr, 64, M, W, nullptr, rscale, dX, nullptr, err}, st);
+  return tb_go<kDx>(TcArgs{dZ, nullptr, 64, M, W, nullptr, rscale, dX, nullptr, err}, st);
 }
 
 // dh[r] = W0^T dZ[r] + W2^T dZ[r^1], da[r] = rscale[r] W1^T dZ[r], W bf16 [64][192], M even
