@@ -170,12 +170,15 @@ __device__ __forceinline__ float4 relu_mask4(const float4 &x, const float4 &m) {
 }
 
 // Clause-major gather: out[c] = sum over the literals l of clause c of
-// src[l] (64 floats), for 4 clauses per warp (8 lanes per clause, 8 floats
-// per lane as two float4).  The literal ids of a clause are loaded 8 at a time
-// by its lanes and broadcast by shuffles; the row loads of all four clauses
-// are issued together, four rows per round (the round count follows the
-// warp's longest clause; a shorter clause's loads past its end are predicated
-// off).
+// src[l] (64 floats).  A warp takes 32 consecutive clauses: their offsets
+// come in two coalesced loads (lane l: cptr[c0 + l], cptr[c0 + l + 1]) and
+// are handed out by shuffles; it then works through them in 8 groups of 4
+// clauses (8 lanes per clause, 8 floats per lane as two float4).  A group's
+// literal ids are loaded 8 at a time by its lanes and broadcast, and the next
+// group's ids are loaded while this group's rows are summed, so only the row
+// loads wait.  The row loads of the four clauses are issued together, four
+// rows per round (the round count follows the group's longest clause; a
+// shorter clause's loads past its end are predicated off).
 //   MODE 0 (forward, clause mean): out[c] = sum * cinv[c]
 //   MODE 1 (backward of the variable-major mean, src pre-scaled by 1 / deg):
 //          out[c] = sum where e[c] > 0 (the clause layer's ReLU), else 0
@@ -184,48 +187,60 @@ __global__ void __launch_bounds__(256) k_mp_clause_gather(ProbDev pd, const floa
                                                           const float *__restrict__ cinv, const float *__restrict__ e,
                                                           float *__restrict__ out) {
   const int lane = threadIdx.x & 31, gl = lane & 7, gbase = lane & ~7;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; c0 < pd.C; c0 += nw * 4) {
-    const int64_t c = c0 + (lane >> 3);
-    int32_t b = 0, n = 0;
-    if (c < pd.C) {
-      b = __ldg(pd.cptr + c);
-      n = __ldg(pd.cptr + c + 1) - b;
-    }
-    const int nmax = warp_max(n);
-    float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
-    for (int o = 0; o < nmax; o += 8) {
-      const int cnt = min(max(n - o, 0), 8);
-      const int32_t myl = gl < cnt ? __ldg(pd.clit + b + o + gl) : 0;
-      const int rounds = min(nmax - o, 8);
-      for (int j = 0; j < rounds; j += 4) {
-        float4 x[4][2];
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5, C = pd.C;
+  for (int64_t c0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; c0 < C; c0 += nw * 32) {
+    const int32_t pb = __ldg(pd.cptr + min(c0 + lane, C)), pe = __ldg(pd.cptr + min(c0 + lane + 1, C));
+    // group g: clauses c0 + 4 g + lane / 8; returns the lane's first literal id (clauses past C are empty)
+    auto ids = [&](int g, int32_t &b, int32_t &n) -> int32_t {
+      const int q = 4 * g + (lane >> 3);
+      b = __shfl_sync(0xFFFFFFFFu, pb, q);
+      n = __shfl_sync(0xFFFFFFFFu, pe, q) - b;
+      return gl < min(n, 8) ? __ldg(pd.clit + b + gl) : 0;
+    };
+    int32_t b, n;
+    int32_t myl = ids(0, b, n);
+    for (int g = 0; g < 8; ++g) {
+      int32_t bn = 0, nn = 0, myln = 0;
+      if (g < 7) myln = ids(g + 1, bn, nn);
+      const int64_t c = c0 + 4 * g + (lane >> 3);
+      const int nmax = warp_max(n);
+      float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+      for (int o = 0; o < nmax; o += 8) {
+        const int cnt = min(max(n - o, 0), 8);
+        const int32_t ml = o == 0 ? myl : (gl < cnt ? __ldg(pd.clit + b + o + gl) : 0);
+        const int rounds = min(nmax - o, 8);
+        for (int j = 0; j < rounds; j += 4) {
+          float4 x[4][2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {   // predicated loads: a clause past its end loads nothing
-          const int32_t l = __shfl_sync(0xFFFFFFFFu, myl, gbase + ((j + q) & 7));
-          const float4 *p = reinterpret_cast<const float4 *>(src + (int64_t)l * kH) + 2 * gl;
-          const bool in = j + q < cnt;
-          x[q][0] = in ? __ldg(p) : make_float4(0.f, 0.f, 0.f, 0.f);
-          x[q][1] = in ? __ldg(p + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+          for (int q = 0; q < 4; ++q) {   // predicated loads: a clause past its end loads nothing
+            const int32_t l = __shfl_sync(0xFFFFFFFFu, ml, gbase + ((j + q) & 7));
+            const float4 *p = reinterpret_cast<const float4 *>(src + (int64_t)l * kH) + 2 * gl;
+            const bool in = j + q < cnt;
+            x[q][0] = in ? __ldg(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[q][1] = in ? __ldg(p + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          add4(s0, x[q][0]);
-          add4(s1, x[q][1]);
+          for (int q = 0; q < 4; ++q) {
+            add4(s0, x[q][0]);
+            add4(s1, x[q][1]);
+          }
         }
       }
-    }
-    if (c < pd.C) {
-      float4 *dst = reinterpret_cast<float4 *>(out + c * kH) + 2 * gl;
-      if (MODE == 0) {
-        const float s = __ldg(cinv + c);
-        dst[0] = scale4(s0, s);
-        dst[1] = scale4(s1, s);
-      } else {
-        const float4 *ep = reinterpret_cast<const float4 *>(e + c * kH) + 2 * gl;
-        dst[0] = relu_mask4(s0, __ldg(ep));
-        dst[1] = relu_mask4(s1, __ldg(ep + 1));
+      if (c < C) {
+        float4 *dst = reinterpret_cast<float4 *>(out + c * kH) + 2 * gl;
+        if (MODE == 0) {
+          const float sc = __ldg(cinv + c);
+          dst[0] = scale4(s0, sc);
+          dst[1] = scale4(s1, sc);
+        } else {
+          const float4 *ep = reinterpret_cast<const float4 *>(e + c * kH) + 2 * gl;
+          dst[0] = relu_mask4(s0, __ldg(ep));
+          dst[1] = relu_mask4(s1, __ldg(ep + 1));
+        }
       }
+      b = bn;
+      n = nn;
+      myl = myln;
     }
   }
 }
@@ -411,7 +426,7 @@ static int mp_forward(const tsat_problem *p, const float *params, MpWs &w, float
   cudaError_t e = mp_dense_tc(w.feat, kFeat, L, w.wb + kOffW0, w.wb + kOffB0, w.h[0], w.err, st);
   if (e != cudaSuccess) return cuda_fail(e, "mpnn input layer");
   for (int t = 0; t < kLayers; ++t) {
-    k_mp_clause_gather<0><<<grid_for(C * 8, 256), 256, 0, st>>>(pd, w.h[t], w.cinv, nullptr, w.m[t]);
+    k_mp_clause_gather<0><<<grid_for(C, 256), 256, 0, st>>>(pd, w.h[t], w.cinv, nullptr, w.m[t]);
     if ((e = mp_dense_tc(w.m[t], kH, C, w.wb + off_wc(t), w.wb + off_bc(t), w.e[t], w.err, st)) != cudaSuccess)
       return cuda_fail(e, "mpnn clause layer");
     k_mp_var_gather<0><<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.e[t], w.linv, nullptr, w.a[t]);
@@ -459,7 +474,7 @@ static int mp_backward(const tsat_problem *p, MpWs &w, const float *dlog, float 
     cudaError_t e = mp_literal_dx_tc(w.dh, L, w.wb + off_wl(t), w.linv, w.dh2, w.da, w.err, st);
     if (e != cudaSuccess) return cuda_fail(e, "mpnn literal-layer input gradient");
     // a = mean over owning clauses of e  ->  de, masked by the clause layer's ReLU (e = relu(Wc m + bc))
-    k_mp_clause_gather<1><<<grid_for(C * 8, 256), 256, 0, st>>>(pd, w.da, nullptr, w.e[t], w.de);
+    k_mp_clause_gather<1><<<grid_for(C, 256), 256, 0, st>>>(pd, w.da, nullptr, w.e[t], w.de);
     if ((rc = wgrad(1, DIn{w.m[t], kH, 0}, none, none, w.de, C, w.part, grad + off_wc(t), grad + off_bc(t), w.err,
                     st)))
       return rc;
