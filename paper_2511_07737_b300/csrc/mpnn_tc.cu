@@ -647,9 +647,10 @@ __global__ void __launch_bounds__(kTcRows) k_mp_tc_wgrad(const float *dZ, int64_
   const int64_t r0 = M * blockIdx.x / gridDim.x, r1 = M * (blockIdx.x + 1) / gridDim.x;
   uint32_t phase = 0;
   bool ok = true, first = true;
-  for (int64_t rt = r0; rt < r1 && ok; rt += kWgRows) {
-    // loads first (X blocks, then the two dZ blocks of this warp), then conversions and stores
-    float2 xv[XT > 0 ? XT : 1][4], zv[2][4];
+  // this warp's X blocks and two dZ blocks of the tile at rt, into registers:
+  // the next tile's loads are issued before the wait for this tile's MMAs
+  float2 xv[XT > 0 ? XT : 1][4], zv[2][4];
+  auto load_tile = [&](int64_t rt) {
 #pragma unroll
     for (int i = 0; i < XT; ++i) {   // column group i: input i / 2, columns 32 (i % 2) ..
       const float *xi = i < 2 ? x0 : (i < 4 ? x1 : x2);
@@ -658,6 +659,9 @@ __global__ void __launch_bounds__(kTcRows) k_mp_tc_wgrad(const float *dZ, int64_
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i) wg_load(dZ, 0, rt, r1, warp, 32 * i, lane, zv[i]);
+  };
+  if (r0 < r1) load_tile(r0);
+  for (int64_t rt = r0; rt < r1 && ok; rt += kWgRows) {
     if (KIN == 3 && tid < 3 * kWgRows) {   // the 3-wide features, one value per thread
       const int row = tid & (kWgRows - 1), f = tid >> 5;
       const int64_t r = rt + row;
@@ -700,6 +704,7 @@ __global__ void __launch_bounds__(kTcRows) k_mp_tc_wgrad(const float *dZ, int64_
       tc_commit(mb);
     }
     first = false;
+    if (rt + kWgRows < r1) load_tile(rt + kWgRows);   // in flight during this tile's MMAs
     ok = __syncthreads_and(tc_wait(mb, phase)) != 0;   // the MMAs are done (block-wide decision)
     phase ^= 1u;
   }
