@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "internal.h"
@@ -206,6 +208,24 @@ static int check_not_shard(const tsat_state *s) {
     return TSAT_ESTATE;
   }
   return TSAT_OK;
+}
+
+}  // namespace tsat
+
+namespace tsat {
+
+cudaError_t ensure_dyn_smem(const void *kern, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, int> have;   // (device, kernel) -> limit set
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  int &h = have[{dev, kern}];
+  if (bytes <= h) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) h = bytes;
+  return e;
 }
 
 }  // namespace tsat

@@ -30,7 +30,6 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
-#include <unordered_map>
 
 #include "internal.h"
 #include "update_long.cuh"
@@ -288,7 +287,7 @@ static int cluster_count(const void *kern, int smem) {
 int cluster_grid_clusters(int N) {
   const int smem = cluster_smem_bytes(N);
   const void *k = reinterpret_cast<const void *>(k_cluster<TSAT_BIN_DET, TSAT_NORM_ABSMEAN>);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+  if (ensure_dyn_smem(k, smem) != cudaSuccess) return 0;
   return cluster_count(k, smem);
 }
 
@@ -323,13 +322,8 @@ cudaError_t launch_cluster(const ProbDev &pd, const StateDev &sd, const Hyper &h
                            int ncl, const int32_t *bin_ptr, const int32_t *bin_inst, cudaStream_t st) {
   const int smem = cluster_smem_bytes(sd.N);
   auto go = [&](auto kern) -> cudaError_t {
-    static std::unordered_map<const void *, int> smem_set;
-    int &have = smem_set[reinterpret_cast<const void *>(kern)];
-    if (smem > have) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e != cudaSuccess) return e;
-      have = smem;
-    }
+    cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(kern), smem);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ncl * kClSize);
     cfg.blockDim = dim3(kClBlock);

@@ -16,6 +16,10 @@ namespace tsat {
 
 void set_error(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
+// Raise kernel `kern`'s dynamic shared-memory limit on the current device to at
+// least `bytes`: one attribute call per kernel, device and larger size,
+// thread-safe (api.cu).
+cudaError_t ensure_dyn_smem(const void *kern, int bytes);
 
 #define TSAT_CUDA(call)                                   \
   do {                                                    \

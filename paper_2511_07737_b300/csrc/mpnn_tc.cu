@@ -735,19 +735,10 @@ __global__ void __launch_bounds__(kTcRows) k_mp_tc_wgrad(const float *dZ, int64_
 // ---------------------------------------------------------------- host side
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-template <typename Kern>
-static cudaError_t set_smem(Kern kern, int bytes, bool &done) {
-  if (done) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done = true;
-  return e;
-}
-
 template <int FORM>
 static cudaError_t tc_go(const TcArgs &g, cudaStream_t st) {
-  static bool attr = false;
   const int smem = FORM == kLiteralDx ? kTcSmemTwoPerSm : kTcSmem;
-  cudaError_t e = set_smem(k_mp_tc<FORM>, smem, attr);
+  cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(k_mp_tc<FORM>), smem);
   if (e != cudaSuccess) return e;
   const int per_sm = FORM == kLiteralDx ? 2 : 3;   // as many as shared and tensor memory allow
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(148 * per_sm, (g.M + kTcRows - 1) / kTcRows));
@@ -757,8 +748,7 @@ static cudaError_t tc_go(const TcArgs &g, cudaStream_t st) {
 
 template <int FORM>
 static cudaError_t tb_go(const TcArgs &g, cudaStream_t st) {
-  static bool attr = false;
-  cudaError_t e = set_smem(k_mp_tcb<FORM>, kTbSmem, attr);
+  cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(k_mp_tcb<FORM>), kTbSmem);
   if (e != cudaSuccess) return e;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(148 * 2, (g.M + kTcRows - 1) / kTcRows));
   k_mp_tcb<FORM><<<grid, kTcRows, kTbSmem, st>>>(g);
@@ -798,8 +788,7 @@ cudaError_t mp_literal_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W,
 template <int NIN, int KIN>
 static cudaError_t wg_go(const float *dZ, int64_t M, const float *const *x, const int *xr, float *part, int nb,
                          int *err, cudaStream_t st) {
-  static bool attr = false;
-  cudaError_t e = set_smem(k_mp_tc_wgrad<NIN, KIN>, kWgSmem, attr);
+  cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(k_mp_tc_wgrad<NIN, KIN>), kWgSmem);
   if (e != cudaSuccess) return e;
   k_mp_tc_wgrad<NIN, KIN><<<nb, kTcRows, kWgSmem, st>>>(dZ, M, x[0], xr[0], x[1], xr[1], x[2], xr[2], part, err);
   return cudaGetLastError();

@@ -14,7 +14,6 @@
 // coefficients of the dL/dR table), so only FP32 rounding order differs from
 // it, and an instance freezes at the step whose forward finds a sample with no
 // unsatisfied clause.
-#include <unordered_map>
 
 #include "internal.h"
 #include "kernels.cuh"
@@ -559,15 +558,8 @@ cudaError_t launch_persist(const ProbDev &pd, const StateDev &sd, const Hyper &h
                            int32_t vmax, bool resident, cudaStream_t st) {
   const int smem = (int)persist_smem_bytes(sd.N, vmax, resident);
   auto go = [&](auto kern, int block) {
-    // the largest dynamic shared memory set so far for each kernel instance:
-    // one attribute call per instance and size, not one per launch
-    static std::unordered_map<const void *, int> smem_set;
-    int &have = smem_set[reinterpret_cast<const void *>(kern)];
-    if (smem > have) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e != cudaSuccess) return e;
-      have = smem;
-    }
+    cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(kern), smem);
+    if (e != cudaSuccess) return e;
     kern<<<pd.n_inst, block, smem, st>>>(pd, sd, hy, ls, K, vmax);
     return cudaGetLastError();
   };

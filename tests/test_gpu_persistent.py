@@ -168,3 +168,41 @@ def test_persistent_k_steps_equal_k_single_step_launches(name, gen, N, kw, k):
     assert sa["inst"] == sb["inst"]
     if name.startswith("resident-3sat") and k == 300:
         assert sa["inst"][0]["found"]        # the freezing path ran inside the long launch
+
+
+def test_persistent_launches_from_two_host_threads():
+    """Two host threads, each with its own problem and state, launch the
+    persistent solver at the same time (the kernels' launch settings are
+    library state shared by the threads): each thread's z, m, v and bits equal
+    those of the same launches run alone, bit for bit."""
+    import threading
+    insts = [cnfgen.planted_ksat(100, 426, 3, 40 + j) for j in range(2)]
+    hp = ts.hparams(seed=3, norm=1, tau=2.0, lr0=0.5)
+
+    def run(inst):
+        prob, st, _ = make([inst], 64)
+        ts.tsat_init(st.h, hp)
+        for _ in range(4):
+            ts.tsat_step_persistent(st.h, hp, 30, stop_on_sat=False)
+        torch.cuda.synchronize()
+        return snapshot(st)
+
+    alone = [run(i) for i in insts]
+    out = [None, None]
+    errs = []
+
+    def worker(j):
+        try:
+            out[j] = run(insts[j])
+        except Exception as e:          # reported by the main thread
+            errs.append(e)
+
+    th = [threading.Thread(target=worker, args=(j,)) for j in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    for a, b in zip(alone, out):
+        for key in ("z", "m", "v", "bits"):
+            np.testing.assert_array_equal(a[key], b[key])
