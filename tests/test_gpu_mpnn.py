@@ -109,3 +109,27 @@ def test_mpnn_forward_closed_form_on_the_hand_sized_graph():
     torch.cuda.synchronize()
     want = _selector_logits_by_hand(4, clauses)
     assert rel_err(logits.cpu().numpy(), want) < 1e-5
+
+
+def test_mpnn_calls_check_their_workspace():
+    """A workspace that is too small or not 256-byte aligned is an argument
+    error (no launch); a good one reports every tensor-core wait completed."""
+    inst = cnfgen.planted_ksat(300, 1150, 3, 2)
+    prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
+    pr = Proposer(seed=7)
+    ws = pr._ws(prob)
+    logits = torch.empty(prob.info["n_vars"], device="cuda")
+    with pytest.raises(ts.TsatError) as e:
+        ts.tsat_mpnn_forward(prob.h, pr.params, ws[: ws.numel() // 2], logits)
+    assert e.value.status == -4                  # TSAT_EWS
+    big = torch.empty(ws.numel() + 64, dtype=torch.int64, device="cuda")
+    shifted = big.view(torch.uint8)[16:16 + ws.numel() * 8]   # large enough, 16 bytes past an aligned start
+    with pytest.raises(ts.TsatError) as e:
+        ts.tsat_mpnn_forward(prob.h, pr.params, shifted, logits)
+    assert e.value.status == -1 and "aligned" in str(e.value)   # TSAT_EINVAL
+    with pytest.raises(ts.TsatError) as e:
+        ts.tsat_mpnn_status(prob.h, shifted)
+    assert e.value.status == -1
+    ts.tsat_mpnn_forward(prob.h, pr.params, ws, logits)
+    ts.tsat_mpnn_status(prob.h, ws)
+    assert torch.isfinite(logits).all()
