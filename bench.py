@@ -784,7 +784,8 @@ def exp_proposer(args):
     3-SAT (0.9 x threshold) and 5-SAT (0.5 x threshold), n 500-5,000; compare
     learned vs random init on held-out planted 4-SAT n=20,000 at ratio 9.0
     (time to 99 % satisfied, remaining unsatisfied clauses) and at 0.6 x
-    threshold (time to SAT, solve-rate matched)."""
+    threshold (time to SAT, solve-rate matched), there also with assignment
+    mixing at the lr restarts and a 5,000-step cap."""
     from paper_2511_07737_b300 import cnfgen
     from paper_2511_07737_b300 import turbosat as ts
     from paper_2511_07737_b300.proposer import Proposer, compare, make_dataset
@@ -805,10 +806,16 @@ def exp_proposer(args):
     easy = cnfgen.batch_ksat(n_eval, 13, n_lo=nv, n_hi=nv, ks=[4], ratio_scale=0.6)
     r_hard = compare(hard, pr, N=32, hp=hp, max_steps=1000, chunk=10)
     r_easy = compare(easy, pr, N=32, hp=hp, max_steps=1000, chunk=10)
+    # the same 0.6 x threshold set with assignment mixing at the lr restarts
+    # (reading M1), under which the solver finds models: time to SAT of the
+    # two inits, solve-rate matched
+    hp_mix = ts.hparams(seed=3, norm=1, tau=2.0, lr0=0.5, mix_restart=1)
+    r_mix = compare(easy, pr, N=32, hp=hp_mix, max_steps=5000, chunk=50)
     _emit({"experiment": "proposer", "train_instances": len(train), "train_kept": len(data), "train_dropped": dropped,
            "data_seconds": t_data, "fit_seconds": t_fit, "loss_first": float(np.mean(hist[:10])),
            "loss_last": float(np.mean(hist[-10:])), "eval_n_vars": nv,
-           "eval_4sat_ratio_9.0": r_hard, "eval_4sat_0.6x_threshold": r_easy})
+           "eval_4sat_ratio_9.0": r_hard, "eval_4sat_0.6x_threshold": r_easy,
+           "eval_4sat_0.6x_threshold_mixing": r_mix})
 
 
 def exp_proposer_step(args):
