@@ -257,8 +257,9 @@ def time_to_sat_summary(ts, torch, n_inst=32, cap=500):
     """Time to the first satisfying assignment on planted 3-SAT n=100 m=426
     (ratio 4.26), N=64, deterministic Eq. 2, cap 500 steps, seeds 0..31: wall
     time from tsat_init to the host seeing the found flag, each instance alone
-    in one persistent launch that stops at the first model ("plain"), and all
-    instances as one batch in one persistent launch ("batched")."""
+    in one persistent launch that stops at the first model ("plain"), all
+    instances as one batch in one persistent launch ("batched"), and (tuned
+    reading) each instance from a learned initialisation ("learned")."""
     from paper_2511_07737_b300 import cnfgen
     insts = [cnfgen.planted_ksat(100, 426, 3, j) for j in range(n_inst)]
     out = {"workload": f"{n_inst} x planted 3-SAT n=100 m=426 (ratio 4.26), N=64, deterministic Eq. 2, "
@@ -298,7 +299,54 @@ def time_to_sat_summary(ts, torch, n_inst=32, cap=500):
                       "median_steps_to_sat": float(np.median(steps)) if steps else None},
             "batched": {"solved": int(sum(x["found"] for x in sb["inst"])), "of": n_inst,
                         "ms_whole_batch": batch_ms, "steps_run": sb["step"]}}
+    name = "tuned: mean |z| Eq. 5, tau 2, lr0 0.5"
+    out["readings"][name]["learned"] = learned_time_to_sat(ts, torch, insts, TTS_READINGS[name], cap)
     return out
+
+
+def learned_time_to_sat(ts, torch, insts, kw, cap, scale=1.0):
+    """The same instances from a learned initialisation: a proposer trained on
+    the solver's own models of 512 generated planted 3-SAT instances (n
+    100..300, ratio 4.26, seeds 1000.., disjoint from the workload's) gives the
+    initial logits (z = logit x scale + noise); wall time from the start of the
+    proposal (the network's forward) to the host seeing the found flag, each
+    instance alone in one persistent launch."""
+    from paper_2511_07737_b300 import cnfgen
+    from paper_2511_07737_b300.proposer import Proposer, make_dataset
+    t0 = time.perf_counter()
+    sizes = np.random.default_rng(5).integers(100, 300, 512)
+    train = [cnfgen.planted_ksat(int(n), int(round(4.26 * n)), 3, 1000 + j) for j, n in enumerate(sizes)]
+    data, dropped = make_dataset(train, N=32, hp=ts.hparams(seed=7, **kw), max_steps=cap)
+    t_data = time.perf_counter() - t0
+    pr = Proposer(seed=1)
+    t1 = time.perf_counter()
+    pr.fit(data, epochs=8, batch=16, lr=3e-3)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t1
+    walls, steps, props = [], [], []
+    for j, inst in enumerate(insts):
+        prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
+        st = ts.State(prob, 64)
+        hp = ts.hparams(seed=j + 1, **kw)
+        ts.tsat_init(st.h, hp, pr.logits(prob), scale)
+        ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)     # first launch: kernel attributes
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lg = pr.logits(prob)
+        props.append(time.perf_counter() - t0)
+        ts.tsat_init(st.h, hp, lg, scale)
+        ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
+        x = ts.tsat_status(st.h, 1)["inst"][0]
+        el = time.perf_counter() - t0
+        if x["found"]:
+            walls.append(el)
+            steps.append(x["found_step"])
+    return {"solved": len(walls), "of": len(insts),
+            "median_ms_to_sat": 1e3 * float(np.median(walls)) if walls else None,
+            "median_steps_to_sat": float(np.median(steps)) if steps else None,
+            "median_proposal_ms": 1e3 * float(np.median(props)), "logit_scale": scale,
+            "training": {"instances": len(train), "kept": len(data), "dropped": dropped,
+                         "data_seconds": t_data, "fit_seconds": t_fit}}
 
 
 def progress_reading(ts, torch, prob, N, K, seed):
