@@ -405,6 +405,10 @@ int tsat_set_tuning(tsat_state *s, const int32_t h_tuning[4]);
  * tsat_mpnn_param_count() entries (FP32 master copy, owned by the caller).
  * Workspace: tsat_mpnn_workspace_bytes (activations for the backward pass),
  * 256-byte aligned (as cudaMalloc returns it; TSAT_EINVAL otherwise).
+ * tsat_mpnn_forward: from the second call with the same parameter, workspace
+ * and logits pointers on the same problem, the forward's launches replay as
+ * one captured CUDA graph (the values behind the pointers are read when it
+ * runs); a call with other pointers runs directly.
  * tsat_mpnn_loss_grad: logits (float [V]), mean binary cross-entropy of the
  * logits against d_targets (uint8 [V], a satisfying assignment per instance)
  * summed over instances into d_loss[0], and its gradient d_grad (float

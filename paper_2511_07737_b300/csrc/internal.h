@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -59,7 +60,23 @@ struct tsat_problem {
   std::vector<tsat::InstInfo> inst;  // host copy (lmax filled after the build)
   std::vector<int64_t> inst_nnz;     // literal occurrences of each instance as loaded (before de-duplication)
   std::vector<int32_t> cperm;        // clause order of a locality load: loaded clause -> caller's index (else empty)
+  // tsat_mpnn_forward's launch sequence captured as a CUDA graph, for the
+  // parameter, workspace and output pointers it was captured with
+  struct MpForwardGraph {
+    const void *params = nullptr, *ws = nullptr, *logits = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t capture = nullptr;   // private stream the capture runs on
+  };
+  mutable MpForwardGraph mp_fwd;
+  mutable std::mutex mp_mu;
   int set_items(int32_t item_clauses, cudaStream_t stream);
+  tsat_problem() = default;
+  tsat_problem(const tsat_problem &) = delete;
+  tsat_problem &operator=(const tsat_problem &) = delete;
+  ~tsat_problem() {
+    if (mp_fwd.exec) cudaGraphExecDestroy(mp_fwd.exec);
+    if (mp_fwd.capture) cudaStreamDestroy(mp_fwd.capture);
+  }
 };
 
 struct GraphKey {

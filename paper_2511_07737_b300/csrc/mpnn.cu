@@ -149,6 +149,7 @@ cudaError_t mp_literal_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W,
                              float *da, int *err, cudaStream_t st);
 int mp_wgrad_tc(const float *dZ, int64_t M, int nin, int K, const float *const *x, const int *xr, float *part,
                 int max_blocks, int *err, cudaStream_t st, cudaError_t *e);
+cudaError_t mp_prepare_forward();
 
 __device__ __forceinline__ int warp_max(int x) {
   for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xFFFFFFFFu, x, o));
@@ -513,13 +514,64 @@ int tsat_mpnn_init(float *d_params, uint64_t seed, cudaStream_t stream) {
   return TSAT_OK;
 }
 
+// The forward's launch sequence (about 18 launches) captured into a CUDA
+// graph on the problem's private stream, for these pointers; the values behind
+// them (the parameters, the workspace) are read when the graph runs.
+static int mp_capture_forward(const tsat_problem *p, const float *params, MpWs &w, void *ws, float *logits) {
+  tsat_problem::MpForwardGraph &gc = p->mp_fwd;
+  TSAT_CUDA(mp_prepare_forward());
+  if (!gc.capture) TSAT_CUDA(cudaStreamCreateWithFlags(&gc.capture, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  TSAT_CUDA(cudaStreamBeginCapture(gc.capture, cudaStreamCaptureModeThreadLocal));
+  const int rc = mp_forward(p, params, w, logits, gc.capture);
+  const cudaError_t ec = cudaStreamEndCapture(gc.capture, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (ec != cudaSuccess) return cuda_fail(ec, "mpnn forward capture");
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return cuda_fail(ei, "mpnn forward graph");
+  if (gc.exec) cudaGraphExecDestroy(gc.exec);
+  gc.exec = exec;
+  gc.params = params;
+  gc.ws = ws;
+  gc.logits = logits;
+  return TSAT_OK;
+}
+
 int tsat_mpnn_forward(const tsat_problem *p, const float *d_params, void *d_ws, size_t ws_bytes, float *d_logits,
                       cudaStream_t stream) {
   if (!p || !d_params || !d_ws || !d_logits) return TSAT_EINVAL;
   if (ws_bytes < mp_ws_bytes(p->V, p->C)) { set_error("mpnn workspace too small"); return TSAT_EWS; }
   if ((uintptr_t)d_ws & 255u) { set_error("mpnn workspace not 256-byte aligned"); return TSAT_EINVAL; }
   MpWs w = mp_ws_plan(d_ws, p->V, p->C);
-  return mp_forward(p, d_params, w, d_logits, stream);
+  // A small graph's forward is bound by its launches: the second call with
+  // the same pointers captures the sequence as a CUDA graph and later ones
+  // replay it in one launch; a call with new pointers runs directly (so a
+  // caller whose buffers move pays no capture).
+  std::lock_guard<std::mutex> lock(p->mp_mu);
+  tsat_problem::MpForwardGraph &gc = p->mp_fwd;
+  const bool same = gc.params == d_params && gc.ws == d_ws && gc.logits == d_logits;
+  if (!same) {
+    if (gc.exec) cudaGraphExecDestroy(gc.exec);
+    gc.exec = nullptr;
+    gc.params = d_params;
+    gc.ws = d_ws;
+    gc.logits = d_logits;
+    return mp_forward(p, d_params, w, d_logits, stream);
+  }
+  if (!gc.exec) {
+    const int rc = mp_capture_forward(p, d_params, w, d_ws, d_logits);
+    if (rc) {
+      gc.params = gc.ws = gc.logits = nullptr;
+      return rc;
+    }
+  }
+  TSAT_CUDA(cudaGraphLaunch(gc.exec, stream));
+  return TSAT_OK;
 }
 
 int tsat_mpnn_loss_grad(const tsat_problem *p, const float *d_params, void *d_ws, size_t ws_bytes,

@@ -755,6 +755,15 @@ static cudaError_t tb_go(const TcArgs &g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// The shared-memory limits of the forward's tensor-core kernels, set ahead of
+// a graph capture of the forward.
+cudaError_t mp_prepare_forward() {
+  cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(k_mp_tc<kDense>), kTcSmem);
+  if (e == cudaSuccess) e = ensure_dyn_smem(reinterpret_cast<const void *>(k_mp_tc<kLiteral>), kTcSmem);
+  if (e == cudaSuccess) e = ensure_dyn_smem(reinterpret_cast<const void *>(k_mp_tcb<kDense>), kTbSmem);
+  return e;
+}
+
 // Y[r] = relu(W x[r] + b), x FP32 [M][K] with K = 3 or 64, W bf16 [64][K]
 cudaError_t mp_dense_tc(const float *x, int K, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias, float *Y,
                         int *err, cudaStream_t st) {

@@ -133,3 +133,36 @@ def test_mpnn_calls_check_their_workspace():
     ts.tsat_mpnn_forward(prob.h, pr.params, ws, logits)
     ts.tsat_mpnn_status(prob.h, ws)
     assert torch.isfinite(logits).all()
+
+
+def test_forward_graph_replay_equals_direct_forward():
+    """The forward replayed as a captured graph (second and later calls with the
+    same buffers) gives the logits of a direct run bit for bit, also after the
+    parameters change in place (the graph reads them when it runs)."""
+    inst = cnfgen.planted_ksat(300, 1150, 3, 2)
+    prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
+    pr = Proposer(seed=7)
+    ws = pr._ws(prob)
+    lg = torch.empty(prob.info["n_vars"], device="cuda")
+
+    def direct():
+        ws2 = pr._ws(prob)   # other buffers: a direct run
+        out = torch.empty_like(lg)
+        ts.tsat_mpnn_forward(prob.h, pr.params, ws2, out)
+        ts.tsat_mpnn_status(prob.h, ws2)
+        return out.cpu().numpy()
+
+    ref = direct()
+    for _ in range(3):                  # direct, capture, replay
+        lg.fill_(float("nan"))
+        ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)
+        ts.tsat_mpnn_status(prob.h, ws)
+        np.testing.assert_array_equal(lg.cpu().numpy(), ref)
+    with torch.no_grad():
+        pr.params.mul_(0.5)
+    ref2 = direct()
+    assert not np.array_equal(ref, ref2)
+    ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)   # the cached graph was dropped by the direct run
+    ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)
+    ts.tsat_mpnn_status(prob.h, ws)
+    np.testing.assert_array_equal(lg.cpu().numpy(), ref2)
