@@ -301,6 +301,71 @@ def time_to_sat_summary(ts, torch, n_inst=32, cap=500):
                         "ms_whole_batch": batch_ms, "steps_run": sb["step"]}}
     name = "tuned: mean |z| Eq. 5, tau 2, lr0 0.5"
     out["readings"][name]["learned"] = learned_time_to_sat(ts, torch, insts, TTS_READINGS[name], cap)
+    out["mid_size"] = mid_size_time_to_sat(ts, torch, TTS_READINGS[name])
+    return out
+
+
+def mid_size_time_to_sat(ts, torch, kw, n_inst=16, n=1000, m=4000, cap=2000):
+    """Time to SAT on mid-size instances (planted 3-SAT n=1000 m=4000, N=64,
+    tuned reading, cap 2000 steps, seeds 0..15), where one block cannot keep
+    an instance's z, m, v in shared memory: each instance alone in one
+    persistent launch on a cluster of blocks (the automatic choice), the same
+    on one block, and on the multi-kernel graph path (10-step replays with a
+    status read after each); then all instances as one batch in one
+    persistent launch.  Wall time from tsat_init to the host seeing the found
+    flag."""
+    from paper_2511_07737_b300 import cnfgen
+    insts = [cnfgen.planted_ksat(n, m, 3, j) for j in range(n_inst)]
+    out = {"workload": f"{n_inst} x planted 3-SAT n={n} m={m} (ratio {m / n:.2f}), N=64, deterministic Eq. 2, "
+                       f"tuned reading, cap {cap} steps", "unit": "ms"}
+    for mode in ("persistent_cluster", "persistent_one_block", "graph_path"):
+        walls, steps, blocks = [], [], None
+        for j, inst in enumerate(insts):
+            prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
+            st = ts.State(prob, 64)
+            if mode == "persistent_one_block":
+                ts.tsat_set_persist_blocks(st.h, 1)
+            blocks = ts.tsat_persist_blocks(st.h)
+            hp = ts.hparams(seed=j + 1, **kw)
+            ts.tsat_init(st.h, hp)
+            if mode == "graph_path":
+                ts.tsat_step(st.h, hp, 10, stop_on_sat=True)       # first replay: the graph is built
+            else:
+                ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ts.tsat_init(st.h, hp)
+            if mode == "graph_path":
+                for _ in range(cap // 10):
+                    ts.tsat_step(st.h, hp, 10, stop_on_sat=True)
+                    x = ts.tsat_status(st.h, 1)["inst"][0]
+                    if x["found"]:
+                        break
+            else:
+                ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
+                x = ts.tsat_status(st.h, 1)["inst"][0]
+            el = time.perf_counter() - t0
+            if x["found"]:
+                walls.append(el)
+                steps.append(x["found_step"])
+        out[mode] = {"solved": len(walls), "of": n_inst,
+                     "median_ms_to_sat": 1e3 * float(np.median(walls)) if walls else None,
+                     "median_steps_to_sat": float(np.median(steps)) if steps else None}
+        if mode != "graph_path":
+            out[mode]["blocks_per_instance"] = blocks
+    prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in insts])
+    st = ts.State(prob, 64)
+    hp = ts.hparams(seed=1, **kw)
+    ts.tsat_init(st.h, hp)
+    ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ts.tsat_init(st.h, hp)
+    ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
+    sb = ts.tsat_status(st.h, n_inst)
+    out["batched"] = {"solved": int(sum(x["found"] for x in sb["inst"])), "of": n_inst,
+                      "ms_whole_batch": 1e3 * (time.perf_counter() - t0), "steps_run": sb["step"],
+                      "blocks_per_instance": ts.tsat_persist_blocks(st.h)}
     return out
 
 

@@ -211,14 +211,34 @@ int tsat_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t st
  * stop_on_sat, the stop once every instance is frozen; FP32 sums may differ
  * from tsat_step in rounding order, integers and bits agree given the same
  * FP32 state.  Each block keeps its instance's bits (both step parities) in
- * shared memory.  Requirements: the STE layer, hp->mix_restart = 0, clauses
- * of at most 7 literals, clauses x longest clause x samples <= 2^26 per
+ * shared memory.  When the batch leaves SMs idle (N <= 256), an instance may
+ * instead get a thread-block cluster of 2, 4 or 8 blocks (see
+ * tsat_set_persist_blocks): the blocks split its clauses in the forward and
+ * its rows in the update, each keeps a copy of the bits, and the histograms
+ * are summed over distributed shared memory between two cluster barriers per
+ * step; integers and every rounding follow one block per instance.
+ * Requirements: the STE layer, hp->mix_restart = 0, clauses of at most 7
+ * literals, clauses x longest clause x samples <= 2^26 per block of the
  * instance, and 4 (18.5 N + 2 n_vars N / 32) bytes of shared memory <= 200
  * KiB for the largest instance (about 25,000 variables at N = 32, 12,500 at
  * N = 64, 500 at N = 1024); else TSAT_EINVAL / TSAT_ERANGE.  Async on
  * `stream`. */
 int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
                          cudaStream_t stream);
+
+/* Blocks per instance of tsat_step_persistent: 0 = automatic (the default:
+ * 1 when one block keeps the largest instance's z, m, v in shared memory or
+ * N > 256, else the largest of 2, 4, 8 with which every instance's cluster
+ * fits on the device at once), or 1, 2, 4, 8 (2..8 need N <= 256).  The
+ * blocks keep their rows' z, m, v in shared memory when those fit (else in
+ * global memory, with 8 instead of 16 samples per thread); two settings with
+ * the same placement give the same results bit for bit, otherwise the FP32
+ * row sums of Eq. 5 differ in rounding order.  tsat_persist_blocks: the
+ * blocks per instance the next tsat_step_persistent call will use and, if
+ * `resident` is not NULL, 1 when they keep z, m, v in shared memory.  Host
+ * only; TSAT_EINVAL on other values. */
+int tsat_set_persist_blocks(tsat_state *s, int32_t blocks_per_instance);
+int tsat_persist_blocks(const tsat_state *s, int32_t *blocks_per_instance, int32_t *resident);
 
 /* The same n_steps steps for a batch whose instances are too large for one
  * block, in one launch of thread-block clusters (4 blocks of 768 threads, one

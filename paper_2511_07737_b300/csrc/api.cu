@@ -459,6 +459,54 @@ int tsat_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t st
   return leave(s, stream);
 }
 
+// Blocks per instance of the persistent solver: the state's setting, or, when
+// it is 0 (N <= 256 only): one block when that block keeps its instance's z,
+// m, v in shared memory, else the largest power of two up to 8 such that the
+// batch's clusters all fit on the device at once.  Measured per step at
+// N = 64 (planted 3-SAT, 1 / 2 / 4 / 8 blocks): n = 100 (resident in one
+// block) 8.4 / 9.2 / 8.5 / 9.4 us, the step being a chain of dependent phases
+// that more blocks do not shorten; n = 1,000 152.8 / 89.0 / 49.7 / 12.9 us
+// (resident from 8 blocks); n = 3,000 436 / 232 / 127 / 73 us; 5-SAT n = 300
+// 235 / 121 / 68 / 59 us.
+static int persist_blocks(const tsat_state *s, int32_t vmax) {
+  const tsat_problem *p = s->prob;
+  if (s->N > 256) return 1;
+  if (s->persist_cs > 0) return s->persist_cs;
+  if (persist_smem_bytes(s->N, vmax, true, 1) <= kPersistMaxSmem) return 1;
+  int cs = 1;
+  while (cs < 8 && (int64_t)p->n_inst * cs * 2 <= s->sm_count) cs *= 2;
+  return cs;
+}
+
+int tsat_persist_blocks(const tsat_state *s, int32_t *blocks, int32_t *resident) {
+  if (!s || !blocks) {
+    set_error("NULL argument");
+    return TSAT_EINVAL;
+  }
+  int32_t vmax = 0;
+  for (const InstInfo &I : s->prob->inst) vmax = std::max(vmax, I.n_vars);
+  *blocks = persist_blocks(s, vmax);
+  if (resident) *resident = persist_smem_bytes(s->N, vmax, true, *blocks) <= kPersistMaxSmem ? 1 : 0;
+  return TSAT_OK;
+}
+
+int tsat_set_persist_blocks(tsat_state *s, int32_t blocks) {
+  if (!s) {
+    set_error("NULL state");
+    return TSAT_EINVAL;
+  }
+  if (blocks != 0 && blocks != 1 && blocks != 2 && blocks != 4 && blocks != 8) {
+    set_error("blocks per instance must be 0 (automatic), 1, 2, 4 or 8, got %d", blocks);
+    return TSAT_EINVAL;
+  }
+  if (blocks > 1 && s->N > 256) {
+    set_error("several blocks per instance need at most 256 samples (N %d)", s->N);
+    return TSAT_EINVAL;
+  }
+  s->persist_cs = blocks;
+  return TSAT_OK;
+}
+
 int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
                          cudaStream_t stream) {
   int rc = check_step_args(s, hp, n_steps);
@@ -473,32 +521,31 @@ int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps,
     return TSAT_EINVAL;
   }
   int32_t vmax = 0;
+  for (const InstInfo &I : p->inst) vmax = std::max(vmax, I.n_vars);
+  const int cs = persist_blocks(s, vmax);
   bool too_big = false;
-  for (const InstInfo &I : p->inst) {
-    vmax = std::max(vmax, I.n_vars);
-    too_big = too_big || (int64_t)I.n_clauses * I.lmax * s->N > kPersistMaxWork;
-  }
-  too_big = too_big || persist_smem_bytes(s->N, vmax, false) > kPersistMaxSmem;
+  for (const InstInfo &I : p->inst) too_big = too_big || (int64_t)I.n_clauses * I.lmax * s->N > cs * kPersistMaxWork;
+  too_big = too_big || persist_smem_bytes(s->N, vmax, false, cs) > kPersistMaxSmem;
   // instances too large for one block: clusters of blocks, when the batch suits them
-  if (too_big && p->dev.rec_stride == 8 && s->N <= 128)
+  if (too_big && s->persist_cs == 0 && p->dev.rec_stride == 8 && s->N <= 128)
     return tsat_step_clustered(s, hp, n_steps, stop_on_sat, stream);
   for (const InstInfo &I : p->inst) {
-    if ((int64_t)I.n_clauses * I.lmax * s->N > kPersistMaxWork) {
-      set_error("instance too large for one block: %d clauses x %d literals x %d samples > %lld", I.n_clauses,
-                I.lmax, s->N, (long long)kPersistMaxWork);
+    if ((int64_t)I.n_clauses * I.lmax * s->N > cs * kPersistMaxWork) {
+      set_error("instance too large for %d block(s): %d clauses x %d literals x %d samples > %lld", cs,
+                I.n_clauses, I.lmax, s->N, (long long)(cs * kPersistMaxWork));
       return TSAT_ERANGE;
     }
   }
-  if (persist_smem_bytes(s->N, vmax, false) > kPersistMaxSmem) {
+  if (persist_smem_bytes(s->N, vmax, false, cs) > kPersistMaxSmem) {
     set_error("instance too large for one block: %d variables x %d samples need %lld bytes of shared memory",
-              vmax, s->N, (long long)persist_smem_bytes(s->N, vmax, false));
+              vmax, s->N, (long long)persist_smem_bytes(s->N, vmax, false, cs));
     return TSAT_ERANGE;
   }
-  const bool resident = persist_smem_bytes(s->N, vmax, true) <= kPersistMaxSmem;
+  const bool resident = persist_smem_bytes(s->N, vmax, true, cs) <= kPersistMaxSmem;
   if ((rc = enter(s, stream))) return rc;
   const Hyper hy = make_hyper(*hp, stop_on_sat ? 1 : 0);
   const LrSched ls = make_sched(*hp);
-  cudaError_t e = launch_persist(p->dev, s->dev, hy, ls, n_steps, vmax, resident, s->stream);
+  cudaError_t e = launch_persist(p->dev, s->dev, hy, ls, n_steps, vmax, resident, cs, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "persistent solver");
   return leave(s, stream);
 }

@@ -133,6 +133,7 @@ struct tsat_state {
   int32_t upd_blocks_per_sm = 0;   // 0: resident blocks per SM from the occupancy API
   mutable int32_t occ_bps = -1;     // that occupancy figure, queried once per state
   int32_t upd_rows_per_item = 1;
+  int32_t persist_cs = 0;           // persistent solver: blocks per instance (0: automatic)
   int32_t sm_count = 148;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;

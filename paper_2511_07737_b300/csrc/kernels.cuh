@@ -79,8 +79,9 @@ int update_smem_bytes(int N, int lm1, bool greg);
 // persistent solver (persist.cu): one block per instance, n_steps steps per launch
 constexpr int64_t kPersistMaxWork = 1LL << 26;   // clauses x longest clause x samples of one instance
 constexpr int64_t kPersistMaxSmem = 200 * 1024;   // shared memory of one block (bits of both parities included)
-int64_t persist_smem_bytes(int N, int32_t vmax, bool resident);
+// cs: blocks per instance (1, or a cluster of 2, 4 or 8 with N <= 256)
+int64_t persist_smem_bytes(int N, int32_t vmax, bool resident, int cs);
 cudaError_t launch_persist(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls, int32_t K,
-                           int32_t vmax, bool resident, cudaStream_t st);
+                           int32_t vmax, bool resident, int cs, cudaStream_t st);
 
 }  // namespace tsat

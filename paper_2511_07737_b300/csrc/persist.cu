@@ -14,9 +14,26 @@
 // coefficients of the dL/dR table), so only FP32 rounding order differs from
 // it, and an instance freezes at the step whose forward finds a sample with no
 // unsatisfied clause.
+//
+// Split instances (SPLIT): when the batch leaves most SMs idle (one instance,
+// or a few), each instance gets a thread-block cluster of CS blocks instead of
+// one block.  Every block keeps a copy of the instance's bits; block q of the
+// cluster runs every CS-th forward task into its own histogram (one per step
+// parity), and after a cluster barrier every block sums the CS histograms over
+// distributed shared memory (integers: every block gets the same table and
+// takes the same found / stop decisions).  Block q updates the rows
+// [V q / CS, V (q + 1) / CS) (their z, m, v and normaliser resident in its
+// shared memory) and writes each new bits word into every block's copy; a
+// second cluster barrier ends the step.  The rows' arithmetic is the one-block
+// kernel's: with the same samples per thread (the same placement of z, m, v)
+// the results are the same bit for bit.
+
+#include <cooperative_groups.h>
 
 #include "internal.h"
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace tsat {
 
@@ -58,10 +75,13 @@ __device__ __forceinline__ uint32_t *ps_bits(const StateDev &sd, int64_t t) {
 template <int SPT>
 constexpr int ps_block() { return SPT == 8 ? 1024 : (SPT == 16 ? 512 : 256); }
 
-template <int BIN, int NORM, bool RES, int SPT>
+// SPLIT: the launch has clusters of CS blocks per instance (see the top of
+// the file); vmax bounds the instances' variables, vown the rows of one block.
+template <int BIN, int NORM, bool RES, int SPT, bool SPLIT>
 __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
-    k_persist(ProbDev pd, StateDev sd, Hyper hy, LrSched ls, int32_t K, int32_t vmax) {
+    k_persist(ProbDev pd, StateDev sd, Hyper hy, LrSched ls, int32_t K, int32_t vmax, int32_t vown) {
   constexpr int BS = ps_block<SPT>(), NW = BS / 32, Q = 32 / SPT;
+  constexpr int HP = SPLIT ? 2 : 1;   // histograms: one per step parity when other blocks read them
   extern __shared__ __align__(16) float smP[];
   __shared__ int64_t sh_t0;
   __shared__ int sh_skip, sh_found, sh_mu0, sh_mi0, sh_fs;
@@ -71,7 +91,16 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
   __shared__ int sh_mu[NW], sh_mi[NW];
   __shared__ StepParams sh_sps[kPsSched];   // step scalars of the next kPsSched steps
   StateHdr *hdr = sd.hdr;
-  const int inst = blockIdx.x;
+  const int CS = SPLIT ? (int)cg::this_cluster().num_blocks() : 1;
+  const int rank = SPLIT ? (int)cg::this_cluster().block_rank() : 0;
+  const int inst = blockIdx.x / CS;
+  // the barrier between the phases of a step: the block's, or the cluster's
+  // (release / acquire: the histograms and bits written before it are seen
+  // by every block after it)
+  auto phase_barrier = [] {
+    if constexpr (SPLIT) cg::this_cluster().sync();
+    else __syncthreads();
+  };
   const int N = sd.N, W = sd.W;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -85,8 +114,10 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
   const int64_t t0 = sh_t0;
   const InstInfo I = pd.inst[inst];
   const int lmax = I.lmax;
-  int32_t *hist = reinterpret_cast<int32_t *>(smP);   // [lmax + 1][N]
-  float *tab = smP + 8 * N;                             // [N][8] with 8 floats of padding per 16 samples (ps_tab)
+  // the rows this block updates (all of them unless SPLIT)
+  const int r_lo = (int)((int64_t)I.n_vars * rank / CS), r_hi = (int)((int64_t)I.n_vars * (rank + 1) / CS);
+  int32_t *hist = reinterpret_cast<int32_t *>(smP);   // [HP][8][N]: [lmax + 1][N] used
+  float *tab = smP + HP * 8 * N;                        // [N][8] with 8 floats of padding per 16 samples (ps_tab)
   // S and the unsatisfied count of every sample, and the instance's status
   // fields, are kept in shared memory and written to the state once at the end
   // of the launch: only the last step's values are visible outside
@@ -98,21 +129,26 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
   const size_t vw = (size_t)vmax * W;
   for (int64_t i = tid; i < (int64_t)I.n_vars * W; i += BS)
     sbits[(t0 & 1) * vw + i] = ps_bits(sd, t0)[(size_t)I.v_off * W + i];
-  float *smz = reinterpret_cast<float *>(sbits + 2 * vw);   // RES: z, m, v [vmax][W][33], then nu [vmax]
-  float *smm = smz + vw * 33, *smv = smm + vw * 33, *snu = smv + vw * 33;
-  const size_t g0 = (size_t)I.v_off * N;
+  // RES: z, m, v of the block's rows [vown][W][33], then their normaliser [vown]
+  const size_t ow = (size_t)vown * W;
+  float *smz = reinterpret_cast<float *>(sbits + 2 * vw);
+  float *smm = smz + ow * 33, *smv = smm + ow * 33, *snu = smv + ow * 33;
+  const int nown = r_hi - r_lo;
+  const size_t g0 = ((size_t)I.v_off + r_lo) * N;   // the block's first row in the state arrays
   if (RES && !sh_found) {
-    for (int64_t i = tid; i < (int64_t)I.n_vars * N; i += BS) {
+    for (int64_t i = tid; i < (int64_t)nown * N; i += BS) {
       const size_t si = (size_t)(i / 32) * 33 + (i & 31);   // [row][word][33]: word index i / 32 of the row-major array
       smz[si] = sd.z[g0 + i];
       smm[si] = sd.m[g0 + i];
       smv[si] = sd.v[g0 + i];
     }
-    for (int i = tid; i < I.n_vars; i += BS) snu[i] = sd.nu[I.v_off + i];
+    for (int i = tid; i < nown; i += BS) snu[i] = sd.nu[I.v_off + r_lo + i];
   }
-  // the histogram starts at zero; each step's update phase clears it again
-  // for the next step's forward (the barrier ending the step orders the two)
-  for (int i = tid; i < (lmax + 1) * N; i += BS) hist[i] = 0;
+  // the histograms start at zero; each step's update phase clears the one the
+  // next step's forward fills (the barrier ending the step orders the two;
+  // with SPLIT that is the other parity, whose last readers in other blocks
+  // passed the barrier that ended the previous step)
+  for (int i = tid; i < HP * 8 * N; i += BS) hist[i] = 0;
   __syncthreads();
   int found = sh_found;
   const bool ran = !found;   // the instance is live at the start of the launch
@@ -125,6 +161,7 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
     // ---- forward (Eq. 1): lane = clause, 32 samples of word w; bit-sliced R,
     // warp transpose, popcounts of the R = r masks into the block histogram
     const uint32_t *bsrc = sbits + (t & 1) * vw;
+    int32_t *hcur = hist + (SPLIT ? (int)(t & 1) * 8 * N : 0);
     // A task is a group of 32 clauses (lane = clause) and WT words of the
     // samples (WT = 2 when N >= 64): the clause is decoded once for both words
     // and a small instance needs half the task rounds (n = 100, N = 64: 14
@@ -134,7 +171,7 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
     constexpr int WTM = SPT == 8 ? 1 : 2;
     const int ngroups = (I.n_clauses + 31) >> 5;
     const int WT = W >= WTM ? WTM : 1, wtasks = W / WT;
-    for (int task = warp; task < ngroups * wtasks; task += NW) {
+    for (int task = warp + NW * rank; task < ngroups * wtasks; task += NW * CS) {
       const int g = task / wtasks, w0 = (task - g * wtasks) * WT;
       const bool active = 32 * g + lane < I.n_clauses;
       uint32_t pl[WTM][3] = {};
@@ -180,21 +217,33 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
           tp[2] = pd.crec ? 0u : warp_transpose32(pl[ww][2], lane);   // R <= 3 with clause records
           for (int r = 0; r <= lmax; ++r) {
             const int cnt = __popc(valid & bitslice_eq<3>(tp, r));
-            if (cnt) atomicAdd(hist + r * N + 32 * (w0 + ww) + lane, cnt);
+            if (cnt) atomicAdd(hcur + r * N + 32 * (w0 + ww) + lane, cnt);
           }
         }
       }
     }
-    __syncthreads();
+    phase_barrier();
     // ---- Eq. 4 per sample, the dL/dR table, loss, fewest-unsatisfied sample
     float lsum = 0.f;
     int mu = 0x7FFFFFFF, mi = 0x7FFFFFFF;
     for (int i = tid; i < N; i += BS) {
+      // the sample's histogram (SPLIT: summed over the cluster's blocks, in
+      // integers, so every block gets the same values)
+      int hv[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) hv[r] = 0;
+      for (int q = 0; q < CS; ++q) {
+        const int32_t *hq = hcur;
+        if constexpr (SPLIT) hq = cg::this_cluster().map_shared_rank(hcur, q);
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+          if (r <= lmax) hv[r] += hq[r * N + i];
+      }
       float Z = 0.f, Y = 0.f;
       for (int r = 0; r <= lmax; ++r) {
-        const float hv = (float)hist[r * N + i];
-        Z += hv * etab[r];
-        Y += (float)r * hv * etab[r];
+        const float h = (float)hv[r];
+        Z += h * etab[r];
+        Y += (float)r * h * etab[r];
       }
       const float S = Y / Z;
       const float invZ = 1.0f / Z;
@@ -204,7 +253,7 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
       ps_moebius(c);   // the update counts product masks of R's bit planes
 #pragma unroll
       for (int r = 0; r < 8; ++r) tab[ps_tab(i) + r] = c[r];
-      const int h0 = hist[i];
+      const int h0 = hv[0];
       lsum += S;
       if (h0 < mu || (h0 == mu && i < mi)) { mu = h0; mi = i; }
       sS[i] = S;
@@ -244,7 +293,10 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
       found = mu == 0;
     }
     if (found) break;   // the bits of step t are the model; z, m, v stay
-    for (int i = tid; i < (lmax + 1) * N; i += BS) hist[i] = 0;   // read for the last time above
+    {   // the histogram the next forward fills (without SPLIT: this one, read for the last time above)
+      int32_t *hnext = hist + (SPLIT ? (int)((t + 1) & 1) * 8 * N : 0);
+      for (int i = tid; i < (lmax + 1) * N; i += BS) hnext[i] = 0;
+    }
     // ---- fused update: thread = (row, word w); G of its 32 samples summed over
     // the row's occurrences in record order, then Eq. 5, AdamW, the new
     // normaliser and the bits of step t + 1
@@ -253,9 +305,9 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
     const int WQ = W * Q;                 // threads of one row: W words x Q parts
     const int rpp = BS / WQ;              // rows per pass
     const int rl = tid % WQ, w = rl / Q, sb = SPT * (rl % Q);   // word, first bit of this thread's samples
-    for (int vb = 0; vb < I.n_vars; vb += rpp) {
+    for (int vb = r_lo; vb < r_hi; vb += rpp) {
       const int vl = vb + tid / WQ;
-      const bool act = vl < I.n_vars;
+      const bool act = vl < r_hi;
       const int64_t v = (int64_t)I.v_off + vl;
       // G of this thread's samples: signed byte counts of the product masks of
       // R's bit planes (mask m of the subset m of {b0, b1, b2}), folded with
@@ -402,9 +454,9 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
 #pragma unroll
         for (int j = 0; j < SPT; ++j) acc[j] = fmaf((float)nsign, tab[tb + ps_tab_rel(j)], acc[j]);
       }
-      const size_t off = RES ? ((size_t)vl * W + w) * 33 + sb : (size_t)v * N + 32 * w + sb;
+      const size_t off = RES ? ((size_t)(vl - r_lo) * W + w) * 33 + sb : (size_t)v * N + 32 * w + sb;
       float *zp = RES ? smz : sd.z, *mp = RES ? smm : sd.m, *vp = RES ? smv : sd.v;
-      const float nu = act ? (RES ? snu[vl] : sd.nu[v]) : 1.0f;
+      const float nu = act ? (RES ? snu[vl - r_lo] : sd.nu[v]) : 1.0f;
       const float rnu = __frcp_rn(nu);
       float part = 0.f;
       if (act && NORM != TSAT_NORM_NONE) {
@@ -466,17 +518,24 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
       if (act && sb == 0) {
         if (!RES) bdst[v * W + w] = word;
         sdst[(size_t)vl * W + w] = word;
+        if constexpr (SPLIT) {   // every block's copy of the bits
+          for (int q = 0; q < CS; ++q)
+            if (q != rank) cg::this_cluster().map_shared_rank(sdst, q)[(size_t)vl * W + w] = word;
+        }
         if (w == 0) {
-          if (RES) snu[vl] = nun;
+          if (RES) snu[vl - r_lo] = nun;
           else sd.nu[v] = nun;
         }
       }
     }
-    __syncthreads();   // the bits, z and normaliser of step t + 1 are written before its forward
+    phase_barrier();   // the bits, z and normaliser of step t + 1 are written before its forward
   }
-  __syncthreads();
-  // the last forward's S, unsatisfied counts and status (and the model's sample and step)
-  if (ran && K > 0) {
+  // SPLIT: no block goes on (and leaves) while another may still read its
+  // histogram: all blocks leave the loop at the same step
+  phase_barrier();
+  // the last forward's S, unsatisfied counts and status (and the model's
+  // sample and step); every block of a cluster holds the same values
+  if (ran && K > 0 && rank == 0) {
     for (int i = tid; i < N; i += BS) {
       sd.S[(size_t)inst * N + i] = sS[i];
       sd.unsat[(size_t)inst * N + i] = sU[i];
@@ -495,23 +554,23 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
   }
   // an instance found in this launch keeps its model in both bit buffers (the
   // multi-kernel path copies a frozen instance's bits at every step)
-  if (found && ran) {
+  if (found && ran) {   // the block's rows
     const int64_t tf = sh_ft;
-    for (int64_t i = tid; i < (int64_t)I.n_vars * W; i += BS) {
+    for (int64_t i = (int64_t)r_lo * W + tid; i < (int64_t)r_hi * W; i += BS) {
       if (RES) sbits[((tf + 1) & 1) * vw + i] = sbits[(tf & 1) * vw + i];
       else ps_bits(sd, tf + 1)[(size_t)I.v_off * W + i] = ps_bits(sd, tf)[(size_t)I.v_off * W + i];
     }
   }
   if (RES && ran) {   // write the resident state back
     __syncthreads();
-    for (int64_t i = tid; i < (int64_t)I.n_vars * N; i += BS) {
+    for (int64_t i = tid; i < (int64_t)nown * N; i += BS) {
       const size_t si = (size_t)(i / 32) * 33 + (i & 31);
       sd.z[g0 + i] = smz[si];
       sd.m[g0 + i] = smm[si];
       sd.v[g0 + i] = smv[si];
     }
-    for (int i = tid; i < I.n_vars; i += BS) sd.nu[I.v_off + i] = snu[i];
-    for (int64_t i = tid; i < (int64_t)I.n_vars * W; i += BS) {
+    for (int i = tid; i < nown; i += BS) sd.nu[I.v_off + r_lo + i] = snu[i];
+    for (int64_t i = (int64_t)r_lo * W + tid; i < (int64_t)r_hi * W; i += BS) {
       ps_bits(sd, 0)[(size_t)I.v_off * W + i] = sbits[i];
       ps_bits(sd, 1)[(size_t)I.v_off * W + i] = sbits[vw + i];
     }
@@ -546,22 +605,36 @@ __global__ void __launch_bounds__(ps_block<SPT>(), SPT == 32 ? 2 : 1)
   }
 }
 
-// histogram [8][N] int32, the table (272 floats per 32-sample word), S and the
-// unsatisfied counts [N] each, the bits [2][vmax][N/32]; resident: z, m, v
-// [vmax][N/32][33] and the normaliser [vmax]
-int64_t persist_smem_bytes(int N, int32_t vmax, bool resident) {
-  const int64_t vw = (int64_t)vmax * (N / 32);
-  return 4 * (8LL * N + 272LL * (N / 32) + 2LL * N + 2 * vw + (resident ? 3 * 33 * vw + vmax : 0));
+// histograms [HP][8][N] int32 (HP = 2 step parities with clusters), the table
+// (272 floats per 32-sample word), S and the unsatisfied counts [N] each, the
+// bits [2][vmax][N/32]; resident: z, m, v of one block's rows
+// [vown][N/32][33] and their normaliser [vown], vown = ceil(vmax / cs)
+int64_t persist_smem_bytes(int N, int32_t vmax, bool resident, int cs) {
+  const int64_t vw = (int64_t)vmax * (N / 32), vown = (vmax + cs - 1) / cs, ow = vown * (N / 32);
+  const int64_t hp = cs > 1 ? 2 : 1;
+  return 4 * (hp * 8LL * N + 272LL * (N / 32) + 2LL * N + 2 * vw + (resident ? 3 * 33 * ow + vown : 0));
 }
 
 cudaError_t launch_persist(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls, int32_t K,
-                           int32_t vmax, bool resident, cudaStream_t st) {
-  const int smem = (int)persist_smem_bytes(sd.N, vmax, resident);
-  auto go = [&](auto kern, int block) {
+                           int32_t vmax, bool resident, int cs, cudaStream_t st) {
+  const int smem = (int)persist_smem_bytes(sd.N, vmax, resident, cs);
+  const int32_t vown = (vmax + cs - 1) / cs;
+  auto go = [&](auto kern, int block) -> cudaError_t {
     cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(kern), smem);
     if (e != cudaSuccess) return e;
-    kern<<<pd.n_inst, block, smem, st>>>(pd, sd, hy, ls, K, vmax);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(pd.n_inst * cs));
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = cs > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, pd, sd, hy, ls, K, vmax, vown);
   };
   const bool ph = hy.binarize == TSAT_BIN_PHILOX;
   // samples per thread: resident instances run at 512 threads (16), the
@@ -569,8 +642,13 @@ cudaError_t launch_persist(const ProbDev &pd, const StateDev &sd, const Hyper &h
   // N = 32..256, n = 100..1000 (16 is 16-31 % faster when resident, 8 is
   // 8-20 % faster when not)
   const int spt = sd.N > 256 ? 32 : (resident ? 16 : 8);
-#define PS_GO1(B, M, S) (resident ? go(k_persist<B, M, true, S>, ps_block<S>()) : go(k_persist<B, M, false, S>, ps_block<S>()))
-#define PS_GO(B, M) (spt == 8 ? PS_GO1(B, M, 8) : (spt == 16 ? PS_GO1(B, M, 16) : PS_GO1(B, M, 32)))
+  if (cs > 1 && spt == 32) return cudaErrorInvalidValue;
+  const bool split = cs > 1;
+  // (clusters only with N <= 256: SPT 8 or 16)
+#define PS_GO2(B, M, R, S) (split ? go(k_persist<B, M, R, S, true>, ps_block<S>()) : go(k_persist<B, M, R, S, false>, ps_block<S>()))
+#define PS_GO1(B, M, S) (resident ? PS_GO2(B, M, true, S) : PS_GO2(B, M, false, S))
+#define PS_GO32(B, M) (resident ? go(k_persist<B, M, true, 32, false>, 256) : go(k_persist<B, M, false, 32, false>, 256))
+#define PS_GO(B, M) (spt == 8 ? PS_GO1(B, M, 8) : (spt == 16 ? PS_GO1(B, M, 16) : PS_GO32(B, M)))
   switch (hy.norm) {
     case TSAT_NORM_SIGNED_MEAN:
       return ph ? PS_GO(TSAT_BIN_PHILOX, TSAT_NORM_SIGNED_MEAN) : PS_GO(TSAT_BIN_DET, TSAT_NORM_SIGNED_MEAN);
@@ -580,7 +658,9 @@ cudaError_t launch_persist(const ProbDev &pd, const StateDev &sd, const Hyper &h
       return ph ? PS_GO(TSAT_BIN_PHILOX, TSAT_NORM_NONE) : PS_GO(TSAT_BIN_DET, TSAT_NORM_NONE);
   }
 #undef PS_GO
+#undef PS_GO32
 #undef PS_GO1
+#undef PS_GO2
 }
 
 }  // namespace tsat

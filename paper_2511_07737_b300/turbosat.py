@@ -86,6 +86,8 @@ def lib():
             "tsat_histogram": (ctypes.c_int, [P, P, P]),
             "tsat_step_persistent": (ctypes.c_int, [P, P, i32, i32, P]),
             "tsat_step_clustered": (ctypes.c_int, [P, P, i32, i32, P]),
+            "tsat_set_persist_blocks": (ctypes.c_int, [P, i32]),
+            "tsat_persist_blocks": (ctypes.c_int, [P, P, P]),
             "tsat_best": (ctypes.c_int, [P, P, i32, i32, P, P, P, P, P, P, P]),
             "tsat_partial_k": (i32, [i32]),
             "tsat_status": (ctypes.c_int, [P, P, P, P, P]),
@@ -255,9 +257,23 @@ def tsat_step(s, hp: tsat_hparams, n_steps: int, stop_on_sat: bool = True, strea
 
 
 def tsat_step_persistent(s, hp: tsat_hparams, n_steps: int, stop_on_sat: bool = True, stream=None):
-    """n_steps steps of a batch of small instances in one launch (one block per instance)."""
+    """n_steps steps of a batch of small instances in one launch (one block, or a
+    cluster of blocks, per instance)."""
     _ck(lib().tsat_step_persistent(s, ctypes.byref(hp), int(n_steps), int(bool(stop_on_sat)), _stream(stream)),
         "tsat_step_persistent")
+
+
+def tsat_set_persist_blocks(s, blocks: int):
+    """Blocks per instance of tsat_step_persistent: 0 automatic, 1, 2, 4 or 8."""
+    _ck(lib().tsat_set_persist_blocks(s, int(blocks)), "tsat_set_persist_blocks")
+
+
+def tsat_persist_blocks(s, with_residency: bool = False):
+    """Blocks per instance of the next tsat_step_persistent call (and, with
+    with_residency, whether they keep z, m, v in shared memory)."""
+    out, res = ctypes.c_int32(0), ctypes.c_int32(0)
+    _ck(lib().tsat_persist_blocks(s, ctypes.byref(out), ctypes.byref(res)), "tsat_persist_blocks")
+    return (int(out.value), bool(res.value)) if with_residency else int(out.value)
 
 
 def tsat_step_clustered(s, hp: tsat_hparams, n_steps: int, stop_on_sat: bool = True, stream=None):

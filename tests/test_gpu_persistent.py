@@ -36,14 +36,23 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("name,gen,N,kw", CASES, ids=[c[0] for c in CASES])
-def test_persistent_lockstep(name, gen, N, kw):
-    insts = gen()
+# one block per instance, and (N <= 256) a cluster of 4 blocks per instance
+LOCK_CASES = [c + (b,) for c in CASES for b in ([1, 4] if c[2] <= 256 else [1])]
+
+
+@pytest.mark.parametrize("name,gen,N,kw,blocks", LOCK_CASES, ids=[f"{c[0]}-x{c[4]}" for c in LOCK_CASES])
+def test_persistent_lockstep(name, gen, N, kw, blocks):
+    _persistent_lockstep(gen(), N, kw, blocks, 4)
+
+
+def _persistent_lockstep(insts, N, kw, blocks, steps):
+    """steps single-step launches (the third one on the multi-kernel path),
+    each checked against one oracle step from the GPU's FP32 state."""
     prob, st, cnfs = make(insts, N)
-    hp = ts.hparams(seed=33, tau=1.3, **kw)
+    ts.tsat_set_persist_blocks(st.h, blocks)
+    hp = ts.hparams(**{"seed": 33, "tau": 1.3, **kw})
     ts.tsat_init(st.h, hp)
     offs = prob.var_offsets
-    steps = 4
     for t in range(steps):
         s0 = snapshot(st)
         # alternate the persistent launch with the multi-kernel step: both leave the same state layout
@@ -206,3 +215,94 @@ def test_persistent_launches_from_two_host_threads():
     for a, b in zip(alone, out):
         for key in ("z", "m", "v", "bits"):
             np.testing.assert_array_equal(a[key], b[key])
+
+
+SPLIT_CASES = [
+    # resident with every block count; solved inside the 300-step launch
+    ("3sat-n100-N64", lambda: [cnfgen.planted_ksat(100, 426, 3, 0)], 64, dict(norm=1, binarize=0, tau=2.0, lr0=0.5)),
+    # a batch: one cluster per instance, Philox bits, clause lengths 3..5
+    ("batch-k3..5-N64-philox", lambda: cnfgen.batch_ksat(6, 40, n_lo=40, n_hi=150, ks=[3, 4, 5]), 64,
+     dict(norm=0, binarize=1, bin_temp=0.5)),
+    # global z, m, v with one block, resident in the blocks of a cluster of 8
+    ("3sat-n1000-N64", lambda: [cnfgen.planted_ksat(1000, 4000, 3, 2)], 64, dict(norm=1, binarize=0, tau=2.0, lr0=0.5)),
+    # clause pointers and literals (length 5), no normalisation, N = 256
+    ("k5-n200-N256-philox", lambda: [cnfgen.planted_ksat(200, 3000, 5, 13)], 256, dict(norm=2, binarize=1)),
+    # N = 32, duplicated literals and short clauses, signed mean
+    ("short-dup-n300-N32", lambda: [cnfgen.tiny_random(300, 2000, 9, kmin=1, kmax=5)], 32, dict(norm=0, binarize=1)),
+]
+
+
+@pytest.mark.parametrize("k", [7, 300])
+@pytest.mark.parametrize("blocks", [2, 4, 8])
+@pytest.mark.parametrize("name,gen,N,kw", SPLIT_CASES, ids=[c[0] for c in SPLIT_CASES])
+def test_persistent_cluster_of_blocks_equals_one_block(name, gen, N, kw, blocks, k):
+    """An instance split over a cluster of 2, 4 or 8 blocks (clauses and rows
+    dealt to the blocks, histograms summed over distributed shared memory)
+    leaves z, m, v, the normaliser, both bits buffers and the status records
+    bit for bit as one block per instance, over a launch of k steps (k = 300
+    crosses the 256-step batch of step scalars and, for the first case, the
+    freezing of the solved instance inside the launch)."""
+    insts = gen()
+    hp = ts.hparams(seed=21, **kw)
+    prob, st_a, _ = make(insts, N)
+    st_b = ts.State(prob, N)
+    ts.tsat_set_persist_blocks(st_a.h, 1)
+    ts.tsat_set_persist_blocks(st_b.h, blocks)
+    (ba, ra), (bb, rb) = ts.tsat_persist_blocks(st_a.h, True), ts.tsat_persist_blocks(st_b.h, True)
+    assert ba == 1 and bb == blocks
+    if ra != rb:
+        # z, m, v in shared memory with the cluster but global with one block
+        # (another number of samples per thread, so the Eq. 5 row sums round
+        # in another order): the split layout against the oracle instead
+        assert rb and not ra
+        if k == 7:
+            _persistent_lockstep(insts, N, kw, blocks, 3)
+        return
+    for st in (st_a, st_b):
+        ts.tsat_init(st.h, hp)
+        ts.tsat_step_persistent(st.h, hp, k, stop_on_sat=False)
+    a, b = snapshot(st_a), snapshot(st_b)
+    for key in ("z", "m", "v", "nu", "bits"):
+        np.testing.assert_array_equal(a[key].view(np.uint32), b[key].view(np.uint32), err_msg=key)
+    sa, sb = ts.tsat_status(st_a.h, len(insts)), ts.tsat_status(st_b.h, len(insts))
+    assert sa["step"] == sb["step"] == k
+    assert sa["inst"] == sb["inst"]
+    if name == "3sat-n100-N64" and k == 300:
+        assert sa["inst"][0]["found"]
+    # and a continuation launch of the split state with stop_on_sat: the same
+    # stop as one block
+    for st in (st_a, st_b):
+        ts.tsat_step_persistent(st.h, hp, 20, stop_on_sat=True)
+    a, b = snapshot(st_a), snapshot(st_b)
+    for key in ("z", "bits"):
+        np.testing.assert_array_equal(a[key].view(np.uint32), b[key].view(np.uint32), err_msg=key)
+    assert ts.tsat_status(st_a.h, len(insts)) == ts.tsat_status(st_b.h, len(insts))
+
+
+def _auto_blocks(n_inst):
+    """The automatic choice for instances one block cannot keep resident."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cs = 1
+    while cs < 8 and n_inst * cs * 2 <= sms:
+        cs *= 2
+    return cs
+
+
+def test_persist_blocks_setting_is_checked():
+    inst = cnfgen.planted_ksat(100, 426, 3, 0)
+    prob, st, _ = make([inst], 64)
+    assert ts.tsat_persist_blocks(st.h, True) == (1, True)    # resident in one block: one block
+    mid = cnfgen.planted_ksat(1000, 4260, 3, 0)
+    prob1, st1, _ = make([mid], 64)
+    assert ts.tsat_persist_blocks(st1.h, True) == (_auto_blocks(1), True) == (8, True)   # resident from 8 blocks
+    for bad in (3, 16, -1):
+        with pytest.raises(ts.TsatError) as e:
+            ts.tsat_set_persist_blocks(st.h, bad)
+        assert e.value.status == -1
+    big = ts.State(prob, 1024)
+    assert ts.tsat_persist_blocks(big.h) == 1         # N > 256: one block per instance
+    with pytest.raises(ts.TsatError):
+        ts.tsat_set_persist_blocks(big.h, 2)
+    batch = [cnfgen.planted_ksat(1000, 4260, 3, j) for j in range(40)]
+    prob2, st2, _ = make(batch, 64)
+    assert ts.tsat_persist_blocks(st2.h) == _auto_blocks(40)   # 2 on 148 SMs: 40 x 4 blocks would not fit
