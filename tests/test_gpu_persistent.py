@@ -279,6 +279,31 @@ def test_persistent_cluster_of_blocks_equals_one_block(name, gen, N, kw, blocks,
     assert ts.tsat_status(st_a.h, len(insts)) == ts.tsat_status(st_b.h, len(insts))
 
 
+@pytest.mark.parametrize("name,gen,N", [
+    # fewer rows than blocks: some blocks of the cluster own no row and no forward task
+    ("tiny-n6-x8", lambda: [cnfgen.tiny_random(6, 20, 3, kmin=1, kmax=3)], 64),
+    # more clusters than fit on the device at once (40 x 8 blocks): they run in waves
+    ("waves-40x-n60-x8", lambda: [cnfgen.planted_ksat(60, 250, 3, 70 + j) for j in range(40)], 32),
+    # instances of different sizes in one launch, one cluster each
+    ("mixed-sizes-x8", lambda: cnfgen.batch_ksat(5, 77, n_lo=10, n_hi=400, ks=[3, 4]), 32),
+])
+def test_persistent_cluster_edge_cases_equal_one_block(name, gen, N):
+    insts = gen()
+    hp = ts.hparams(seed=5, norm=1, binarize=1, bin_temp=0.5)
+    prob, st_a, _ = make(insts, N)
+    st_b = ts.State(prob, N)
+    ts.tsat_set_persist_blocks(st_a.h, 1)
+    ts.tsat_set_persist_blocks(st_b.h, 8)
+    assert ts.tsat_persist_blocks(st_a.h, True)[1] == ts.tsat_persist_blocks(st_b.h, True)[1]
+    for st in (st_a, st_b):
+        ts.tsat_init(st.h, hp)
+        ts.tsat_step_persistent(st.h, hp, 40, stop_on_sat=True)
+    a, b = snapshot(st_a), snapshot(st_b)
+    for key in ("z", "m", "v", "nu", "bits"):
+        np.testing.assert_array_equal(a[key].view(np.uint32), b[key].view(np.uint32), err_msg=key)
+    assert ts.tsat_status(st_a.h, len(insts)) == ts.tsat_status(st_b.h, len(insts))
+
+
 def _auto_blocks(n_inst):
     """The automatic choice for instances one block cannot keep resident."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
