@@ -300,25 +300,29 @@ def time_to_sat_summary(ts, torch, n_inst=32, cap=500):
             "batched": {"solved": int(sum(x["found"] for x in sb["inst"])), "of": n_inst,
                         "ms_whole_batch": batch_ms, "steps_run": sb["step"]}}
     name = "tuned: mean |z| Eq. 5, tau 2, lr0 0.5"
-    out["readings"][name]["learned"] = learned_time_to_sat(ts, torch, insts, TTS_READINGS[name], cap)
-    out["mid_size"] = mid_size_time_to_sat(ts, torch, TTS_READINGS[name])
+    learned, pr = learned_time_to_sat(ts, torch, insts, TTS_READINGS[name], cap)
+    out["readings"][name]["learned"] = learned
+    out["mid_size"] = mid_size_time_to_sat(ts, torch, TTS_READINGS[name], pr)
     return out
 
 
-def mid_size_time_to_sat(ts, torch, kw, n_inst=16, n=1000, m=4000, cap=2000):
+def mid_size_time_to_sat(ts, torch, kw, pr, n_inst=16, n=1000, m=4000, cap=2000):
     """Time to SAT on mid-size instances (planted 3-SAT n=1000 m=4000, N=64,
     tuned reading, cap 2000 steps, seeds 0..15), where one block cannot keep
     an instance's z, m, v in shared memory: each instance alone in one
     persistent launch on a cluster of blocks (the automatic choice), the same
-    on one block, and on the multi-kernel graph path (10-step replays with a
-    status read after each); then all instances as one batch in one
-    persistent launch.  Wall time from tsat_init to the host seeing the found
-    flag."""
+    on one block, on the multi-kernel graph path (10-step replays with a
+    status read after each), and on the cluster from the logits of the
+    proposer `pr` (trained on n 100..300, logit scale 1; timed from the start
+    of the proposal), with the median steps of the fastest k solves of the
+    random and the learned initialisation at the same k (equal solve rate);
+    then all instances as one batch in one persistent launch.  Wall time from
+    tsat_init (or the proposal) to the host seeing the found flag."""
     from paper_2511_07737_b300 import cnfgen
     insts = [cnfgen.planted_ksat(n, m, 3, j) for j in range(n_inst)]
     out = {"workload": f"{n_inst} x planted 3-SAT n={n} m={m} (ratio {m / n:.2f}), N=64, deterministic Eq. 2, "
                        f"tuned reading, cap {cap} steps", "unit": "ms"}
-    for mode in ("persistent_cluster", "persistent_one_block", "graph_path"):
+    for mode in ("persistent_cluster", "persistent_one_block", "graph_path", "learned_cluster"):
         walls, steps, blocks = [], [], None
         for j, inst in enumerate(insts):
             prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
@@ -327,14 +331,22 @@ def mid_size_time_to_sat(ts, torch, kw, n_inst=16, n=1000, m=4000, cap=2000):
                 ts.tsat_set_persist_blocks(st.h, 1)
             blocks = ts.tsat_persist_blocks(st.h)
             hp = ts.hparams(seed=j + 1, **kw)
-            ts.tsat_init(st.h, hp)
+            lg = None
+            if mode == "learned_cluster":
+                ws = pr._ws(prob)
+                lg = torch.empty(inst.n_vars, dtype=torch.float32, device="cuda")
+                for _ in range(2):   # the second call with these buffers captures the forward's graph
+                    ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)
+            ts.tsat_init(st.h, hp, lg, 1.0)
             if mode == "graph_path":
                 ts.tsat_step(st.h, hp, 10, stop_on_sat=True)       # first replay: the graph is built
             else:
                 ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ts.tsat_init(st.h, hp)
+            if lg is not None:
+                ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)
+            ts.tsat_init(st.h, hp, lg, 1.0)
             if mode == "graph_path":
                 for _ in range(cap // 10):
                     ts.tsat_step(st.h, hp, 10, stop_on_sat=True)
@@ -345,14 +357,28 @@ def mid_size_time_to_sat(ts, torch, kw, n_inst=16, n=1000, m=4000, cap=2000):
                 ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
                 x = ts.tsat_status(st.h, 1)["inst"][0]
             el = time.perf_counter() - t0
+            if lg is not None:
+                ts.tsat_mpnn_status(prob.h, ws)
             if x["found"]:
                 walls.append(el)
                 steps.append(x["found_step"])
         out[mode] = {"solved": len(walls), "of": n_inst,
                      "median_ms_to_sat": 1e3 * float(np.median(walls)) if walls else None,
-                     "median_steps_to_sat": float(np.median(steps)) if steps else None}
+                     "median_steps_to_sat": float(np.median(steps)) if steps else None,
+                     "_steps": sorted(steps), "_walls": sorted(walls)}
         if mode != "graph_path":
             out[mode]["blocks_per_instance"] = blocks
+    # equal solve rate: the fastest k solves of each initialisation
+    rnd, lrn = out["persistent_cluster"], out["learned_cluster"]
+    k = min(rnd["solved"], lrn["solved"])
+    out["learned_vs_random_equal_solve_rate"] = {
+        "k": k,
+        "random_median_steps": float(np.median(rnd["_steps"][:k])) if k else None,
+        "learned_median_steps": float(np.median(lrn["_steps"][:k])) if k else None,
+        "random_median_ms": 1e3 * float(np.median(rnd["_walls"][:k])) if k else None,
+        "learned_median_ms": 1e3 * float(np.median(lrn["_walls"][:k])) if k else None}
+    for mode in ("persistent_cluster", "persistent_one_block", "graph_path", "learned_cluster"):
+        del out[mode]["_steps"], out[mode]["_walls"]
     prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in insts])
     st = ts.State(prob, 64)
     hp = ts.hparams(seed=1, **kw)
@@ -376,7 +402,7 @@ def learned_time_to_sat(ts, torch, insts, kw, cap, scale=1.0):
     initial logits (z = logit x scale + noise); wall time from the start of the
     proposal (the network's forward) to the host seeing the found flag, each
     instance alone in one persistent launch, and all of them as one batch in
-    one persistent launch."""
+    one persistent launch.  Returns the result and the trained proposer."""
     from paper_2511_07737_b300 import cnfgen
     from paper_2511_07737_b300.proposer import Proposer, make_dataset
     t0 = time.perf_counter()
@@ -442,7 +468,7 @@ def learned_time_to_sat(ts, torch, insts, kw, cap, scale=1.0):
             "batched": {"solved": int(sum(x["found"] for x in sb["inst"])), "of": len(insts),
                         "ms_whole_batch": batch_ms, "steps_run": sb["step"]},
             "training": {"instances": len(train), "kept": len(data), "dropped": dropped,
-                         "data_seconds": t_data, "fit_seconds": t_fit}}
+                         "data_seconds": t_data, "fit_seconds": t_fit}}, pr
 
 
 def progress_reading(ts, torch, prob, N, K, seed):
