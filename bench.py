@@ -250,6 +250,10 @@ TTS_READINGS = {
     "paper: signed-mean Eq. 5, tau 1, lr0 0.1": dict(norm=0, tau=1.0, lr0=0.1),
     "paper schedule, sign-keeping Eq. 5 (mean |z|), tau 2, lr0 0.1": dict(norm=1, tau=2.0, lr0=0.1),
     "tuned: mean |z| Eq. 5, tau 2, lr0 0.5": dict(norm=1, tau=2.0, lr0=0.5),
+    # chosen by a sweep of tau in 0.75..4 and lr0 in 0.3..3 (mean |z| and no
+    # normalisation) on 64 other planted instances (seeds 5000..5063), for the
+    # fewest median steps to SAT at 62 / 64 solved
+    "swept on other instances: mean |z| Eq. 5, tau 1.5, lr0 1.2": dict(norm=1, tau=1.5, lr0=1.2),
 }
 
 
@@ -302,6 +306,8 @@ def time_to_sat_summary(ts, torch, n_inst=32, cap=500):
     name = "tuned: mean |z| Eq. 5, tau 2, lr0 0.5"
     learned, pr = learned_time_to_sat(ts, torch, insts, TTS_READINGS[name], cap)
     out["readings"][name]["learned"] = learned
+    swept = "swept on other instances: mean |z| Eq. 5, tau 1.5, lr0 1.2"
+    out["readings"][swept]["learned"], _ = learned_time_to_sat(ts, torch, insts, TTS_READINGS[swept], cap, pr=pr)
     out["mid_size"] = mid_size_time_to_sat(ts, torch, TTS_READINGS[name], pr)
     return out
 
@@ -395,26 +401,30 @@ def mid_size_time_to_sat(ts, torch, kw, pr, n_inst=16, n=1000, m=4000, cap=2000)
     return out
 
 
-def learned_time_to_sat(ts, torch, insts, kw, cap, scale=1.0):
+def learned_time_to_sat(ts, torch, insts, kw, cap, scale=1.0, pr=None):
     """The same instances from a learned initialisation: a proposer trained on
     the solver's own models of 512 generated planted 3-SAT instances (n
     100..300, ratio 4.26, seeds 1000.., disjoint from the workload's) gives the
     initial logits (z = logit x scale + noise); wall time from the start of the
     proposal (the network's forward) to the host seeing the found flag, each
     instance alone in one persistent launch, and all of them as one batch in
-    one persistent launch.  Returns the result and the trained proposer."""
+    one persistent launch.  Returns the result and the trained proposer (pr:
+    a proposer trained already, evaluated under this reading)."""
     from paper_2511_07737_b300 import cnfgen
     from paper_2511_07737_b300.proposer import Proposer, make_dataset
-    t0 = time.perf_counter()
-    sizes = np.random.default_rng(5).integers(100, 300, 512)
-    train = [cnfgen.planted_ksat(int(n), int(round(4.26 * n)), 3, 1000 + j) for j, n in enumerate(sizes)]
-    data, dropped = make_dataset(train, N=32, hp=ts.hparams(seed=7, **kw), max_steps=cap)
-    t_data = time.perf_counter() - t0
-    pr = Proposer(seed=1)
-    t1 = time.perf_counter()
-    pr.fit(data, epochs=8, batch=16, lr=3e-3)
-    torch.cuda.synchronize()
-    t_fit = time.perf_counter() - t1
+    training = None
+    if pr is None:
+        t0 = time.perf_counter()
+        sizes = np.random.default_rng(5).integers(100, 300, 512)
+        train = [cnfgen.planted_ksat(int(n), int(round(4.26 * n)), 3, 1000 + j) for j, n in enumerate(sizes)]
+        data, dropped = make_dataset(train, N=32, hp=ts.hparams(seed=7, **kw), max_steps=cap)
+        t_data = time.perf_counter() - t0
+        pr = Proposer(seed=1)
+        t1 = time.perf_counter()
+        pr.fit(data, epochs=8, batch=16, lr=3e-3)
+        torch.cuda.synchronize()
+        training = {"instances": len(train), "kept": len(data), "dropped": dropped,
+                    "data_seconds": t_data, "fit_seconds": time.perf_counter() - t1}
     walls, steps, props = [], [], []
     for j, inst in enumerate(insts):
         prob = ts.Problem([(inst.n_vars, inst.clause_ptr, inst.lits)])
@@ -467,8 +477,7 @@ def learned_time_to_sat(ts, torch, insts, kw, cap, scale=1.0):
             "median_proposal_ms": 1e3 * float(np.median(props)), "logit_scale": scale,
             "batched": {"solved": int(sum(x["found"] for x in sb["inst"])), "of": len(insts),
                         "ms_whole_batch": batch_ms, "steps_run": sb["step"]},
-            "training": {"instances": len(train), "kept": len(data), "dropped": dropped,
-                         "data_seconds": t_data, "fit_seconds": t_fit}}, pr
+            "training": training if training else "the proposer trained for the tuned reading"}, pr
 
 
 def progress_reading(ts, torch, prob, N, K, seed):
