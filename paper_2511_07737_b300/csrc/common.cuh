@@ -87,7 +87,7 @@ struct StateDev {
   int32_t *unsat;              // [n_inst][N]
   float *zy;                   // relaxed: [n_items][2][N] partial (Z, Y) sums
   float *zs;                   // relaxed: [n_inst][2][N] (Z, S)
-  float *rbuf;                 // relaxed: [C][N] clause sums R (FP32 storage: then dL/dR in place)
+  float *rbuf;                 // relaxed: [C][N] clause sums R
   uint32_t *dr16;              // relaxed, BF16 storage: [C][N] dL/dR as bf16 (pairs of samples per word), else NULL
   void *lit;                   // relaxed: [V][N] literal values (f32 or bf16)
   int32_t lit_bf16, pad;

@@ -578,6 +578,13 @@ __device__ __forceinline__ float sel4(int r, float g0, float g1, float g2, float
   return (r & 2) ? b : a;
 }
 
+// 2^x by the PTX base-2 exponential (flushes subnormal results to zero)
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 template <int P, bool GREG, bool RELAX, bool DR16 = false>
 __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, Hyper hy, int mode,
                                                       const float *zin, float *grad, float dL,
@@ -601,6 +608,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
   uint32_t *bdst = const_cast<uint32_t *>(cur_bits(sd, tcur + 1));
   const float b1 = hy.beta1, b2 = hy.beta2;
   float gam[4][4];
+  // relaxed layer, FP32 storage: dL/dR_ci = e^{-tau R} (ra R + rb) per sample,
+  // ra = tau / Z_i, rb = -(1 + tau S_i) / Z_i (Eq. 4 differentiated), formed
+  // from the gathered R of each occurrence
+  float ra[4] = {0.f, 0.f, 0.f, 0.f}, rb[4] = {0.f, 0.f, 0.f, 0.f};
   int cur_inst = -1;
   const int64_t NG = (int64_t)gridDim.x * RPB;
   const int64_t n_items = ((int64_t)pd.V + rows_per_item - 1) / rows_per_item;
@@ -616,6 +627,17 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
         cur_inst = inst;
         const float *gsrc = sd.gamma + (size_t)inst * lm1 * N;
         if constexpr (RELAX) {
+          if constexpr (!DR16) {
+            const float4 zz = *reinterpret_cast<const float4 *>(sd.zs + (size_t)inst * 2 * N + s0);
+            const float4 ss = *reinterpret_cast<const float4 *>(sd.zs + ((size_t)inst * 2 + 1) * N + s0);
+            const float Zq[4] = {zz.x, zz.y, zz.z, zz.w}, Sq[4] = {ss.x, ss.y, ss.z, ss.w};
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+              const float iz = 1.0f / Zq[s];
+              ra[s] = hy.tau * iz;
+              rb[s] = -(1.0f + hy.tau * Sq[s]) * iz;
+            }
+          }
         } else if constexpr (GREG) {
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
@@ -637,11 +659,14 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
       const float nu = sd.nu[v];
       float G[4] = {0.f, 0.f, 0.f, 0.f};
       if constexpr (RELAX) {
-        // ---- relaxed backward: sum of +-dL/dR_ci over the row's occurrences; the
-        // buffer holds dL/dR (k_relaxed_dr), 8 occurrences' loads in flight
+        // ---- relaxed backward: sum of +-dL/dR_ci over the row's occurrences, 8
+        // occurrences' loads in flight.  BF16 storage: the buffer holds dL/dR
+        // (k_relaxed_dr); FP32: the buffer holds R, and dL/dR is formed here
+        // (one exponential per occurrence and sample instead of a pass that
+        // writes and re-reads the whole [C][N] buffer)
         const int32_t ob = __ldg(pd.vptr + v), oe = __ldg(pd.vptr + v + 1);
         int32_t o = ob;
-        // dL/dR of clause c for this thread's 4 samples (FP32 or bf16 storage)
+        // the stored value of clause c for this thread's 4 samples
         auto dR = [&](int32_t c) -> float4 {
           if constexpr (DR16) {
             const uint2 u = __ldg(reinterpret_cast<const uint2 *>(sd.dr16 + ((size_t)c * N + s0) / 2));
@@ -650,6 +675,18 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
             return make_float4(lo.x, lo.y, hi.x, hi.y);
           } else {
             return __ldg(reinterpret_cast<const float4 *>(sd.rbuf + (size_t)c * N + s0));
+          }
+        };
+        // dL/dR from the stored value: e^{-tau R} as 2^{c R}, c = -tau log2(e),
+        // one multiply and the hardware base-2 exponential (relative error
+        // about 2^-22, plus c R's rounding)
+        const float c2 = -hy.tau * 1.4426950408889634f;
+        auto toD = [&](float4 x) -> float4 {
+          if constexpr (DR16) {
+            return x;
+          } else {
+            return make_float4(ex2_approx(c2 * x.x) * fmaf(ra[0], x.x, rb[0]), ex2_approx(c2 * x.y) * fmaf(ra[1], x.y, rb[1]),
+                               ex2_approx(c2 * x.z) * fmaf(ra[2], x.z, rb[2]), ex2_approx(c2 * x.w) * fmaf(ra[3], x.w, rb[3]));
           }
         };
         for (; o + 8 <= oe; o += 8) {
@@ -662,15 +699,16 @@ __global__ void __launch_bounds__(kBlock, 3) k_update(ProbDev pd, StateDev sd, H
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const float sg = (e[q] & 1) ? -1.0f : 1.0f;
-            G[0] = fmaf(sg, D[q].x, G[0]);
-            G[1] = fmaf(sg, D[q].y, G[1]);
-            G[2] = fmaf(sg, D[q].z, G[2]);
-            G[3] = fmaf(sg, D[q].w, G[3]);
+            const float4 Dq = toD(D[q]);
+            G[0] = fmaf(sg, Dq.x, G[0]);
+            G[1] = fmaf(sg, Dq.y, G[1]);
+            G[2] = fmaf(sg, Dq.z, G[2]);
+            G[3] = fmaf(sg, Dq.w, G[3]);
           }
         }
         for (; o < oe; ++o) {
           const int32_t e = __ldg(pd.vocc + o);
-          const float4 D = dR(e >> 1);
+          const float4 D = toD(dR(e >> 1));
           const float sg = (e & 1) ? -1.0f : 1.0f;
           G[0] = fmaf(sg, D.x, G[0]);
           G[1] = fmaf(sg, D.y, G[1]);
@@ -1449,10 +1487,9 @@ __global__ void __launch_bounds__(kBlock) k_relaxed_fwd(ProbDev pd, StateDev sd,
 }
 
 // dL/dR_ci = -(e^{-tau R_ci} / Z_i)(1 - tau (R_ci - S_i)) (Eq. 4 differentiated),
-// once per (clause, sample): the update then only gathers and adds it per
-// occurrence.  FP32 storage: in place over the stored R; BF16 storage: into
-// the bf16 buffer, so that the update gathers half the bytes (the sums stay
-// FP32).
+// once per (clause, sample), for BF16 storage only: into the bf16 buffer, so
+// that the update gathers half the bytes (the sums stay FP32).  With FP32
+// storage the update forms dL/dR from the gathered R itself.
 __global__ void __launch_bounds__(kBlock) k_relaxed_dr(ProbDev pd, StateDev sd, Hyper hy, int skip_frozen) {
   if (skip_frozen && sd.hdr->all_done) return;
   const int4 it = pd.items[blockIdx.x];
@@ -1464,19 +1501,14 @@ __global__ void __launch_bounds__(kBlock) k_relaxed_dr(ProbDev pd, StateDev sd, 
   const float4 ss = *reinterpret_cast<const float4 *>(sd.zs + ((size_t)inst * 2 + 1) * N + s0);
   const float Zr[4] = {zz.x, zz.y, zz.z, zz.w}, Sr[4] = {ss.x, ss.y, ss.z, ss.w};
   for (int c = it.y + cs; c < it.z; c += CPB) {
-    float4 *p = reinterpret_cast<float4 *>(sd.rbuf + (size_t)c * N + s0);
-    const float4 R4 = *p;
+    const float4 R4 = *reinterpret_cast<const float4 *>(sd.rbuf + (size_t)c * N + s0);
     const float Rq[4] = {R4.x, R4.y, R4.z, R4.w};
     float D[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) D[s] = -(expf(-hy.tau * Rq[s]) / Zr[s]) * (1.0f - hy.tau * (Rq[s] - Sr[s]));
-    if (sd.dr16) {
-      const __nv_bfloat162 lo = __floats2bfloat162_rn(D[0], D[1]), hi = __floats2bfloat162_rn(D[2], D[3]);
-      *reinterpret_cast<uint2 *>(sd.dr16 + ((size_t)c * N + s0) / 2) =
-          make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
-    } else {
-      *p = make_float4(D[0], D[1], D[2], D[3]);
-    }
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(D[0], D[1]), hi = __floats2bfloat162_rn(D[2], D[3]);
+    *reinterpret_cast<uint2 *>(sd.dr16 + ((size_t)c * N + s0) / 2) =
+        make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
   }
 }
 
@@ -1530,12 +1562,12 @@ cudaError_t launch_relaxed_fwd(const ProbDev &pd, const StateDev &sd, const Hype
   return cudaGetLastError();
 }
 
-// S and Z (k_relaxed_zs), the loss and step bookkeeping (k_relaxed_gamma), then
-// dL/dR in place over the stored R (k_relaxed_dr) for the backward.
+// S and Z (k_relaxed_zs), the loss and step bookkeeping (k_relaxed_gamma), and
+// with BF16 storage dL/dR into the bf16 buffer (k_relaxed_dr) for the backward.
 cudaError_t launch_relaxed_gamma(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls,
                                  int step_mode, float *loss_out, float *S_out, cudaStream_t st) {
   k_relaxed_zs<<<dim3(pd.n_inst, (sd.N + 31) / 32), dim3(32, 32), 0, st>>>(pd, sd, step_mode, S_out);
-  k_relaxed_dr<<<pd.n_items, kBlock, 0, st>>>(pd, sd, hy, step_mode);
+  if (sd.dr16) k_relaxed_dr<<<pd.n_items, kBlock, 0, st>>>(pd, sd, hy, step_mode);
   k_relaxed_gamma<<<1, 1024, 0, st>>>(pd, sd, hy, ls, step_mode, loss_out, S_out);
   return cudaGetLastError();
 }
