@@ -220,9 +220,9 @@ int tsat_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t st
  * Requirements: the STE layer, hp->mix_restart = 0, clauses of at most 7
  * literals, clauses x longest clause x samples <= 2^26 per block of the
  * instance, and 4 (18.5 N + 2 n_vars N / 32) bytes of shared memory <= 200
- * KiB for the largest instance (about 25,000 variables at N = 32, 12,500 at
- * N = 64, 500 at N = 1024); else TSAT_EINVAL / TSAT_ERANGE.  Async on
- * `stream`. */
+ * KiB for the largest instance (26.5 N with a cluster; about 25,000 variables
+ * at N = 32, 12,500 at N = 64, 500 at N = 1024); else TSAT_EINVAL /
+ * TSAT_ERANGE.  Async on `stream`. */
 int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
                          cudaStream_t stream);
 
