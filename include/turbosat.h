@@ -389,8 +389,8 @@ int tsat_backward(tsat_state *s, const tsat_hparams *hp, const float *d_z, float
                   float *d_grad, cudaStream_t stream);
 
 /* ---- schedules ----
- * Launch shapes of the forward and update kernels (the survey's tile /
- * warps-per-clause schedules reduce to these two knobs).
+ * Launch shapes of the forward and update kernels (tile and
+ * warps-per-clause schedules reduce to these knobs here).
  * tsat_autotune times candidate shapes on this state and keeps the fastest:
  * the forward's work-item size (clauses per item) on the forward, then the
  * update's blocks per SM and rows per work item on the step's own fused
