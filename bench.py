@@ -300,7 +300,8 @@ def time_to_sat_summary(ts, torch, n_inst=32, cap=500):
         out["readings"][name] = {
             "plain": {"solved": len(walls), "of": n_inst,
                       "median_ms_to_sat": 1e3 * float(np.median(walls)) if walls else None,
-                      "median_steps_to_sat": float(np.median(steps)) if steps else None},
+                      "median_steps_to_sat": float(np.median(steps)) if steps else None,
+                      "_walls": sorted(walls), "_steps": sorted(steps)},
             "batched": {"solved": int(sum(x["found"] for x in sb["inst"])), "of": n_inst,
                         "ms_whole_batch": batch_ms, "steps_run": sb["step"]}}
     name = "tuned: mean |z| Eq. 5, tau 2, lr0 0.5"
@@ -309,6 +310,22 @@ def time_to_sat_summary(ts, torch, n_inst=32, cap=500):
     out["readings"][name]["learned"] = learned
     swept = "swept on other instances: mean |z| Eq. 5, tau 1.5, lr0 1.2"
     out["readings"][swept]["learned"], _ = learned_time_to_sat(ts, torch, insts, TTS_READINGS[swept], cap, pr=pr)
+    # learned against random at equal solve rate: the fastest k solves of each
+    for rd in (name, swept):
+        r = out["readings"][rd]
+        rnd, lrn = r["plain"], r["learned"]
+        k = min(rnd["solved"], lrn["solved"])
+        r["learned_vs_random_equal_solve_rate"] = {
+            "k": k,
+            "random_median_steps": float(np.median(rnd["_steps"][:k])) if k else None,
+            "learned_median_steps": float(np.median(lrn["_steps"][:k])) if k else None,
+            "random_median_ms": 1e3 * float(np.median(rnd["_walls"][:k])) if k else None,
+            "learned_median_ms": 1e3 * float(np.median(lrn["_walls"][:k])) if k else None}
+    for r in out["readings"].values():
+        for leg in ("plain", "learned"):
+            if leg in r:
+                r[leg].pop("_walls", None)
+                r[leg].pop("_steps", None)
     out["mid_size"] = mid_size_time_to_sat(ts, torch, TTS_READINGS[name], pr)
     return out
 
@@ -501,6 +518,7 @@ def learned_time_to_sat(ts, torch, insts, kw, cap, scale=1.0, pr=None):
     return {"solved": len(walls), "of": len(insts),
             "median_ms_to_sat": 1e3 * float(np.median(walls)) if walls else None,
             "median_steps_to_sat": float(np.median(steps)) if steps else None,
+            "_walls": sorted(walls), "_steps": sorted(steps),
             "median_proposal_ms": 1e3 * float(np.median(props)), "logit_scale": scale,
             "batched": {"solved": int(sum(x["found"] for x in sb["inst"])), "of": len(insts),
                         "ms_whole_batch": batch_ms, "steps_run": sb["step"]},
