@@ -108,29 +108,34 @@ static MpWs mp_ws_plan(void *base, int64_t V, int64_t C) {
 }
 
 // ------------------------------------------------------------------ kernels
-__global__ void k_mp_to_bf16(const float *p, __nv_bfloat16 *b, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = __float2bfloat16_rn(p[i]);
-}
-
-// input features and the inverse literal degrees (1 / max(deg, 1), the
-// variable-major mean's scale)
-__global__ void k_mp_feat(ProbDev pd, float *linv, float *feat) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < pd.V; v += (int64_t)gridDim.x * blockDim.x) {
-    int dp = 0, dn = 0;
-    for (int32_t o = pd.vptr[v]; o < pd.vptr[v + 1]; ++o) (pd.vocc[o] & 1) ? ++dn : ++dp;
-    linv[2 * v] = 1.0f / fmaxf((float)dp, 1.f);
-    linv[2 * v + 1] = 1.0f / fmaxf((float)dn, 1.f);
-    const float lp = logf(1.0f + (float)dp), ln = logf(1.0f + (float)dn);
-    float *f0 = feat + (2 * v) * kFeat, *f1 = feat + (2 * v + 1) * kFeat;
-    f0[0] = 1.f; f0[1] = lp; f0[2] = ln;
-    f1[0] = 1.f; f1[1] = ln; f1[2] = lp;
+// The forward's preparation in one launch (a small graph's forward is a chain
+// of short kernels, each paying its launch): the error flag cleared, the BF16
+// copy of the parameters (items [0, n)), the input features and inverse
+// literal degrees 1 / max(deg, 1), the variable-major mean's scale (items
+// [n, n + V), one variable each), and the inverse clause lengths, the
+// clause-major mean's scale (items [n + V, n + V + C)).
+__global__ void k_mp_prep(const float *p, __nv_bfloat16 *b, int n, ProbDev pd, float *linv, float *feat,
+                          float *cinv, int *err) {
+  const int64_t total = (int64_t)n + pd.V + pd.C;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *err = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) {
+      b[i] = __float2bfloat16_rn(p[i]);
+    } else if (i < n + pd.V) {
+      const int64_t v = i - n;
+      int dp = 0, dn = 0;
+      for (int32_t o = pd.vptr[v]; o < pd.vptr[v + 1]; ++o) (pd.vocc[o] & 1) ? ++dn : ++dp;
+      linv[2 * v] = 1.0f / fmaxf((float)dp, 1.f);
+      linv[2 * v + 1] = 1.0f / fmaxf((float)dn, 1.f);
+      const float lp = logf(1.0f + (float)dp), ln = logf(1.0f + (float)dn);
+      float *f0 = feat + (2 * v) * kFeat, *f1 = feat + (2 * v + 1) * kFeat;
+      f0[0] = 1.f; f0[1] = lp; f0[2] = ln;
+      f1[0] = 1.f; f1[1] = ln; f1[2] = lp;
+    } else {
+      const int64_t c = i - n - pd.V;
+      cinv[c] = 1.0f / (float)(pd.cptr[c + 1] - pd.cptr[c]);
+    }
   }
-}
-
-// 1 / clause length (the clause-major mean's scale)
-__global__ void k_mp_cinv(ProbDev pd, float *cinv) {
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < pd.C; c += (int64_t)gridDim.x * blockDim.x)
-    cinv[c] = 1.0f / (float)(pd.cptr[c + 1] - pd.cptr[c]);
 }
 
 struct DIn {
@@ -171,10 +176,13 @@ __device__ __forceinline__ float4 relu_mask4(const float4 &x, const float4 &m) {
 }
 
 // Clause-major gather: out[c] = sum over the literals l of clause c of
-// src[l] (64 floats).  A warp takes 32 consecutive clauses: their offsets
-// come in two coalesced loads (lane l: cptr[c0 + l], cptr[c0 + l + 1]) and
-// are handed out by shuffles; it then works through them in 8 groups of 4
-// clauses (8 lanes per clause, 8 floats per lane as two float4).  A group's
+// src[l] (64 floats).  A warp takes 4 gpw consecutive clauses (gpw = 1..8
+// groups; 8 for large graphs, fewer when the graph is too small to give every
+// SM enough warps, so that a small graph's warps do not walk eight groups one
+// after another): their offsets come in two coalesced loads (lane l:
+// cptr[c0 + l], cptr[c0 + l + 1]) and are handed out by shuffles; it then
+// works through them in gpw groups of 4 clauses (8 lanes per clause, 8 floats
+// per lane as two float4).  A group's
 // literal ids are loaded 8 at a time by its lanes and broadcast, and the next
 // group's ids are loaded while this group's rows are summed, so only the row
 // loads wait.  The row loads of the four clauses are issued together, four
@@ -186,10 +194,11 @@ __device__ __forceinline__ float4 relu_mask4(const float4 &x, const float4 &m) {
 template <int MODE>
 __global__ void __launch_bounds__(256) k_mp_clause_gather(ProbDev pd, const float *__restrict__ src,
                                                           const float *__restrict__ cinv, const float *__restrict__ e,
-                                                          float *__restrict__ out) {
+                                                          float *__restrict__ out, int gpw) {
   const int lane = threadIdx.x & 31, gl = lane & 7, gbase = lane & ~7;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5, C = pd.C;
-  for (int64_t c0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; c0 < C; c0 += nw * 32) {
+  const int cpw = 4 * gpw;   // clauses per warp
+  for (int64_t c0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * cpw; c0 < C; c0 += nw * cpw) {
     const int32_t pb = __ldg(pd.cptr + min(c0 + lane, C)), pe = __ldg(pd.cptr + min(c0 + lane + 1, C));
     // group g: clauses c0 + 4 g + lane / 8; returns the lane's first literal id (clauses past C are empty)
     auto ids = [&](int g, int32_t &b, int32_t &n) -> int32_t {
@@ -200,9 +209,9 @@ __global__ void __launch_bounds__(256) k_mp_clause_gather(ProbDev pd, const floa
     };
     int32_t b, n;
     int32_t myl = ids(0, b, n);
-    for (int g = 0; g < 8; ++g) {
+    for (int g = 0; g < gpw; ++g) {
       int32_t bn = 0, nn = 0, myln = 0;
-      if (g < 7) myln = ids(g + 1, bn, nn);
+      if (g + 1 < gpw) myln = ids(g + 1, bn, nn);
       const int64_t c = c0 + 4 * g + (lane >> 3);
       const int nmax = warp_max(n);
       float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
@@ -416,18 +425,28 @@ static int grid_for(int64_t work, int per_block) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(148 * 16, (work + per_block - 1) / per_block));
 }
 
+// Groups of 4 clauses per warp of the clause-major gather, and its grid: 8
+// groups when the graph gives at least 16 warps per SM that way, else fewer
+// (down to one group per warp).
+static int mp_cgather_gpw(int64_t C) {
+  const int64_t target = 148 * 16;
+  int gpw = 8;
+  while (gpw > 1 && (C + 4 * gpw - 1) / (4 * gpw) < target) gpw >>= 1;
+  return gpw;
+}
+static int mp_cgather_grid(int64_t C, int gpw) { return grid_for((C + 4 * gpw - 1) / (4 * gpw) * 32, 256); }
+
 static int mp_forward(const tsat_problem *p, const float *params, MpWs &w, float *logits, cudaStream_t st) {
   const ProbDev &pd = p->dev;
   const int64_t L = 2 * (int64_t)p->V, C = p->C;
-  TSAT_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-  k_mp_to_bf16<<<64, 256, 0, st>>>(params, w.wb, kNParams);
-  k_mp_feat<<<grid_for(p->V, 256), 256, 0, st>>>(pd, w.linv, w.feat);
-  k_mp_cinv<<<grid_for(C, 256), 256, 0, st>>>(pd, w.cinv);
+  k_mp_prep<<<grid_for(kNParams + p->V + C, 256), 256, 0, st>>>(params, w.wb, kNParams, pd, w.linv, w.feat, w.cinv,
+                                                                  w.err);
   TSAT_LAUNCH_CHECK("mpnn features");
   cudaError_t e = mp_dense_tc(w.feat, kFeat, L, w.wb + kOffW0, w.wb + kOffB0, w.h[0], w.err, st);
   if (e != cudaSuccess) return cuda_fail(e, "mpnn input layer");
   for (int t = 0; t < kLayers; ++t) {
-    k_mp_clause_gather<0><<<grid_for(C, 256), 256, 0, st>>>(pd, w.h[t], w.cinv, nullptr, w.m[t]);
+    const int gpw = mp_cgather_gpw(C);
+    k_mp_clause_gather<0><<<mp_cgather_grid(C, gpw), 256, 0, st>>>(pd, w.h[t], w.cinv, nullptr, w.m[t], gpw);
     if ((e = mp_dense_tc(w.m[t], kH, C, w.wb + off_wc(t), w.wb + off_bc(t), w.e[t], w.err, st)) != cudaSuccess)
       return cuda_fail(e, "mpnn clause layer");
     k_mp_var_gather<0><<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.e[t], w.linv, nullptr, w.a[t]);
@@ -475,7 +494,8 @@ static int mp_backward(const tsat_problem *p, MpWs &w, const float *dlog, float 
     cudaError_t e = mp_literal_dx_tc(w.dh, L, w.wb + off_wl(t), w.linv, w.dh2, w.da, w.err, st);
     if (e != cudaSuccess) return cuda_fail(e, "mpnn literal-layer input gradient");
     // a = mean over owning clauses of e  ->  de, masked by the clause layer's ReLU (e = relu(Wc m + bc))
-    k_mp_clause_gather<1><<<grid_for(C, 256), 256, 0, st>>>(pd, w.da, nullptr, w.e[t], w.de);
+    const int gpw = mp_cgather_gpw(C);
+    k_mp_clause_gather<1><<<mp_cgather_grid(C, gpw), 256, 0, st>>>(pd, w.da, nullptr, w.e[t], w.de, gpw);
     if ((rc = wgrad(1, DIn{w.m[t], kH, 0}, none, none, w.de, C, w.part, grad + off_wc(t), grad + off_bc(t), w.err,
                     st)))
       return rc;
