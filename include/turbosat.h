@@ -216,7 +216,8 @@ int tsat_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t st
  * tsat_set_persist_blocks): the blocks split its clauses in the forward and
  * its rows in the update, each keeps a copy of the bits, and the histograms
  * are summed over distributed shared memory between two cluster barriers per
- * step; integers and every rounding follow one block per instance.
+ * step; where one block and the cluster keep z, m, v in the same place, the
+ * results are those of one block per instance, bit for bit.
  * Requirements: the STE layer, hp->mix_restart = 0, clauses of at most 7
  * literals, clauses x longest clause x samples <= 2^26 per block of the
  * instance, and 4 (18.5 N + 2 n_vars N / 32) bytes of shared memory <= 200
