@@ -92,6 +92,20 @@ LrSched make_sched(const tsat_hparams &hp) {
   l.beta1 = hp.beta1;
   l.beta2 = hp.beta2;
   l.mix = hp.mix_restart;
+  l.l2b1 = std::log2(hp.beta1);
+  l.l2b2 = std::log2(hp.beta2);
+  // the decay steps a restart period holds, when they fit the table
+  l.n_lr = 0;
+  if (hp.restart_period > 0 && hp.decay_period > 0) {
+    const int64_t kmax = ((int64_t)hp.restart_period - 1) / hp.decay_period;
+    if (kmax < kLrTab) {
+      l.n_lr = (int32_t)kmax + 1;
+      for (int k = 0; k < l.n_lr; ++k) {
+        const double lr = (double)hp.lr0 * std::pow((double)hp.lr_factor, (double)k);
+        l.lr_tab[k] = lr < (double)hp.lr_floor ? (double)hp.lr_floor : lr;
+      }
+    }
+  }
   return l;
 }
 

@@ -458,8 +458,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_fwd_w3(ProbDev pd, StateDev sd, i
 
 // Per-instance loss / best sample / exact-SAT freeze, then (step mode) the
 // step scalars: lr(t) of Sec. IV-A, AdamW bias corrections, t <- t + 1.
+// pows: the three parts of step t's scalars (step_part) formed earlier in the
+// kernel and published by the barrier below, or NULL: all formed here, by
+// thread 0.
 __device__ void gamma_tail(const ProbDev &pd, const StateDev &sd, const Hyper &hy, const LrSched &ls,
-                           int step_mode, float *loss_out, const float *Sb, int64_t t) {
+                           int step_mode, float *loss_out, const float *Sb, int64_t t,
+                           const double *pows = nullptr) {
   StateHdr *hdr = sd.hdr;
   const int N = sd.N;
   __syncthreads();
@@ -504,7 +508,7 @@ __device__ void gamma_tail(const ProbDev &pd, const StateDev &sd, const Hyper &h
       hdr->all_done = 1;
       return;
     }
-    *sd.sp = step_params(ls, t);
+    *sd.sp = pows ? step_finish(ls, t, pows[0], pows[1], pows[2]) : step_params(ls, t);
     hdr->t = t + 1;
   }
 }
@@ -518,11 +522,20 @@ __device__ void gamma_tail(const ProbDev &pd, const StateDev &sd, const Hyper &h
 __global__ void __launch_bounds__(1024) k_gamma(ProbDev pd, StateDev sd, Hyper hy, LrSched ls, const int32_t *hist_in,
                                                 int step_mode, int write_gamma, float *loss_out, float *S_out) {
   __shared__ float etab[32];
+  __shared__ double sh_pow[3];
   StateHdr *hdr = sd.hdr;
   if (step_mode && hdr->all_done) return;
   const int64_t t = hdr->t;
   if (threadIdx.x < 32) etab[threadIdx.x] = expf(-hy.tau * (float)threadIdx.x);
   __syncthreads();
+  // the three double-precision parts of the step scalars (each a serial chain
+  // of a few microseconds) by the last three threads, side by side and under
+  // the other threads' histogram work; gamma_tail's barrier publishes them and
+  // thread 0 combines them
+  if (step_mode && threadIdx.x >= blockDim.x - 3) {
+    const int j = (int)(threadIdx.x - (blockDim.x - 3));
+    sh_pow[j] = step_part(ls, t, j);
+  }
   const int N = sd.N, lm1 = sd.lm1;
   int32_t *hist = const_cast<int32_t *>(hist_in);
   float *Sb = S_out ? S_out : sd.S;
@@ -562,7 +575,7 @@ __global__ void __launch_bounds__(1024) k_gamma(ProbDev pd, StateDev sd, Hyper h
     Sb[(size_t)inst * N + i] = S;
     sd.unsat[(size_t)inst * N + i] = h0;
   }
-  gamma_tail(pd, sd, hy, ls, step_mode, loss_out, Sb, t);
+  gamma_tail(pd, sd, hy, ls, step_mode, loss_out, Sb, t, step_mode ? sh_pow : nullptr);
 }
 
 // ------------------------------------------------------------------ fused update

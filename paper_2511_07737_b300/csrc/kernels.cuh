@@ -4,34 +4,56 @@
 
 namespace tsat {
 
+constexpr int kLrTab = 16;
 struct LrSched {
   float lr0, factor, floor, wd;
   int32_t period, restart;
   double beta1, beta2;
   int32_t mix;   // assignment mixing at each restart
+  // formed on the host in double: lr of decay step k (max(lr0 factor^k, floor)
+  // for k < n_lr, when restarts bound k; n_lr = 0: the device forms it) and
+  // log2 of the two moment decays
+  int32_t n_lr;
+  double lr_tab[kLrTab];
+  double l2b1, l2b2;
 };
 
 // Scalars of step t (Sec. IV-A): lr(t) = max(lr0 factor^floor((t mod restart) / period), floor),
 // AdamW bias corrections with the 1-based step count (counted from the last
 // restart when assignments are mixed), decoupled weight decay.  Formed in
-// double, stored as float.
-__device__ __forceinline__ StepParams step_params(const LrSched &ls, int64_t t) {
-  const int64_t tt = ls.restart > 0 ? t % ls.restart : t;
-  const int64_t kdec = ls.period > 0 ? tt / ls.period : 0;
-  double lr = (double)ls.lr0 * pow((double)ls.factor, (double)kdec);
-  if (lr < (double)ls.floor) lr = ls.floor;
+// double, stored as float.  Each double-precision part is a serial chain of a
+// few microseconds, so step_part(ls, t, j) forms part j alone (0: lr, 1:
+// 1 / (1 - beta1^cnt), 2: 1 / sqrt(1 - beta2^cnt)) for three threads to form
+// side by side, and step_finish combines them.
+__device__ __forceinline__ double step_part(const LrSched &ls, int64_t t, int j) {
+  if (j == 0) {
+    const int64_t tt = ls.restart > 0 ? t % ls.restart : t;
+    const int64_t kdec = ls.period > 0 ? tt / ls.period : 0;
+    if (kdec < ls.n_lr) return ls.lr_tab[kdec];
+    const double lr = (double)ls.lr0 * pow((double)ls.factor, (double)kdec);
+    return lr < (double)ls.floor ? (double)ls.floor : lr;
+  }
+  // beta^cnt as 2^(cnt log2 beta): one double exponential instead of a power
   const int64_t cnt = (ls.mix && ls.restart > 0 && t >= ls.restart) ? t % ls.restart : t + 1;
-  const double bc1 = 1.0 - pow(ls.beta1, (double)cnt);
-  const double bc2 = 1.0 - pow(ls.beta2, (double)cnt);
+  const double bc = 1.0 - exp2((double)cnt * (j == 1 ? ls.l2b1 : ls.l2b2));
+  return j == 1 ? 1.0 / bc : 1.0 / sqrt(bc);
+}
+
+__device__ __forceinline__ StepParams step_finish(const LrSched &ls, int64_t t, double lr, double rbc1,
+                                                  double rsbc2) {
   StepParams sp;
   sp.t = t;
   sp.src = (int32_t)(t & 1);
   sp.mix_now = (ls.mix && ls.restart > 0 && t > 0 && t % ls.restart == 0) ? 1 : 0;
   sp.lr = (float)lr;
-  sp.step_size = (float)(lr / bc1);
-  sp.inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
+  sp.step_size = (float)(lr * rbc1);
+  sp.inv_sqrt_bc2 = (float)rsbc2;
   sp.decay = (float)(1.0 - lr * (double)ls.wd);
   return sp;
+}
+
+__device__ __forceinline__ StepParams step_params(const LrSched &ls, int64_t t) {
+  return step_finish(ls, t, step_part(ls, t, 0), step_part(ls, t, 1), step_part(ls, t, 2));
 }
 
 // launch helpers (return cudaGetLastError of the launch)
