@@ -246,6 +246,23 @@ def reference_arm(args, w, rank, world):
 
 
 # ---------------------------------------------------------------- time to SAT (metric 2) for the default line
+TTS_REPEATS = 3   # each timed solve is run this many times from the same init; the fastest wall time is kept
+
+
+def best_of(torch, run, repeats=TTS_REPEATS):
+    """(fastest wall seconds, last result) of `repeats` runs of run() -> result;
+    every run starts from tsat_init with the same seed, so all take the same
+    steps and only host and launch jitter differ."""
+    best, res = None, None
+    for _ in range(repeats):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = run()
+        el = time.perf_counter() - t0
+        best = el if best is None else min(best, el)
+    return best, res
+
+
 TTS_READINGS = {
     "paper: signed-mean Eq. 5, tau 1, lr0 0.1": dict(norm=0, tau=1.0, lr0=0.1),
     "paper schedule, sign-keeping Eq. 5 (mean |z|), tau 2, lr0 0.1": dict(norm=1, tau=2.0, lr0=0.1),
@@ -268,7 +285,8 @@ def time_to_sat_summary(ts, torch, n_inst=32, cap=500):
     insts = [cnfgen.planted_ksat(100, 426, 3, j) for j in range(n_inst)]
     out = {"workload": f"{n_inst} x planted 3-SAT n=100 m=426 (ratio 4.26), N=64, deterministic Eq. 2, "
                        f"cap {cap} steps, persistent solver",
-           "unit": "ms", "readings": {}}
+           "unit": "ms", "timing": f"wall time per solve, fastest of {TTS_REPEATS} runs from the same init",
+           "readings": {}}
     for name, kw in TTS_READINGS.items():
         walls, steps = [], []
         for j, inst in enumerate(insts):
@@ -277,12 +295,12 @@ def time_to_sat_summary(ts, torch, n_inst=32, cap=500):
             hp = ts.hparams(seed=j + 1, **kw)
             ts.tsat_init(st.h, hp)
             ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)     # first launch: kernel attributes
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ts.tsat_init(st.h, hp)
-            ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
-            x = ts.tsat_status(st.h, 1)["inst"][0]
-            el = time.perf_counter() - t0
+
+            def run():
+                ts.tsat_init(st.h, hp)
+                ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
+                return ts.tsat_status(st.h, 1)["inst"][0]
+            el, x = best_of(torch, run)
             if x["found"]:
                 walls.append(el)
                 steps.append(x["found_step"])
@@ -291,12 +309,13 @@ def time_to_sat_summary(ts, torch, n_inst=32, cap=500):
         hp = ts.hparams(seed=1, **kw)
         ts.tsat_init(st.h, hp)
         ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ts.tsat_init(st.h, hp)
-        ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
-        sb = ts.tsat_status(st.h, n_inst)
-        batch_ms = 1e3 * (time.perf_counter() - t0)
+
+        def run_batch():
+            ts.tsat_init(st.h, hp)
+            ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
+            return ts.tsat_status(st.h, n_inst)
+        el, sb = best_of(torch, run_batch)
+        batch_ms = 1e3 * el
         out["readings"][name] = {
             "plain": {"solved": len(walls), "of": n_inst,
                       "median_ms_to_sat": 1e3 * float(np.median(walls)) if walls else None,
@@ -341,16 +360,19 @@ def time_to_99pct(ts, torch, insts, kw, cap):
         hp = ts.hparams(seed=j + 1, **kw)
         ts.tsat_init(st.h, hp)
         ts.tsat_step_prepare(st.h, hp, 1, stop_on_sat=True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ts.tsat_init(st.h, hp)
-        for t in range(cap):
-            ts.tsat_step(st.h, hp, 1, stop_on_sat=True)
-            x = ts.tsat_status(st.h, 1)["inst"][0]
-            if (inst.n_clauses - x["min_unsat"]) / inst.n_clauses > 0.99:
-                walls.append(time.perf_counter() - t0)
-                steps.append(t)
-                break
+
+        def run():
+            ts.tsat_init(st.h, hp)
+            for t in range(cap):
+                ts.tsat_step(st.h, hp, 1, stop_on_sat=True)
+                x = ts.tsat_status(st.h, 1)["inst"][0]
+                if (inst.n_clauses - x["min_unsat"]) / inst.n_clauses > 0.99:
+                    return t
+            return None
+        el, t = best_of(torch, run)
+        if t is not None:
+            walls.append(el)
+            steps.append(t)
     return {"reached": len(walls), "of": len(insts), "path": "graph, one step per replay, status read after each",
             "median_ms": 1e3 * float(np.median(walls)) if walls else None,
             "median_steps": float(np.median(steps)) if steps else None}
@@ -392,21 +414,22 @@ def mid_size_time_to_sat(ts, torch, kw, pr, n_inst=16, n=1000, m=4000, cap=2000)
                 ts.tsat_step(st.h, hp, 10, stop_on_sat=True)       # first replay: the graph is built
             else:
                 ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            if lg is not None:
-                ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)
-            ts.tsat_init(st.h, hp, lg, 1.0)
-            if mode == "graph_path":
-                for _ in range(cap // 10):
-                    ts.tsat_step(st.h, hp, 10, stop_on_sat=True)
+
+            def run():
+                if lg is not None:
+                    ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)
+                ts.tsat_init(st.h, hp, lg, 1.0)
+                if mode == "graph_path":
+                    for _ in range(cap // 10):
+                        ts.tsat_step(st.h, hp, 10, stop_on_sat=True)
+                        x = ts.tsat_status(st.h, 1)["inst"][0]
+                        if x["found"]:
+                            break
+                else:
+                    ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
                     x = ts.tsat_status(st.h, 1)["inst"][0]
-                    if x["found"]:
-                        break
-            else:
-                ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
-                x = ts.tsat_status(st.h, 1)["inst"][0]
-            el = time.perf_counter() - t0
+                return x
+            el, x = best_of(torch, run)
             if lg is not None:
                 ts.tsat_mpnn_status(prob.h, ws)
             if x["found"]:
@@ -434,13 +457,14 @@ def mid_size_time_to_sat(ts, torch, kw, pr, n_inst=16, n=1000, m=4000, cap=2000)
     hp = ts.hparams(seed=1, **kw)
     ts.tsat_init(st.h, hp)
     ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ts.tsat_init(st.h, hp)
-    ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
-    sb = ts.tsat_status(st.h, n_inst)
+
+    def run_batch():
+        ts.tsat_init(st.h, hp)
+        ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
+        return ts.tsat_status(st.h, n_inst)
+    el, sb = best_of(torch, run_batch)
     out["batched"] = {"solved": int(sum(x["found"] for x in sb["inst"])), "of": n_inst,
-                      "ms_whole_batch": 1e3 * (time.perf_counter() - t0), "steps_run": sb["step"],
+                      "ms_whole_batch": 1e3 * el, "steps_run": sb["step"],
                       "blocks_per_instance": ts.tsat_persist_blocks(st.h)}
     return out
 
@@ -481,17 +505,18 @@ def learned_time_to_sat(ts, torch, insts, kw, cap, scale=1.0, pr=None):
         ts.tsat_mpnn_status(prob.h, ws)
         ts.tsat_init(st.h, hp, lg, scale)
         ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)     # first launch: kernel attributes
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)
-        torch.cuda.synchronize()
-        props.append(time.perf_counter() - t0)
-        t0 = time.perf_counter()
-        ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)
-        ts.tsat_init(st.h, hp, lg, scale)
-        ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
-        x = ts.tsat_status(st.h, 1)["inst"][0]
-        el = time.perf_counter() - t0
+
+        def propose():
+            ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)
+            torch.cuda.synchronize()
+        props.append(best_of(torch, propose)[0])
+
+        def run():
+            ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)
+            ts.tsat_init(st.h, hp, lg, scale)
+            ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
+            return ts.tsat_status(st.h, 1)["inst"][0]
+        el, x = best_of(torch, run)
         ts.tsat_mpnn_status(prob.h, ws)
         if x["found"]:
             walls.append(el)
@@ -507,13 +532,14 @@ def learned_time_to_sat(ts, torch, insts, kw, cap, scale=1.0, pr=None):
         ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)
     ts.tsat_init(st.h, hp, lg, scale)
     ts.tsat_step_persistent(st.h, hp, 1, stop_on_sat=True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)
-    ts.tsat_init(st.h, hp, lg, scale)
-    ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
-    sb = ts.tsat_status(st.h, len(insts))
-    batch_ms = 1e3 * (time.perf_counter() - t0)
+
+    def run_batch():
+        ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg)
+        ts.tsat_init(st.h, hp, lg, scale)
+        ts.tsat_step_persistent(st.h, hp, cap, stop_on_sat=True)
+        return ts.tsat_status(st.h, len(insts))
+    el, sb = best_of(torch, run_batch)
+    batch_ms = 1e3 * el
     ts.tsat_mpnn_status(prob.h, ws)
     return {"solved": len(walls), "of": len(insts),
             "median_ms_to_sat": 1e3 * float(np.median(walls)) if walls else None,
