@@ -412,9 +412,9 @@ static int get_graph(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int
   key.n_steps = n_steps;
   key.stop = stop_on_sat ? 1 : 0;
   key.hp.assign((const uint8_t *)hp, (const uint8_t *)hp + sizeof(tsat_hparams));
-  key.hp.push_back((uint8_t)s->upd_blocks_per_sm);
-  key.hp.push_back((uint8_t)s->upd_rows_per_item);
-  key.hp.push_back((uint8_t)(s->prob->item_clauses / kItemMin));
+  // the launch shapes baked into the graph (every byte: no two shapes share a key)
+  for (int32_t x : {s->upd_blocks_per_sm, s->upd_rows_per_item, s->prob->item_clauses})
+    for (int b = 0; b < 4; ++b) key.hp.push_back((uint8_t)((uint32_t)x >> (8 * b)));
   auto it = s->graphs.find(key);
   if (it != s->graphs.end()) {
     *out = it->second;

@@ -36,8 +36,9 @@ cudaError_t ensure_dyn_smem(const void *kern, int bytes);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Forward work items cover at most this many clauses (autotuned multiple of it).
-constexpr int kItemMin = 512;
+// Forward work items hold a multiple of this many clauses (the smallest item;
+// the default and the autotuned sizes are larger on large problems).
+constexpr int kItemMin = 64;
 
 struct Layout {  // byte offsets inside the problem workspace
   size_t cptr, clit, xptr, xrec, vptr, vocc, var_inst, items, inst, err, crec;

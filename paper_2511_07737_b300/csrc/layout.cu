@@ -605,7 +605,13 @@ int tsat_load_batch_ex(int32_t n_inst, const tsat_cnf_desc *descs, uint32_t flag
   D.inst = dinst;
   D.crec = L.crec ? (const int4 *)(w + L.crec) : nullptr;
   D.full3 = (L.crec && p->nnz == 3LL * p->C) ? 1 : 0;
-  int rc3 = p->set_items(1024, stream);   // forward work items of 1024 clauses (measured 512..4096: near the best)
+  // forward work items of 1024 clauses (measured 512..4096: near the best on
+  // large problems); on small problems fewer clauses per item, down to
+  // kItemMin, so that the forward has a couple of items per SM (one planted
+  // 3-SAT instance of n = 100 would otherwise be one block)
+  int32_t ic = 1024;
+  while (ic > kItemMin && ((int64_t)p->C + ic - 1) / ic < 2 * 148) ic >>= 1;
+  int rc3 = p->set_items(ic, stream);
   if (rc3) return fail(rc3);
   *out = p;
   return TSAT_OK;
