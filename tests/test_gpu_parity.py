@@ -416,3 +416,38 @@ def test_autotune_times_the_step_update_and_leaves_the_state():
     b = snapshot(st)
     for k in ("z", "m", "v", "nu", "bits"):
         np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_step_graph_is_rebuilt_for_each_launch_shape():
+    """The cached step graph has the forward's work-item count and the update
+    grid baked in, so a new launch shape must give a new graph: forward items
+    of 64 clauses, then of 16,448 (a shape whose item count once shared the
+    64-clause shape's cache key byte), each step from the same saved state,
+    equal a fresh state run with that shape, bit for bit, and the exact
+    unsatisfied counts equal the oracle's."""
+    inst = cnfgen.planted_ksat(100, 426, 3, 4)
+    hp = ts.hparams(seed=9, norm=1, tau=2.0, lr0=0.5)
+    prob, st, cnfs = make([inst], 64)
+    ts.tsat_init(st.h, hp)
+    before = st.buf.clone()
+    tun = ts.tsat_get_tuning(st.h)
+    outs = {}
+    for items in (64, 16448):
+        ts.tsat_set_tuning(st.h, [items, tun[1], tun[2], tun[3]])
+        st.buf.copy_(before)
+        ts.tsat_step(st.h, hp, 3, stop_on_sat=False)
+        outs[items] = snapshot(st)
+    for items in (64, 16448):
+        prob2, st2, _ = make([inst], 64)
+        ts.tsat_set_tuning(st2.h, [items, tun[1], tun[2], tun[3]])
+        ts.tsat_init(st2.h, hp)
+        ts.tsat_step(st2.h, hp, 3, stop_on_sat=False)
+        fresh = snapshot(st2)
+        for k in ("z", "m", "v", "nu", "bits"):
+            np.testing.assert_array_equal(outs[items][k], fresh[k], err_msg=f"{k} items={items}")
+        u, _ = oracle.check(cnfs[0], fresh["X"])
+        unsat = torch.zeros(64, dtype=torch.int32, device="cuda")
+        sm = torch.zeros(2, dtype=torch.int32, device="cuda")
+        ts.tsat_evaluate(st2.h, hp, unsat, sm)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(unsat.cpu().numpy(), u)
