@@ -41,6 +41,39 @@ def test_mpnn_forward_and_gradient_match_oracle():
     assert rel_err(grad.cpu().numpy(), g_ref) < 1e-4
 
 
+@pytest.mark.parametrize("name,gen", [
+    # every forward layer at most 2,048 rows: the CUDA-core form of the layers
+    ("n100", lambda: [cnfgen.planted_ksat(100, 426, 3, 8)]),
+    # literal layer on CUDA cores (1,600 rows), clause layer on the tensor cores (3,408 rows)
+    ("n800", lambda: [cnfgen.planted_ksat(800, 3408, 3, 9)]),
+])
+def test_mpnn_small_layers_match_oracle(name, gen):
+    """Forward logits, loss and gradient on graphs whose layers are small
+    enough for the CUDA-core form (a forward layer of at most 2,048 rows),
+    alone and mixed with tensor-core layers."""
+    insts = gen()
+    prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in insts])
+    pr = Proposer(seed=13)
+    y = np.concatenate([i.planted for i in insts]).astype(np.uint8)
+    ws = pr._ws(prob)
+    logits = torch.empty(prob.info["n_vars"], device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros_like(pr.params)
+    ts.tsat_mpnn_loss_grad(prob.h, pr.params, ws, torch.tensor(y, device="cuda"), logits, loss, grad)
+    ts.tsat_mpnn_status(prob.h, ws)
+    params = mpnn.bf16_round(pr.params.cpu().numpy())
+    g = mpnn.Graph([oracle.CNF(i.n_vars, i.clause_ptr, i.lits) for i in insts])
+    l_ref, g_ref, lg_ref = mpnn.loss_and_grad(g, params, y)
+    assert rel_err(logits.cpu().numpy(), lg_ref) < 1e-5
+    assert abs(loss.item() - l_ref) < 1e-5 * abs(l_ref)
+    assert rel_err(grad.cpu().numpy(), g_ref) < 1e-4
+    # the forward alone (the proposal path) gives the same logits
+    lg2 = torch.empty_like(logits)
+    ts.tsat_mpnn_forward(prob.h, pr.params, ws, lg2)
+    ts.tsat_mpnn_status(prob.h, ws)
+    assert rel_err(lg2.cpu().numpy(), lg_ref) < 1e-5
+
+
 def test_mpnn_matches_oracle_when_blocks_loop_over_tiles():
     # 66,000 literal rows and 156,000 clause rows: more 128-row tiles than the
     # dense layers launch blocks (148 x 3), so every block loops over tiles,
