@@ -790,6 +790,106 @@ __global__ void __launch_bounds__(256) k_mp_fma(TcArgs g) {
   }
 }
 
+// The dot product of the CUDA-core layers: output o of staged row q, over K
+// inputs, plus the bias, through the ReLU.
+template <int KT>
+__device__ __forceinline__ float fma_row(const float (&xs)[4][KT], int q, int o, const __nv_bfloat16 *W, int K,
+                                         const __nv_bfloat16 *bias) {
+  const __nv_bfloat16 *wr = W + (size_t)o * K;
+  float acc = 0.f;
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4 *>(wr + k0));
+    const __nv_bfloat162 *w2 = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 w = __bfloat1622float2(w2[j]);
+      acc = fmaf(w.x, xs[q][k0 + 2 * j], acc);
+      acc = fmaf(w.y, xs[q][k0 + 2 * j + 1], acc);
+    }
+  }
+  return fmaxf(acc + __bfloat162float(bias[o]), 0.f);
+}
+
+// A small graph's clause layer with its gather in one kernel: the clause
+// mean x[c] = cinv[c] sum over the literals l of c of h[l] (summed in the
+// clause's literal order, as the separate gather does) is staged, stored to m
+// for the backward, and Y[c] = relu(W x[c] + b).
+__global__ void __launch_bounds__(256) k_mp_fma_clause(ProbDev pd, const float *h, const float *cinv, float *m,
+                                                       const __nv_bfloat16 *W, const __nv_bfloat16 *bias, float *Y) {
+  __shared__ __align__(16) float xs[4][64];
+  const int tid = threadIdx.x, q = tid >> 6, o = tid & 63;
+  const int64_t C = pd.C;
+  for (int64_t r0 = 4 * (int64_t)blockIdx.x; r0 < C; r0 += 4 * (int64_t)gridDim.x) {
+    __syncthreads();
+    {
+      const int64_t c = r0 + q;   // element (q, o): clause r0 + q, input o
+      float v = 0.f;
+      if (c < C) {
+        for (int32_t j = __ldg(pd.cptr + c); j < __ldg(pd.cptr + c + 1); ++j)
+          v += __ldg(h + (int64_t)__ldg(pd.clit + j) * 64 + o);
+        v *= __ldg(cinv + c);
+        m[c * 64 + o] = v;
+      }
+      xs[q][o] = v;
+    }
+    __syncthreads();
+    const int64_t c = r0 + q;
+    if (c < C) Y[c * 64 + o] = fma_row<64>(xs, q, o, W, 64, bias);
+  }
+}
+
+// A small graph's literal layer with its gather: a[r] = linv[r] sum over the
+// clauses c holding literal r of e[c] (in occurrence order, as the separate
+// gather does) is staged with h[r] and h[r^1], stored to a for the backward,
+// and Y[r] = relu(W0 h[r] + W1 a[r] + W2 h[r^1] + b).
+__global__ void __launch_bounds__(256) k_mp_fma_literal(ProbDev pd, const float *h, const float *e,
+                                                        const float *linv, float *a, const __nv_bfloat16 *W,
+                                                        const __nv_bfloat16 *bias, float *Y) {
+  __shared__ __align__(16) float xs[4][192];
+  const int tid = threadIdx.x, q = tid >> 6, o = tid & 63;
+  const int64_t L = 2 * (int64_t)pd.V;
+  for (int64_t r0 = 4 * (int64_t)blockIdx.x; r0 < L; r0 += 4 * (int64_t)gridDim.x) {
+    __syncthreads();
+    {
+      const int64_t r = r0 + q;   // element (q, o) of each of the three inputs
+      float hv = 0.f, av = 0.f, hp = 0.f;
+      if (r < L) {
+        hv = __ldg(h + r * 64 + o);
+        hp = __ldg(h + (r ^ 1) * 64 + o);
+        const int64_t v = r >> 1;
+        const int32_t sgn = (int32_t)(r & 1);
+        for (int32_t j = __ldg(pd.vptr + v); j < __ldg(pd.vptr + v + 1); ++j) {
+          const int32_t oc = __ldg(pd.vocc + j);
+          if ((oc & 1) == sgn) av += __ldg(e + (int64_t)(oc >> 1) * 64 + o);
+        }
+        av *= __ldg(linv + r);
+        a[r * 64 + o] = av;
+      }
+      xs[q][o] = hv;
+      xs[q][64 + o] = av;
+      xs[q][128 + o] = hp;
+    }
+    __syncthreads();
+    const int64_t r = r0 + q;
+    if (r < L) Y[r * 64 + o] = fma_row<192>(xs, q, o, W, 192, bias);
+  }
+}
+
+cudaError_t mp_clause_small(const ProbDev &pd, const float *h, const float *cinv, float *m, const __nv_bfloat16 *W,
+                            const __nv_bfloat16 *bias, float *Y, cudaStream_t st) {
+  k_mp_fma_clause<<<(int)std::max<int64_t>(1, ((int64_t)pd.C + 3) / 4), 256, 0, st>>>(pd, h, cinv, m, W, bias, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t mp_literal_small(const ProbDev &pd, const float *h, const float *e, const float *linv, float *a,
+                             const __nv_bfloat16 *W, const __nv_bfloat16 *bias, float *Y, cudaStream_t st) {
+  k_mp_fma_literal<<<(int)std::max<int64_t>(1, (2 * (int64_t)pd.V + 3) / 4), 256, 0, st>>>(pd, h, e, linv, a, W,
+                                                                                           bias, Y);
+  return cudaGetLastError();
+}
+
+int mp_small_rows() { return kFmaRows; }
+
 template <int FORM>
 static cudaError_t fma_go(const TcArgs &g, cudaStream_t st) {
   const int grid = (int)std::max<int64_t>(1, (g.M + 3) / 4);
