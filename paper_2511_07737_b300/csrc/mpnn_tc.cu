@@ -825,8 +825,19 @@ __global__ void __launch_bounds__(256) k_mp_fma_clause(ProbDev pd, const float *
       const int64_t c = r0 + q;   // element (q, o): clause r0 + q, input o
       float v = 0.f;
       if (c < C) {
-        for (int32_t j = __ldg(pd.cptr + c); j < __ldg(pd.cptr + c + 1); ++j)
-          v += __ldg(h + (int64_t)__ldg(pd.clit + j) * 64 + o);
+        // literal ids, then rows, 8 at a time (loads in flight together)
+        const int32_t jb = __ldg(pd.cptr + c), je = __ldg(pd.cptr + c + 1);
+        for (int32_t j0 = jb; j0 < je; j0 += 8) {
+          int32_t l[8];
+          float x[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) l[u] = j0 + u < je ? __ldg(pd.clit + j0 + u) : -1;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) x[u] = l[u] >= 0 ? __ldg(h + (int64_t)l[u] * 64 + o) : 0.f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (l[u] >= 0) v += x[u];
+        }
         v *= __ldg(cinv + c);
         m[c * 64 + o] = v;
       }
@@ -858,9 +869,19 @@ __global__ void __launch_bounds__(256) k_mp_fma_literal(ProbDev pd, const float 
         hp = __ldg(h + (r ^ 1) * 64 + o);
         const int64_t v = r >> 1;
         const int32_t sgn = (int32_t)(r & 1);
-        for (int32_t j = __ldg(pd.vptr + v); j < __ldg(pd.vptr + v + 1); ++j) {
-          const int32_t oc = __ldg(pd.vocc + j);
-          if ((oc & 1) == sgn) av += __ldg(e + (int64_t)(oc >> 1) * 64 + o);
+        // occurrence records, then the matching clauses' rows, 8 at a time
+        const int32_t jb = __ldg(pd.vptr + v), je = __ldg(pd.vptr + v + 1);
+        for (int32_t j0 = jb; j0 < je; j0 += 8) {
+          int32_t oc[8];
+          float x[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) oc[u] = j0 + u < je ? __ldg(pd.vocc + j0 + u) : -1;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            x[u] = (oc[u] >= 0 && (oc[u] & 1) == sgn) ? __ldg(e + (int64_t)(oc[u] >> 1) * 64 + o) : 0.f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (oc[u] >= 0 && (oc[u] & 1) == sgn) av += x[u];
         }
         av *= __ldg(linv + r);
         a[r * 64 + o] = av;
