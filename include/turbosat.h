@@ -241,6 +241,17 @@ int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps,
 int tsat_set_persist_blocks(tsat_state *s, int32_t blocks_per_instance);
 int tsat_persist_blocks(const tsat_state *s, int32_t *blocks_per_instance, int32_t *resident);
 
+/* Times n_steps persistent steps (no early stop) from the state's current
+ * contents with each candidate number of blocks per instance (1, and with
+ * N <= 256 clusters of 2, 4 and 8 while the batch's clusters fit the device at
+ * most twice over), keeps the fastest (tsat_set_persist_blocks) and returns it
+ * in *h_blocks.  d_snapshot: caller-owned device scratch of
+ * tsat_autotune_bytes; every trial starts from the saved state and the state
+ * is put back at the end, so no result changes.  Synchronises with the
+ * trials; TSAT_EINVAL / TSAT_ERANGE as tsat_step_persistent. */
+int tsat_autotune_persistent(tsat_state *s, const tsat_hparams *hp, void *d_snapshot, size_t snapshot_bytes,
+                             int32_t n_steps, cudaStream_t stream, int32_t *h_blocks);
+
 /* The same n_steps steps for a batch whose instances are too large for one
  * block, in one launch of thread-block clusters (4 blocks of 768 threads, one
  * per SM, as many clusters as fit on the device).  The host deals the

@@ -521,10 +521,12 @@ int tsat_set_persist_blocks(tsat_state *s, int32_t blocks) {
   return TSAT_OK;
 }
 
-int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
-                         cudaStream_t stream) {
-  int rc = check_step_args(s, hp, n_steps);
-  if (rc) return rc;
+// Checks and launch of the persistent solver on the state's stream (the
+// caller has entered it).  *to_clustered: the instances suit the cluster
+// solver instead (nothing launched).
+static int persist_launch(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
+                          bool *to_clustered) {
+  *to_clustered = false;
   const tsat_problem *p = s->prob;
   if (s->layer != TSAT_LAYER_STE || hp->mix_restart) {
     set_error("the persistent solver runs the STE layer without assignment mixing");
@@ -541,8 +543,10 @@ int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps,
   for (const InstInfo &I : p->inst) too_big = too_big || (int64_t)I.n_clauses * I.lmax * s->N > cs * kPersistMaxWork;
   too_big = too_big || persist_smem_bytes(s->N, vmax, false, cs) > kPersistMaxSmem;
   // instances too large for one block: clusters of blocks, when the batch suits them
-  if (too_big && s->persist_cs == 0 && p->dev.rec_stride == 8 && s->N <= 128)
-    return tsat_step_clustered(s, hp, n_steps, stop_on_sat, stream);
+  if (too_big && s->persist_cs == 0 && p->dev.rec_stride == 8 && s->N <= 128) {
+    *to_clustered = true;
+    return TSAT_OK;
+  }
   for (const InstInfo &I : p->inst) {
     if ((int64_t)I.n_clauses * I.lmax * s->N > cs * kPersistMaxWork) {
       set_error("instance too large for %d block(s): %d clauses x %d literals x %d samples > %lld", cs,
@@ -556,12 +560,26 @@ int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps,
     return TSAT_ERANGE;
   }
   const bool resident = persist_smem_bytes(s->N, vmax, true, cs) <= kPersistMaxSmem;
-  if ((rc = enter(s, stream))) return rc;
   const Hyper hy = make_hyper(*hp, stop_on_sat ? 1 : 0);
   const LrSched ls = make_sched(*hp);
   cudaError_t e = launch_persist(p->dev, s->dev, hy, ls, n_steps, vmax, resident, cs, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "persistent solver");
-  return leave(s, stream);
+  return TSAT_OK;
+}
+
+int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
+                         cudaStream_t stream) {
+  int rc = check_step_args(s, hp, n_steps);
+  if (rc) return rc;
+  if ((rc = enter(s, stream))) return rc;
+  bool to_clustered = false;
+  if ((rc = persist_launch(s, hp, n_steps, stop_on_sat, &to_clustered))) {
+    leave(s, stream);
+    return rc;
+  }
+  if ((rc = leave(s, stream))) return rc;
+  if (to_clustered) return tsat_step_clustered(s, hp, n_steps, stop_on_sat, stream);
+  return TSAT_OK;
 }
 
 int tsat_step_clustered(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t stop_on_sat,
@@ -885,6 +903,65 @@ int tsat_tuning_space(const tsat_state *s, int32_t h_fwd_items[4], int32_t h_upd
   for (int j = 0; j < 5; ++j) h_upd_bps[j] = b[j];
   for (int j = 0; j < 3; ++j) h_upd_rpi[j] = kTuneRpi[j];
   return TSAT_OK;
+}
+
+int tsat_autotune_persistent(tsat_state *s, const tsat_hparams *hp, void *d_snapshot, size_t snapshot_bytes,
+                             int32_t n_steps, cudaStream_t stream, int32_t *h_blocks) {
+  if (!s || !h_blocks || !d_snapshot) { set_error("NULL argument"); return TSAT_EINVAL; }
+  int rc = check_step_args(s, hp, n_steps);
+  if (rc) return rc;
+  const size_t need = s->core_bytes + s->lit_bytes;
+  if (snapshot_bytes < need) { set_error("snapshot buffer %zu < %zu bytes", snapshot_bytes, need); return TSAT_EWS; }
+  if ((rc = enter(s, stream))) return rc;
+  cudaStream_t st = s->stream;
+  char *base = static_cast<char *>(s->base);
+  char *snap = static_cast<char *>(d_snapshot);
+  TSAT_CUDA(cudaMemcpyAsync(snap, base, s->core_bytes, cudaMemcpyDeviceToDevice, st));
+  EventPair ev;
+  TSAT_CUDA(cudaEventCreate(&ev.a));
+  TSAT_CUDA(cudaEventCreate(&ev.b));
+  const int32_t keep = s->persist_cs;
+  int32_t best_cs = 1;
+  float best = 1e30f;
+  // candidates: one block, and (N <= 256) clusters of 2, 4, 8 blocks while
+  // the batch's clusters fit the device at most twice over
+  for (int cs : {1, 2, 4, 8}) {
+    if (cs > 1 && (s->N > 256 || (int64_t)s->prob->n_inst * cs > 2LL * s->sm_count)) continue;
+    s->persist_cs = cs;
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2 && rc == TSAT_OK; ++rep) {
+      TSAT_CUDA(cudaMemcpyAsync(base, snap, s->core_bytes, cudaMemcpyDeviceToDevice, st));
+      TSAT_CUDA(cudaEventRecord(ev.a, st));
+      bool to_clustered = false;
+      rc = persist_launch(s, hp, n_steps, 0, &to_clustered);
+      if (rc == TSAT_OK && to_clustered) {
+        set_error("the instances suit the cluster solver, not the persistent one");
+        rc = TSAT_EINVAL;
+      }
+      if (rc != TSAT_OK) break;
+      TSAT_CUDA(cudaEventRecord(ev.b, st));
+      TSAT_CUDA(cudaEventSynchronize(ev.b));
+      float x = 0;
+      TSAT_CUDA(cudaEventElapsedTime(&x, ev.a, ev.b));
+      ms = std::min(ms, x);
+    }
+    if (rc == TSAT_ERANGE && cs == 1) {   // one block cannot take the instances: try the clusters
+      rc = TSAT_OK;
+      continue;
+    }
+    if (rc != TSAT_OK) break;
+    if (ms < best) { best = ms; best_cs = cs; }
+  }
+  TSAT_CUDA(cudaMemcpyAsync(base, snap, s->core_bytes, cudaMemcpyDeviceToDevice, st));
+  if (rc != TSAT_OK || best >= 1e30f) {
+    s->persist_cs = keep;
+    leave(s, stream);
+    if (rc == TSAT_OK) { set_error("no persistent launch shape runs these instances"); rc = TSAT_ERANGE; }
+    return rc;
+  }
+  s->persist_cs = best_cs;
+  *h_blocks = best_cs;
+  return leave(s, stream);
 }
 
 int tsat_autotune_bytes(const tsat_state *s, size_t *bytes) {

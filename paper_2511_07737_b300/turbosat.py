@@ -88,6 +88,7 @@ def lib():
             "tsat_step_clustered": (ctypes.c_int, [P, P, i32, i32, P]),
             "tsat_set_persist_blocks": (ctypes.c_int, [P, i32]),
             "tsat_persist_blocks": (ctypes.c_int, [P, P, P]),
+            "tsat_autotune_persistent": (ctypes.c_int, [P, P, P, sz, i32, P, P]),
             "tsat_best": (ctypes.c_int, [P, P, i32, i32, P, P, P, P, P, P, P]),
             "tsat_partial_k": (i32, [i32]),
             "tsat_status": (ctypes.c_int, [P, P, P, P, P]),
@@ -274,6 +275,19 @@ def tsat_persist_blocks(s, with_residency: bool = False):
     out, res = ctypes.c_int32(0), ctypes.c_int32(0)
     _ck(lib().tsat_persist_blocks(s, ctypes.byref(out), ctypes.byref(res)), "tsat_persist_blocks")
     return (int(out.value), bool(res.value)) if with_residency else int(out.value)
+
+
+def tsat_autotune_persistent(s, hp: tsat_hparams, n_steps: int = 50, stream=None) -> int:
+    """Times the persistent solver with each candidate number of blocks per
+    instance from the current state, keeps the fastest and returns it (the
+    state is left as it was)."""
+    nbytes = tsat_autotune_bytes(s)
+    snap = torch.empty(max(nbytes, 1), dtype=torch.uint8, device="cuda")
+    out = ctypes.c_int32(0)
+    _ck(lib().tsat_autotune_persistent(s, ctypes.byref(hp), _ptr(snap), nbytes, int(n_steps), _stream(stream),
+                                       ctypes.byref(out)), "tsat_autotune_persistent")
+    torch.cuda.synchronize()
+    return int(out.value)
 
 
 def tsat_step_clustered(s, hp: tsat_hparams, n_steps: int, stop_on_sat: bool = True, stream=None):

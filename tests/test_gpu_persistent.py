@@ -331,3 +331,35 @@ def test_persist_blocks_setting_is_checked():
     batch = [cnfgen.planted_ksat(1000, 4260, 3, j) for j in range(40)]
     prob2, st2, _ = make(batch, 64)
     assert ts.tsat_persist_blocks(st2.h) == _auto_blocks(40)   # 2 on 148 SMs: 40 x 4 blocks would not fit
+
+
+def test_autotune_persistent_keeps_the_state_and_picks_the_cluster_where_it_pays():
+    """The persistent autotuner times each candidate number of blocks per
+    instance from the saved state, puts the state back, and keeps the fastest:
+    at n = 1,000 (N = 64) an instance is resident only on a cluster of 8 blocks,
+    which takes about a tenth of one block's step time; at n = 100 (resident in
+    every shape) any shape it keeps steps bit for bit like the others."""
+    hp = ts.hparams(seed=2, norm=1, tau=2.0, lr0=0.5)
+    for n, m, expect in ((1000, 4000, 8), (100, 426, None)):
+        inst = cnfgen.planted_ksat(n, m, 3, 0)
+        prob, st, _ = make([inst], 64)
+        ts.tsat_init(st.h, hp)
+        ts.tsat_step_persistent(st.h, hp, 3, stop_on_sat=False)
+        torch.cuda.synchronize()
+        nb = ts.tsat_autotune_bytes(st.h)
+        before = st.buf.view(torch.uint8)[:nb].clone()
+        b = ts.tsat_autotune_persistent(st.h, hp, 40)
+        assert b in (1, 2, 4, 8) and ts.tsat_persist_blocks(st.h) == b
+        assert torch.equal(st.buf.view(torch.uint8)[:nb], before)
+        if expect is not None:
+            assert b == expect
+        # the tuned shape steps like any other: continuing gives the one-block result
+        st_b = ts.State(prob, 64)
+        ts.tsat_set_persist_blocks(st_b.h, b)
+        ts.tsat_init(st_b.h, hp)
+        ts.tsat_step_persistent(st_b.h, hp, 3, stop_on_sat=False)
+        ts.tsat_step_persistent(st.h, hp, 5, stop_on_sat=False)
+        ts.tsat_step_persistent(st_b.h, hp, 5, stop_on_sat=False)
+        a, c = snapshot(st), snapshot(st_b)
+        if ts.tsat_persist_blocks(st.h, True)[1] == ts.tsat_persist_blocks(st_b.h, True)[1]:
+            np.testing.assert_array_equal(a["bits"], c["bits"])
