@@ -230,7 +230,9 @@ int tsat_step_persistent(tsat_state *s, const tsat_hparams *hp, int32_t n_steps,
 /* Blocks per instance of tsat_step_persistent: 0 = automatic (the default:
  * 1 when one block keeps the largest instance's z, m, v in shared memory or
  * N > 256, else the largest of 2, 4, 8 with which every instance's cluster
- * fits on the device at once), or 1, 2, 4, 8 (2..8 need N <= 256).  The
+ * fits on the device at once, or, when that does not keep the instances in
+ * shared memory, the smallest larger one that does within two waves of
+ * clusters), or 1, 2, 4, 8 (2..8 need N <= 256).  The
  * blocks keep their rows' z, m, v in shared memory when those fit (else in
  * global memory, with 8 instead of 16 samples per thread); two settings with
  * the same placement give the same results bit for bit, otherwise the FP32

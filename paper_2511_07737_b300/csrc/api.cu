@@ -476,7 +476,7 @@ int tsat_step(tsat_state *s, const tsat_hparams *hp, int32_t n_steps, int32_t st
 // Blocks per instance of the persistent solver: the state's setting, or, when
 // it is 0 (N <= 256 only): one block when that block keeps its instance's z,
 // m, v in shared memory, else the largest power of two up to 8 such that the
-// batch's clusters all fit on the device at once.  Measured per step at
+// batch's clusters all fit on the device at once (or a larger one, below).  Measured per step at
 // N = 64 (planted 3-SAT, 1 / 2 / 4 / 8 blocks): n = 100 (resident in one
 // block) 8.4 / 9.2 / 8.5 / 9.4 us, the step being a chain of dependent phases
 // that more blocks do not shorten; n = 1,000 152.8 / 89.0 / 49.7 / 12.9 us
@@ -486,9 +486,20 @@ static int persist_blocks(const tsat_state *s, int32_t vmax) {
   const tsat_problem *p = s->prob;
   if (s->N > 256) return 1;
   if (s->persist_cs > 0) return s->persist_cs;
-  if (persist_smem_bytes(s->N, vmax, true, 1) <= kPersistMaxSmem) return 1;
+  auto resident = [&](int c) { return persist_smem_bytes(s->N, vmax, true, c) <= kPersistMaxSmem; };
+  if (resident(1)) return 1;
   int cs = 1;
   while (cs < 8 && (int64_t)p->n_inst * cs * 2 <= s->sm_count) cs *= 2;
+  // a larger cluster that keeps the instances resident beats one that fits the
+  // device at once but does not, up to two waves of clusters (32 instances of
+  // n = 1,000: 4 blocks, all at once, 52.2 us per step; 8 blocks, two waves,
+  // 34.1 us)
+  if (!resident(cs))
+    for (int c2 = cs * 2; c2 <= 8; c2 *= 2)
+      if (resident(c2) && ((int64_t)p->n_inst * c2 + s->sm_count - 1) / s->sm_count <= 2) {
+        cs = c2;
+        break;
+      }
   return cs;
 }
 
