@@ -345,7 +345,10 @@ def time_to_sat_summary(ts, torch, n_inst=32, cap=500):
             if leg in r:
                 r[leg].pop("_walls", None)
                 r[leg].pop("_steps", None)
-    out["mid_size"] = mid_size_time_to_sat(ts, torch, TTS_READINGS[name], pr)
+    try:
+        out["mid_size"] = mid_size_time_to_sat(ts, torch, TTS_READINGS[name], pr)
+    except Exception as ex:
+        out["mid_size"] = {"error": repr(ex)[:400]}
     return out
 
 
@@ -647,7 +650,12 @@ def ours(args, w, rank, world, local):
     progress = progress_reading(ts, torch, prob, N, K, w["seed"] + rank) if rank == 0 else None
     del prob
     torch.cuda.empty_cache()
-    tts = time_to_sat_summary(ts, torch) if rank == 0 and not args.no_tts else None
+    tts = None
+    if rank == 0 and not args.no_tts:
+        try:   # metric 2 rides along; a failure there must not cost the throughput line
+            tts = time_to_sat_summary(ts, torch)
+        except Exception as ex:
+            tts = {"error": repr(ex)[:400]}
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
