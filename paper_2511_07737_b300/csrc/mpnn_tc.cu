@@ -740,55 +740,10 @@ __global__ void __launch_bounds__(kTcRows) k_mp_tc_wgrad(const float *dZ, int64_
 // 4 rows (their inputs staged in shared memory) and thread (q, o) forms output
 // o of row q as an FP32 sum over k of W[o][k] x[k] in k order, reading its
 // BF16 weight row through L1 (the layer's weights stay cached there).
-// Literal form: x = [h[r], a[r], h[r^1]] with W = [W0 W1 W2]; rows r and r^1
-// share a block (the block's first row is a multiple of 4).
+// The literal layer's form, x = [h[r], a[r], h[r^1]] with W = [W0 W1 W2], is
+// k_mp_fma_literal below (rows r and r^1 share a block: its first row is a
+// multiple of 4).
 constexpr int kFmaRows = 2048;
-
-template <int FORM>
-__global__ void __launch_bounds__(256) k_mp_fma(TcArgs g) {
-  constexpr int KT = FORM == kLiteral ? 192 : 64;   // inputs per row (dense: K of 3 or 64)
-  __shared__ __align__(16) float xs[4][KT];
-  const int tid = threadIdx.x, q = tid >> 6, o = tid & 63;
-  const int K = FORM == kLiteral ? 192 : g.K;
-  for (int64_t r0 = 4 * (int64_t)blockIdx.x; r0 < g.M; r0 += 4 * (int64_t)gridDim.x) {
-    __syncthreads();   // the previous rows' readers are done
-    for (int e = tid; e < 4 * K; e += 256) {
-      const int rq = e / K, k = e - rq * K;
-      const int64_t r = r0 + rq;
-      float v = 0.f;
-      if (r < g.M) {
-        if (FORM == kLiteral) {
-          if (k < 64) v = g.x0[r * 64 + k];
-          else if (k < 128) v = g.x1[r * 64 + (k - 64)];
-          else v = g.x0[(r ^ 1) * 64 + (k - 128)];
-        } else {
-          v = g.x0[r * (int64_t)K + k];
-        }
-      }
-      xs[rq][k] = v;
-    }
-    __syncthreads();
-    const int64_t r = r0 + q;
-    if (r >= g.M) continue;
-    const __nv_bfloat16 *wr = g.W + (size_t)o * K;
-    float acc = 0.f;
-    if (K % 8 == 0) {
-      for (int k0 = 0; k0 < K; k0 += 8) {
-        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(wr + k0));
-        const __nv_bfloat162 *w2 = reinterpret_cast<const __nv_bfloat162 *>(&u);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float2 w = __bfloat1622float2(w2[j]);
-          acc = fmaf(w.x, xs[q][k0 + 2 * j], acc);
-          acc = fmaf(w.y, xs[q][k0 + 2 * j + 1], acc);
-        }
-      }
-    } else {
-      for (int k = 0; k < K; ++k) acc = fmaf(__bfloat162float(wr[k]), xs[q][k], acc);
-    }
-    g.y0[r * 64 + o] = fmaxf(acc + __bfloat162float(g.bias[o]), 0.f);
-  }
-}
 
 // The dot product of the CUDA-core layers: output o of staged row q, over K
 // inputs, plus the bias, through the ReLU.
@@ -808,6 +763,38 @@ __device__ __forceinline__ float fma_row(const float (&xs)[4][KT], int q, int o,
     }
   }
   return fmaxf(acc + __bfloat162float(bias[o]), 0.f);
+}
+
+// Dense form (the input layer, K = 3, and a 64-wide layer given its inputs);
+// the message-passing layers of a small graph use the fused kernels below.
+template <int FORM>
+__global__ void __launch_bounds__(256) k_mp_fma(TcArgs g) {
+  static_assert(FORM == kDense, "CUDA-core form of the dense layer only");
+  constexpr int KT = 64;   // inputs per row (K of 3 or 64)
+  __shared__ __align__(16) float xs[4][KT];
+  const int tid = threadIdx.x, q = tid >> 6, o = tid & 63;
+  const int K = g.K;
+  for (int64_t r0 = 4 * (int64_t)blockIdx.x; r0 < g.M; r0 += 4 * (int64_t)gridDim.x) {
+    __syncthreads();   // the previous rows' readers are done
+    for (int e = tid; e < 4 * K; e += 256) {
+      const int rq = e / K, k = e - rq * K;
+      const int64_t r = r0 + rq;
+      float v = 0.f;
+      if (r < g.M) v = g.x0[r * (int64_t)K + k];
+      xs[rq][k] = v;
+    }
+    __syncthreads();
+    const int64_t r = r0 + q;
+    if (r >= g.M) continue;   // the next round's barrier is reached by every thread
+    if (K % 8 == 0) {
+      g.y0[r * 64 + o] = fma_row<KT>(xs, q, o, g.W, K, g.bias);
+    } else {   // the 3-wide input features
+      const __nv_bfloat16 *wr = g.W + (size_t)o * K;
+      float acc = 0.f;
+      for (int k = 0; k < K; ++k) acc = fmaf(__bfloat162float(wr[k]), xs[q][k], acc);
+      g.y0[r * 64 + o] = fmaxf(acc + __bfloat162float(g.bias[o]), 0.f);
+    }
+  }
 }
 
 // A small graph's clause layer with its gather in one kernel: the clause
@@ -963,9 +950,7 @@ cudaError_t mp_dense_tc(const float *x, int K, int64_t M, const __nv_bfloat16 *W
 cudaError_t mp_literal_tc(const float *h, const float *a, int64_t M, const __nv_bfloat16 *W, const __nv_bfloat16 *bias,
                           float *Y, int *err, cudaStream_t st) {
   if ((M & 1) || !aligned16(h) || !aligned16(a) || !aligned16(W) || !aligned16(Y)) return cudaErrorInvalidValue;
-  const TcArgs g{h, a, 64, M, W, bias, nullptr, Y, nullptr, err};
-  if (M <= kFmaRows) return fma_go<kLiteral>(g, st);
-  return tc_go<kLiteral>(g, st);
+  return tc_go<kLiteral>(TcArgs{h, a, 64, M, W, bias, nullptr, Y, nullptr, err}, st);
 }
 
 // dX[r] = rscale[r] W^T dZ[r], W bf16 [64][64]
