@@ -155,13 +155,13 @@ cudaError_t mp_literal_dx_tc(const float *dZ, int64_t M, const __nv_bfloat16 *W,
 int mp_wgrad_tc(const float *dZ, int64_t M, int nin, int K, const float *const *x, const int *xr, float *part,
                 int max_blocks, int *err, cudaStream_t st, cudaError_t *e);
 cudaError_t mp_prepare_forward();
-// small graphs (a layer of at most mp_small_rows() rows): each message-passing
-// layer's gather fused into its CUDA-core dense layer
+// small graphs (a layer of at most mp_small_rows(literal) rows): each
+// message-passing layer's gather fused into its CUDA-core dense layer
 cudaError_t mp_clause_small(const ProbDev &pd, const float *h, const float *cinv, float *m, const __nv_bfloat16 *W,
                             const __nv_bfloat16 *bias, float *Y, cudaStream_t st);
 cudaError_t mp_literal_small(const ProbDev &pd, const float *h, const float *e, const float *linv, float *a,
                              const __nv_bfloat16 *W, const __nv_bfloat16 *bias, float *Y, cudaStream_t st);
-int mp_small_rows();
+int mp_small_rows(bool literal);
 
 __device__ __forceinline__ int warp_max(int x) {
   for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xFFFFFFFFu, x, o));
@@ -452,7 +452,7 @@ static int mp_forward(const tsat_problem *p, const float *params, MpWs &w, float
   cudaError_t e = mp_dense_tc(w.feat, kFeat, L, w.wb + kOffW0, w.wb + kOffB0, w.h[0], w.err, st);
   if (e != cudaSuccess) return cuda_fail(e, "mpnn input layer");
   for (int t = 0; t < kLayers; ++t) {
-    if (C <= mp_small_rows()) {
+    if (C <= mp_small_rows(false)) {
       e = mp_clause_small(pd, w.h[t], w.cinv, w.m[t], w.wb + off_wc(t), w.wb + off_bc(t), w.e[t], st);
     } else {
       const int gpw = mp_cgather_gpw(C);
@@ -460,7 +460,7 @@ static int mp_forward(const tsat_problem *p, const float *params, MpWs &w, float
       e = mp_dense_tc(w.m[t], kH, C, w.wb + off_wc(t), w.wb + off_bc(t), w.e[t], w.err, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "mpnn clause layer");
-    if (L <= mp_small_rows()) {
+    if (L <= mp_small_rows(true)) {
       e = mp_literal_small(pd, w.h[t], w.e[t], w.linv, w.a[t], w.wb + off_wl(t), w.wb + off_bl(t), w.h[t + 1], st);
     } else {
       k_mp_var_gather<0><<<grid_for((int64_t)p->V * 32, 256), 256, 0, st>>>(pd, w.e[t], w.linv, nullptr, w.a[t]);

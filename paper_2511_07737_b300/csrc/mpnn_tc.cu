@@ -896,7 +896,14 @@ cudaError_t mp_literal_small(const ProbDev &pd, const float *h, const float *e, 
   return cudaGetLastError();
 }
 
-int mp_small_rows() { return kFmaRows; }
+// Rows up to which a message-passing layer takes the fused CUDA-core kernel:
+// 2,048 for the clause layer, 1,536 for the literal layer, whose per-row work
+// (the literal mean walks the variable's occurrences, and 192 inputs) is
+// larger (forward back to back: one n = 1,000 instance, 2,000 literal rows,
+// 86.2 us with the literal layer on the CUDA cores, 76.7 us on the tensor
+// cores; n = 600, 1,200 rows, 76.0 against 77.9 us; n = 300, 600 literal and
+// 1,278 clause rows, 55.5 us against 77.0 us with both on the tensor cores).
+int mp_small_rows(bool literal) { return literal ? 1536 : kFmaRows; }
 
 template <int FORM>
 static cudaError_t fma_go(const TcArgs &g, cudaStream_t st) {

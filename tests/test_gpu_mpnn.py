@@ -44,13 +44,13 @@ def test_mpnn_forward_and_gradient_match_oracle():
 @pytest.mark.parametrize("name,gen", [
     # every forward layer at most 2,048 rows: the CUDA-core form of the layers
     ("n100", lambda: [cnfgen.planted_ksat(100, 426, 3, 8)]),
-    # literal layer on CUDA cores (1,600 rows), clause layer on the tensor cores (3,408 rows)
-    ("n800", lambda: [cnfgen.planted_ksat(800, 3408, 3, 9)]),
+    # literal layer on CUDA cores (1,400 rows), clause layer on the tensor cores (2,982 rows)
+    ("n700", lambda: [cnfgen.planted_ksat(700, 2982, 3, 9)]),
 ])
 def test_mpnn_small_layers_match_oracle(name, gen):
     """Forward logits, loss and gradient on graphs whose layers are small
-    enough for the CUDA-core form (a forward layer of at most 2,048 rows),
-    alone and mixed with tensor-core layers."""
+    enough for the CUDA-core form (a clause layer of at most 2,048 rows, a
+    literal layer of at most 1,536), alone and mixed with tensor-core layers."""
     insts = gen()
     prob = ts.Problem([(i.n_vars, i.clause_ptr, i.lits) for i in insts])
     pr = Proposer(seed=13)
