@@ -298,6 +298,29 @@ __global__ void k_var_inst(const InstInfo *inst, int32_t n_inst, int32_t V, int3
   if (v < V) var_inst[v] = find_inst_by_var(inst, n_inst, v);
 }
 
+// Clause offsets of a batch: each instance's clause pointers were copied as
+// given (from 0), and the instance's first literal position in the batch is
+// added here, up to kRawChunk instances per launch (their first clauses and
+// literal offsets by value).
+constexpr int kRawChunk = 64;
+struct RawOffChunk {
+  int32_t n;              // instances in this chunk
+  int64_t coff[kRawChunk + 1];   // first clause of each instance, then the end of the last
+  int64_t loff[kRawChunk];
+};
+
+__global__ void k_raw_offsets(int64_t *raw_cptr, RawOffChunk ch) {
+  const int64_t c = ch.coff[0] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ch.coff[ch.n]) return;
+  int lo = 0, hi = ch.n - 1;   // the instance whose clauses hold c
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ch.coff[mid] <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  raw_cptr[c] += ch.loff[lo];
+}
+
 // ------------------------------------------------------------------ host side
 struct Sizes {
   int32_t n_inst;
@@ -461,7 +484,7 @@ int tsat_load_batch_ex(int32_t n_inst, const tsat_cnf_desc *descs, uint32_t flag
   // host: instance table and global raw clause offsets
   p->inst.resize(n_inst);
   p->inst_nnz.resize(n_inst);
-  std::vector<int64_t> raw_cptr((size_t)s.C + 1);
+  std::vector<int64_t> raw_cptr(locality ? (size_t)s.C + 1 : 0);
   // clause order: as given, or (locality) each instance's clauses ordered by
   // their smallest variable, ties in the given order (a counting sort);
   // cperm maps a loaded clause to its index in the caller's batch
@@ -479,7 +502,7 @@ int tsat_load_batch_ex(int32_t n_inst, const tsat_cnf_desc *descs, uint32_t flag
     const int64_t *cp = descs[j].h_clause_ptr;
     p->inst_nnz[j] = cp[descs[j].n_clauses];
     if (!locality) {
-      for (int32_t c = 0; c < descs[j].n_clauses; ++c) raw_cptr[coff + c] = loff + cp[c];
+      // copied as given below, the literal offset added on the device
     } else {
       const int32_t nc = descs[j].n_clauses, nv = descs[j].n_vars;
       const int32_t *lits = descs[j].h_lits;
@@ -509,11 +532,41 @@ int tsat_load_batch_ex(int32_t n_inst, const tsat_cnf_desc *descs, uint32_t flag
     coff += descs[j].n_clauses;
     loff += cp[descs[j].n_clauses];
   }
-  raw_cptr[s.C] = loff;
+  const int64_t total_lits = loff;
   auto fail = [&](int code) { delete p; return code; };
 #define CK(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return fail(cuda_fail(e_, #call)); } while (0)
-  CK(cudaMemcpyAsync(w + L.raw_cptr, raw_cptr.data(), sizeof(int64_t) * raw_cptr.size(),
-                     cudaMemcpyHostToDevice, stream));
+  if (locality) {
+    raw_cptr[s.C] = total_lits;
+    CK(cudaMemcpyAsync(w + L.raw_cptr, raw_cptr.data(), sizeof(int64_t) * raw_cptr.size(),
+                       cudaMemcpyHostToDevice, stream));
+  } else {
+    // the caller's clause pointers straight to the device (no host pass over
+    // the clauses), then each instance's literal offset added there
+    int64_t *dcp = (int64_t *)(w + L.raw_cptr);
+    RawOffChunk ch{};
+    int64_t lo2 = 0;
+    for (int32_t j = 0; j < n_inst; ++j) {
+      const int32_t nc = descs[j].n_clauses;
+      const int64_t c0 = p->inst[j].c_off;
+      CK(cudaMemcpyAsync(dcp + c0, descs[j].h_clause_ptr, sizeof(int64_t) * nc, cudaMemcpyHostToDevice, stream));
+      ch.coff[ch.n] = c0;
+      ch.loff[ch.n] = lo2;
+      ++ch.n;
+      ch.coff[ch.n] = c0 + nc;
+      lo2 += descs[j].h_clause_ptr[nc];
+      if (ch.n == kRawChunk || j == n_inst - 1) {
+        const int64_t span = ch.coff[ch.n] - ch.coff[0];
+        if (ch.n > 1 || ch.loff[0] != 0)   // the first instance alone needs no offset
+          k_raw_offsets<<<(unsigned)((span + 255) / 256), 256, 0, stream>>>(dcp, ch);
+        CK(cudaGetLastError());
+        ch = RawOffChunk{};
+      }
+    }
+    // the end of the last clause: a host scalar that lives until the
+    // synchronisation after the dedup below
+    static_assert(sizeof(total_lits) == sizeof(int64_t), "offset width");
+    CK(cudaMemcpyAsync(dcp + s.C, &total_lits, sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  }
   int64_t lo = 0;
   for (int32_t j = 0; j < n_inst; ++j) {
     int64_t n = descs[j].h_clause_ptr[descs[j].n_clauses];
