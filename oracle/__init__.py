@@ -25,6 +25,12 @@ Parity status per function (the pins live in ``tests/test_oracle_*.py``):
   binarize_f32                  : deterministic mode vs sign rule, T -> 0
                                   reduction to it, Philox mode frequency
   best_sample / topk            : brute force on small arrays
+  partial_k                     : the sizes of the top-k rule at small,
+                                  round and just-above-round V
+  step                          : equal to the pinned pieces composed by
+                                  hand; the mixing reading's closed forms
+                                  (best sample kept, the rest averaged,
+                                  moments zeroed, first AdamW step after it)
   mpnn.forward                  : closed form of a selector network on a
                                   hand-sized graph (feature vector, block
                                   order [h; a; h_neg], output head), a dense
