@@ -250,7 +250,9 @@ int tsat_persist_blocks(const tsat_state *s, int32_t *blocks_per_instance, int32
  * in *h_blocks.  d_snapshot: caller-owned device scratch of
  * tsat_autotune_bytes; every trial starts from the saved state and the state
  * is put back at the end, so no result changes.  Synchronises with the
- * trials; TSAT_EINVAL / TSAT_ERANGE as tsat_step_persistent. */
+ * trials; TSAT_EINVAL / TSAT_ERANGE as tsat_step_persistent, TSAT_ERANGE when
+ * no candidate runs the batch.  On any error the previous blocks-per-instance
+ * setting is kept and the saved state is copied back. */
 int tsat_autotune_persistent(tsat_state *s, const tsat_hparams *hp, void *d_snapshot, size_t snapshot_bytes,
                              int32_t n_steps, cudaStream_t stream, int32_t *h_blocks);
 
@@ -414,7 +416,8 @@ int tsat_backward(tsat_state *s, const tsat_hparams *hp, const float *d_z, float
  * literal values) is saved into the caller's device buffer d_snapshot of at
  * least tsat_autotune_bytes bytes before the first trial, restored before
  * every trial and restored again at the end, so the call leaves the state
- * unchanged.  A failed trial leaves the previous launch shape.  Synchronous
+ * unchanged.  A failed trial leaves the previous launch shapes (forward work
+ * items and update grid) and copies the saved state back.  Synchronous
  * (returns after the last trial).  tsat_get_tuning / tsat_set_tuning read or
  * force the shapes.
  * h_tuning = {fwd_chunk_clauses, fwd_block_threads, upd_blocks_per_sm, upd_rows_per_item};

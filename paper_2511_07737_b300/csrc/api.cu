@@ -927,52 +927,57 @@ int tsat_autotune_persistent(tsat_state *s, const tsat_hparams *hp, void *d_snap
   cudaStream_t st = s->stream;
   char *base = static_cast<char *>(s->base);
   char *snap = static_cast<char *>(d_snapshot);
-  TSAT_CUDA(cudaMemcpyAsync(snap, base, s->core_bytes, cudaMemcpyDeviceToDevice, st));
-  EventPair ev;
-  TSAT_CUDA(cudaEventCreate(&ev.a));
-  TSAT_CUDA(cudaEventCreate(&ev.b));
   const int32_t keep = s->persist_cs;
   int32_t best_cs = 1;
   float best = 1e30f;
+  EventPair ev;
+  bool saved = false;
   // candidates: one block, and (N <= 256) clusters of 2, 4, 8 blocks while
-  // the batch's clusters fit the device at most twice over
-  for (int cs : {1, 2, 4, 8}) {
-    if (cs > 1 && (s->N > 256 || (int64_t)s->prob->n_inst * cs > 2LL * s->sm_count)) continue;
-    s->persist_cs = cs;
-    float ms = 1e30f;
-    for (int rep = 0; rep < 2 && rc == TSAT_OK; ++rep) {
-      TSAT_CUDA(cudaMemcpyAsync(base, snap, s->core_bytes, cudaMemcpyDeviceToDevice, st));
-      TSAT_CUDA(cudaEventRecord(ev.a, st));
-      bool to_clustered = false;
-      rc = persist_launch(s, hp, n_steps, 0, &to_clustered);
-      if (rc == TSAT_OK && to_clustered) {
-        set_error("the instances suit the cluster solver, not the persistent one");
-        rc = TSAT_EINVAL;
+  // the batch's clusters fit the device at most twice over; every trial
+  // starts from the caller's state
+  auto trials = [&]() -> int {
+    TSAT_CUDA(cudaMemcpyAsync(snap, base, s->core_bytes, cudaMemcpyDeviceToDevice, st));
+    saved = true;
+    TSAT_CUDA(cudaEventCreate(&ev.a));
+    TSAT_CUDA(cudaEventCreate(&ev.b));
+    for (int cs : {1, 2, 4, 8}) {
+      if (cs > 1 && (s->N > 256 || (int64_t)s->prob->n_inst * cs > 2LL * s->sm_count)) continue;
+      s->persist_cs = cs;
+      float ms = 1e30f;
+      int r = TSAT_OK;
+      for (int rep = 0; rep < 2; ++rep) {
+        TSAT_CUDA(cudaMemcpyAsync(base, snap, s->core_bytes, cudaMemcpyDeviceToDevice, st));
+        TSAT_CUDA(cudaEventRecord(ev.a, st));
+        bool to_clustered = false;
+        r = persist_launch(s, hp, n_steps, 0, &to_clustered);
+        if (r == TSAT_OK && to_clustered) {
+          set_error("the instances suit the cluster solver, not the persistent one");
+          r = TSAT_EINVAL;
+        }
+        if (r != TSAT_OK) break;
+        TSAT_CUDA(cudaEventRecord(ev.b, st));
+        TSAT_CUDA(cudaEventSynchronize(ev.b));
+        float x = 0;
+        TSAT_CUDA(cudaEventElapsedTime(&x, ev.a, ev.b));
+        ms = std::min(ms, x);
       }
-      if (rc != TSAT_OK) break;
-      TSAT_CUDA(cudaEventRecord(ev.b, st));
-      TSAT_CUDA(cudaEventSynchronize(ev.b));
-      float x = 0;
-      TSAT_CUDA(cudaEventElapsedTime(&x, ev.a, ev.b));
-      ms = std::min(ms, x);
+      if (r == TSAT_ERANGE && cs == 1) continue;   // one block cannot take the instances: try the clusters
+      if (r != TSAT_OK) return r;
+      if (ms < best) { best = ms; best_cs = cs; }
     }
-    if (rc == TSAT_ERANGE && cs == 1) {   // one block cannot take the instances: try the clusters
-      rc = TSAT_OK;
-      continue;
-    }
-    if (rc != TSAT_OK) break;
-    if (ms < best) { best = ms; best_cs = cs; }
-  }
-  TSAT_CUDA(cudaMemcpyAsync(base, snap, s->core_bytes, cudaMemcpyDeviceToDevice, st));
-  if (rc != TSAT_OK || best >= 1e30f) {
-    s->persist_cs = keep;
-    leave(s, stream);
-    if (rc == TSAT_OK) { set_error("no persistent launch shape runs these instances"); rc = TSAT_ERANGE; }
-    return rc;
-  }
-  s->persist_cs = best_cs;
+    TSAT_CUDA(cudaMemcpyAsync(base, snap, s->core_bytes, cudaMemcpyDeviceToDevice, st));
+    return TSAT_OK;
+  };
+  rc = trials();
+  if (rc == TSAT_OK && best >= 1e30f) { set_error("no persistent launch shape runs these instances"); rc = TSAT_ERANGE; }
+  // a failed call keeps the previous setting and, as far as the device allows,
+  // the caller's state
+  if (rc != TSAT_OK && saved) (void)cudaMemcpyAsync(base, snap, s->core_bytes, cudaMemcpyDeviceToDevice, st);
+  s->persist_cs = rc == TSAT_OK ? best_cs : keep;
+  const int rl = leave(s, stream);
+  if (rc != TSAT_OK) return rc;
   *h_blocks = best_cs;
-  return leave(s, stream);
+  return rl;
 }
 
 int tsat_autotune_bytes(const tsat_state *s, size_t *bytes) {
@@ -1010,34 +1015,35 @@ int tsat_autotune(tsat_state *s, const tsat_hparams *hp, void *d_snapshot, size_
       TSAT_CUDA(cudaMemcpyAsync(base + s->lit_off, snap + s->core_bytes, s->lit_bytes, cudaMemcpyDeviceToDevice, st));
     return TSAT_OK;
   };
-  if ((rc = save())) return rc;
   EventPair ev;
-  TSAT_CUDA(cudaEventCreate(&ev.a));
-  TSAT_CUDA(cudaEventCreate(&ev.b));
   const Hyper hy = make_hyper(*hp, 0);
   const LrSched ls = make_sched(*hp);
   const ProbDev &pd = s->prob->dev;
   // forward work-item size: the forward reads the bits and writes a scratch histogram
-  int best_items = s->prob->item_clauses;
+  const int keep_items = s->prob->item_clauses;
+  int best_items = keep_items;
   float best = 1e30f;
-  for (int ic : kTuneItems) {
-    if ((rc = s->prob->set_items(ic, st))) return rc;
-    float ms = 1e30f;
-    for (int rep = 0; rep < 2; ++rep) {
-      TSAT_CUDA(cudaMemsetAsync(s->eval_hist, 0, sizeof(int32_t) * pd.n_inst * s->dev.lm1 * s->N, st));
-      TSAT_CUDA(cudaEventRecord(ev.a, st));
-      cudaError_t e = s->layer == TSAT_LAYER_RELAXED ? launch_relaxed_fwd(pd, s->dev, hy, 1, st)
-                                                    : launch_fwd_hist(pd, s->dev, s->eval_hist, 0, st);
-      if (e != cudaSuccess) return cuda_fail(e, "forward");
-      TSAT_CUDA(cudaEventRecord(ev.b, st));
-      TSAT_CUDA(cudaEventSynchronize(ev.b));
-      float x = 0;
-      TSAT_CUDA(cudaEventElapsedTime(&x, ev.a, ev.b));
-      ms = std::min(ms, x);
+  auto tune_items = [&]() -> int {
+    for (int ic : kTuneItems) {
+      int r;
+      if ((r = s->prob->set_items(ic, st))) return r;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        TSAT_CUDA(cudaMemsetAsync(s->eval_hist, 0, sizeof(int32_t) * pd.n_inst * s->dev.lm1 * s->N, st));
+        TSAT_CUDA(cudaEventRecord(ev.a, st));
+        cudaError_t e = s->layer == TSAT_LAYER_RELAXED ? launch_relaxed_fwd(pd, s->dev, hy, 1, st)
+                                                      : launch_fwd_hist(pd, s->dev, s->eval_hist, 0, st);
+        if (e != cudaSuccess) return cuda_fail(e, "forward");
+        TSAT_CUDA(cudaEventRecord(ev.b, st));
+        TSAT_CUDA(cudaEventSynchronize(ev.b));
+        float x = 0;
+        TSAT_CUDA(cudaEventElapsedTime(&x, ev.a, ev.b));
+        ms = std::min(ms, x);
+      }
+      if (ms < best) { best = ms; best_items = ic; }
     }
-    if (ms < best) { best = ms; best_items = ic; }
-  }
-  if ((rc = s->prob->set_items(best_items, st))) return rc;
+    return TSAT_OK;
+  };
   // update launch shape: the step's own update (mode 0, hp's binarisation and
   // Eq. 5 mode), timed after the step's forward and gamma from the saved state;
   // blocks per SM around the default (resident blocks x 8 waves): 1, 2, 4, 8 and 10 waves
@@ -1045,8 +1051,8 @@ int tsat_autotune(tsat_state *s, const tsat_hparams *hp, void *d_snapshot, size_
   tune_bps(s, bps);
   const int keep_b = s->upd_blocks_per_sm, keep_r = s->upd_rows_per_item;
   int best_b = keep_b, best_r = keep_r;
-  best = 1e30f;
   auto sweep = [&]() -> int {
+    best = 1e30f;
     for (int bb : bps)
       for (int rr : kTuneRpi) {
         s->upd_blocks_per_sm = bb;
@@ -1068,12 +1074,31 @@ int tsat_autotune(tsat_state *s, const tsat_hparams *hp, void *d_snapshot, size_
       }
     return TSAT_OK;
   };
-  rc = sweep();
-  // a failed trial leaves the launch shape as it was before the call
-  s->upd_blocks_per_sm = rc ? keep_b : best_b;
-  s->upd_rows_per_item = rc ? keep_r : best_r;
-  if (rc) return rc;
-  if ((rc = restore())) return rc;
+  bool saved = false;
+  auto run = [&]() -> int {
+    int r;
+    if ((r = save())) return r;
+    saved = true;
+    TSAT_CUDA(cudaEventCreate(&ev.a));
+    TSAT_CUDA(cudaEventCreate(&ev.b));
+    if ((r = tune_items())) return r;
+    if ((r = s->prob->set_items(best_items, st))) return r;
+    if ((r = sweep())) return r;
+    return restore();
+  };
+  rc = run();
+  if (rc) {
+    // a failed trial leaves the launch shapes as they were before the call
+    // and, as far as the device allows, the caller's state
+    if (saved) (void)restore();
+    (void)s->prob->set_items(keep_items, st);
+    s->upd_blocks_per_sm = keep_b;
+    s->upd_rows_per_item = keep_r;
+    (void)leave(s, stream);
+    return rc;
+  }
+  s->upd_blocks_per_sm = best_b;
+  s->upd_rows_per_item = best_r;
   if ((rc = leave(s, stream))) return rc;
   return tsat_get_tuning(s, h_tuning);
 }

@@ -363,3 +363,29 @@ def test_autotune_persistent_keeps_the_state_and_picks_the_cluster_where_it_pays
         a, c = snapshot(st), snapshot(st_b)
         if ts.tsat_persist_blocks(st.h, True)[1] == ts.tsat_persist_blocks(st_b.h, True)[1]:
             np.testing.assert_array_equal(a["bits"], c["bits"])
+
+
+@pytest.mark.gpu
+def test_autotune_persistent_failure_keeps_setting_and_state():
+    """When no candidate runs the batch (N = 512 allows one block only, and an
+    n = 3,000 instance's bits do not fit its shared memory), the tuner reports
+    TSAT_ERANGE, keeps the caller's blocks-per-instance setting and leaves the
+    state as it was; the refusal is decided on the host before any launch."""
+    hp = ts.hparams(seed=4, norm=1, tau=2.0, lr0=0.5)
+    inst = cnfgen.planted_ksat(3000, 12000, 3, 1)
+    prob, st, _ = make([inst], 512)
+    ts.tsat_init(st.h, hp)
+    ts.tsat_step(st.h, hp, 2, stop_on_sat=False)
+    ts.tsat_set_persist_blocks(st.h, 1)
+    torch.cuda.synchronize()
+    nb = ts.tsat_autotune_bytes(st.h)
+    before = st.buf.view(torch.uint8)[:nb].clone()
+    with pytest.raises(ts.TsatError) as e:
+        ts.tsat_autotune_persistent(st.h, hp, 10)
+    assert e.value.status == -10
+    assert ts.tsat_persist_blocks(st.h) == 1
+    torch.cuda.synchronize()
+    assert torch.equal(st.buf.view(torch.uint8)[:nb], before)
+    # the state still steps on the graph path
+    ts.tsat_step(st.h, hp, 1, stop_on_sat=False)
+    assert ts.tsat_status(st.h, 1)["inst"][0]["min_unsat"] >= 0
